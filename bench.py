@@ -1,0 +1,315 @@
+"""Benchmark: d=5 rotated-surface-code noisy QEC rounds per second on GB300.
+
+Workload (one "step" = one trajectory of the whole hot path): d=5 reduced
+register (25 data qubits resident + the ancilla, 2^26 amplitudes of the
+d^2+1 register), cross-resonance gate set, 5 noisy rounds after the noise-free
+init round, final Z readout; the 9 noise points p in {1e-3, 3e-3, 5e-3} x
+theta_rx in {0, 0.01, 0.05}, ZZ crosstalk 0.02, taken in turn by successive
+steps.  value = noisy rounds / s over the timed steps (inputs resident in HBM,
+outputs left in device memory); e2e = the same through the host-output call.
+
+Multi-GPU (torchrun): trajectories are independent; each rank runs its own
+trajectory indices with no data-path collective (weak scaling).
+
+--impl reference times the FP64 CPU oracle on the host cores, on bounded
+samples of the same workload (one stabilizer circuit of a d=5 round per step).
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "d=5 QEC rounds/s (26-qubit SV), HBM GB/s vs peak; serve p50/p99 latency"
+UNIT = "rounds/s"
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2070 MHz
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=9)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--precision", default="c128", choices=["c128", "c64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---- clocks ---------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---- oracle (CPU baseline / reference arm) -----------------------------------------------------
+class OracleSampler:
+    """The FP64 oracle on bounded samples of the d=5 workload: stabilizer circuits of a noisy round
+    (the ops between two ancilla measurements, measurement included) on a resident 26-qubit state
+    that starts from the code state (the oracle's own noise-free init round)."""
+
+    def __init__(self, point_index=8):
+        import numpy as np
+
+        from oracle.circuit import Trajectory
+        from oracle.runner import build_core, get_threads, run_ops
+
+        build_core()
+        self.run_ops, self.threads = run_ops, get_threads()
+        pt = W.D5_CR["points"][point_index]
+        T = Trajectory(5, 1, "cr", "reduced", pt, W.D5_CR["seed_base"] + point_index, 0).build()
+        self.n, self.nstab = T.n, 24
+        groups, cur = [], []
+        for op in T.ops:
+            cur.append(op)
+            if op[0] == "M" and op[4] == 1:
+                groups.append(cur)
+                cur = []
+        self.init_ops = [op for g in groups[: self.nstab] for op in g]
+        self.blocks = groups[self.nstab: 2 * self.nstab]
+        self.psi = np.zeros(1 << self.n, dtype=np.complex128)
+        self.psi[0] = 1.0
+        self.run_ops(self.psi, self.n, self.init_ops)
+        self.next = 0
+
+    def run(self, n_samples):
+        t0 = time.perf_counter()
+        for _ in range(n_samples):
+            self.run_ops(self.psi, self.n, self.blocks[self.next % self.nstab])
+            self.next += 1
+        return time.perf_counter() - t0
+
+
+def reference_arm(args, rank, world):
+    if rank != 0:
+        return
+    smp = OracleSampler()
+    smp.run(args.warmup)
+    secs = smp.run(args.steps)
+    nst, threads = args.steps, smp.threads
+    rounds = nst / 24.0
+    value = rounds / secs
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": workload_config(args, world),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": "%d stabilizer circuits (with measurement) of a d=5 cr noisy round, "
+                                   "p=5e-3 theta_rx=0.05 phi_zz=0.02, on a resident 2^26 FP64 state; "
+                                   "rounds = circuits / 24" % nst},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out))
+
+
+def workload_config(args, world):
+    return {"workload": "d=5 rotated surface code, reduced 26-qubit register (25 data resident + ancilla), "
+                        "cr gate set, 5 noisy rounds + init + Z readout, 9 noise points "
+                        "(p x theta_rx) with ZZ 0.02",
+            "d": 5, "rounds": 5, "precision": args.precision, "trajectories_per_rank": args.steps,
+            "parallelism": "trajectory-sharded x%d" % world,
+            "l2": "state 512 MiB (c128) / 256 MiB (c64) per pass > 129 MB L2, no flush needed"}
+
+
+# ---- native arm ------------------------------------------------------------------------------
+def traffic_record(precision):
+    """dram bytes per launch of the apply pass from the committed ncu summary, if it still
+    describes the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "apply_pass_traffic.json")
+    try:
+        rec = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    src = open(os.path.join(ROOT, "paper_2204_11404_gb300", "csrc", "kernels.cu"), "rb").read()
+    if rec.get("kernels_cu_sha256") != hashlib.sha256(src).hexdigest():
+        return None
+    return rec.get(precision, {}).get("dram_bytes_per_launch")
+
+
+def native_arm(args, rank, world, local):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2204_11404_gb300 import capi
+    from paper_2204_11404_gb300.simulator import Simulator
+
+    torch.cuda.set_device(local)
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group("nccl")
+    pts = W.D5_CR["points"]
+    R = W.D5_CR["rounds"]
+    sims = [Simulator(5, R, "cr", args.precision, **pt) for pt in pts]
+    seeds = [W.D5_CR["seed_base"] + i for i in range(len(pts))]
+    nst = 24
+    syn = torch.empty((1, R + 1, nst), dtype=torch.uint8, device="cuda")
+    bits = torch.empty((1, 25), dtype=torch.uint8, device="cuda")
+    log = torch.empty((1,), dtype=torch.uint8, device="cuda")
+
+    def traj_index(i):
+        return (i // len(pts)) * world + rank
+
+    def step(i):
+        j = i % len(pts)
+        sims[j].run_device(seeds[j], traj_index(i), 1, syn.data_ptr(), bits.data_ptr(), log.data_ptr())
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    kt = []
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for i in range(args.steps):
+            step(args.warmup + i)
+            kt.append(capi.qec_kernel_times(sims[(args.warmup + i) % len(pts)].h))
+        e1.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    secs = e0.elapsed_time(e1) / 1e3
+    if world > 1:
+        t = torch.tensor([secs], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        secs = float(t.item())
+    rounds = world * args.steps * R
+    value = rounds / secs
+
+    # e2e through the host-output call (inputs: seed + trajectory index; outputs copied to host)
+    n_e2e = min(args.steps, len(pts))
+    h0 = time.perf_counter()
+    for i in range(n_e2e):
+        j = i % len(pts)
+        sims[j].run(seeds[j], 10_000 + traj_index(i), 1)
+    e2e_secs = time.perf_counter() - h0
+    if world > 1:
+        t = torch.tensor([e2e_secs], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_secs = float(t.item())
+    e2e = {"value": world * n_e2e * R / e2e_secs, "unit": UNIT,
+           "h2d_bytes_per_step": 32, "d2h_bytes_per_step": (R + 1) * nst + 25 + 1}
+
+    # roofline of the dominant kernel: the apply pass (psi <- K_m psi / sqrt(N)) of a weight-4 block
+    ms_prob = float(np.mean([k[0] for k in kt]))
+    ms_apply = float(np.mean([k[1] for k in kt]))
+    amps = 1 << 25
+    flops_apply = amps * 16 * 8            # 16x16 complex mat-vec per 16 amplitudes: 16 cmacs/amp
+    bytes_apply = amps * (32 if args.precision == "c128" else 16)
+    flops_prob = amps * (16 * 8 * 136 // 256 + 4)
+    if args.precision == "c128":
+        roof = {"bound": "alu", "achieved": flops_apply / (ms_apply * 1e-3) / 1e12, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s"}
+    else:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        roof = {"bound": "hbm", "achieved": bytes_apply / (ms_apply * 1e-3) / 1e9, "peak": peaks["hbm_gbs"],
+                "unit": "GB/s"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = traffic_record(args.precision)
+    roof["kernel"] = "k_apply<%s,4> (weight-4 block, 2^25 amplitudes)" % ("double" if args.precision == "c128" else "float")
+    roof["ms_apply"] = ms_apply
+    roof["ms_prob"] = ms_prob
+    roof["apply_hbm_gbs"] = bytes_apply / (ms_apply * 1e-3) / 1e9
+    roof["prob_fp64_tflops"] = flops_prob / (ms_prob * 1e-3) / 1e12
+
+    launches_per_traj = 1 + 2 * nst * R + 3
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "c128" else "f32",
+        "data": "synthetic", "config": workload_config(args, world), "clocks": clk.summary(),
+        "e2e": e2e, "gpu_launches": launches_per_traj * args.steps, "roofline": roof,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        smp = OracleSampler()
+        secs_o = smp.run(24)
+        out["cpu_baseline"] = {"value": 1.0 / secs_o, "unit": UNIT, "cores": smp.threads, "kind": "oracle",
+                               "sample": "one d=5 cr noisy round (24 stabilizer circuits with measurement), "
+                                         "p=5e-3 theta_rx=0.05 phi_zz=0.02, on a resident 2^26 FP64 state"}
+    for s in sims:
+        s.close()
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        reference_arm(args, rank, world)
+    else:
+        native_arm(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

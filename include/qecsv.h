@@ -1,0 +1,162 @@
+/*
+ * qecsv: GB300 state-vector trajectories of the rotated surface code under
+ * Pauli + coherent noise (Katsuda, Mitarai, Fujii, arXiv:2204.11404).
+ *
+ * C ABI.  No C++ types cross it; nothing throws across it.  Every call returns
+ * a qec_status; on a non-OK status, qec_last_error() gives a thread-local
+ * message and the caller's output buffers hold unspecified contents.
+ * A qec_sim handle is not thread-safe: use one handle per host thread.
+ */
+#ifndef QECSV_H
+#define QECSV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  QEC_OK = 0,
+  QEC_EINVAL = -1,       /* bad argument: size, pointer, enum or parameter range */
+  QEC_ENOMEM = -2,       /* device or host allocation failed */
+  QEC_ECUDA = -3,        /* a CUDA runtime call failed (message has the CUDA error string) */
+  QEC_ETIMEOUT = -4,     /* a bounded device wait gave up */
+  QEC_EUNSUPPORTED = -6  /* valid request this build does not implement */
+} qec_status;
+
+/* Register layout (Sec. II.B).  REDUCED: d^2 data qubits + one reused ancilla
+ * (26 qubits at d=5); UNREDUCED: all 2d^2-1 qubits (only the oracle runs it). */
+typedef enum { QEC_LAYOUT_REDUCED = 0, QEC_LAYOUT_UNREDUCED = 1 } qec_layout;
+
+/* Gate set.  CNOT: H + CNOT stabilizer circuits (Fig. 1b/c).  CR: the
+ * cross-resonance native set {Rx(pi/2), Rx^dagger(pi/2), Rzx(pi/2), Rz(pi/2)}
+ * with data corrections after each part (Sec. III.A, Fig. 4). */
+typedef enum { QEC_GATES_CNOT = 0, QEC_GATES_CR = 1 } qec_gateset;
+
+/* Amplitude storage / arithmetic.  C128: complex128 state, FP64 arithmetic.
+ * C64: complex64 state, FP32 gate arithmetic, FP64 probability reductions. */
+typedef enum { QEC_C128 = 0, QEC_C64 = 1 } qec_precision;
+
+/* Noise (Sec. III.A).  Probabilities in [0, 1]; angles in radians, |angle| <= 4. */
+typedef struct {
+  double p1;        /* Eq. 1 after every one-qubit gate */
+  double p2;        /* Eq. 2 (15 non-identity pairs, uniform) after every two-qubit gate */
+  double p_idle;    /* Eq. 1 on a qubit that waits during a step */
+  double theta_rx;  /* extra R_X(theta) = exp(-i theta X/2) after every Rx / Rx^dagger */
+  double theta_rz;  /* extra R_Z(theta) after every Rz */
+  double theta_rzx; /* extra exp(-i theta Z(x)X/2) after every Rzx */
+  double phi_zz;    /* ZZ crosstalk exp(-i phi Z(x)Z) after every two-qubit gate */
+  double round_rz;  /* R_Z(angle) on every data qubit at the start of each noisy round */
+  double round_rx;  /* R_X(angle) on every data qubit at the start of each noisy round */
+} qec_noise;
+
+typedef struct {
+  int32_t d;          /* code distance: odd, 3 <= d <= 5 (2^(d^2) amplitudes resident) */
+  int32_t rounds;     /* noisy syndrome rounds after the noise-free init round, 0..64 */
+  int32_t layout;     /* qec_layout; only QEC_LAYOUT_REDUCED runs on the GPU */
+  int32_t gates;      /* qec_gateset */
+  int32_t precision;  /* qec_precision */
+  int32_t reserved;   /* must be 0 */
+  qec_noise noise;
+} qec_params;
+
+typedef struct qec_sim qec_sim;
+
+/*
+ * Create a simulator (Sec. III.B protocol): allocates the state vectors on
+ * the current CUDA device, builds the per-round circuit program, and runs the
+ * noise-free init round whose outcomes are forced to the zero syndrome; the
+ * resulting code state stays resident and seeds every trajectory.
+ * cuda_stream: a cudaStream_t owned by the caller (e.g. torch's current
+ * stream) that all work is ordered on, or NULL for a stream owned by the sim.
+ * *out receives the handle; the sim owns all device memory it allocates.
+ */
+qec_status qec_create(const qec_params* params, void* cuda_stream, qec_sim** out);
+
+/*
+ * Run trajectories first_traj .. first_traj+n-1 (Sec. III.B: init state, then
+ * `rounds` noisy rounds of the X part and Z part, then a Z measurement of every
+ * data qubit in index order).  Results are a pure function of (params, seed,
+ * trajectory index): noise and measurement draws come from Philox4x64-10 with
+ * key (seed, 0) and counter (trajectory, round, step<<32 | physical site, tag).
+ * Outputs are caller-owned HOST buffers (may be NULL to skip):
+ *   syndromes  [n][rounds+1][d*d-1]  uint8: row 0 is the forced init round
+ *              (all 0); stabilizers in Table I order, X then Z
+ *   data_bits  [n][d*d]              uint8: final Z outcome of each data qubit
+ *   raw_logical[n]                   uint8: parity of data_bits over the first
+ *              data row (logical Z), before any decoding
+ * Blocks until the results are on the host.
+ */
+qec_status qec_run_trajectories(qec_sim* sim, uint64_t seed, uint64_t first_traj, uint32_t n,
+                                uint8_t* syndromes, uint8_t* data_bits, uint8_t* raw_logical);
+
+/*
+ * Same as qec_run_trajectories, but the outputs are DEVICE buffers of the
+ * same shapes (on the sim's device), filled asynchronously on the sim's
+ * stream; nothing is copied to the host and the call does not synchronize.
+ */
+qec_status qec_run_trajectories_device(qec_sim* sim, uint64_t seed, uint64_t first_traj, uint32_t n,
+                                       uint8_t* d_syndromes, uint8_t* d_data_bits, uint8_t* d_raw_logical);
+
+/* Number of amplitudes of the resident data register (2^(d*d)); the ancilla
+ * of the d^2+1 register is |0> at every point a snapshot can be taken. */
+uint64_t qec_state_len(const qec_sim* sim);
+
+/*
+ * Test hook: copy the normalised data-register state after the last noisy
+ * round of the most recent trajectory (before the final readout, which does
+ * not modify it) into host_buf as complex128 (re, im) pairs, whatever the
+ * precision.  bytes must be >= 16 * qec_state_len(sim).
+ */
+qec_status qec_get_state(qec_sim* sim, void* host_buf, size_t bytes);
+
+/*
+ * Test hook: enable (max_events > 0) or disable recording of the Pauli errors
+ * sampled on the device (Eqs. 1-2).  qec_get_events copies the events of the
+ * most recent trajectory as int32 quadruples (round, step, physical site,
+ * code) in unspecified order; code = Pauli 1..3 (X, Y, Z) for Eq. 1 sites and
+ * 4*ancilla_pauli + data_pauli for Eq. 2 sites.  *count gets the number
+ * recorded (capped at max_events).
+ */
+qec_status qec_record_events(qec_sim* sim, uint32_t max_events);
+qec_status qec_get_events(qec_sim* sim, int32_t* host_events, uint32_t max_events, uint32_t* count);
+
+/*
+ * Measurement hook: device time in milliseconds of the probability pass
+ * (ms[0]) and of the collapse/apply pass (ms[1]) of one weight-4 stabilizer
+ * block of the middle noisy round, in the most recent trajectory (CUDA events
+ * recorded inside the trajectory's graph).  *block gets that block's index
+ * (round-major, d^2-1 per round).  QEC_EINVAL if no trajectory ran yet or the
+ * sim has no noisy round.
+ */
+qec_status qec_kernel_times(qec_sim* sim, float* ms, int32_t* block);
+
+qec_status qec_destroy(qec_sim* sim);
+const char* qec_last_error(void);
+
+/*
+ * Host-only test hook (no GPU needed): the static per-round circuit program
+ * that the device instantiates, for checking the schedule on the CPU.
+ * Writes up to `cap` int32 sextuples per op (block, kind, local q0, local q1,
+ * step, site) in block order and returns the op count in *n_ops; block
+ * metadata goes to block_info as int32 sextuples (w, q0, q1, q2, q3, offset).
+ */
+qec_status qec_debug_program(const qec_params* params, int32_t* ops, uint32_t cap, uint32_t* n_ops,
+                             int32_t* block_info, uint32_t block_cap, uint32_t* n_blocks);
+
+/*
+ * Host-only test hook (no GPU needed): runs the same block-instantiation code
+ * the device runs, on the CPU, for trajectory `traj` of round `round` (0 = the
+ * forced init round).  For each of the d^2-1 blocks writes K0 and K1 (16x16
+ * complex128, row-major, (re, im) pairs; rows/cols beyond 2^w are zero) to
+ * kraus[block][2][16][16][2] and the measurement uniform to u[block].
+ */
+qec_status qec_debug_blocks(const qec_params* params, uint64_t seed, uint64_t traj, int32_t round,
+                            double* kraus, double* u);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,148 @@
+"""ctypes binding of include/qecsv.h: same names, argument marshalling only.
+
+Every step of the simulation runs in libqecsv.so (CUDA kernels for sm_103a);
+this module only converts arguments.  If the library is missing or fails to
+load, importing a function raises: there is no CPU fallback.
+"""
+import ctypes
+import os
+
+from .build import LIB, build
+
+QEC_OK, QEC_EINVAL, QEC_ENOMEM, QEC_ECUDA, QEC_ETIMEOUT, QEC_EUNSUPPORTED = 0, -1, -2, -3, -4, -6
+QEC_LAYOUT_REDUCED, QEC_LAYOUT_UNREDUCED = 0, 1
+QEC_GATES_CNOT, QEC_GATES_CR = 0, 1
+QEC_C128, QEC_C64 = 0, 1
+
+NOISE_FIELDS = ("p1", "p2", "p_idle", "theta_rx", "theta_rz", "theta_rzx", "phi_zz", "round_rz", "round_rx")
+
+
+class qec_noise(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_double) for f in NOISE_FIELDS]
+
+
+class qec_params(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_int32), ("rounds", ctypes.c_int32), ("layout", ctypes.c_int32),
+                ("gates", ctypes.c_int32), ("precision", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("noise", qec_noise)]
+
+
+class QecError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("qecsv status %d: %s" % (status, msg))
+        self.status = status
+
+
+_lib = None
+_P = ctypes.c_void_p
+_U8P = ctypes.POINTER(ctypes.c_uint8)
+
+SIGNATURES = {
+    "qec_create": ([ctypes.POINTER(qec_params), _P, ctypes.POINTER(_P)], ctypes.c_int),
+    "qec_run_trajectories": ([_P, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32, _P, _P, _P], ctypes.c_int),
+    "qec_run_trajectories_device": ([_P, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32, _P, _P, _P], ctypes.c_int),
+    "qec_state_len": ([_P], ctypes.c_uint64),
+    "qec_get_state": ([_P, _P, ctypes.c_size_t], ctypes.c_int),
+    "qec_record_events": ([_P, ctypes.c_uint32], ctypes.c_int),
+    "qec_get_events": ([_P, _P, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32)], ctypes.c_int),
+    "qec_kernel_times": ([_P, _P, _P], ctypes.c_int),
+    "qec_destroy": ([_P], ctypes.c_int),
+    "qec_last_error": ([], ctypes.c_char_p),
+    "qec_debug_program": ([ctypes.POINTER(qec_params), _P, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32),
+                           _P, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32)], ctypes.c_int),
+    "qec_debug_blocks": ([ctypes.POINTER(qec_params), ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int32, _P, _P],
+                         ctypes.c_int),
+}
+
+
+def lib(path=None):
+    """Load libqecsv.so (building it in-tree if absent or stale)."""
+    global _lib
+    if _lib is None:
+        p = path or os.environ.get("QECSV_LIB") or build()
+        L = ctypes.CDLL(p)
+        for name, (argtypes, restype) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.argtypes = argtypes
+            fn.restype = restype
+        _lib = L
+    return _lib
+
+
+def check(status):
+    if status != QEC_OK:
+        raise QecError(status, lib().qec_last_error().decode(errors="replace"))
+    return status
+
+
+def make_params(d, rounds, gates="cr", precision="c128", layout="reduced", **noise):
+    p = qec_params()
+    p.d, p.rounds = int(d), int(rounds)
+    p.layout = {"reduced": QEC_LAYOUT_REDUCED, "unreduced": QEC_LAYOUT_UNREDUCED}[layout]
+    p.gates = {"cnot": QEC_GATES_CNOT, "cr": QEC_GATES_CR}[gates]
+    p.precision = {"c128": QEC_C128, "c64": QEC_C64}[precision]
+    p.reserved = 0
+    for k, v in noise.items():
+        if k not in NOISE_FIELDS:
+            raise KeyError(k)
+        setattr(p.noise, k, float(v))
+    return p
+
+
+def qec_create(params, cuda_stream=None):
+    h = _P()
+    check(lib().qec_create(ctypes.byref(params), cuda_stream, ctypes.byref(h)))
+    return h
+
+
+def qec_run_trajectories(sim, seed, first_traj, n, syndromes_ptr, data_bits_ptr, raw_logical_ptr):
+    return check(lib().qec_run_trajectories(sim, seed, first_traj, n, syndromes_ptr, data_bits_ptr, raw_logical_ptr))
+
+
+def qec_run_trajectories_device(sim, seed, first_traj, n, d_syn_ptr, d_bits_ptr, d_log_ptr):
+    return check(lib().qec_run_trajectories_device(sim, seed, first_traj, n, d_syn_ptr, d_bits_ptr, d_log_ptr))
+
+
+def qec_state_len(sim):
+    return int(lib().qec_state_len(sim))
+
+
+def qec_get_state(sim, host_ptr, nbytes):
+    return check(lib().qec_get_state(sim, host_ptr, nbytes))
+
+
+def qec_record_events(sim, max_events):
+    return check(lib().qec_record_events(sim, max_events))
+
+
+def qec_get_events(sim, host_ptr, max_events):
+    c = ctypes.c_uint32(0)
+    check(lib().qec_get_events(sim, host_ptr, max_events, ctypes.byref(c)))
+    return int(c.value)
+
+
+def qec_kernel_times(sim):
+    """(probability-pass ms, apply-pass ms, block index) of the instrumented block."""
+    ms = (ctypes.c_float * 2)()
+    blk = ctypes.c_int32(0)
+    check(lib().qec_kernel_times(sim, ctypes.cast(ms, _P), ctypes.cast(ctypes.pointer(blk), _P)))
+    return float(ms[0]), float(ms[1]), int(blk.value)
+
+
+def qec_destroy(sim):
+    return check(lib().qec_destroy(sim))
+
+
+def qec_last_error():
+    return lib().qec_last_error().decode(errors="replace")
+
+
+def qec_debug_program(params, ops_ptr, cap, block_ptr, block_cap):
+    n_ops, n_blk = ctypes.c_uint32(0), ctypes.c_uint32(0)
+    check(lib().qec_debug_program(ctypes.byref(params), ops_ptr, cap, ctypes.byref(n_ops), block_ptr, block_cap,
+                                  ctypes.byref(n_blk)))
+    return int(n_ops.value), int(n_blk.value)
+
+
+def qec_debug_blocks(params, seed, traj, rnd, kraus_ptr, u_ptr):
+    return check(lib().qec_debug_blocks(ctypes.byref(params), seed, traj, rnd, kraus_ptr, u_ptr))

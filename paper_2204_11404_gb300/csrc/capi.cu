@@ -1,0 +1,471 @@
+// C-ABI of the simulator: handle lifetime, device buffers, the noise-free init
+// round, the per-trajectory CUDA graph, and the host-side test hooks.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstddef>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/qecsv.h"
+#include "common.cuh"
+#include "kernels.hpp"
+#include "program.hpp"
+
+using namespace qec;
+
+namespace {
+
+thread_local std::string g_err;
+
+qec_status fail(qec_status s, const std::string& msg) {
+  g_err = msg;
+  return s;
+}
+
+#define QEC_CUDA(call)                                                                   \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess) {                                                             \
+      return fail(e_ == cudaErrorMemoryAllocation ? QEC_ENOMEM : QEC_ECUDA,              \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                   \
+    }                                                                                    \
+  } while (0)
+
+constexpr uint32_t kBatchCap = 1024;
+
+}  // namespace
+
+struct qec_sim {
+  qec_params p{};
+  int device = 0, num_sms = 0;
+  cudaStream_t work = nullptr;          // owned; all kernels and the graph run here
+  cudaStream_t user = nullptr;          // caller's stream (ordering only)
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  cudaEvent_t kev[3] = {nullptr, nullptr, nullptr};   // around the instrumented block's two passes
+  int timed_block = -1;
+  Program init_prog, prog;
+  int D = 0, nstab = 0, R = 0, S = 0;
+  size_t amp = 16;
+  void* psi = nullptr;
+  void* psi0 = nullptr;
+  ProgOp* d_ops[2] = {nullptr, nullptr};       // [0] init, [1] noisy
+  BlockInfo* d_blocks[2] = {nullptr, nullptr};
+  double* d_mats[2] = {nullptr, nullptr};
+  void* d_kraus = nullptr;                     // S (>= nstab) blocks
+  double* d_u = nullptr;
+  double* d_A = nullptr;
+  double* d_N = nullptr;
+  int* d_m = nullptr;
+  double* d_partials = nullptr;
+  Ctl* d_ctl = nullptr;
+  Ctl* h_ctl = nullptr;                        // pinned
+  double* d_hist_part = nullptr;
+  double* d_hist = nullptr;
+  uint8_t* d_syn = nullptr;
+  uint8_t* d_bits = nullptr;
+  uint8_t* d_log = nullptr;
+  int32_t* d_events = nullptr;
+  uint32_t ev_cap = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  bool ran = false;
+
+  int syn_stride() const { return (R + 1) * nstab; }
+};
+
+namespace {
+
+template <typename T>
+qec_status dmalloc(T** p, size_t bytes) {
+  QEC_CUDA(cudaMalloc((void**)p, bytes));
+  return QEC_OK;
+}
+
+qec_status upload_program(qec_sim* s, int which, const Program& P) {
+  qec_status st;
+  if ((st = dmalloc(&s->d_ops[which], sizeof(ProgOp) * (P.ops.size() + 1))) != QEC_OK) return st;
+  if ((st = dmalloc(&s->d_blocks[which], sizeof(BlockInfo) * P.blocks.size())) != QEC_OK) return st;
+  if ((st = dmalloc(&s->d_mats[which], sizeof(P.mats))) != QEC_OK) return st;
+  if (!P.ops.empty())
+    QEC_CUDA(cudaMemcpy(s->d_ops[which], P.ops.data(), sizeof(ProgOp) * P.ops.size(), cudaMemcpyHostToDevice));
+  QEC_CUDA(cudaMemcpy(s->d_blocks[which], P.blocks.data(), sizeof(BlockInfo) * P.blocks.size(), cudaMemcpyHostToDevice));
+  QEC_CUDA(cudaMemcpy(s->d_mats[which], P.mats, sizeof(P.mats), cudaMemcpyHostToDevice));
+  return QEC_OK;
+}
+
+InstArgs inst_args(const qec_sim* s, int which, int round_base, int nblk, bool with_ctl) {
+  const Program& P = which ? s->prog : s->init_prog;
+  InstArgs a;
+  a.ops = s->d_ops[which];
+  a.blocks = s->d_blocks[which];
+  a.mats = s->d_mats[which];
+  for (int i = 0; i < 3; ++i) a.prob[i] = P.prob[i];
+  a.nstab = s->nstab;
+  a.nd = s->D;
+  a.round_base = round_base;
+  a.nblk = nblk;
+  a.kraus = s->d_kraus;
+  a.u = s->d_u;
+  a.ctl = with_ctl ? s->d_ctl : nullptr;
+  a.events = (with_ctl && s->ev_cap) ? s->d_events : nullptr;
+  return a;
+}
+
+PassArgs pass_args(const qec_sim* s, const Program& P, int blk, const void* src, void* dst, bool forced,
+                   uint8_t* syn, int syn_idx) {
+  const BlockInfo& bi = P.blocks[blk % s->nstab];
+  PassArgs a;
+  a.src = src;
+  a.dst = dst;
+  a.D = s->D;
+  a.w = bi.w;
+  for (int j = 0; j < 4; ++j) a.q[j] = bi.q[j] < 0 ? 0 : bi.q[j];
+  a.kraus = static_cast<const char*>(s->d_kraus) + (size_t)blk * KRAUS_STRIDE * s->amp;
+  a.u = s->d_u + blk;
+  a.forced = forced ? bi.offset : -1;
+  a.A = s->d_A + blk;
+  a.N = s->d_N + blk;
+  a.m = s->d_m + blk;
+  a.ctl = s->d_ctl;
+  a.partials = s->d_partials;
+  a.syn = syn;
+  a.syn_stride = s->syn_stride();
+  a.syn_idx = syn_idx;
+  a.offset = bi.offset;
+  return a;
+}
+
+// Noise-free init round with outcomes forced to the zero syndrome (Sec. III.B); result in psi0.
+qec_status run_init_round(qec_sim* s) {
+  QEC_CUDA(launch_set_basis0(s->p.precision, s->psi0, s->D, s->work));
+  QEC_CUDA(launch_instantiate(s->p.precision, inst_args(s, 0, 0, s->nstab, false), s->work));
+  for (int k = 0; k < s->nstab; ++k) {
+    PassArgs a = pass_args(s, s->init_prog, k, s->psi0, s->psi0, true, nullptr, 0);
+    const int grid = pass_grid(s->D, a.w, s->num_sms);
+    QEC_CUDA(launch_prob(s->p.precision, a, grid, s->work));
+    QEC_CUDA(launch_apply(s->p.precision, a, grid, s->work));
+  }
+  QEC_CUDA(cudaStreamSynchronize(s->work));
+  return QEC_OK;
+}
+
+qec_status enqueue_trajectory(qec_sim* s) {
+  if (s->S > 0) QEC_CUDA(launch_instantiate(s->p.precision, inst_args(s, 1, 1, s->S, true), s->work));
+  for (int b = 0; b < s->S; ++b) {
+    const void* src = b == 0 ? s->psi0 : s->psi;
+    const int rnd = 1 + b / s->nstab, k = b % s->nstab;
+    PassArgs a = pass_args(s, s->prog, b, src, s->psi, false, s->d_syn, rnd * s->nstab + k);
+    const int grid = pass_grid(s->D, a.w, s->num_sms);
+    const bool timed = b == s->timed_block;
+    if (timed) QEC_CUDA(cudaEventRecord(s->kev[0], s->work));
+    QEC_CUDA(launch_prob(s->p.precision, a, grid, s->work));
+    if (timed) QEC_CUDA(cudaEventRecord(s->kev[1], s->work));
+    QEC_CUDA(launch_apply(s->p.precision, a, grid, s->work));
+    if (timed) QEC_CUDA(cudaEventRecord(s->kev[2], s->work));
+  }
+  ReadArgs r;
+  r.src = s->S > 0 ? s->psi : s->psi0;
+  r.D = s->D;
+  r.k1 = hist_k1(s->D);
+  r.d = s->p.d;
+  r.rounds = s->R;
+  r.grid_hist = hist_grid(s->D, s->num_sms);
+  r.hist_part = s->d_hist_part;
+  r.hist = s->d_hist;
+  r.ctl = s->d_ctl;
+  r.bits = s->d_bits;
+  r.logical = s->d_log;
+  r.syn = s->d_syn;
+  r.syn_stride = s->syn_stride();
+  r.nstab = s->nstab;
+  QEC_CUDA(launch_readout(s->p.precision, r, s->work));
+  return QEC_OK;
+}
+
+qec_status ensure_graph(qec_sim* s) {
+  if (s->gexec) return QEC_OK;
+  QEC_CUDA(cudaStreamBeginCapture(s->work, cudaStreamCaptureModeThreadLocal));
+  qec_status st = enqueue_trajectory(s);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(s->work, &g);
+  if (st != QEC_OK) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  if (e != cudaSuccess) return fail(QEC_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  s->graph = g;
+  QEC_CUDA(cudaGraphInstantiate(&s->gexec, g, 0));
+  return QEC_OK;
+}
+
+void drop_graph(qec_sim* s) {
+  if (s->gexec) cudaGraphExecDestroy(s->gexec);
+  if (s->graph) cudaGraphDestroy(s->graph);
+  s->gexec = nullptr;
+  s->graph = nullptr;
+}
+
+void free_all(qec_sim* s) {
+  drop_graph(s);
+  void* ptrs[] = {s->psi, s->psi0, s->d_kraus, s->d_u, s->d_A, s->d_N, s->d_m, s->d_partials, s->d_ctl,
+                  s->d_hist_part, s->d_hist, s->d_syn, s->d_bits, s->d_log, s->d_events,
+                  s->d_ops[0], s->d_ops[1], s->d_blocks[0], s->d_blocks[1], s->d_mats[0], s->d_mats[1]};
+  for (void* p : ptrs) if (p) cudaFree(p);
+  if (s->h_ctl) cudaFreeHost(s->h_ctl);
+  for (cudaEvent_t ev : s->kev) if (ev) cudaEventDestroy(ev);
+  if (s->ev_in) cudaEventDestroy(s->ev_in);
+  if (s->ev_out) cudaEventDestroy(s->ev_out);
+  if (s->work) cudaStreamDestroy(s->work);
+}
+
+qec_status create_impl(const qec_params* params, void* stream, qec_sim** out) {
+  if (!params || !out) return fail(QEC_EINVAL, "null argument");
+  *out = nullptr;
+  std::string err;
+  if (!validate_params(*params, err)) return fail(QEC_EINVAL, err);
+  if (params->layout != QEC_LAYOUT_REDUCED)
+    return fail(QEC_EUNSUPPORTED, "only the reduced (d^2+1 qubit) register runs on the GPU");
+  qec_sim* s = new (std::nothrow) qec_sim();
+  if (!s) return fail(QEC_ENOMEM, "host allocation failed");
+  qec_status st = QEC_OK;
+  auto bail = [&](qec_status x) { free_all(s); delete s; return x; };
+  s->p = *params;
+  s->user = static_cast<cudaStream_t>(stream);
+  if (!build_program(s->p, false, s->init_prog, err) || !build_program(s->p, true, s->prog, err))
+    return bail(fail(QEC_EINVAL, err));
+  s->D = s->prog.nd;
+  s->nstab = s->prog.nstab;
+  s->R = s->p.rounds;
+  s->S = s->nstab * s->R;
+  s->amp = s->p.precision == QEC_C128 ? 16 : 8;
+  if (s->R > 0) {   // first weight-4 block of the middle noisy round
+    const int rnd = (s->R + 1) / 2;
+    for (int k = 0; k < s->nstab && s->timed_block < 0; ++k)
+      if (s->prog.blocks[k].w == 4) s->timed_block = (rnd - 1) * s->nstab + k;
+  }
+  cudaError_t e = cudaGetDevice(&s->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, s->device);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->work, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_in, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_out, cudaEventDisableTiming);
+  for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaEventCreate(&s->kev[i]);
+  if (e == cudaSuccess) e = setup_kernels(s->p.precision, s->D);
+  if (e != cudaSuccess) return bail(fail(QEC_ECUDA, std::string("CUDA setup: ") + cudaGetErrorString(e)));
+  const size_t state_bytes = ((size_t)1 << s->D) * s->amp;
+  const int nblk = s->S > s->nstab ? s->S : s->nstab;
+  const int k1 = hist_k1(s->D);
+  if ((st = dmalloc(&s->psi, state_bytes)) || (st = dmalloc(&s->psi0, state_bytes)) ||
+      (st = dmalloc(&s->d_kraus, (size_t)nblk * KRAUS_STRIDE * s->amp)) ||
+      (st = dmalloc(&s->d_u, sizeof(double) * nblk)) || (st = dmalloc(&s->d_A, sizeof(double) * nblk)) ||
+      (st = dmalloc(&s->d_N, sizeof(double) * nblk)) || (st = dmalloc(&s->d_m, sizeof(int) * nblk)) ||
+      (st = dmalloc(&s->d_partials, sizeof(double) * 2 * MAX_PASS_GRID)) ||
+      (st = dmalloc(&s->d_ctl, sizeof(Ctl))) ||
+      (st = dmalloc(&s->d_hist_part, sizeof(double) * ((size_t)hist_grid(s->D, s->num_sms) << k1))) ||
+      (st = dmalloc(&s->d_hist, sizeof(double) << k1)) ||
+      (st = dmalloc(&s->d_syn, (size_t)kBatchCap * s->syn_stride())) ||
+      (st = dmalloc(&s->d_bits, (size_t)kBatchCap * s->D)) || (st = dmalloc(&s->d_log, kBatchCap)))
+    return bail(st);
+  e = cudaMallocHost((void**)&s->h_ctl, sizeof(Ctl));
+  if (e != cudaSuccess) return bail(fail(QEC_ENOMEM, "pinned allocation failed"));
+  std::memset(s->h_ctl, 0, sizeof(Ctl));
+  e = cudaMemcpy(s->d_ctl, s->h_ctl, sizeof(Ctl), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return bail(fail(QEC_ECUDA, cudaGetErrorString(e)));
+  if ((st = upload_program(s, 0, s->init_prog)) || (st = upload_program(s, 1, s->prog))) return bail(st);
+  if ((st = run_init_round(s))) return bail(st);
+  *out = s;
+  return QEC_OK;
+}
+
+qec_status run_impl(qec_sim* s, uint64_t seed, uint64_t first, uint32_t n, uint8_t* syn, uint8_t* bits,
+                    uint8_t* logical, bool host_out) {
+  if (!s) return fail(QEC_EINVAL, "null handle");
+  qec_status st = ensure_graph(s);
+  if (st) return st;
+  if (s->user) {
+    QEC_CUDA(cudaEventRecord(s->ev_in, s->user));
+    QEC_CUDA(cudaStreamWaitEvent(s->work, s->ev_in, 0));
+  }
+  const cudaMemcpyKind kind = host_out ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  const size_t ss = (size_t)s->syn_stride(), bs = (size_t)s->D;
+  for (uint32_t done = 0; done < n;) {
+    const uint32_t chunk = (n - done) < kBatchCap ? (n - done) : kBatchCap;
+    QEC_CUDA(cudaStreamSynchronize(s->work));   // h_ctl is reused below
+    s->h_ctl->seed = seed;
+    s->h_ctl->first = first + done;
+    s->h_ctl->traj = first + done;
+    s->h_ctl->ticket = 0;
+    s->h_ctl->ev_cap = s->ev_cap;
+    const size_t head = done == 0 ? offsetof(Ctl, pad) : offsetof(Ctl, ticket);   // events reset per call
+    if (done == 0) s->h_ctl->n_events = 0;
+    QEC_CUDA(cudaMemcpyAsync(s->d_ctl, s->h_ctl, head, cudaMemcpyHostToDevice, s->work));
+    for (uint32_t t = 0; t < chunk; ++t) QEC_CUDA(cudaGraphLaunch(s->gexec, s->work));
+    if (syn) QEC_CUDA(cudaMemcpyAsync(syn + done * ss, s->d_syn, chunk * ss, kind, s->work));
+    if (bits) QEC_CUDA(cudaMemcpyAsync(bits + done * bs, s->d_bits, chunk * bs, kind, s->work));
+    if (logical) QEC_CUDA(cudaMemcpyAsync(logical + done, s->d_log, chunk, kind, s->work));
+    done += chunk;
+  }
+  if (s->user) {
+    QEC_CUDA(cudaEventRecord(s->ev_out, s->work));
+    QEC_CUDA(cudaStreamWaitEvent(s->user, s->ev_out, 0));
+  }
+  if (host_out) QEC_CUDA(cudaStreamSynchronize(s->work));
+  QEC_CUDA(cudaGetLastError());
+  if (n) s->ran = true;
+  return QEC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+qec_status qec_create(const qec_params* params, void* cuda_stream, qec_sim** out) {
+  try {
+    return create_impl(params, cuda_stream, out);
+  } catch (...) {
+    return fail(QEC_ENOMEM, "exception in qec_create");
+  }
+}
+
+qec_status qec_run_trajectories(qec_sim* sim, uint64_t seed, uint64_t first_traj, uint32_t n,
+                                uint8_t* syndromes, uint8_t* data_bits, uint8_t* raw_logical) {
+  try {
+    return run_impl(sim, seed, first_traj, n, syndromes, data_bits, raw_logical, true);
+  } catch (...) {
+    return fail(QEC_ENOMEM, "exception in qec_run_trajectories");
+  }
+}
+
+qec_status qec_run_trajectories_device(qec_sim* sim, uint64_t seed, uint64_t first_traj, uint32_t n,
+                                       uint8_t* d_syndromes, uint8_t* d_data_bits, uint8_t* d_raw_logical) {
+  try {
+    return run_impl(sim, seed, first_traj, n, d_syndromes, d_data_bits, d_raw_logical, false);
+  } catch (...) {
+    return fail(QEC_ENOMEM, "exception in qec_run_trajectories_device");
+  }
+}
+
+uint64_t qec_state_len(const qec_sim* sim) { return sim ? (1ull << sim->D) : 0ull; }
+
+qec_status qec_get_state(qec_sim* s, void* host_buf, size_t bytes) {
+  if (!s || !host_buf) return fail(QEC_EINVAL, "null argument");
+  const size_t n = (size_t)1 << s->D;
+  if (bytes < 16 * n) return fail(QEC_EINVAL, "host buffer too small");
+  if (!s->ran) return fail(QEC_EINVAL, "no trajectory has run yet");
+  QEC_CUDA(cudaStreamSynchronize(s->work));
+  Ctl c;
+  QEC_CUDA(cudaMemcpy(&c, s->d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
+  const void* src = s->S > 0 ? s->psi : s->psi0;
+  double* out = static_cast<double*>(host_buf);
+  const double scale = 1.0 / std::sqrt(c.final_norm);
+  if (s->p.precision == QEC_C128) {
+    QEC_CUDA(cudaMemcpy(out, src, 16 * n, cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < 2 * n; ++i) out[i] *= scale;
+  } else {
+    std::vector<float> tmp(2 * n);
+    QEC_CUDA(cudaMemcpy(tmp.data(), src, 8 * n, cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < 2 * n; ++i) out[i] = (double)tmp[i] * scale;
+  }
+  return QEC_OK;
+}
+
+qec_status qec_record_events(qec_sim* s, uint32_t max_events) {
+  if (!s) return fail(QEC_EINVAL, "null handle");
+  QEC_CUDA(cudaStreamSynchronize(s->work));
+  if (s->d_events) {
+    QEC_CUDA(cudaFree(s->d_events));
+    s->d_events = nullptr;
+  }
+  s->ev_cap = 0;
+  if (max_events) {
+    qec_status st = dmalloc(&s->d_events, (size_t)max_events * 5 * sizeof(int32_t));
+    if (st) return st;
+    s->ev_cap = max_events;
+  }
+  drop_graph(s);   // the instantiate node holds the events pointer
+  return QEC_OK;
+}
+
+qec_status qec_get_events(qec_sim* s, int32_t* host_events, uint32_t max_events, uint32_t* count) {
+  if (!s || !count) return fail(QEC_EINVAL, "null argument");
+  QEC_CUDA(cudaStreamSynchronize(s->work));
+  Ctl c;
+  QEC_CUDA(cudaMemcpy(&c, s->d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
+  uint32_t n = c.n_events < s->ev_cap ? c.n_events : s->ev_cap;
+  if (n > max_events) n = max_events;
+  *count = n;
+  if (n && host_events) QEC_CUDA(cudaMemcpy(host_events, s->d_events, (size_t)n * 5 * sizeof(int32_t), cudaMemcpyDeviceToHost));
+  return QEC_OK;
+}
+
+qec_status qec_kernel_times(qec_sim* s, float* ms, int32_t* block) {
+  if (!s || !ms || !block) return fail(QEC_EINVAL, "null argument");
+  if (!s->ran || s->timed_block < 0) return fail(QEC_EINVAL, "no instrumented trajectory has run");
+  QEC_CUDA(cudaStreamSynchronize(s->work));
+  QEC_CUDA(cudaEventElapsedTime(&ms[0], s->kev[0], s->kev[1]));
+  QEC_CUDA(cudaEventElapsedTime(&ms[1], s->kev[1], s->kev[2]));
+  *block = s->timed_block;
+  return QEC_OK;
+}
+
+qec_status qec_destroy(qec_sim* s) {
+  if (!s) return QEC_OK;
+  if (s->work) cudaStreamSynchronize(s->work);
+  free_all(s);
+  delete s;
+  return QEC_OK;
+}
+
+const char* qec_last_error(void) { return g_err.c_str(); }
+
+qec_status qec_debug_program(const qec_params* params, int32_t* ops, uint32_t cap, uint32_t* n_ops,
+                             int32_t* block_info, uint32_t block_cap, uint32_t* n_blocks) {
+  if (!params || !n_ops || !n_blocks) return fail(QEC_EINVAL, "null argument");
+  std::string err;
+  Program P;
+  if (!build_program(*params, true, P, err)) return fail(QEC_EINVAL, err);
+  *n_ops = (uint32_t)P.ops.size();
+  *n_blocks = (uint32_t)P.blocks.size();
+  for (size_t b = 0; b < P.blocks.size(); ++b) {
+    const BlockInfo& bi = P.blocks[b];
+    if (block_info && b < block_cap) {
+      int32_t* o = block_info + 6 * b;
+      o[0] = bi.w; o[1] = bi.q[0]; o[2] = bi.q[1]; o[3] = bi.q[2]; o[4] = bi.q[3]; o[5] = bi.offset;
+    }
+    for (int i = bi.op_begin; i < bi.op_end; ++i) {
+      if (ops && (uint32_t)i < cap) {
+        const ProgOp& op = P.ops[i];
+        int32_t* o = ops + 6 * i;
+        o[0] = (int32_t)b; o[1] = op.kind; o[2] = op.q0; o[3] = op.q1; o[4] = op.step; o[5] = (int32_t)op.site;
+      }
+    }
+  }
+  return QEC_OK;
+}
+
+qec_status qec_debug_blocks(const qec_params* params, uint64_t seed, uint64_t traj, int32_t round,
+                            double* kraus, double* u) {
+  if (!params || !kraus || !u) return fail(QEC_EINVAL, "null argument");
+  std::string err;
+  Program P;
+  if (round < 0 || !build_program(*params, round > 0, P, err)) return fail(QEC_EINVAL, err.empty() ? "bad round" : err);
+  InstArgs a;
+  a.ops = P.ops.data();
+  a.blocks = P.blocks.data();
+  a.mats = &P.mats[0][0][0];
+  for (int i = 0; i < 3; ++i) a.prob[i] = P.prob[i];
+  a.nstab = P.nstab;
+  a.nd = P.nd;
+  a.round_base = round;
+  a.nblk = P.nstab;
+  for (int k = 0; k < P.nstab; ++k) {
+    double2* k0 = reinterpret_cast<double2*>(kraus) + (size_t)k * 512;
+    instantiate_block_host(a, k, seed, traj, k0, k0 + 256, u + k);
+  }
+  return QEC_OK;
+}
+
+}  // extern "C"

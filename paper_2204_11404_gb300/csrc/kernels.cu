@@ -1,0 +1,532 @@
+// Trajectory kernels for GB300 (sm_103a).
+//
+// Per stabilizer of a round (Sec. II.B: one stabilizer circuit at a time on the
+// reused ancilla) the ancilla starts in |0>, so the block's unitary U acts on
+// the data register through two Kraus matrices K_m = <m|U|0> (16x16 on its <= 4
+// data qubits).  A measurement is then one FP64-accumulated probability pass
+// P(1) = <psi|K1^dag K1|psi> / <psi|psi> over the register (warp shuffle ->
+// block -> last-CTA reduction in a fixed order), an on-device outcome
+// u < P(1), and one pass psi <- K_m psi / sqrt(<psi|psi>) that collapses,
+// renormalises and resets in one go.
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "kernels.hpp"
+
+namespace qec {
+
+template <typename T> struct V2;
+template <> struct V2<double> { using t = double2; };
+template <> struct V2<float> { using t = float2; };
+
+__device__ __forceinline__ double2 to_v2(double2 v, double*) { return v; }
+
+// Shared-memory loads the compiler may not hoist out of the group loop (hoisting all
+// 256 matrix entries into registers would spill).
+__device__ __forceinline__ double2 lds_v2(const double2* p) {
+  double2 r;
+  asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(r.x), "=d"(r.y) : "r"((unsigned)__cvta_generic_to_shared(p)));
+  return r;
+}
+__device__ __forceinline__ float2 lds_v2(const float2* p) {
+  float2 r;
+  asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(r.x), "=f"(r.y) : "r"((unsigned)__cvta_generic_to_shared(p)));
+  return r;
+}
+__device__ __forceinline__ float2 to_v2(double2 v, float*) { return make_float2((float)v.x, (float)v.y); }
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Deterministic block sum of two values (fixed shuffle tree, then warp 0); result valid in thread 0.
+__device__ __forceinline__ void block_sum2(double& a, double& b, double* sh /* >= 2*32 */) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  a = warp_sum(a);
+  b = warp_sum(b);
+  if (lane == 0) { sh[wid] = a; sh[32 + wid] = b; }
+  __syncthreads();
+  if (wid == 0) {
+    a = lane < nw ? sh[lane] : 0.0;
+    b = lane < nw ? sh[32 + lane] : 0.0;
+    a = warp_sum(a);
+    b = warp_sum(b);
+  }
+  __syncthreads();
+}
+
+// ---- instantiate: draw this trajectory's noise and fuse every block -----------------------
+__device__ void inst_block(const InstArgs& a, double2* U, double (*sm)[16][2], int* scode,
+                           int blk, uint64_t seed, uint64_t traj) {
+  const int k = blk % a.nstab;
+  const int rnd = a.round_base + blk / a.nstab;
+  const BlockInfo bi = a.blocks[k];
+  const int w = bi.w, C = 1 << w;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int i = tid; i < 32 * 16; i += nt) {
+    int r = i / 16, c = i % 16;
+    U[i] = make_double2((r < C && r == c) ? 1.0 : 0.0, 0.0);
+  }
+  __syncthreads();
+  for (int oi = bi.op_begin; oi < bi.op_end; ++oi) {
+    const ProgOp op = a.ops[oi];
+    if (op.kind == OP_N1 || op.kind == OP_N2) {
+      if (tid == 0) {
+        int code = noise_code(op, a.prob[op.pidx], seed, traj, rnd);
+        *scode = code;
+        if (code && a.events && a.ctl) {
+          unsigned int e = atomicAdd(&a.ctl->n_events, 1u);
+          if (e < a.ctl->ev_cap) {
+            int32_t* ev = a.events + 5 * (size_t)e;
+            ev[0] = (int32_t)traj; ev[1] = rnd; ev[2] = op.step; ev[3] = (int32_t)op.site;
+            ev[4] = op.kind == OP_N1 ? code : code;
+          }
+        }
+      }
+      __syncthreads();
+      const int code = *scode;
+      __syncthreads();
+      if (code == 0) continue;
+      if (op.kind == OP_N1) {
+        for (int it = tid; it < items_1q(w); it += nt) apply1_item(U, w, op.q0, sm[code], it);
+      } else {
+        const int pa = code >> 2, pd = code & 3;
+        if (pa) for (int it = tid; it < items_1q(w); it += nt) apply1_item(U, w, op.q0, sm[pa], it);
+        __syncthreads();
+        if (pd) for (int it = tid; it < items_1q(w); it += nt) apply1_item(U, w, op.q1, sm[pd], it);
+      }
+    } else if (op.kind == OP_U1) {
+      for (int it = tid; it < items_1q(w); it += nt) apply1_item(U, w, op.q0, sm[op.mat], it);
+    } else {
+      for (int it = tid; it < items_2q(w); it += nt) apply2_item(U, w, op.q0, op.q1, sm[op.mat], it);
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_instantiate(InstArgs a) {
+  using T2 = typename V2<T>::t;
+  __shared__ double2 U[32 * 16];
+  __shared__ double sm[M_COUNT][16][2];
+  __shared__ int scode;
+  for (int i = threadIdx.x; i < M_COUNT * 32; i += blockDim.x) (&sm[0][0][0])[i] = a.mats[i];
+  __syncthreads();
+  const uint64_t seed = a.ctl ? a.ctl->seed : 0ull;
+  const uint64_t traj = a.ctl ? a.ctl->traj : 0ull;
+  const int blk = blockIdx.x;
+  inst_block(a, U, sm, &scode, blk, seed, traj);
+  const int k = blk % a.nstab;
+  const int C = 1 << a.blocks[k].w;
+  T2* out = reinterpret_cast<T2*>(a.kraus) + (size_t)blk * KRAUS_STRIDE;
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) {
+    const int r = i / 16, c = i % 16;
+    double2 k0 = make_double2(0, 0), k1 = make_double2(0, 0), mm = make_double2(0, 0);
+    if (r < C && c < C) {
+      k0 = U[r * 16 + c];
+      k1 = U[(C + r) * 16 + c];
+      for (int x = 0; x < C; ++x) {           // M_rc = sum_x conj(K1_xr) K1_xc
+        double2 p = U[(C + x) * 16 + r], q = U[(C + x) * 16 + c];
+        mm.x += p.x * q.x + p.y * q.y;
+        mm.y += p.x * q.y - p.y * q.x;
+      }
+    }
+    out[i] = to_v2(k0, (T*)nullptr);
+    out[256 + i] = to_v2(k1, (T*)nullptr);
+    out[512 + i] = to_v2(mm, (T*)nullptr);
+  }
+  if (threadIdx.x == 0) {
+    const int rnd = a.round_base + blk / a.nstab;
+    a.u[blk] = uniform53(draw(seed, traj, (uint64_t)rnd, 0u, (uint32_t)(a.nd + k), TAG_MEASURE).v[0]);
+  }
+}
+
+// ---- probability pass: A = <psi|M|psi>, N = <psi|psi>, then the outcome ----------------
+// Register index of member 0 of group g: insert a zero bit at each block qubit (ascending).
+template <int W>
+__device__ __forceinline__ uint32_t group_base(uint32_t g, const int (&q)[4]) {
+#pragma unroll
+  for (int j = 0; j < W; ++j) g = ((g >> q[j]) << (q[j] + 1)) | (g & ((1u << q[j]) - 1u));
+  return g;
+}
+
+template <int W>
+__device__ __forceinline__ void load_q(const PassArgs& a, int (&q)[4]) {
+#pragma unroll
+  for (int j = 0; j < 4; ++j) q[j] = j < W ? a.q[j] : 0;
+}
+
+// Offset of member l of a group (bit j of l -> register bit q[j]).
+template <int W>
+__device__ __forceinline__ uint32_t member_off(int l, const int (&q)[4]) {
+  uint32_t o = 0;
+#pragma unroll
+  for (int j = 0; j < W; ++j) o |= (uint32_t)((l >> j) & 1) << q[j];
+  return o;
+}
+
+template <typename T, int W>
+__global__ void __launch_bounds__(256) k_prob(PassArgs a) {
+  using T2 = typename V2<T>::t;
+  constexpr int C = 1 << W;
+  __shared__ T2 sM[C * C];
+  __shared__ double sred[64];
+  __shared__ int s_last;
+  const T2* Mg = reinterpret_cast<const T2*>(a.kraus) + 512;
+  for (int i = threadIdx.x; i < C * C; i += blockDim.x) sM[i] = Mg[(i / C) * 16 + (i % C)];
+  __syncthreads();
+  int q[4];
+  load_q<W>(a, q);
+  uint32_t off[C];
+#pragma unroll
+  for (int l = 0; l < C; ++l) off[l] = member_off<W>(l, q);
+  const T2* src = reinterpret_cast<const T2*>(a.src);
+  const uint32_t G = 1u << (a.D - W);
+  double accA = 0.0, accN = 0.0;
+  for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
+    const uint32_t base = group_base<W>(g, q);
+    T2 v[C];
+#pragma unroll
+    for (int l = 0; l < C; ++l) v[l] = src[base + off[l]];
+    T sa = 0, sn = 0;
+#pragma unroll
+    for (int i = 0; i < C; ++i) {
+      T tr = 0, ti = 0;
+#pragma unroll
+      for (int j = i + 1; j < C; ++j) {
+        const T2 m = lds_v2(&sM[i * C + j]);
+        tr += m.x * v[j].x - m.y * v[j].y;
+        ti += m.x * v[j].y + m.y * v[j].x;
+      }
+      const T nv = v[i].x * v[i].x + v[i].y * v[i].y;
+      sa += 2 * (v[i].x * tr + v[i].y * ti) + lds_v2(&sM[i * C + i]).x * nv;
+      sn += nv;
+    }
+    accA += (double)sa;
+    accN += (double)sn;
+  }
+  block_sum2(accA, accN, sred);
+  if (threadIdx.x == 0) {
+    a.partials[2 * blockIdx.x] = accA;
+    a.partials[2 * blockIdx.x + 1] = accN;
+    __threadfence();
+    const unsigned int t = atomicAdd(&a.ctl->ticket, 1u);
+    s_last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  double sA = 0.0, sN = 0.0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
+    sA += __ldcg(&a.partials[2 * i]);
+    sN += __ldcg(&a.partials[2 * i + 1]);
+  }
+  block_sum2(sA, sN, sred);
+  if (threadIdx.x == 0) {
+    const double p1 = sA / sN;
+    const int m = a.forced >= 0 ? a.forced : (*a.u < p1 ? 1 : 0);
+    *a.A = sA;
+    *a.N = sN;
+    *a.m = m;
+    if (a.syn) {
+      const unsigned long long t = a.ctl->traj - a.ctl->first;
+      a.syn[t * (unsigned long long)a.syn_stride + a.syn_idx] = (uint8_t)(m ^ a.offset);
+    }
+    a.ctl->ticket = 0u;
+  }
+}
+
+// ---- apply pass: psi <- K_m psi / sqrt(N) ---------------------------------------------
+template <typename T, int W>
+__global__ void __launch_bounds__(256) k_apply(PassArgs a) {
+  using T2 = typename V2<T>::t;
+  constexpr int C = 1 << W;
+  __shared__ T2 sK[C * C];
+  const int m = *a.m;
+  const double scale = 1.0 / sqrt(*a.N);
+  const T2* Kg = reinterpret_cast<const T2*>(a.kraus) + (m ? 256 : 0);
+  for (int i = threadIdx.x; i < C * C; i += blockDim.x) {
+    T2 kv = Kg[(i / C) * 16 + (i % C)];
+    kv.x = (T)((double)kv.x * scale);
+    kv.y = (T)((double)kv.y * scale);
+    sK[i] = kv;
+  }
+  __syncthreads();
+  int q[4];
+  load_q<W>(a, q);
+  uint32_t off[C];
+#pragma unroll
+  for (int l = 0; l < C; ++l) off[l] = member_off<W>(l, q);
+  const T2* src = reinterpret_cast<const T2*>(a.src);
+  T2* dst = reinterpret_cast<T2*>(a.dst);
+  const uint32_t G = 1u << (a.D - W);
+  for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
+    const uint32_t base = group_base<W>(g, q);
+    T2 v[C];
+#pragma unroll
+    for (int l = 0; l < C; ++l) v[l] = src[base + off[l]];
+#pragma unroll
+    for (int r = 0; r < C; ++r) {
+      T sr = 0, si = 0;
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        const T2 k = lds_v2(&sK[r * C + c]);
+        sr += k.x * v[c].x - k.y * v[c].y;
+        si += k.x * v[c].y + k.y * v[c].x;
+      }
+      T2 o;
+      o.x = sr;
+      o.y = si;
+      dst[base + off[r]] = o;
+    }
+  }
+}
+
+// ---- final Z readout (Sec. III.B): sequential per-qubit sampling -------------------------
+// Qubit j gets outcome [u_j < P(q_j = 1 | outcomes of qubits < j)].  The conditional
+// marginals of the low k1 qubits come from one histogram pass over the register; the
+// remaining qubits from the 2^(D-k1) amplitudes that carry the sampled low bits.
+template <typename T>
+__global__ void __launch_bounds__(256) k_hist(ReadArgs a) {
+  using T2 = typename V2<T>::t;
+  const int B = 1 << a.k1;
+  const int nb = B >> 8;                 // bins per thread (B >= 256)
+  const int64_t nchunk = 1ll << (a.D - a.k1);
+  const T2* src = reinterpret_cast<const T2*>(a.src);
+  double acc[16];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) acc[j] = 0.0;
+  for (int64_t ch = blockIdx.x; ch < nchunk; ch += gridDim.x) {
+    const int64_t base = ch << a.k1;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      if (j < nb) {
+        const T2 v = src[base + threadIdx.x + 256 * j];
+        acc[j] += (double)v.x * (double)v.x + (double)v.y * (double)v.y;
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < 16; ++j)
+    if (j < nb) a.hist_part[(size_t)blockIdx.x * B + threadIdx.x + 256 * j] = acc[j];
+}
+
+__global__ void __launch_bounds__(256) k_hist_reduce(ReadArgs a) {
+  const int B = 1 << a.k1;
+  const int bin = blockIdx.x * blockDim.x + threadIdx.x;
+  if (bin >= B) return;
+  double s = 0.0;
+  for (int c = 0; c < a.grid_hist; ++c) s += a.hist_part[(size_t)c * B + bin];
+  a.hist[bin] = s;
+}
+
+// Samples the bits [0, nbits) of the index over the weights w[0, n) (n = 2^nbits),
+// qubit-by-qubit; bit j of the result goes to out_bits[bit_base + j].
+__device__ int sample_bits(const double* w, int nbits, int bit_base, uint64_t seed, uint64_t traj,
+                           uint64_t rnd, uint8_t* out_bits, double* sred, int* sbit) {
+  const int n = 1 << nbits;
+  int prefix = 0;
+  for (int j = 0; j < nbits; ++j) {
+    const int mask = (1 << j) - 1;
+    double s_all = 0.0, s_one = 0.0;
+    for (int x = threadIdx.x; x < n; x += blockDim.x) {
+      if ((x & mask) == prefix) {
+        s_all += w[x];
+        if ((x >> j) & 1) s_one += w[x];
+      }
+    }
+    block_sum2(s_all, s_one, sred);
+    if (threadIdx.x == 0) {
+      const double u = uniform53(draw(seed, traj, rnd, 0u, (uint32_t)(bit_base + j), TAG_READOUT).v[0]);
+      const int b = (u < s_one / s_all) ? 1 : 0;
+      *sbit = b;
+      out_bits[bit_base + j] = (uint8_t)b;
+    }
+    __syncthreads();
+    prefix |= (*sbit) << j;
+    __syncthreads();
+  }
+  return prefix;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_sample(ReadArgs a) {
+  using T2 = typename V2<T>::t;
+  extern __shared__ double sh[];
+  __shared__ double sred[64];
+  __shared__ int sbit;
+  const int B = 1 << a.k1;
+  const uint64_t seed = a.ctl->seed, traj = a.ctl->traj;
+  const unsigned long long t = traj - a.ctl->first;
+  const uint64_t rnd = (uint64_t)a.rounds + 1;
+  const int nd = a.d * a.d;
+  uint8_t* bits = a.bits + t * (unsigned long long)nd;
+  double tot = 0.0, dummy = 0.0;
+  for (int i = threadIdx.x; i < B; i += blockDim.x) {
+    sh[i] = a.hist[i];
+    tot += sh[i];
+  }
+  block_sum2(tot, dummy, sred);
+  if (threadIdx.x == 0) a.ctl->final_norm = tot;
+  const int low = sample_bits(sh, a.k1, 0, seed, traj, rnd, bits, sred, &sbit);
+  if (a.D > a.k1) {
+    const int H = 1 << (a.D - a.k1);
+    const T2* src = reinterpret_cast<const T2*>(a.src);
+    __syncthreads();
+    for (int y = threadIdx.x; y < H; y += blockDim.x) {
+      const T2 v = src[((int64_t)y << a.k1) | low];
+      sh[y] = (double)v.x * (double)v.x + (double)v.y * (double)v.y;
+    }
+    __syncthreads();
+    sample_bits(sh, a.D - a.k1, a.k1, seed, traj, rnd, bits, sred, &sbit);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int par = 0;
+    for (int c = 0; c < a.d; ++c) par ^= bits[c];
+    a.logical[t] = (uint8_t)par;
+    for (int k = 0; k < a.nstab; ++k) a.syn[t * (unsigned long long)a.syn_stride + k] = 0;
+    a.ctl->traj = traj + 1;
+  }
+}
+
+template <typename T>
+__global__ void k_set_basis0(void* psi, int64_t n) {
+  using T2 = typename V2<T>::t;
+  T2* p = reinterpret_cast<T2*>(psi);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    T2 z;
+    z.x = (i == 0) ? (T)1 : (T)0;
+    z.y = 0;
+    p[i] = z;
+  }
+}
+
+// ---- launchers --------------------------------------------------------------------------
+int pass_grid(int D, int w, int num_sms) {
+  const int64_t G = 1ll << (D - w);
+  int64_t g = (G + 255) / 256;
+  int64_t cap = (int64_t)num_sms * 4;
+  if (g > cap) g = cap;
+  if (g > MAX_PASS_GRID) g = MAX_PASS_GRID;
+  return (int)(g < 1 ? 1 : g);
+}
+
+int hist_k1(int D) { return D < 12 ? D : 12; }
+
+int hist_grid(int D, int num_sms) {
+  const int64_t nchunk = 1ll << (D - hist_k1(D));
+  int64_t g = nchunk < (int64_t)num_sms * 2 ? nchunk : (int64_t)num_sms * 2;
+  return (int)g;
+}
+
+cudaError_t launch_instantiate(int precision, const InstArgs& a, cudaStream_t s) {
+  if (precision == QEC_C128) k_instantiate<double><<<a.nblk, 256, 0, s>>>(a);
+  else k_instantiate<float><<<a.nblk, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename T>
+static void prob_t(const PassArgs& a, int grid, cudaStream_t s) {
+  if (a.w == 4) k_prob<T, 4><<<grid, 256, 0, s>>>(a);
+  else k_prob<T, 2><<<grid, 256, 0, s>>>(a);
+}
+
+template <typename T>
+static void apply_t(const PassArgs& a, int grid, cudaStream_t s) {
+  if (a.w == 4) k_apply<T, 4><<<grid, 256, 0, s>>>(a);
+  else k_apply<T, 2><<<grid, 256, 0, s>>>(a);
+}
+
+cudaError_t launch_prob(int precision, const PassArgs& a, int grid, cudaStream_t s) {
+  if (a.w != 2 && a.w != 4) return cudaErrorInvalidValue;
+  if (precision == QEC_C128) prob_t<double>(a, grid, s);
+  else prob_t<float>(a, grid, s);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_apply(int precision, const PassArgs& a, int grid, cudaStream_t s) {
+  if (a.w != 2 && a.w != 4) return cudaErrorInvalidValue;
+  if (precision == QEC_C128) apply_t<double>(a, grid, s);
+  else apply_t<float>(a, grid, s);
+  return cudaGetLastError();
+}
+
+static size_t sample_smem(int D) {
+  const int k1 = hist_k1(D);
+  const size_t B = (size_t)1 << k1, H = D > k1 ? ((size_t)1 << (D - k1)) : 0;
+  return sizeof(double) * (B > H ? B : H);
+}
+
+cudaError_t setup_kernels(int precision, int D) {
+  const int smem = (int)sample_smem(D);
+  if (precision == QEC_C128)
+    return cudaFuncSetAttribute(k_sample<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  return cudaFuncSetAttribute(k_sample<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+
+cudaError_t launch_readout(int precision, const ReadArgs& a, cudaStream_t s) {
+  const int B = 1 << a.k1;
+  const size_t smem = sample_smem(a.D);
+  if (precision == QEC_C128) {
+    k_hist<double><<<a.grid_hist, 256, 0, s>>>(a);
+    k_hist_reduce<<<(B + 255) / 256, 256, 0, s>>>(a);
+    k_sample<double><<<1, 256, smem, s>>>(a);
+  } else {
+    k_hist<float><<<a.grid_hist, 256, 0, s>>>(a);
+    k_hist_reduce<<<(B + 255) / 256, 256, 0, s>>>(a);
+    k_sample<float><<<1, 256, smem, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_basis0(int precision, void* psi, int D, cudaStream_t s) {
+  const int64_t n = 1ll << D;
+  int grid = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+  if (precision == QEC_C128) k_set_basis0<double><<<grid, 256, 0, s>>>(psi, n);
+  else k_set_basis0<float><<<grid, 256, 0, s>>>(psi, n);
+  return cudaGetLastError();
+}
+
+// ---- host instantiation (test hook; same op arithmetic as inst_block) -------------------
+void instantiate_block_host(const InstArgs& a, int blk, uint64_t seed, uint64_t traj,
+                            double2* k0, double2* k1, double* u) {
+  const int k = blk % a.nstab;
+  const int rnd = a.round_base + blk / a.nstab;
+  const BlockInfo bi = a.blocks[k];
+  const int w = bi.w, C = 1 << w;
+  const double (*sm)[16][2] = reinterpret_cast<const double (*)[16][2]>(a.mats);
+  double2 U[32 * 16];
+  for (int i = 0; i < 32 * 16; ++i) {
+    int r = i / 16, c = i % 16;
+    U[i] = make_double2((r < C && r == c) ? 1.0 : 0.0, 0.0);
+  }
+  for (int oi = bi.op_begin; oi < bi.op_end; ++oi) {
+    const ProgOp op = a.ops[oi];
+    if (op.kind == OP_N1 || op.kind == OP_N2) {
+      const int code = noise_code(op, a.prob[op.pidx], seed, traj, rnd);
+      if (!code) continue;
+      if (op.kind == OP_N1) {
+        for (int it = 0; it < items_1q(w); ++it) apply1_item(U, w, op.q0, sm[code], it);
+      } else {
+        const int pa = code >> 2, pd = code & 3;
+        if (pa) for (int it = 0; it < items_1q(w); ++it) apply1_item(U, w, op.q0, sm[pa], it);
+        if (pd) for (int it = 0; it < items_1q(w); ++it) apply1_item(U, w, op.q1, sm[pd], it);
+      }
+    } else if (op.kind == OP_U1) {
+      for (int it = 0; it < items_1q(w); ++it) apply1_item(U, w, op.q0, sm[op.mat], it);
+    } else {
+      for (int it = 0; it < items_2q(w); ++it) apply2_item(U, w, op.q0, op.q1, sm[op.mat], it);
+    }
+  }
+  for (int i = 0; i < 256; ++i) {
+    const int r = i / 16, c = i % 16;
+    k0[i] = (r < C && c < C) ? U[r * 16 + c] : make_double2(0, 0);
+    k1[i] = (r < C && c < C) ? U[(C + r) * 16 + c] : make_double2(0, 0);
+  }
+  *u = uniform53(draw(seed, traj, (uint64_t)rnd, 0u, (uint32_t)(a.nd + k), TAG_MEASURE).v[0]);
+}
+
+}  // namespace qec

@@ -1,0 +1,88 @@
+// Launch interface of the trajectory kernels (kernels.cu).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "program.hpp"
+
+namespace qec {
+
+// Device control block of one simulator.
+struct Ctl {
+  unsigned long long seed;
+  unsigned long long first;     // first trajectory index of the current call
+  unsigned long long traj;      // trajectory being simulated (advanced by the readout)
+  unsigned int ticket;          // last-CTA ticket of the reductions (always returned to 0)
+  unsigned int n_events;
+  unsigned int ev_cap;
+  unsigned int pad;
+  double final_norm;            // sum |psi|^2 of the state the readout sampled
+};
+
+constexpr int KRAUS_STRIDE = 768;   // per block: K0, K1, M = K1^dagger K1, 16x16 each
+constexpr int MAX_PASS_GRID = 2048;
+
+struct InstArgs {
+  const ProgOp* ops;
+  const BlockInfo* blocks;
+  const double* mats;     // [M_COUNT][16][2]
+  double prob[3];
+  int nstab, nd;
+  int round_base;         // round of block 0 of this launch
+  int nblk;               // blocks in this launch (nstab x rounds)
+  void* kraus;            // [nblk][KRAUS_STRIDE] complex (T2)
+  double* u;              // [nblk] measurement uniforms
+  Ctl* ctl;               // seed / trajectory source; nullptr = trajectory 0, seed 0 (init round)
+  int32_t* events;        // [ev_cap][5] (traj, round, step, site, code) or nullptr
+};
+
+struct PassArgs {
+  const void* src;
+  void* dst;
+  int D;                  // data-register qubits (2^D amplitudes)
+  int w;                  // 2 or 4
+  int q[4];               // data bits of the block, ascending
+  const void* kraus;      // this block's KRAUS_STRIDE entries
+  const double* u;        // this block's measurement uniform
+  int forced;             // -1: sample; else forced raw outcome
+  double* A;              // this block's <psi|K1^dag K1|psi>
+  double* N;              // this block's <psi|psi>
+  int* m;                 // this block's raw outcome
+  Ctl* ctl;
+  double* partials;       // [MAX_PASS_GRID][2]
+  uint8_t* syn;           // syndrome output (nullptr = none)
+  int syn_stride;         // bytes per trajectory
+  int syn_idx;            // round * nstab + stab
+  int offset;             // syndrome = raw ^ offset
+};
+
+struct ReadArgs {
+  const void* src;
+  int D, k1, d;
+  int rounds;
+  int grid_hist;
+  double* hist_part;      // [grid_hist][2^k1]
+  double* hist;           // [2^k1]
+  Ctl* ctl;
+  uint8_t* bits;          // [traj][d^2]
+  uint8_t* logical;       // [traj]
+  uint8_t* syn;           // [traj][syn_stride]; round-0 row zeroed here
+  int syn_stride;
+  int nstab;
+};
+
+cudaError_t launch_instantiate(int precision, const InstArgs& a, cudaStream_t s);
+cudaError_t launch_prob(int precision, const PassArgs& a, int grid, cudaStream_t s);
+cudaError_t launch_apply(int precision, const PassArgs& a, int grid, cudaStream_t s);
+cudaError_t launch_readout(int precision, const ReadArgs& a, cudaStream_t s);
+cudaError_t launch_set_basis0(int precision, void* psi, int D, cudaStream_t s);
+cudaError_t setup_kernels(int precision, int D);   // once per process/device, before any capture
+int pass_grid(int D, int w, int num_sms);
+int hist_k1(int D);
+int hist_grid(int D, int num_sms);
+
+// Host version of the per-block instantiation (same arithmetic as the device kernel).
+void instantiate_block_host(const InstArgs& a, int blk, uint64_t seed, uint64_t traj,
+                            double2* k0, double2* k1, double* u);
+
+}  // namespace qec

@@ -1,0 +1,263 @@
+// Builds the static per-round block program (see program.hpp).
+#include "program.hpp"
+
+#include <algorithm>
+#include <cmath>
+#include <tuple>
+
+namespace qec {
+
+namespace {
+
+// Plaquette with top-left grid cell (r, c); X-type iff r + c odd (Table I, Fig. 1a).
+struct Plaq { int r, c; char kind; };
+
+int cell(int d, int r, int c) { return (r >= 0 && r < d && c >= 0 && c < d) ? r * d + c : -1; }
+
+void set_mat(double m[16][2], int idx, double re, double im) { m[idx][0] = re; m[idx][1] = im; }
+
+void mat1(double m[16][2], double a_re, double a_im, double b_re, double b_im,
+          double c_re, double c_im, double d_re, double d_im) {
+  for (int i = 0; i < 16; ++i) m[i][0] = m[i][1] = 0.0;
+  set_mat(m, 0, a_re, a_im); set_mat(m, 1, b_re, b_im);
+  set_mat(m, 4, c_re, c_im); set_mat(m, 5, d_re, d_im);
+}
+
+// exp(-i theta/2 P) for P in {X, Z} on one qubit
+void rot1(double m[16][2], char P, double theta) {
+  double c = std::cos(theta / 2), s = std::sin(theta / 2);
+  if (P == 'X') mat1(m, c, 0, 0, -s, 0, -s, c, 0);
+  else mat1(m, c, -s, 0, 0, 0, 0, c, s);
+}
+
+// exp(-i theta/2 Z(x)X), local index 2*a + b (a: Z side, b: X side)
+void rot_zx(double m[16][2], double theta) {
+  double c = std::cos(theta / 2), s = std::sin(theta / 2);
+  for (int i = 0; i < 16; ++i) m[i][0] = m[i][1] = 0.0;
+  for (int r = 0; r < 4; ++r) {
+    set_mat(m, 5 * r, c, 0);
+    int a = r >> 1, b = r & 1;
+    int col = (a << 1) | (b ^ 1);             // X flips b
+    double sign = a ? -1.0 : 1.0;             // Z phase on a
+    m[4 * r + col][1] += -s * sign;
+  }
+}
+
+void fill_mats(Program& P, const qec_noise& nz, bool noisy) {
+  const double h = 1.0 / std::sqrt(2.0);
+  mat1(P.mats[M_I], 1, 0, 0, 0, 0, 0, 1, 0);
+  mat1(P.mats[M_X], 0, 0, 1, 0, 1, 0, 0, 0);
+  mat1(P.mats[M_Y], 0, 0, 0, -1, 0, 1, 0, 0);
+  mat1(P.mats[M_Z], 1, 0, 0, 0, 0, 0, -1, 0);
+  mat1(P.mats[M_H], h, 0, h, 0, h, 0, -h, 0);
+  rot1(P.mats[M_RX90], 'X', M_PI / 2);
+  rot1(P.mats[M_RX90DG], 'X', -M_PI / 2);
+  rot1(P.mats[M_RZ90], 'Z', M_PI / 2);
+  for (int i = 0; i < 16; ++i) P.mats[M_CNOT][i][0] = P.mats[M_CNOT][i][1] = 0.0;
+  P.mats[M_CNOT][0][0] = P.mats[M_CNOT][5][0] = P.mats[M_CNOT][11][0] = P.mats[M_CNOT][14][0] = 1.0;
+  rot_zx(P.mats[M_RZX90], M_PI / 2);
+  double g = noisy ? 1.0 : 0.0;
+  rot1(P.mats[M_ROT_RX], 'X', g * nz.theta_rx);
+  rot1(P.mats[M_ROT_RZ], 'Z', g * nz.theta_rz);
+  rot_zx(P.mats[M_ROT_RZX], g * nz.theta_rzx);
+  for (int i = 0; i < 16; ++i) P.mats[M_ZZ][i][0] = P.mats[M_ZZ][i][1] = 0.0;
+  for (int r = 0; r < 4; ++r) {               // exp(-i phi Z(x)Z): eigenvalue +1 on 00, 11
+    double zz = ((r >> 1) ^ (r & 1)) ? -1.0 : 1.0;
+    double ph = -g * nz.phi_zz * zz;
+    set_mat(P.mats[M_ZZ], 5 * r, std::cos(ph), std::sin(ph));
+  }
+  rot1(P.mats[M_ROUND_RZ], 'Z', g * nz.round_rz);
+  rot1(P.mats[M_ROUND_RX], 'X', g * nz.round_rx);
+}
+
+bool finite_in(double v, double lo, double hi) { return std::isfinite(v) && v >= lo && v <= hi; }
+
+}  // namespace
+
+std::vector<Stab> make_stabilizers(int d) {
+  std::vector<std::tuple<int, int, Stab>> xs, zs;
+  for (int r = -1; r < d; ++r) {
+    for (int c = -1; c < d; ++c) {
+      int tl = cell(d, r, c), tr = cell(d, r, c + 1), bl = cell(d, r + 1, c), br = cell(d, r + 1, c + 1);
+      int w = (tl >= 0) + (tr >= 0) + (bl >= 0) + (br >= 0);
+      char kind = ((r + c) & 1) ? 'X' : 'Z';
+      bool top_bottom = (r == -1 || r == d - 1), left_right = (c == -1 || c == d - 1);
+      bool keep = (w == 4) || (w == 2 && kind == 'X' && top_bottom && !left_right) ||
+                  (w == 2 && kind == 'Z' && left_right && !top_bottom);
+      if (!keep) continue;
+      Stab s;
+      s.kind = kind;
+      s.w = w;
+      if (kind == 'X') {  // clockwise from bottom-right
+        int sl[4] = {br, bl, tl, tr};
+        std::copy(sl, sl + 4, s.slots);
+        xs.emplace_back(r, c, s);
+      } else {            // clockwise from top-right
+        int sl[4] = {tr, br, bl, tl};
+        std::copy(sl, sl + 4, s.slots);
+        zs.emplace_back(c, -r, s);
+      }
+    }
+  }
+  auto key_less = [](const std::tuple<int, int, Stab>& a, const std::tuple<int, int, Stab>& b) {
+    return std::make_pair(std::get<0>(a), std::get<1>(a)) < std::make_pair(std::get<0>(b), std::get<1>(b));
+  };
+  std::sort(xs.begin(), xs.end(), key_less);
+  std::sort(zs.begin(), zs.end(), key_less);
+  std::vector<Stab> out;
+  for (auto& t : xs) out.push_back(std::get<2>(t));
+  for (auto& t : zs) out.push_back(std::get<2>(t));
+  return out;
+}
+
+bool validate_params(const qec_params& p, std::string& err) {
+  if (p.d < 3 || p.d > 5 || (p.d % 2) == 0) { err = "d must be 3 or 5"; return false; }
+  if (p.rounds < 0 || p.rounds > 64) { err = "rounds must be in [0, 64]"; return false; }
+  if (p.layout != QEC_LAYOUT_REDUCED && p.layout != QEC_LAYOUT_UNREDUCED) { err = "bad layout"; return false; }
+  if (p.gates != QEC_GATES_CNOT && p.gates != QEC_GATES_CR) { err = "bad gate set"; return false; }
+  if (p.precision != QEC_C128 && p.precision != QEC_C64) { err = "bad precision"; return false; }
+  if (p.reserved != 0) { err = "reserved must be 0"; return false; }
+  const qec_noise& n = p.noise;
+  if (!finite_in(n.p1, 0, 1) || !finite_in(n.p2, 0, 1) || !finite_in(n.p_idle, 0, 1)) {
+    err = "noise probabilities must be in [0, 1]";
+    return false;
+  }
+  const double a[6] = {n.theta_rx, n.theta_rz, n.theta_rzx, n.phi_zz, n.round_rz, n.round_rx};
+  for (double v : a) {
+    if (!finite_in(v, -4.0, 4.0)) { err = "angles must be finite with |angle| <= 4"; return false; }
+  }
+  return true;
+}
+
+bool build_program(const qec_params& p, bool noisy, Program& P, std::string& err) {
+  if (!validate_params(p, err)) return false;
+  const int d = p.d, nd = d * d;
+  const bool cr = p.gates == QEC_GATES_CR;
+  const qec_noise& nz = p.noise;
+  std::vector<Stab> S = make_stabilizers(d);
+  P = Program();
+  P.d = d;
+  P.nd = nd;
+  P.nstab = (int)S.size();
+  fill_mats(P, nz, noisy);
+  P.prob[PR_P1] = noisy ? nz.p1 : 0.0;
+  P.prob[PR_P2] = noisy ? nz.p2 : 0.0;
+  P.prob[PR_IDLE] = noisy ? nz.p_idle : 0.0;
+
+  // Gate steps of each data qubit, in serial (block) order.
+  std::vector<int> nx(nd, 0), nzc(nd, 0);
+  std::vector<std::vector<std::pair<int, int>>> gates_of(nd);   // (step, block)
+  for (int k = 0; k < P.nstab; ++k) {
+    for (int i = 0; i < 4; ++i) {
+      int q = S[k].slots[i];
+      if (q < 0) continue;
+      (S[k].kind == 'X' ? nx : nzc)[q]++;
+      gates_of[q].push_back({S[k].kind == 'X' ? 2 + i : 7 + i, k});
+    }
+  }
+  for (int q = 0; q < nd; ++q) {
+    for (size_t i = 1; i < gates_of[q].size(); ++i) {
+      if (gates_of[q][i].first <= gates_of[q][i - 1].first) {
+        err = "serial order does not respect a data qubit's gate order";
+        return false;
+      }
+    }
+  }
+  // Single-qubit events of each data qubit: steps 0..11 without a gate on it.
+  // Each goes to the block of the next gate on that qubit (pre) or, after the
+  // last gate of the round, to the block of the last gate (post).
+  std::vector<std::vector<std::pair<int, int>>> pre(P.nstab), post(P.nstab);   // (data qubit, step)
+  for (int q = 0; q < nd; ++q) {
+    const auto& g = gates_of[q];
+    for (int t = 0; t <= 11; ++t) {
+      bool busy = false;
+      for (auto& e : g) busy |= (e.first == t);
+      if (busy) continue;
+      int blk = -1;
+      for (auto& e : g) {
+        if (e.first > t) { blk = e.second; break; }
+      }
+      if (blk >= 0) pre[blk].push_back({q, t});
+      else post[g.back().second].push_back({q, t});
+    }
+  }
+
+  for (int k = 0; k < P.nstab; ++k) {
+    const Stab& s = S[k];
+    BlockInfo bi;
+    bi.op_begin = (int)P.ops.size();
+    bi.w = s.w;
+    std::vector<int> qs;
+    for (int i = 0; i < 4; ++i) if (s.slots[i] >= 0) qs.push_back(s.slots[i]);
+    std::sort(qs.begin(), qs.end());
+    for (int i = 0; i < 4; ++i) bi.q[i] = i < (int)qs.size() ? qs[i] : -1;
+    bi.offset = (cr && s.w == 2) ? 1 : 0;
+    bi.stab = k;
+    const uint8_t anc = (uint8_t)s.w;
+    const uint32_t site_a = (uint32_t)(nd + k);
+    auto local = [&](int q) { return (uint8_t)(std::find(qs.begin(), qs.end(), q) - qs.begin()); };
+    auto u1 = [&](uint8_t q, uint16_t m) { P.ops.push_back({OP_U1, q, 0, 0, m, 0, 0}); };
+    auto u2 = [&](uint8_t a, uint8_t b, uint16_t m) { P.ops.push_back({OP_U2, a, b, 0, m, 0, 0}); };
+    auto n1 = [&](uint8_t q, int step, uint32_t site, uint8_t pid) {
+      if (P.prob[pid] > 0.0) P.ops.push_back({OP_N1, q, 0, pid, 0, (uint16_t)step, site});
+    };
+    auto n2 = [&](uint8_t a, uint8_t b, int step, uint32_t site) {
+      if (P.prob[PR_P2] > 0.0) P.ops.push_back({OP_N2, a, b, PR_P2, 0, (uint16_t)step, site});
+    };
+    auto data_event = [&](int q, int t) {
+      uint8_t lq = local(q);
+      if (t == 0) {
+        if (noisy && nz.round_rz != 0.0) u1(lq, M_ROUND_RZ);
+        if (noisy && nz.round_rx != 0.0) u1(lq, M_ROUND_RX);
+      } else if (cr && (t == 6 || t == 11)) {
+        int nfac = t == 6 ? nx[q] : nzc[q];
+        for (int f = 0; f < nfac; ++f) {
+          u1(lq, t == 6 ? M_RX90 : M_RZ90);
+          if (noisy && (t == 6 ? nz.theta_rx : nz.theta_rz) != 0.0) u1(lq, t == 6 ? M_ROT_RX : M_ROT_RZ);
+        }
+        n1(lq, t, (uint32_t)q, PR_P1);
+      } else {
+        n1(lq, t, (uint32_t)q, PR_IDLE);
+      }
+    };
+    for (auto& e : pre[k]) data_event(e.first, e.second);
+    const int t0 = s.kind == 'X' ? 1 : 7, t1 = s.kind == 'X' ? 6 : 11;
+    for (int t = t0; t <= t1; ++t) {
+      if (s.kind == 'X' && (t == 1 || t == 6)) {
+        if (!cr) {
+          u1(anc, M_H);
+        } else {
+          u1(anc, t == 1 ? M_RX90DG : M_RX90);
+          if (noisy && nz.theta_rx != 0.0) u1(anc, M_ROT_RX);
+        }
+        n1(anc, t, site_a, PR_P1);
+        continue;
+      }
+      if (s.kind == 'Z' && t == 11) {
+        n1(anc, t, site_a, PR_IDLE);
+        continue;
+      }
+      int q = s.slots[s.kind == 'X' ? t - 2 : t - 7];
+      if (q < 0) {
+        n1(anc, t, site_a, PR_IDLE);
+        continue;
+      }
+      uint8_t lq = local(q);
+      uint8_t first = s.kind == 'X' ? anc : lq, second = s.kind == 'X' ? lq : anc;
+      if (!cr) {
+        u2(first, second, M_CNOT);
+      } else {
+        u2(first, second, M_RZX90);
+        if (noisy && nz.theta_rzx != 0.0) u2(first, second, M_ROT_RZX);
+      }
+      if (noisy && nz.phi_zz != 0.0) u2(first, second, M_ZZ);
+      n2(anc, lq, t, (uint32_t)q);
+    }
+    for (auto& e : post[k]) data_event(e.first, e.second);
+    bi.op_end = (int)P.ops.size();
+    P.blocks.push_back(bi);
+  }
+  return true;
+}
+
+}  // namespace qec

@@ -1,0 +1,65 @@
+// Static per-round circuit program of the delayed-measurement register.
+//
+// One round of syndrome extraction (X part, steps 1-6, then Z part, steps
+// 7-11; Sec. II.A, Sec. III.A/D) becomes d^2-1 blocks, one per stabilizer in
+// serial order (Table I order, X then Z; Sec. II.B).  A block holds every op
+// on its ancilla and on its <= 4 data qubits that falls between those data
+// qubits' neighbouring gates, so the delayed, one-ancilla order reproduces
+// each qubit's own time order.  Noise sites are placeholders here; the device
+// draws them per trajectory and fuses each block into two Kraus matrices.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/qecsv.h"
+
+namespace qec {
+
+enum OpKind : uint8_t { OP_U1 = 0, OP_U2 = 1, OP_N1 = 2, OP_N2 = 3 };
+enum ProbId : uint8_t { PR_P1 = 0, PR_P2 = 1, PR_IDLE = 2 };
+
+// Local qubits of a block: data j = 0..w-1 (ascending global bit), ancilla = w.
+struct ProgOp {
+  uint8_t kind;   // OpKind
+  uint8_t q0;     // U1/N1: qubit; U2: first-listed (control side); N2: ancilla
+  uint8_t q1;     // U2: second-listed (target side); N2: data qubit
+  uint8_t pidx;   // N1/N2: ProbId
+  uint16_t mat;   // U1/U2: matrix id
+  uint16_t step;  // N1/N2: circuit step 1..11 (0 = round start)
+  uint32_t site;  // N1/N2: physical site (data 0..d^2-1, ancilla of stabilizer k: d^2+k)
+};
+
+struct BlockInfo {
+  int32_t op_begin, op_end;
+  int32_t w;        // number of data qubits (2 or 4)
+  int32_t q[4];     // global data bits, ascending; unused entries -1
+  int32_t offset;   // syndrome bit = raw ancilla bit ^ offset
+  int32_t stab;     // stabilizer index in serial order
+};
+
+enum MatId : uint16_t {
+  M_I = 0, M_X, M_Y, M_Z, M_H, M_RX90, M_RX90DG, M_RZ90, M_CNOT, M_RZX90,
+  M_ROT_RX, M_ROT_RZ, M_ROT_RZX, M_ZZ, M_ROUND_RZ, M_ROUND_RX, M_COUNT
+};
+
+struct Program {
+  int d = 0, nd = 0, nstab = 0;
+  std::vector<ProgOp> ops;
+  std::vector<BlockInfo> blocks;    // nstab blocks, serial order
+  double mats[M_COUNT][16][2];      // 4x4 complex row-major; one-qubit gates in the top-left 2x2
+  double prob[3];                   // p1, p2, p_idle (0 in the init program)
+};
+
+struct Stab {
+  char kind;        // 'X' or 'Z'
+  int slots[4];     // data qubit per gate slot in gate order, -1 = wait
+  int w;
+};
+
+std::vector<Stab> make_stabilizers(int d);
+bool validate_params(const qec_params& p, std::string& err);
+// noisy = false: the noise-free init round (no noise sites, no coherent terms).
+bool build_program(const qec_params& p, bool noisy, Program& out, std::string& err);
+
+}  // namespace qec

@@ -1,0 +1,64 @@
+"""Numpy application of the library's host-instantiated Kraus blocks (CPU check of the compile path).
+
+Takes the blocks produced by qec_debug_blocks (the same fusion arithmetic the
+device kernel runs) and applies them with plain numpy to a dense data
+register, so the schedule, op assignment and fusion can be compared with the
+oracle on the CPU.  It does not exercise the GPU kernels.
+"""
+import ctypes
+
+import numpy as np
+
+from paper_2204_11404_gb300 import capi
+
+
+def blocks(params, seed, traj, rnd):
+    d = params.d
+    nst = d * d - 1
+    kr = np.zeros((nst, 2, 16, 16), dtype=np.complex128)
+    u = np.zeros(nst, dtype=np.float64)
+    capi.qec_debug_blocks(params, seed, traj, rnd, kr.ctypes.data, u.ctypes.data)
+    return kr, u
+
+
+def block_meta(params):
+    nst = params.d * params.d - 1
+    ops = np.zeros((4096, 6), dtype=np.int32)
+    info = np.zeros((nst, 6), dtype=np.int32)
+    capi.qec_debug_program(params, ops.ctypes.data, 4096, info.ctypes.data, nst)
+    return info
+
+
+def apply_block(psi, D, qs, K):
+    w = len(qs)
+    t = psi.reshape([2] * D)
+    axes = [D - 1 - q for q in reversed(qs)]
+    t = np.moveaxis(t, axes, list(range(D - w, D)))
+    shp = t.shape
+    g = t.reshape(-1, 1 << w) @ K.T
+    t = np.moveaxis(g.reshape(shp), list(range(D - w, D)), axes)
+    return np.ascontiguousarray(t).reshape(-1)
+
+
+def run(params, seed, traj):
+    d, R = params.d, params.rounds
+    D = d * d
+    nst = D - 1
+    info = block_meta(params)
+    psi = np.zeros(1 << D, dtype=np.complex128)
+    psi[0] = 1.0
+    syn = np.zeros((R + 1, nst), dtype=np.uint8)
+    for rnd in range(R + 1):
+        kr, u = blocks(params, seed, traj, rnd)
+        for k in range(nst):
+            w, offset = info[k, 0], info[k, 5]
+            qs = [int(x) for x in info[k, 1:1 + w]]
+            C = 1 << w
+            K0, K1 = kr[k, 0, :C, :C], kr[k, 1, :C, :C]
+            N = np.vdot(psi, psi).real
+            A = np.vdot(apply_block(psi, D, qs, K1), apply_block(psi, D, qs, K1)).real
+            m = offset if rnd == 0 else int(u[k] < A / N)
+            psi = apply_block(psi, D, qs, K1 if m else K0) / np.sqrt(N)
+            syn[rnd, k] = m ^ offset
+    psi = psi / np.linalg.norm(psi)
+    return syn, psi

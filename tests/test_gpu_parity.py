@@ -1,0 +1,144 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the same seeded inputs.
+
+Sampled Pauli errors, syndromes and final data bits are compared bit for bit
+(subject to the near-threshold rule in parity_util); amplitudes after the last
+round within 1e-12 (complex128) and 2e-5 (complex64) max-abs.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import run_trajectory
+from parity_util import AMP_TOL, TAU, compare_trajectory
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2204_11404_gb300.simulator import Simulator  # noqa: E402
+
+
+def oracle_traj(d, rounds, gates, noise, seed, traj, want_state=False):
+    return run_trajectory(d, rounds, gates, "reduced", noise, seed=seed, traj=traj, want_state=want_state)
+
+
+def check_batch(sim, d, rounds, gates, noise, seed, first, n, prec, oracle_idx=None):
+    syn, bits, log = sim.run(seed, first, n)
+    idx = range(n) if oracle_idx is None else oracle_idx
+    kinds = []
+    for i in idx:
+        o = oracle_traj(d, rounds, gates, noise, seed, first + i)
+        kinds.append(compare_trajectory(syn[i], bits[i], o, TAU[prec]))
+        if kinds[-1] == "exact":
+            assert log[i] == o["raw_logical"]
+    return kinds
+
+
+def test_d3_cnot_workload_matches_oracle():
+    w = W.D3_CNOT
+    with Simulator(w["d"], w["rounds"], w["gates"], "c128", **w["noise"]) as sim:
+        kinds = check_batch(sim, w["d"], w["rounds"], w["gates"], w["noise"], w["seed"], 0, 200, "c128")
+    assert kinds.count("exact") == len(kinds)
+
+
+@pytest.mark.parametrize("gates", ["cnot", "cr"])
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+def test_d3_stress_matches_oracle(gates, prec):
+    nz = W.STRESS
+    with Simulator(3, 3, gates, prec, **nz) as sim:
+        kinds = check_batch(sim, 3, 3, gates, nz, 31, 0, 60, prec)
+        assert kinds.count("ambiguous") <= (0 if prec == "c128" else 2)
+        sim.record_events(4096)
+        for traj in (3, 7, 11):
+            syn, bits, log = sim.run(31, traj, 1)
+            o = oracle_traj(3, 3, gates, nz, 31, traj, want_state=True)
+            if compare_trajectory(syn[0], bits[0], o, TAU[prec]) != "exact":
+                continue
+            ref = o["state"][: 1 << 9]
+            assert np.abs(sim.state() - ref).max() < AMP_TOL[prec]
+            ev = sorted(tuple(int(x) for x in e[1:]) for e in sim.events())
+            assert all(int(e[0]) == traj for e in sim.events())
+            assert ev == sorted(o["events"])
+
+
+def test_offsets_chunking_and_device_outputs():
+    nz = W.STRESS
+    n = 1100   # more than one internal batch
+    with Simulator(3, 2, "cr", "c128", **nz) as sim:
+        syn, bits, log = sim.run(5, 0, n)
+        syn_a, bits_a, log_a = sim.run(5, 0, 600)
+        syn_b, bits_b, log_b = sim.run(5, 600, n - 600)
+        assert (np.concatenate([syn_a, syn_b]) == syn).all()
+        assert (np.concatenate([bits_a, bits_b]) == bits).all()
+        assert (np.concatenate([log_a, log_b]) == log).all()
+        d_syn = torch.zeros((n, 3, 8), dtype=torch.uint8, device="cuda")
+        d_bits = torch.zeros((n, 9), dtype=torch.uint8, device="cuda")
+        d_log = torch.zeros((n,), dtype=torch.uint8, device="cuda")
+        sim.run_device(5, 0, n, d_syn.data_ptr(), d_bits.data_ptr(), d_log.data_ptr())
+        torch.cuda.synchronize()
+        assert (d_syn.cpu().numpy() == syn).all()
+        assert (d_bits.cpu().numpy() == bits).all()
+        assert (d_log.cpu().numpy() == log).all()
+        for i in (0, 599, 600, 1023, 1024, 1099):
+            o = oracle_traj(3, 2, "cr", nz, 5, i)
+            assert compare_trajectory(syn[i], bits[i], o, TAU["c128"]) == "exact"
+        syn0, _, _ = sim.run(5, 0, 0)
+        assert syn0.shape == (0, 3, 8)
+
+
+@pytest.mark.parametrize("gates", ["cnot", "cr"])
+def test_zero_rounds_samples_init_state(gates):
+    with Simulator(3, 0, gates, "c128", **W.STRESS) as sim:
+        syn, bits, log = sim.run(2, 0, 40)
+        assert not syn.any()
+        for i in range(40):
+            o = oracle_traj(3, 0, gates, W.STRESS, 2, i)
+            assert (bits[i] == o["data_bits"]).all() and log[i] == o["raw_logical"] == 0
+
+
+def test_d5_noiseless_properties():
+    with Simulator(5, 2, "cr", "c128") as sim:
+        syn, bits, log = sim.run(0, 0, 2)
+        assert not syn.any() and not log.any()
+        psi = sim.state()
+        assert abs(np.vdot(psi, psi).real - 1) < 1e-12
+        # the code state has 2^12 equal-magnitude amplitudes (X-stabilizer orbit of a basis state)
+        mags = np.abs(psi[np.abs(psi) > 1e-9])
+        assert mags.size == 4096 and np.allclose(mags, 1 / 64, atol=1e-12)
+
+
+_D5 = {}
+
+
+def _d5_oracle():
+    if "o" not in _D5:
+        pt = W.D5_CR["points"][-1]          # p = 5e-3, theta_rx = 0.05, phi_zz = 0.02
+        seed = W.D5_CR["seed_base"] + len(W.D5_CR["points"]) - 1
+        _D5["o"] = (pt, seed, oracle_traj(5, 5, "cr", pt, seed, 0, want_state=True))
+    return _D5["o"]
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+def test_d5_full_size_trajectory_matches_oracle(prec):
+    pt, seed, o = _d5_oracle()
+    with Simulator(5, 5, "cr", prec, **pt) as sim:
+        sim.record_events(1 << 16)
+        syn, bits, log = sim.run(seed, 0, 1)
+        kind = compare_trajectory(syn[0], bits[0], o, TAU[prec])
+        if prec == "c128":
+            assert kind == "exact"
+        if kind == "exact":
+            ref = o["state"][: 1 << 25]
+            assert np.abs(o["state"][1 << 25:]).max() == 0
+            assert np.abs(sim.state() - ref).max() < AMP_TOL[prec]
+            ev = sorted(tuple(int(x) for x in e[1:]) for e in sim.events())
+            assert ev == sorted(o["events"])
+        ms_prob, ms_apply, blk = sim_kernel_times(sim)
+        assert ms_prob > 0 and ms_apply > 0 and blk >= 0
+
+
+def sim_kernel_times(sim):
+    from paper_2204_11404_gb300 import capi
+    return capi.qec_kernel_times(sim.h)

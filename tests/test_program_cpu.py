@@ -1,0 +1,52 @@
+"""CPU checks of the library's host side: exported symbols, the static program, and the
+host-instantiated Kraus blocks against the oracle (no GPU needed)."""
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+from oracle import run_trajectory
+from paper_2204_11404_gb300 import capi
+from kraus_ref import run as kraus_run
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_library_exports_every_declared_symbol():
+    hdr = open(os.path.join(ROOT, "include", "qecsv.h")).read()
+    declared = set(re.findall(r"^\s*(?:qec_status|uint64_t|const char\*)\s+(qec_\w+)\s*\(", hdr, re.M))
+    assert len(declared) >= 10
+    out = subprocess.check_output(["nm", "-D", "--defined-only", capi.lib()._name]).decode()
+    exported = set(re.findall(r" T (qec_\w+)", out))
+    assert declared <= exported, declared - exported
+    for name in declared:
+        getattr(capi.lib(), name)
+
+
+NOISY = dict(p1=0.03, p2=0.03, p_idle=0.02, theta_rx=0.1, theta_rz=0.07, theta_rzx=0.05,
+             phi_zz=0.08, round_rz=0.1, round_rx=0.05)
+
+
+@pytest.mark.parametrize("gates", ["cnot", "cr"])
+def test_host_blocks_match_oracle_d3(gates):
+    params = capi.make_params(3, 3, gates, **NOISY)
+    for traj in range(6):
+        syn, psi = kraus_run(params, 17, traj)
+        o = run_trajectory(3, 3, gates, "reduced", NOISY, seed=17, traj=traj, want_state=True)
+        assert (syn == o["syndromes"]).all()
+        ref = o["state"][: 1 << 9]
+        assert np.abs(o["state"][1 << 9:]).max() == 0
+        assert np.abs(psi - ref).max() < 1e-13
+
+
+def test_invalid_params_rejected():
+    bad = capi.make_params(4, 3)
+    n = np.zeros(8, dtype=np.int32)
+    with pytest.raises(capi.QecError) as e:
+        capi.qec_debug_program(bad, n.ctypes.data, 0, n.ctypes.data, 0)
+    assert e.value.status == capi.QEC_EINVAL
+    p = capi.make_params(3, 3, p1=1.5)
+    with pytest.raises(capi.QecError):
+        capi.qec_debug_program(p, n.ctypes.data, 0, n.ctypes.data, 0)

@@ -70,8 +70,11 @@ struct qec_sim {
   uint8_t* d_log = nullptr;
   int32_t* d_events = nullptr;
   uint32_t ev_cap = 0;
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t gexec = nullptr;
+  // The trajectory runs as graph[0] (instantiate + blocks before the timed block), the timed
+  // block's two passes launched directly between timing events, then graph[1] (the rest).
+  // Without a timed block (no noisy round) graph[0] holds everything.
+  cudaGraph_t graph[2] = {nullptr, nullptr};
+  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
   bool ran = false;
 
   int syn_stride() const { return (R + 1) * nstab; }
@@ -153,20 +156,23 @@ qec_status run_init_round(qec_sim* s) {
   return QEC_OK;
 }
 
-qec_status enqueue_trajectory(qec_sim* s) {
-  if (s->S > 0) QEC_CUDA(launch_instantiate(s->p.precision, inst_args(s, 1, 1, s->S, true), s->work));
-  for (int b = 0; b < s->S; ++b) {
-    const void* src = b == 0 ? s->psi0 : s->psi;
-    const int rnd = 1 + b / s->nstab, k = b % s->nstab;
-    PassArgs a = pass_args(s, s->prog, b, src, s->psi, false, s->d_syn, rnd * s->nstab + k);
+PassArgs traj_pass(const qec_sim* s, int b) {
+  const void* src = b == 0 ? s->psi0 : s->psi;
+  const int rnd = 1 + b / s->nstab, k = b % s->nstab;
+  return pass_args(s, s->prog, b, src, s->psi, false, s->d_syn, rnd * s->nstab + k);
+}
+
+qec_status enqueue_blocks(qec_sim* s, int b0, int b1) {
+  for (int b = b0; b < b1; ++b) {
+    PassArgs a = traj_pass(s, b);
     const int grid = pass_grid(s->D, a.w, s->num_sms);
-    const bool timed = b == s->timed_block;
-    if (timed) QEC_CUDA(cudaEventRecord(s->kev[0], s->work));
     QEC_CUDA(launch_prob(s->p.precision, a, grid, s->work));
-    if (timed) QEC_CUDA(cudaEventRecord(s->kev[1], s->work));
     QEC_CUDA(launch_apply(s->p.precision, a, grid, s->work));
-    if (timed) QEC_CUDA(cudaEventRecord(s->kev[2], s->work));
   }
+  return QEC_OK;
+}
+
+qec_status enqueue_readout(qec_sim* s) {
   ReadArgs r;
   r.src = s->S > 0 ? s->psi : s->psi0;
   r.D = s->D;
@@ -186,10 +192,24 @@ qec_status enqueue_trajectory(qec_sim* s) {
   return QEC_OK;
 }
 
-qec_status ensure_graph(qec_sim* s) {
-  if (s->gexec) return QEC_OK;
+// Part 0: instantiate + blocks [0, timed); part 1: blocks (timed, S) + readout.
+qec_status enqueue_part(qec_sim* s, int part) {
+  const int tb = s->timed_block;
+  qec_status st = QEC_OK;
+  if (part == 0) {
+    if (s->S > 0) QEC_CUDA(launch_instantiate(s->p.precision, inst_args(s, 1, 1, s->S, true), s->work));
+    st = enqueue_blocks(s, 0, tb < 0 ? s->S : tb);
+    if (st == QEC_OK && tb < 0) st = enqueue_readout(s);
+  } else {
+    st = enqueue_blocks(s, tb + 1, s->S);
+    if (st == QEC_OK) st = enqueue_readout(s);
+  }
+  return st;
+}
+
+qec_status capture(qec_sim* s, int part) {
   QEC_CUDA(cudaStreamBeginCapture(s->work, cudaStreamCaptureModeThreadLocal));
-  qec_status st = enqueue_trajectory(s);
+  qec_status st = enqueue_part(s, part);
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamEndCapture(s->work, &g);
   if (st != QEC_OK) {
@@ -197,16 +217,39 @@ qec_status ensure_graph(qec_sim* s) {
     return st;
   }
   if (e != cudaSuccess) return fail(QEC_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
-  s->graph = g;
-  QEC_CUDA(cudaGraphInstantiate(&s->gexec, g, 0));
+  s->graph[part] = g;
+  QEC_CUDA(cudaGraphInstantiate(&s->gexec[part], g, 0));
+  return QEC_OK;
+}
+
+qec_status ensure_graph(qec_sim* s) {
+  if (s->gexec[0]) return QEC_OK;
+  qec_status st = capture(s, 0);
+  if (st == QEC_OK && s->timed_block >= 0) st = capture(s, 1);
+  return st;
+}
+
+qec_status launch_trajectory(qec_sim* s) {
+  QEC_CUDA(cudaGraphLaunch(s->gexec[0], s->work));
+  if (s->timed_block < 0) return QEC_OK;
+  PassArgs a = traj_pass(s, s->timed_block);
+  const int grid = pass_grid(s->D, a.w, s->num_sms);
+  QEC_CUDA(cudaEventRecord(s->kev[0], s->work));
+  QEC_CUDA(launch_prob(s->p.precision, a, grid, s->work));
+  QEC_CUDA(cudaEventRecord(s->kev[1], s->work));
+  QEC_CUDA(launch_apply(s->p.precision, a, grid, s->work));
+  QEC_CUDA(cudaEventRecord(s->kev[2], s->work));
+  QEC_CUDA(cudaGraphLaunch(s->gexec[1], s->work));
   return QEC_OK;
 }
 
 void drop_graph(qec_sim* s) {
-  if (s->gexec) cudaGraphExecDestroy(s->gexec);
-  if (s->graph) cudaGraphDestroy(s->graph);
-  s->gexec = nullptr;
-  s->graph = nullptr;
+  for (int i = 0; i < 2; ++i) {
+    if (s->gexec[i]) cudaGraphExecDestroy(s->gexec[i]);
+    if (s->graph[i]) cudaGraphDestroy(s->graph[i]);
+    s->gexec[i] = nullptr;
+    s->graph[i] = nullptr;
+  }
 }
 
 void free_all(qec_sim* s) {
@@ -302,7 +345,10 @@ qec_status run_impl(qec_sim* s, uint64_t seed, uint64_t first, uint32_t n, uint8
     const size_t head = done == 0 ? offsetof(Ctl, pad) : offsetof(Ctl, ticket);   // events reset per call
     if (done == 0) s->h_ctl->n_events = 0;
     QEC_CUDA(cudaMemcpyAsync(s->d_ctl, s->h_ctl, head, cudaMemcpyHostToDevice, s->work));
-    for (uint32_t t = 0; t < chunk; ++t) QEC_CUDA(cudaGraphLaunch(s->gexec, s->work));
+    for (uint32_t t = 0; t < chunk; ++t) {
+      st = launch_trajectory(s);
+      if (st) return st;
+    }
     if (syn) QEC_CUDA(cudaMemcpyAsync(syn + done * ss, s->d_syn, chunk * ss, kind, s->work));
     if (bits) QEC_CUDA(cudaMemcpyAsync(bits + done * bs, s->d_bits, chunk * bs, kind, s->work));
     if (logical) QEC_CUDA(cudaMemcpyAsync(logical + done, s->d_log, chunk, kind, s->work));

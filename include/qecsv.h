@@ -133,6 +133,32 @@ qec_status qec_get_events(qec_sim* sim, int32_t* host_events, uint32_t max_event
  */
 qec_status qec_kernel_times(qec_sim* sim, float* ms, int32_t* block);
 
+/*
+ * Trajectories without any device allocation (the paper has no counterpart;
+ * this is a deployment variant of qec_run_trajectories_device).
+ * For callers that cannot call cudaMalloc: code whose framework owns all
+ * device memory through its own pool or arena, code on a latency-critical
+ * path where cudaMalloc's implicit device synchronisation is not acceptable,
+ * or plug-ins handed only a stream and output buffers.  The caller passes the
+ * parameters, the trajectory range and DEVICE output buffers with the shapes
+ * of qec_run_trajectories (all three required when n > 0); results are
+ * identical to qec_run_trajectories for the same parameters, seed and
+ * trajectory indices.  Work is enqueued asynchronously on cuda_stream (NULL =
+ * the legacy default stream); no sim handle is involved.
+ * All device working memory (program, state vectors, Kraus blocks, reduction
+ * and readout scratch) is one static 2 MiB device array inside the library,
+ * which every GPU that loads the library holds until the process exits.  It
+ * fits d = 3 with at most 16 noisy rounds; larger requests return QEC_EINVAL.
+ * The first call on a device looks up that array's device address (once per
+ * device, with the device current); make that first call before any stream
+ * capture.  Every call reuses the same array and resets what must start from
+ * zero, so calls that overlap on the GPU (different streams, or concurrent host
+ * threads) race and corrupt each other: serialise them.
+ */
+qec_status qec_run_trajectories_noalloc(const qec_params* params, uint64_t seed, uint64_t first_traj, uint32_t n,
+                                        uint8_t* d_syndromes, uint8_t* d_data_bits, uint8_t* d_raw_logical,
+                                        void* cuda_stream);
+
 qec_status qec_destroy(qec_sim* sim);
 const char* qec_last_error(void);
 

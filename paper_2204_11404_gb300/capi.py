@@ -46,6 +46,8 @@ SIGNATURES = {
     "qec_record_events": ([_P, ctypes.c_uint32], ctypes.c_int),
     "qec_get_events": ([_P, _P, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32)], ctypes.c_int),
     "qec_kernel_times": ([_P, _P, _P], ctypes.c_int),
+    "qec_run_trajectories_noalloc": ([ctypes.POINTER(qec_params), ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32,
+                                      _P, _P, _P, _P], ctypes.c_int),
     "qec_destroy": ([_P], ctypes.c_int),
     "qec_last_error": ([], ctypes.c_char_p),
     "qec_debug_program": ([ctypes.POINTER(qec_params), _P, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32),
@@ -127,6 +129,12 @@ def qec_kernel_times(sim):
     blk = ctypes.c_int32(0)
     check(lib().qec_kernel_times(sim, ctypes.cast(ms, _P), ctypes.cast(ctypes.pointer(blk), _P)))
     return float(ms[0]), float(ms[1]), int(blk.value)
+
+
+def qec_run_trajectories_noalloc(params, seed, first_traj, n, d_syn_ptr, d_bits_ptr, d_log_ptr, cuda_stream=None):
+    """Device-allocation-free variant of qec_run_trajectories_device (d = 3, <= 16 rounds)."""
+    return check(lib().qec_run_trajectories_noalloc(ctypes.byref(params), seed, first_traj, n, d_syn_ptr, d_bits_ptr,
+                                                    d_log_ptr, cuda_stream))
 
 
 def qec_destroy(sim):

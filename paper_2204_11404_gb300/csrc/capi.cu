@@ -39,6 +39,10 @@ constexpr uint32_t kBatchCap = 1024;
 
 }  // namespace
 
+namespace qec {
+void set_last_error(const std::string& msg) { g_err = msg; }
+}  // namespace qec
+
 struct qec_sim {
   qec_params p{};
   int device = 0, num_sms = 0;

@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 #include "program.hpp"
 
 namespace qec {
@@ -80,6 +82,9 @@ cudaError_t setup_kernels(int precision, int D);   // once per process/device, b
 int pass_grid(int D, int w, int num_sms);
 int hist_k1(int D);
 int hist_grid(int D, int num_sms);
+
+// Sets the thread-local message returned by qec_last_error().
+void set_last_error(const std::string& msg);
 
 // Host version of the per-block instantiation (same arithmetic as the device kernel).
 void instantiate_block_host(const InstArgs& a, int blk, uint64_t seed, uint64_t traj,

@@ -41,6 +41,7 @@ def parse():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--precision", default="c128", choices=["c128", "c64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--points", type=int, default=9, help="noise points used (1..9); fewer = smaller device footprint")
     return ap.parse_args()
 
 
@@ -202,7 +203,7 @@ def native_arm(args, rank, world, local):
     torch.cuda.set_device(local)
     if world > 1 and not dist.is_initialized():
         dist.init_process_group("nccl")
-    pts = W.D5_CR["points"]
+    pts = W.D5_CR["points"][: max(1, min(args.points, len(W.D5_CR["points"])))]
     R = W.D5_CR["rounds"]
     sims = [Simulator(5, R, "cr", args.precision, **pt) for pt in pts]
     seeds = [W.D5_CR["seed_base"] + i for i in range(len(pts))]

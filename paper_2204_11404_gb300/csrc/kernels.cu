@@ -35,6 +35,9 @@ __device__ __forceinline__ float2 lds_v2(const float2* p) {
 }
 __device__ __forceinline__ float2 to_v2(double2 v, float*) { return make_float2((float)v.x, (float)v.y); }
 
+__device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(a, b, c); }
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -190,21 +193,27 @@ __global__ void __launch_bounds__(256) k_prob(PassArgs a) {
     T2 v[C];
 #pragma unroll
     for (int l = 0; l < C; ++l) v[l] = src[base + off[l]];
-    T sa = 0, sn = 0;
+    // <v|M|v> = sum_i M_ii |v_i|^2 + 2 Re sum_i conj(v_i) sum_{j>i} M_ij v_j  (M Hermitian);
+    // every product is an FMA into its accumulator.
+    T cross = 0, diag = 0, sn = 0;
 #pragma unroll
     for (int i = 0; i < C; ++i) {
       T tr = 0, ti = 0;
 #pragma unroll
       for (int j = i + 1; j < C; ++j) {
         const T2 m = lds_v2(&sM[i * C + j]);
-        tr += m.x * v[j].x - m.y * v[j].y;
-        ti += m.x * v[j].y + m.y * v[j].x;
+        tr = fma_t(m.x, v[j].x, tr);
+        tr = fma_t(-m.y, v[j].y, tr);
+        ti = fma_t(m.x, v[j].y, ti);
+        ti = fma_t(m.y, v[j].x, ti);
       }
-      const T nv = v[i].x * v[i].x + v[i].y * v[i].y;
-      sa += 2 * (v[i].x * tr + v[i].y * ti) + lds_v2(&sM[i * C + i]).x * nv;
+      cross = fma_t(v[i].x, tr, cross);
+      cross = fma_t(v[i].y, ti, cross);
+      const T nv = fma_t(v[i].x, v[i].x, v[i].y * v[i].y);
+      diag = fma_t(lds_v2(&sM[i * C + i]).x, nv, diag);
       sn += nv;
     }
-    accA += (double)sa;
+    accA += (double)(2 * cross + diag);
     accN += (double)sn;
   }
   block_sum2(accA, accN, sred);
@@ -271,10 +280,12 @@ __global__ void __launch_bounds__(256) k_apply(PassArgs a) {
     for (int r = 0; r < C; ++r) {
       T sr = 0, si = 0;
 #pragma unroll
-      for (int c = 0; c < C; ++c) {
+      for (int c = 0; c < C; ++c) {   // 4 FMAs per complex multiply-add
         const T2 k = lds_v2(&sK[r * C + c]);
-        sr += k.x * v[c].x - k.y * v[c].y;
-        si += k.x * v[c].y + k.y * v[c].x;
+        sr = fma_t(k.x, v[c].x, sr);
+        sr = fma_t(-k.y, v[c].y, sr);
+        si = fma_t(k.x, v[c].y, si);
+        si = fma_t(k.y, v[c].x, si);
       }
       T2 o;
       o.x = sr;

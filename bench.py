@@ -198,6 +198,7 @@ def native_arm(args, rank, world, local):
     import torch.distributed as dist
 
     from paper_2204_11404_gb300 import capi
+    from paper_2204_11404_gb300.shard import interleaved_index
     from paper_2204_11404_gb300.simulator import Simulator
 
     torch.cuda.set_device(local)
@@ -213,7 +214,7 @@ def native_arm(args, rank, world, local):
     log = torch.empty((1,), dtype=torch.uint8, device="cuda")
 
     def traj_index(i):
-        return (i // len(pts)) * world + rank
+        return interleaved_index(i, len(pts), rank, world)
 
     def step(i):
         j = i % len(pts)

@@ -260,7 +260,8 @@ def native_arm(args, rank, world, local):
     e2e = {"value": world * n_e2e * R / e2e_secs, "unit": UNIT,
            "h2d_bytes_per_step": 32, "d2h_bytes_per_step": (R + 1) * nst + 25 + 1}
 
-    # roofline of the dominant kernel: the apply pass (psi <- K_m psi / sqrt(N)) of a weight-4 block
+    # roofline of the dominant kernel: the pass that applies a weight-4 block (psi <- K_m psi / sqrt(N));
+    # in the complex64 form it also accumulates the next block's probability (fused, one read + write)
     ms_prob = float(np.mean([k[0] for k in kt]))
     ms_apply = float(np.mean([k[1] for k in kt]))
     amps = 1 << 25
@@ -276,7 +277,8 @@ def native_arm(args, rank, world, local):
                 "unit": "GB/s"}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["traffic"] = traffic_record(args.precision)
-    roof["kernel"] = "k_apply<%s,4> (weight-4 block, 2^25 amplitudes)" % ("double" if args.precision == "c128" else "float")
+    roof["kernel"] = ("k_apply<double,4> (weight-4 block, 2^25 amplitudes)" if args.precision == "c128" else
+                      "k_fused<float,4,4> (apply weight-4 block + next block's probability, 2^25 amplitudes)")
     roof["ms_apply"] = ms_apply
     roof["ms_prob"] = ms_prob
     roof["apply_hbm_gbs"] = bytes_apply / (ms_apply * 1e-3) / 1e9

@@ -152,9 +152,8 @@ qec_status run_init_round(qec_sim* s) {
   QEC_CUDA(launch_instantiate(s->p.precision, inst_args(s, 0, 0, s->nstab, false), s->work));
   for (int k = 0; k < s->nstab; ++k) {
     PassArgs a = pass_args(s, s->init_prog, k, s->psi0, s->psi0, true, nullptr, 0);
-    const int grid = pass_grid(s->D, a.w, s->num_sms);
-    QEC_CUDA(launch_prob(s->p.precision, a, grid, s->work));
-    QEC_CUDA(launch_apply(s->p.precision, a, grid, s->work));
+    QEC_CUDA(launch_prob(s->p.precision, a, pass_grid_for(s->p.precision, true, s->D, a.w, s->num_sms), s->work));
+    QEC_CUDA(launch_apply(s->p.precision, a, pass_grid_for(s->p.precision, false, s->D, a.w, s->num_sms), s->work));
   }
   QEC_CUDA(cudaStreamSynchronize(s->work));
   return QEC_OK;
@@ -166,14 +165,38 @@ PassArgs traj_pass(const qec_sim* s, int b) {
   return pass_args(s, s->prog, b, src, s->psi, false, s->d_syn, rnd * s->nstab + k);
 }
 
-qec_status enqueue_blocks(qec_sim* s, int b0, int b1) {
-  for (int b = b0; b < b1; ++b) {
-    PassArgs a = traj_pass(s, b);
-    const int grid = pass_grid(s->D, a.w, s->num_sms);
-    QEC_CUDA(launch_prob(s->p.precision, a, grid, s->work));
-    QEC_CUDA(launch_apply(s->p.precision, a, grid, s->work));
-  }
+// The complex64 form fuses block b's apply pass with block b+1's probability pass (one HBM
+// read + write per stabilizer); complex128 keeps them separate (both passes are FP64-ALU
+// bound, so fusing saves nothing there).
+bool fused_mode(const qec_sim* s) { return s->p.precision == QEC_C64; }
+
+qec_status enqueue_prob(qec_sim* s, int b) {
+  PassArgs a = traj_pass(s, b);
+  QEC_CUDA(launch_prob(s->p.precision, a, pass_grid_for(s->p.precision, true, s->D, a.w, s->num_sms), s->work));
   return QEC_OK;
+}
+
+// The pass(es) that apply block b: apply(b) + prob(b+1) fused, or apply(b) then prob(b+1).
+qec_status enqueue_apply(qec_sim* s, int b) {
+  PassArgs a = traj_pass(s, b);
+  const bool last = b + 1 >= s->S;
+  if (fused_mode(s) && !last) {
+    PassArgs n = traj_pass(s, b + 1);
+    n.src = s->psi;
+    QEC_CUDA(launch_fused(s->p.precision, a, n, s->num_sms, s->work));
+    return QEC_OK;
+  }
+  QEC_CUDA(launch_apply(s->p.precision, a, pass_grid_for(s->p.precision, false, s->D, a.w, s->num_sms), s->work));
+  return (fused_mode(s) || last) ? QEC_OK : enqueue_prob(s, b + 1);
+}
+
+// Blocks [b0, b1): block b0's probability pass is enqueued only when b0 == 0 (later blocks
+// get theirs from the previous block's apply step).
+qec_status enqueue_blocks(qec_sim* s, int b0, int b1) {
+  qec_status st = QEC_OK;
+  if (b0 == 0 && b1 > 0) st = enqueue_prob(s, 0);
+  for (int b = b0; b < b1 && st == QEC_OK; ++b) st = enqueue_apply(s, b);
+  return st;
 }
 
 qec_status enqueue_readout(qec_sim* s) {
@@ -197,15 +220,32 @@ qec_status enqueue_readout(qec_sim* s) {
 }
 
 // Part 0: instantiate + blocks [0, timed); part 1: blocks (timed, S) + readout.
+// Part 0: instantiate, then blocks [0, b*) except b*'s probability pass; part 1: everything after
+// block b*'s apply step, then the readout.  Without a timed block part 0 is the whole trajectory.
 qec_status enqueue_part(qec_sim* s, int part) {
   const int tb = s->timed_block;
   qec_status st = QEC_OK;
   if (part == 0) {
     if (s->S > 0) QEC_CUDA(launch_instantiate(s->p.precision, inst_args(s, 1, 1, s->S, true), s->work));
-    st = enqueue_blocks(s, 0, tb < 0 ? s->S : tb);
-    if (st == QEC_OK && tb < 0) st = enqueue_readout(s);
+    if (tb < 0) {
+      st = enqueue_blocks(s, 0, s->S);
+      if (st == QEC_OK) st = enqueue_readout(s);
+      return st;
+    }
+    if (s->S > 0) st = enqueue_prob(s, 0);
+    for (int b = 0; b < tb && st == QEC_OK; ++b) {
+      // in the separate-pass form, stop before block b*'s probability pass (timed directly)
+      PassArgs a = traj_pass(s, b);
+      if (fused_mode(s)) {
+        st = enqueue_apply(s, b);
+      } else {
+        QEC_CUDA(launch_apply(s->p.precision, a, pass_grid_for(s->p.precision, false, s->D, a.w, s->num_sms), s->work));
+        if (b + 1 < tb) st = enqueue_prob(s, b + 1);
+      }
+    }
   } else {
-    st = enqueue_blocks(s, tb + 1, s->S);
+    if (!fused_mode(s) && tb + 1 < s->S) st = enqueue_prob(s, tb + 1);
+    for (int b = tb + 1; b < s->S && st == QEC_OK; ++b) st = enqueue_apply(s, b);
     if (st == QEC_OK) st = enqueue_readout(s);
   }
   return st;
@@ -233,15 +273,24 @@ qec_status ensure_graph(qec_sim* s) {
   return st;
 }
 
+// Timed block b*: its apply step (fused apply + next probability in the complex64 form) runs
+// between kev[1] and kev[2]; in the complex128 form kev[0]..kev[1] brackets nothing and the
+// probability pass of b* is timed from the end of graph part 0 instead (see enqueue_part).
 qec_status launch_trajectory(qec_sim* s) {
   QEC_CUDA(cudaGraphLaunch(s->gexec[0], s->work));
   if (s->timed_block < 0) return QEC_OK;
-  PassArgs a = traj_pass(s, s->timed_block);
-  const int grid = pass_grid(s->D, a.w, s->num_sms);
+  const int b = s->timed_block;
+  PassArgs a = traj_pass(s, b);
   QEC_CUDA(cudaEventRecord(s->kev[0], s->work));
-  QEC_CUDA(launch_prob(s->p.precision, a, grid, s->work));
+  if (!fused_mode(s)) QEC_CUDA(launch_prob(s->p.precision, a, pass_grid_for(s->p.precision, true, s->D, a.w, s->num_sms), s->work));
   QEC_CUDA(cudaEventRecord(s->kev[1], s->work));
-  QEC_CUDA(launch_apply(s->p.precision, a, grid, s->work));
+  if (fused_mode(s)) {
+    PassArgs n = traj_pass(s, b + 1);
+    n.src = s->psi;
+    QEC_CUDA(launch_fused(s->p.precision, a, n, s->num_sms, s->work));
+  } else {
+    QEC_CUDA(launch_apply(s->p.precision, a, pass_grid_for(s->p.precision, false, s->D, a.w, s->num_sms), s->work));
+  }
   QEC_CUDA(cudaEventRecord(s->kev[2], s->work));
   QEC_CUDA(cudaGraphLaunch(s->gexec[1], s->work));
   return QEC_OK;

@@ -295,6 +295,186 @@ __global__ void __launch_bounds__(256) k_apply(PassArgs a) {
   }
 }
 
+// ---- fused pass: apply block s, then probability of block s+1, per shared-memory tile ----
+template <int W>
+__device__ __forceinline__ uint32_t local_base(uint32_t g, const int (&q)[4]) {
+#pragma unroll
+  for (int j = 0; j < W; ++j) g = ((g >> q[j]) << (q[j] + 1)) | (g & ((1u << q[j]) - 1u));
+  return g;
+}
+
+// Last-CTA reduction of (A, N) into the result slots of a probability block; shared with k_prob.
+__device__ __forceinline__ void finish_prob(const PassArgs& a, double accA, double accN, double* sred, int* s_last) {
+  block_sum2(accA, accN, sred);
+  if (threadIdx.x == 0) {
+    a.partials[2 * blockIdx.x] = accA;
+    a.partials[2 * blockIdx.x + 1] = accN;
+    __threadfence();
+    const unsigned int t = atomicAdd(&a.ctl->ticket, 1u);
+    *s_last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!*s_last) return;
+  __threadfence();
+  double sA = 0.0, sN = 0.0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
+    sA += __ldcg(&a.partials[2 * i]);
+    sN += __ldcg(&a.partials[2 * i + 1]);
+  }
+  block_sum2(sA, sN, sred);
+  if (threadIdx.x == 0) {
+    const double p1 = sA / sN;
+    const int m = a.forced >= 0 ? a.forced : (*a.u < p1 ? 1 : 0);
+    *a.A = sA;
+    *a.N = sN;
+    *a.m = m;
+    if (a.syn) {
+      const unsigned long long t = a.ctl->traj - a.ctl->first;
+      a.syn[t * (unsigned long long)a.syn_stride + a.syn_idx] = (uint8_t)(m ^ a.offset);
+    }
+    a.ctl->ticket = 0u;
+  }
+}
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Tiles stream through two shared-memory buffers: while tile i is computed, tile i+1 arrives by
+// 16-byte asynchronous copies (runs of 2^lb contiguous amplitudes, >= 128 bytes, 16-byte aligned).
+template <typename T, int W, int W2>
+__global__ void __launch_bounds__(256) k_fused(FusedArgs f) {
+  using T2 = typename V2<T>::t;
+  constexpr int C = 1 << W, C2 = 1 << W2;
+  constexpr int CH = 16 / sizeof(T2);   // amplitudes per 16-byte copy
+  extern __shared__ __align__(16) unsigned char fsm[];
+  const uint32_t tsz = 1u << f.nt, lmask = (1u << f.lb) - 1u;
+  T2* buf0 = reinterpret_cast<T2*>(fsm);
+  T2* buf1 = buf0 + tsz;
+  uint32_t* hoff = reinterpret_cast<uint32_t*>(buf1 + tsz);
+  __shared__ T2 sK[C * C];
+  __shared__ T2 sM[C2 * C2];
+  __shared__ double sred[64];
+  __shared__ int s_last;
+  {
+    const int m = *f.ap.m;
+    const double scale = 1.0 / sqrt(*f.ap.N);
+    const T2* Kg = reinterpret_cast<const T2*>(f.ap.kraus) + (m ? 256 : 0);
+    for (int i = threadIdx.x; i < C * C; i += blockDim.x) {
+      T2 kv = Kg[(i / C) * 16 + (i % C)];
+      kv.x = (T)((double)kv.x * scale);
+      kv.y = (T)((double)kv.y * scale);
+      sK[i] = kv;
+    }
+    const T2* Mg = reinterpret_cast<const T2*>(f.pr.kraus) + 512;
+    for (int i = threadIdx.x; i < C2 * C2; i += blockDim.x) sM[i] = Mg[(i / C2) * 16 + (i % C2)];
+    const int nh = f.nt - f.lb;
+    for (int h = threadIdx.x; h < (1 << nh); h += blockDim.x) {
+      uint32_t o = 0;
+      for (int j = 0; j < nh; ++j) o |= (uint32_t)((h >> j) & 1) << f.hbits[j];
+      hoff[h] = o;
+    }
+  }
+  __syncthreads();
+  int qa[4], qp[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    qa[j] = j < W ? f.qa[j] : 0;
+    qp[j] = j < W2 ? f.qp[j] : 0;
+  }
+  uint32_t offa[C], offp[C2];
+#pragma unroll
+  for (int l = 0; l < C; ++l) offa[l] = member_off<W>(l, qa);
+#pragma unroll
+  for (int l = 0; l < C2; ++l) offp[l] = member_off<W2>(l, qp);
+  const T2* src = reinterpret_cast<const T2*>(f.ap.src);
+  T2* dst = reinterpret_cast<T2*>(f.ap.dst);
+  const uint32_t ntile = 1u << f.nout;
+  auto tile_base = [&](uint32_t tix) {
+    uint32_t tb = 0;
+    for (int j = 0; j < f.nout; ++j) tb |= ((tix >> j) & 1u) << f.obits[j];
+    return tb;
+  };
+  auto issue = [&](uint32_t tix, T2* buf) {
+    const uint32_t tb = tile_base(tix);
+    for (uint32_t e = threadIdx.x * CH; e < tsz; e += blockDim.x * CH)
+      cp_async16(buf + e, src + (tb | hoff[e >> f.lb] | (e & lmask)));
+    cp_async_commit();
+  };
+  double accA = 0.0, accN = 0.0;
+  uint32_t tix = blockIdx.x;
+  if (tix < ntile) issue(tix, buf0);
+  int cur = 0;
+  for (; tix < ntile; tix += gridDim.x) {
+    T2* tile = cur ? buf1 : buf0;
+    const uint32_t nxt = tix + gridDim.x;
+    if (nxt < ntile) issue(nxt, cur ? buf0 : buf1);
+    else cp_async_commit();
+    cp_async_wait<1>();
+    __syncthreads();
+    for (uint32_t g = threadIdx.x; g < (tsz >> W); g += blockDim.x) {
+      const uint32_t b = local_base<W>(g, qa);
+      T2 v[C];
+#pragma unroll
+      for (int l = 0; l < C; ++l) v[l] = tile[b + offa[l]];
+#pragma unroll
+      for (int r = 0; r < C; ++r) {
+        T sr = 0, si = 0;
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          const T2 k = lds_v2(&sK[r * C + c]);
+          sr = fma_t(k.x, v[c].x, sr);
+          sr = fma_t(-k.y, v[c].y, sr);
+          si = fma_t(k.x, v[c].y, si);
+          si = fma_t(k.y, v[c].x, si);
+        }
+        T2 o;
+        o.x = sr;
+        o.y = si;
+        tile[b + offa[r]] = o;
+      }
+    }
+    __syncthreads();
+    for (uint32_t g = threadIdx.x; g < (tsz >> W2); g += blockDim.x) {
+      const uint32_t b = local_base<W2>(g, qp);
+      T2 v[C2];
+#pragma unroll
+      for (int l = 0; l < C2; ++l) v[l] = tile[b + offp[l]];
+      T cross = 0, diag = 0, sn = 0;
+#pragma unroll
+      for (int i = 0; i < C2; ++i) {
+        T tr = 0, ti = 0;
+#pragma unroll
+        for (int j = i + 1; j < C2; ++j) {
+          const T2 m = lds_v2(&sM[i * C2 + j]);
+          tr = fma_t(m.x, v[j].x, tr);
+          tr = fma_t(-m.y, v[j].y, tr);
+          ti = fma_t(m.x, v[j].y, ti);
+          ti = fma_t(m.y, v[j].x, ti);
+        }
+        cross = fma_t(v[i].x, tr, cross);
+        cross = fma_t(v[i].y, ti, cross);
+        const T nv = fma_t(v[i].x, v[i].x, v[i].y * v[i].y);
+        diag = fma_t(lds_v2(&sM[i * C2 + i]).x, nv, diag);
+        sn += nv;
+      }
+      accA += (double)(2 * cross + diag);
+      accN += (double)sn;
+    }
+    const uint32_t tb = tile_base(tix);
+    for (uint32_t e = threadIdx.x * CH; e < tsz; e += blockDim.x * CH)
+      *reinterpret_cast<float4*>(dst + (tb | hoff[e >> f.lb] | (e & lmask))) = *reinterpret_cast<const float4*>(tile + e);
+    __syncthreads();
+    cur ^= 1;
+  }
+  cp_async_wait<0>();
+  finish_prob(f.pr, accA, accN, sred, &s_last);
+}
+
 // ---- final Z readout (Sec. III.B): sequential per-qubit sampling -------------------------
 // Qubit j gets outcome [u_j < P(q_j = 1 | outcomes of qubits < j)].  The conditional
 // marginals of the low k1 qubits come from one histogram pass over the register; the
@@ -415,6 +595,23 @@ __global__ void k_set_basis0(void* psi, int64_t n) {
   }
 }
 
+constexpr int kFusedSmemMax = 160 * 1024;
+
+// Resident CTAs of 256 threads per SM for this kernel and dynamic shared memory.
+static int blocks_per_sm(const void* fn, size_t smem) {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, 256, smem) != cudaSuccess || n < 1) n = 1;
+  return n;
+}
+
+// One wave of resident CTAs (grid-stride loops cover the rest), capped by the work and the partials.
+static int wave_grid(const void* fn, size_t smem, int num_sms, int64_t work) {
+  int64_t g = (int64_t)num_sms * blocks_per_sm(fn, smem);
+  if (g > work) g = work;
+  if (g > MAX_PASS_GRID) g = MAX_PASS_GRID;
+  return (int)(g < 1 ? 1 : g);
+}
+
 // ---- launchers --------------------------------------------------------------------------
 int pass_grid(int D, int w, int num_sms) {
   const int64_t G = 1ll << (D - w);
@@ -451,6 +648,17 @@ static void apply_t(const PassArgs& a, int grid, cudaStream_t s) {
   else k_apply<T, 2><<<grid, 256, 0, s>>>(a);
 }
 
+int pass_grid_for(int precision, bool prob, int D, int w, int num_sms) {
+  const void* fn;
+  if (precision == QEC_C128)
+    fn = prob ? (w == 4 ? (const void*)k_prob<double, 4> : (const void*)k_prob<double, 2>)
+              : (w == 4 ? (const void*)k_apply<double, 4> : (const void*)k_apply<double, 2>);
+  else
+    fn = prob ? (w == 4 ? (const void*)k_prob<float, 4> : (const void*)k_prob<float, 2>)
+              : (w == 4 ? (const void*)k_apply<float, 4> : (const void*)k_apply<float, 2>);
+  return wave_grid(fn, 0, num_sms, ((1ll << (D - w)) + 255) / 256);
+}
+
 cudaError_t launch_prob(int precision, const PassArgs& a, int grid, cudaStream_t s) {
   if (a.w != 2 && a.w != 4) return cudaErrorInvalidValue;
   if (precision == QEC_C128) prob_t<double>(a, grid, s);
@@ -471,13 +679,6 @@ static size_t sample_smem(int D) {
   return sizeof(double) * (B > H ? B : H);
 }
 
-cudaError_t setup_kernels(int precision, int D) {
-  const int smem = (int)sample_smem(D);
-  if (precision == QEC_C128)
-    return cudaFuncSetAttribute(k_sample<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  return cudaFuncSetAttribute(k_sample<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-}
-
 cudaError_t launch_readout(int precision, const ReadArgs& a, cudaStream_t s) {
   const int B = 1 << a.k1;
   const size_t smem = sample_smem(a.D);
@@ -493,12 +694,100 @@ cudaError_t launch_readout(int precision, const ReadArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+static int tile_pos(int q, int lb, const int* hb, int nh) {
+  if (q < lb) return q;
+  for (int j = 0; j < nh; ++j)
+    if (hb[j] == q) return lb + j;
+  return -1;
+}
+
+template <typename T, int W, int W2>
+static cudaError_t fused_t(FusedArgs f, size_t smem, int num_sms, cudaStream_t s) {
+  f.grid = wave_grid((const void*)k_fused<T, W, W2>, smem, num_sms, 1ll << f.nout);
+  k_fused<T, W, W2><<<f.grid, 256, smem, s>>>(f);
+  return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t fused_attrs() {
+  const void* fns[4] = {(const void*)k_fused<T, 2, 2>, (const void*)k_fused<T, 2, 4>, (const void*)k_fused<T, 4, 2>,
+                        (const void*)k_fused<T, 4, 4>};
+  for (const void* fn : fns) {
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kFusedSmemMax);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_fused(int precision, const PassArgs& ap, const PassArgs& pr, int num_sms, cudaStream_t s) {
+  if ((ap.w != 2 && ap.w != 4) || (pr.w != 2 && pr.w != 4)) return cudaErrorInvalidValue;
+  const size_t amp = precision == QEC_C128 ? 16 : 8;
+  FusedArgs f;
+  f.ap = ap;
+  f.pr = pr;
+  // Tile bits: both blocks' qubits plus the low bits [0, lb), lb chosen for >= 128-byte runs
+  // and then raised until the tile has >= 2^12 amplitudes (or the register ends), so that a
+  // weight-4 block has one 16-amplitude group per thread.
+  uint32_t mask = 0;
+  for (int j = 0; j < ap.w; ++j) mask |= 1u << ap.q[j];
+  for (int j = 0; j < pr.w; ++j) mask |= 1u << pr.q[j];
+  int lb = amp == 16 ? 3 : 4;
+  if (lb > ap.D) lb = ap.D;
+  auto count = [&](int lbits) {
+    uint32_t m = mask | ((1u << lbits) - 1u);
+    return __builtin_popcount(m);
+  };
+  while (count(lb) < 12 && lb < ap.D) ++lb;
+  const uint32_t tmask = mask | ((1u << lb) - 1u);
+  f.lb = lb;
+  int nh = 0, no = 0;
+  for (int q = lb; q < ap.D; ++q) {
+    if (tmask & (1u << q)) f.hbits[nh++] = q;
+  }
+  for (int q = 0; q < ap.D; ++q) {
+    if (!(tmask & (1u << q))) f.obits[no++] = q;
+  }
+  f.nt = lb + nh;
+  f.nout = no;
+  for (int j = 0; j < 4; ++j) {
+    f.qa[j] = j < ap.w ? tile_pos(ap.q[j], lb, f.hbits, nh) : 0;
+    f.qp[j] = j < pr.w ? tile_pos(pr.q[j], lb, f.hbits, nh) : 0;
+  }
+  const size_t smem = 2 * amp * ((size_t)1 << f.nt) + sizeof(uint32_t) * ((size_t)1 << nh);
+  if (smem > (size_t)kFusedSmemMax) return cudaErrorInvalidValue;
+  const int key = (ap.w == 4 ? 2 : 0) + (pr.w == 4 ? 1 : 0);
+  if (precision == QEC_C128) {
+    switch (key) {
+      case 0: return fused_t<double, 2, 2>(f, smem, num_sms, s);
+      case 1: return fused_t<double, 2, 4>(f, smem, num_sms, s);
+      case 2: return fused_t<double, 4, 2>(f, smem, num_sms, s);
+      default: return fused_t<double, 4, 4>(f, smem, num_sms, s);
+    }
+  }
+  switch (key) {
+    case 0: return fused_t<float, 2, 2>(f, smem, num_sms, s);
+    case 1: return fused_t<float, 2, 4>(f, smem, num_sms, s);
+    case 2: return fused_t<float, 4, 2>(f, smem, num_sms, s);
+    default: return fused_t<float, 4, 4>(f, smem, num_sms, s);
+  }
+}
+
 cudaError_t launch_set_basis0(int precision, void* psi, int D, cudaStream_t s) {
   const int64_t n = 1ll << D;
   int grid = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
   if (precision == QEC_C128) k_set_basis0<double><<<grid, 256, 0, s>>>(psi, n);
   else k_set_basis0<float><<<grid, 256, 0, s>>>(psi, n);
   return cudaGetLastError();
+}
+
+cudaError_t setup_kernels(int precision, int D) {
+  const int smem = (int)sample_smem(D);
+  if (precision == QEC_C128) {
+    cudaError_t e = cudaFuncSetAttribute(k_sample<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    return e != cudaSuccess ? e : fused_attrs<double>();
+  }
+  cudaError_t e = cudaFuncSetAttribute(k_sample<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  return e != cudaSuccess ? e : fused_attrs<float>();
 }
 
 // ---- host instantiation (test hook; same op arithmetic as inst_block) -------------------

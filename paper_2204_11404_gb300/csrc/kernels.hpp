@@ -58,6 +58,21 @@ struct PassArgs {
   int offset;             // syndrome = raw ^ offset
 };
 
+// Fused pass: apply block s (ap) and accumulate the probability of block s+1 (pr) on tiles
+// of amplitudes staged in shared memory, one HBM read + one write per stabilizer.
+// Tile index bits: [0, lb) = register bits [0, lb); [lb, nt) = register bits hbits[0..nt-lb).
+struct FusedArgs {
+  PassArgs ap;
+  PassArgs pr;
+  int nt, lb;
+  int hbits[16];
+  int nout;
+  int obits[32];          // register bits outside the tile, ascending
+  int qa[4];              // apply block's qubits as tile-index bits (ascending)
+  int qp[4];              // probability block's qubits as tile-index bits (ascending)
+  int grid;
+};
+
 struct ReadArgs {
   const void* src;
   int D, k1, d;
@@ -77,9 +92,13 @@ cudaError_t launch_instantiate(int precision, const InstArgs& a, cudaStream_t s)
 cudaError_t launch_prob(int precision, const PassArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_apply(int precision, const PassArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_readout(int precision, const ReadArgs& a, cudaStream_t s);
+// Builds the tile for (apply block ap, probability block pr) and launches the fused pass.
+cudaError_t launch_fused(int precision, const PassArgs& ap, const PassArgs& pr, int num_sms, cudaStream_t s);
 cudaError_t launch_set_basis0(int precision, void* psi, int D, cudaStream_t s);
 cudaError_t setup_kernels(int precision, int D);   // once per process/device, before any capture
 int pass_grid(int D, int w, int num_sms);
+// One wave of resident CTAs for the probability (prob = true) or apply pass kernel.
+int pass_grid_for(int precision, bool prob, int D, int w, int num_sms);
 int hist_k1(int D);
 int hist_grid(int D, int num_sms);
 

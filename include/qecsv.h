@@ -159,6 +159,43 @@ qec_status qec_run_trajectories_noalloc(const qec_params* params, uint64_t seed,
                                         uint8_t* d_syndromes, uint8_t* d_data_bits, uint8_t* d_raw_logical,
                                         void* cuda_stream);
 
+/* ---- Batched form: many small-register trajectories in one persistent launch ----------- */
+typedef struct qec_batch qec_batch;
+
+/*
+ * Batched simulator for the d = 3 delayed-measurement register (9 data qubits
+ * + reused ancilla, Sec. II.B), `rounds` noisy rounds, gate set `gates`.
+ * One warp runs one trajectory in shared memory; a single graph-captured
+ * persistent kernel processes a whole batch, taking trajectories from a
+ * device work counter.  max_traj bounds n of every run.  Only d = 3 is
+ * accepted (QEC_EUNSUPPORTED otherwise).  cuda_stream as in qec_create.
+ */
+qec_status qec_batch_create(int32_t d, int32_t rounds, int32_t gates, uint32_t max_traj, void* cuda_stream,
+                            qec_batch** out);
+
+/*
+ * Run n trajectories (Sec. III.B protocol, as qec_run_trajectories), each with
+ * its own trajectory index traj[i], precision kind[i] (QEC_C128 or QEC_C64)
+ * and noise parameters noise[i] (Sec. III.A).  Inputs and outputs are HOST
+ * arrays: syndromes [n][rounds+1][8], data_bits [n][9], raw_logical [n] (any
+ * output may be NULL).  Trajectory i equals qec_run_trajectories for
+ * (noise[i], kind[i], seed, traj[i]).  Blocks until the outputs are on the host.
+ */
+qec_status qec_batch_run(qec_batch* b, uint64_t seed, uint32_t n, const uint64_t* traj, const int32_t* kind,
+                         const qec_noise* noise, uint8_t* syndromes, uint8_t* data_bits, uint8_t* raw_logical);
+
+/*
+ * Autotuner: times qec_batch_run on the given sample for each candidate CTA
+ * shape (warps per CTA; one resident wave per SM) and keeps the fastest.
+ * *chosen_warps and *best_ms report the choice and its device time.
+ */
+qec_status qec_batch_autotune(qec_batch* b, uint64_t seed, uint32_t n, const uint64_t* traj, const int32_t* kind,
+                              const qec_noise* noise, int32_t* chosen_warps, float* best_ms);
+
+/* Device time (ms, CUDA events around the persistent launch) of the last qec_batch_run. */
+qec_status qec_batch_last_ms(const qec_batch* b, float* ms);
+qec_status qec_batch_destroy(qec_batch* b);
+
 qec_status qec_destroy(qec_sim* sim);
 const char* qec_last_error(void);
 

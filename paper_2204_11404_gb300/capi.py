@@ -49,6 +49,12 @@ SIGNATURES = {
     "qec_run_trajectories_noalloc": ([ctypes.POINTER(qec_params), ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32,
                                       _P, _P, _P, _P], ctypes.c_int),
     "qec_destroy": ([_P], ctypes.c_int),
+    "qec_batch_create": ([ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint32, _P, ctypes.POINTER(_P)],
+                         ctypes.c_int),
+    "qec_batch_run": ([_P, ctypes.c_uint64, ctypes.c_uint32, _P, _P, _P, _P, _P, _P], ctypes.c_int),
+    "qec_batch_autotune": ([_P, ctypes.c_uint64, ctypes.c_uint32, _P, _P, _P, _P, _P], ctypes.c_int),
+    "qec_batch_last_ms": ([_P, _P], ctypes.c_int),
+    "qec_batch_destroy": ([_P], ctypes.c_int),
     "qec_last_error": ([], ctypes.c_char_p),
     "qec_debug_program": ([ctypes.POINTER(qec_params), _P, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32),
                            _P, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32)], ctypes.c_int),
@@ -135,6 +141,34 @@ def qec_run_trajectories_noalloc(params, seed, first_traj, n, d_syn_ptr, d_bits_
     """Device-allocation-free variant of qec_run_trajectories_device (d = 3, <= 16 rounds)."""
     return check(lib().qec_run_trajectories_noalloc(ctypes.byref(params), seed, first_traj, n, d_syn_ptr, d_bits_ptr,
                                                     d_log_ptr, cuda_stream))
+
+
+def qec_batch_create(d, rounds, gates, max_traj, cuda_stream=None):
+    h = _P()
+    check(lib().qec_batch_create(d, rounds, gates, max_traj, cuda_stream, ctypes.byref(h)))
+    return h
+
+
+def qec_batch_run(b, seed, n, traj_ptr, kind_ptr, noise_ptr, syn_ptr, bits_ptr, log_ptr):
+    return check(lib().qec_batch_run(b, seed, n, traj_ptr, kind_ptr, noise_ptr, syn_ptr, bits_ptr, log_ptr))
+
+
+def qec_batch_autotune(b, seed, n, traj_ptr, kind_ptr, noise_ptr):
+    w = ctypes.c_int32(0)
+    ms = ctypes.c_float(0)
+    check(lib().qec_batch_autotune(b, seed, n, traj_ptr, kind_ptr, noise_ptr, ctypes.cast(ctypes.pointer(w), _P),
+                                   ctypes.cast(ctypes.pointer(ms), _P)))
+    return int(w.value), float(ms.value)
+
+
+def qec_batch_last_ms(b):
+    ms = ctypes.c_float(0)
+    check(lib().qec_batch_last_ms(b, ctypes.cast(ctypes.pointer(ms), _P)))
+    return float(ms.value)
+
+
+def qec_batch_destroy(b):
+    return check(lib().qec_batch_destroy(b))
 
 
 def qec_destroy(sim):

@@ -63,3 +63,56 @@ class Simulator:
             self.close()
         except Exception:
             pass
+
+
+class BatchSimulator:
+    """qec_batch handle: d = 3 trajectories with per-trajectory precision and noise in one launch."""
+
+    def __init__(self, rounds, gates="cr", max_traj=8192, stream=None, d=3):
+        self.d, self.rounds, self.nstab = d, rounds, d * d - 1
+        self.h = capi.qec_batch_create(d, rounds, {"cnot": capi.QEC_GATES_CNOT, "cr": capi.QEC_GATES_CR}[gates],
+                                       max_traj, ctypes.c_void_p(stream) if stream else None)
+
+    @staticmethod
+    def _inputs(traj, kind, noise):
+        n = len(traj)
+        t = np.ascontiguousarray(traj, dtype=np.uint64)
+        k = np.ascontiguousarray([{"c128": capi.QEC_C128, "c64": capi.QEC_C64}.get(x, x) for x in kind], dtype=np.int32)
+        nz = (capi.qec_noise * max(n, 1))()
+        for i, d in enumerate(noise):
+            for f in capi.NOISE_FIELDS:
+                setattr(nz[i], f, float(d.get(f, 0.0)))
+        return n, t, k, nz
+
+    def run(self, seed, traj, kind, noise):
+        n, t, k, nz = self._inputs(traj, kind, noise)
+        syn = np.zeros((n, self.rounds + 1, self.nstab), dtype=np.uint8)
+        bits = np.zeros((n, self.d * self.d), dtype=np.uint8)
+        log = np.zeros(n, dtype=np.uint8)
+        capi.qec_batch_run(self.h, seed, n, t.ctypes.data, k.ctypes.data, ctypes.addressof(nz), syn.ctypes.data,
+                           bits.ctypes.data, log.ctypes.data)
+        return syn, bits, log
+
+    def autotune(self, seed, traj, kind, noise):
+        n, t, k, nz = self._inputs(traj, kind, noise)
+        return capi.qec_batch_autotune(self.h, seed, n, t.ctypes.data, k.ctypes.data, ctypes.addressof(nz))
+
+    def last_ms(self):
+        return capi.qec_batch_last_ms(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            capi.qec_batch_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

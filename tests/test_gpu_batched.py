@@ -1,0 +1,59 @@
+"""Batched form (many d=3 trajectories in one persistent launch) against the oracle and the
+single-trajectory path: per-trajectory precision and noise, bit-exact outcomes (near-threshold
+rule for complex64)."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import run_trajectory
+from parity_util import TAU, compare_trajectory
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2204_11404_gb300.simulator import BatchSimulator, Simulator  # noqa: E402
+
+
+@pytest.mark.parametrize("gates", ["cr", "cnot"])
+def test_batched_mix_matches_oracle(gates):
+    n = 96
+    traj = [1000 + 7 * i for i in range(n)]
+    kinds = ["c128" if i % 3 else "c64" for i in range(n)]
+    rng = np.random.default_rng(3)
+    noise = []
+    for i in range(n):
+        if i % 4 == 0:
+            noise.append(dict(W.STRESS))
+        else:
+            p = float(rng.uniform(1e-4, 3e-2))
+            noise.append(dict(p1=p, p2=p, p_idle=p, theta_rx=float(rng.uniform(0, 0.1)), phi_zz=0.02))
+    with BatchSimulator(3, gates, max_traj=256) as b:
+        syn, bits, log = b.run(77, traj, kinds, noise)
+    amb = 0
+    for i in range(n):
+        o = run_trajectory(3, 3, gates, "reduced", noise[i], seed=77, traj=traj[i])
+        kind = compare_trajectory(syn[i], bits[i], o, TAU[kinds[i]])
+        if kinds[i] == "c128":
+            assert kind == "exact"
+        amb += kind == "ambiguous"
+        if kind == "exact":
+            assert log[i] == o["raw_logical"]
+    assert amb <= 2
+
+
+def test_batched_equals_single_trajectory_path_and_autotune():
+    traj, kinds, noise, rounds, seed = W.batched_mix(n=512)
+    with BatchSimulator(rounds, "cr", max_traj=512) as b:
+        w, ms = b.autotune(seed, traj, kinds, noise)
+        assert w > 0 and ms > 0
+        syn, bits, log = b.run(seed, traj, kinds, noise)
+        syn2, bits2, log2 = b.run(seed, traj, kinds, noise)
+    assert (syn == syn2).all() and (bits == bits2).all() and (log == log2).all()
+    for i in (0, 1, 2, 3, 200, 511):
+        with Simulator(3, rounds, "cr", kinds[i], **noise[i]) as sim:
+            s1, b1, l1 = sim.run(seed, traj[i], 1)
+        if kinds[i] == "c128":
+            assert (s1[0] == syn[i]).all() and (b1[0] == bits[i]).all() and l1[0] == log[i]

@@ -42,8 +42,13 @@ def parse():
     ap.add_argument("--precision", default="c128", choices=["c128", "c64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--points", type=int, default=9, help="noise points used (1..9); fewer = smaller device footprint")
-    ap.add_argument("--workload", default="d5", choices=["d5", "batched"],
-                    help="d5: the d=5 26-qubit trajectories (default); batched: 8192 d=3 trajectories per launch")
+    ap.add_argument("--workload", default="d5", choices=["d5", "batched", "serve"],
+                    help="d5: the d=5 26-qubit trajectories (default); batched: 8192 d=3 trajectories per "
+                         "launch; serve: Poisson trace of mixed jobs through the continuous-batching server")
+    ap.add_argument("--requests", type=int, default=64, help="serve: requests in the trace")
+    ap.add_argument("--rate", type=float, default=50.0, help="serve: mean arrival rate (requests/s)")
+    ap.add_argument("--max-traj", type=int, default=8, help="serve: trajectories per request drawn from 1..max")
+    ap.add_argument("--mem-gib", type=float, default=32.0, help="serve: device memory budget for state vectors")
     return ap.parse_args()
 
 
@@ -348,6 +353,48 @@ def batched_arm(args, rank, world, local):
         print(json.dumps(out))
 
 
+def serve_arm(args, rank, world, local):
+    """A Poisson trace of mixed jobs (d in {3,5}, rounds 1..10, complex64/complex128, per-job noise)
+    through the continuous-batching server; latency percentiles beside throughput."""
+    import torch
+
+    from paper_2204_11404_gb300.serve import Job, Server, latency_summary
+
+    torch.cuda.set_device(local)
+    warm = [Job(**j) for j in W.serving_trace(n_req=4, rate=1e6, seed=1, max_traj=1)]
+    trace = W.serving_trace(n_req=args.requests, rate=args.rate, seed=5000 + rank, max_traj=args.max_traj)
+    jobs = [Job(**j) for j in trace]
+    srv = Server(int(args.mem_gib * 2**30))
+    try:
+        srv.run(warm)
+        with ClockSampler(local) as clk:
+            t0 = time.perf_counter()
+            srv.run(jobs)
+            makespan = time.perf_counter() - t0
+    finally:
+        srv.close()
+    traj = sum(j.n_traj for j in jobs)
+    tr_rounds = sum(j.n_traj * j.rounds for j in jobs)
+    span = max(j.arrival for j in jobs)
+    lat = latency_summary(jobs)
+    out = {
+        "metric": "serving: trajectories/s with p50/p99 job latency (continuous batching)",
+        "value": world * traj / makespan, "unit": "trajectories/s", "n_gpus": world, "steps": len(jobs),
+        "warmup": len(warm), "ms_per_step": 1e3 * makespan / len(jobs), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+        "config": {"workload": "Poisson trace: d in {3,5}, rounds U{1..10}, trajectories U{1..%d}, c64/c128, "
+                               "p~U[1e-4,1e-2], theta_rx~U[0,0.1]" % args.max_traj,
+                   "requests": len(jobs), "rate_per_s": args.rate, "mem_budget_gib": args.mem_gib,
+                   "offered_trajectory_rounds_per_s": tr_rounds / span if span > 0 else None,
+                   "achieved_trajectory_rounds_per_s": tr_rounds / makespan},
+        "latency_ms": lat, "clocks": clk.summary(),
+        "e2e": {"value": world * traj / makespan, "unit": "trajectories/s",
+                "h2d_bytes_per_step": 32, "d2h_bytes_per_step": None},
+    }
+    if rank == 0:
+        print(json.dumps(out))
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -355,6 +402,8 @@ def main():
         reference_arm(args, rank, world)
     elif args.workload == "batched":
         batched_arm(args, rank, world, local)
+    elif args.workload == "serve":
+        serve_arm(args, rank, world, local)
     else:
         native_arm(args, rank, world, local)
 

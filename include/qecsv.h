@@ -70,7 +70,9 @@ typedef struct qec_sim qec_sim;
  * noise-free init round whose outcomes are forced to the zero syndrome; the
  * resulting code state stays resident and seeds every trajectory.
  * cuda_stream: a cudaStream_t owned by the caller (e.g. torch's current
- * stream) that all work is ordered on, or NULL for a stream owned by the sim.
+ * stream) that every run is ordered after and before (through events), or
+ * NULL.  Kernels run on a stream owned by the sim, created with the caller
+ * stream's priority.
  * *out receives the handle; the sim owns all device memory it allocates.
  */
 qec_status qec_create(const qec_params* params, void* cuda_stream, qec_sim** out);
@@ -99,6 +101,14 @@ qec_status qec_run_trajectories(qec_sim* sim, uint64_t seed, uint64_t first_traj
  */
 qec_status qec_run_trajectories_device(qec_sim* sim, uint64_t seed, uint64_t first_traj, uint32_t n,
                                        uint8_t* d_syndromes, uint8_t* d_data_bits, uint8_t* d_raw_logical);
+
+/*
+ * Re-point an existing simulator at new noise parameters and round count,
+ * keeping its device buffers and its resident init code state (which does not
+ * depend on noise or rounds).  d, gate set, precision and layout must match
+ * the handle's (QEC_EINVAL otherwise).  Waits for the handle's queued work.
+ */
+qec_status qec_reconfigure(qec_sim* sim, const qec_params* params);
 
 /* Number of amplitudes of the resident data register (2^(d*d)); the ancilla
  * of the d^2+1 register is |0> at every point a snapshot can be taken. */

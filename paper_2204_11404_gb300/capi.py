@@ -42,6 +42,7 @@ SIGNATURES = {
     "qec_run_trajectories": ([_P, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32, _P, _P, _P], ctypes.c_int),
     "qec_run_trajectories_device": ([_P, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32, _P, _P, _P], ctypes.c_int),
     "qec_state_len": ([_P], ctypes.c_uint64),
+    "qec_reconfigure": ([_P, ctypes.POINTER(qec_params)], ctypes.c_int),
     "qec_get_state": ([_P, _P, ctypes.c_size_t], ctypes.c_int),
     "qec_record_events": ([_P, ctypes.c_uint32], ctypes.c_int),
     "qec_get_events": ([_P, _P, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32)], ctypes.c_int),
@@ -109,6 +110,10 @@ def qec_run_trajectories(sim, seed, first_traj, n, syndromes_ptr, data_bits_ptr,
 
 def qec_run_trajectories_device(sim, seed, first_traj, n, d_syn_ptr, d_bits_ptr, d_log_ptr):
     return check(lib().qec_run_trajectories_device(sim, seed, first_traj, n, d_syn_ptr, d_bits_ptr, d_log_ptr))
+
+
+def qec_reconfigure(sim, params):
+    return check(lib().qec_reconfigure(sim, ctypes.byref(params)))
 
 
 def qec_state_len(sim):

@@ -36,6 +36,8 @@ qec_status fail(qec_status s, const std::string& msg) {
   } while (0)
 
 constexpr uint32_t kBatchCap = 1024;
+constexpr int kCtlRing = 8;          // pinned control headers in flight per simulator
+constexpr int kMaxRounds = 64;       // per-block buffers are sized for this many rounds
 
 }  // namespace
 
@@ -66,7 +68,10 @@ struct qec_sim {
   int* d_m = nullptr;
   double* d_partials = nullptr;
   Ctl* d_ctl = nullptr;
-  Ctl* h_ctl = nullptr;                        // pinned
+  Ctl* h_ctl = nullptr;                        // pinned ring of kCtlRing headers
+  cudaEvent_t ctl_ev[kCtlRing] = {};           // recorded after each header's H2D copy
+  int ctl_next = 0;
+  size_t ops_cap = 0;                          // ProgOp entries d_ops[1] holds
   double* d_hist_part = nullptr;
   double* d_hist = nullptr;
   uint8_t* d_syn = nullptr;
@@ -80,6 +85,8 @@ struct qec_sim {
   cudaGraph_t graph[2] = {nullptr, nullptr};
   cudaGraphExec_t gexec[2] = {nullptr, nullptr};
   bool ran = false;
+  int blk_cap = 0;      // blocks the Kraus/measurement buffers hold
+  int syn_cap = 0;      // bytes per trajectory the syndrome buffer holds
 
   int syn_stride() const { return (R + 1) * nstab; }
 };
@@ -94,7 +101,16 @@ qec_status dmalloc(T** p, size_t bytes) {
 
 qec_status upload_program(qec_sim* s, int which, const Program& P) {
   qec_status st;
-  if ((st = dmalloc(&s->d_ops[which], sizeof(ProgOp) * (P.ops.size() + 1))) != QEC_OK) return st;
+  size_t cap = P.ops.size() + 1;
+  if (which == 1) {   // room for every noise site and coherent op, so qec_reconfigure never reallocates
+    qec_params full = s->p;
+    full.noise = qec_noise{1, 1, 1, 1, 1, 1, 1, 1, 1};
+    Program F;
+    std::string err;
+    if (build_program(full, true, F, err) && F.ops.size() + 1 > cap) cap = F.ops.size() + 1;
+    s->ops_cap = cap;
+  }
+  if ((st = dmalloc(&s->d_ops[which], sizeof(ProgOp) * cap)) != QEC_OK) return st;
   if ((st = dmalloc(&s->d_blocks[which], sizeof(BlockInfo) * P.blocks.size())) != QEC_OK) return st;
   if ((st = dmalloc(&s->d_mats[which], sizeof(P.mats))) != QEC_OK) return st;
   if (!P.ops.empty())
@@ -155,8 +171,7 @@ qec_status run_init_round(qec_sim* s) {
     QEC_CUDA(launch_prob(s->p.precision, a, pass_grid_for(s->p.precision, true, s->D, a.w, s->num_sms), s->work));
     QEC_CUDA(launch_apply(s->p.precision, a, pass_grid_for(s->p.precision, false, s->D, a.w, s->num_sms), s->work));
   }
-  QEC_CUDA(cudaStreamSynchronize(s->work));
-  return QEC_OK;
+  return QEC_OK;   // no host wait: every later call is ordered after it on the same stream
 }
 
 PassArgs traj_pass(const qec_sim* s, int b) {
@@ -313,6 +328,7 @@ void free_all(qec_sim* s) {
   for (void* p : ptrs) if (p) cudaFree(p);
   if (s->h_ctl) cudaFreeHost(s->h_ctl);
   for (cudaEvent_t ev : s->kev) if (ev) cudaEventDestroy(ev);
+  for (cudaEvent_t ev : s->ctl_ev) if (ev) cudaEventDestroy(ev);
   if (s->ev_in) cudaEventDestroy(s->ev_in);
   if (s->ev_out) cudaEventDestroy(s->ev_out);
   if (s->work) cudaStreamDestroy(s->work);
@@ -345,14 +361,18 @@ qec_status create_impl(const qec_params* params, void* stream, qec_sim** out) {
   }
   cudaError_t e = cudaGetDevice(&s->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, s->device);
-  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->work, cudaStreamNonBlocking);
+  int prio = 0;   // the work stream inherits the caller's stream priority
+  if (e == cudaSuccess && s->user) e = cudaStreamGetPriority(s->user, &prio);
+  if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&s->work, cudaStreamNonBlocking, prio);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_in, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_out, cudaEventDisableTiming);
   for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaEventCreate(&s->kev[i]);
+  for (int i = 0; i < kCtlRing && e == cudaSuccess; ++i)
+    e = cudaEventCreateWithFlags(&s->ctl_ev[i], cudaEventDisableTiming);
   if (e == cudaSuccess) e = setup_kernels(s->p.precision, s->D);
   if (e != cudaSuccess) return bail(fail(QEC_ECUDA, std::string("CUDA setup: ") + cudaGetErrorString(e)));
   const size_t state_bytes = ((size_t)1 << s->D) * s->amp;
-  const int nblk = s->S > s->nstab ? s->S : s->nstab;
+  const int nblk = s->nstab * kMaxRounds;   // room for any round count (qec_reconfigure)
   const int k1 = hist_k1(s->D);
   if ((st = dmalloc(&s->psi, state_bytes)) || (st = dmalloc(&s->psi0, state_bytes)) ||
       (st = dmalloc(&s->d_kraus, (size_t)nblk * KRAUS_STRIDE * s->amp)) ||
@@ -362,12 +382,14 @@ qec_status create_impl(const qec_params* params, void* stream, qec_sim** out) {
       (st = dmalloc(&s->d_ctl, sizeof(Ctl))) ||
       (st = dmalloc(&s->d_hist_part, sizeof(double) * ((size_t)hist_grid(s->D, s->num_sms) << k1))) ||
       (st = dmalloc(&s->d_hist, sizeof(double) << k1)) ||
-      (st = dmalloc(&s->d_syn, (size_t)kBatchCap * s->syn_stride())) ||
+      (st = dmalloc(&s->d_syn, (size_t)kBatchCap * (kMaxRounds + 1) * s->nstab)) ||
       (st = dmalloc(&s->d_bits, (size_t)kBatchCap * s->D)) || (st = dmalloc(&s->d_log, kBatchCap)))
     return bail(st);
-  e = cudaMallocHost((void**)&s->h_ctl, sizeof(Ctl));
+  s->blk_cap = nblk;
+  s->syn_cap = (kMaxRounds + 1) * s->nstab;
+  e = cudaMallocHost((void**)&s->h_ctl, sizeof(Ctl) * kCtlRing);
   if (e != cudaSuccess) return bail(fail(QEC_ENOMEM, "pinned allocation failed"));
-  std::memset(s->h_ctl, 0, sizeof(Ctl));
+  std::memset(s->h_ctl, 0, sizeof(Ctl) * kCtlRing);
   e = cudaMemcpy(s->d_ctl, s->h_ctl, sizeof(Ctl), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return bail(fail(QEC_ECUDA, cudaGetErrorString(e)));
   if ((st = upload_program(s, 0, s->init_prog)) || (st = upload_program(s, 1, s->prog))) return bail(st);
@@ -389,15 +411,20 @@ qec_status run_impl(qec_sim* s, uint64_t seed, uint64_t first, uint32_t n, uint8
   const size_t ss = (size_t)s->syn_stride(), bs = (size_t)s->D;
   for (uint32_t done = 0; done < n;) {
     const uint32_t chunk = (n - done) < kBatchCap ? (n - done) : kBatchCap;
-    QEC_CUDA(cudaStreamSynchronize(s->work));   // h_ctl is reused below
-    s->h_ctl->seed = seed;
-    s->h_ctl->first = first + done;
-    s->h_ctl->traj = first + done;
-    s->h_ctl->ticket = 0;
-    s->h_ctl->ev_cap = s->ev_cap;
+    if (done > 0) QEC_CUDA(cudaStreamSynchronize(s->work));   // the device output batch is reused
+    const int slot = s->ctl_next;
+    s->ctl_next = (s->ctl_next + 1) % kCtlRing;
+    QEC_CUDA(cudaEventSynchronize(s->ctl_ev[slot]));          // this header's previous copy is done
+    Ctl* h = s->h_ctl + slot;
+    h->seed = seed;
+    h->first = first + done;
+    h->traj = first + done;
+    h->ticket = 0;
+    h->ev_cap = s->ev_cap;
     const size_t head = done == 0 ? offsetof(Ctl, pad) : offsetof(Ctl, ticket);   // events reset per call
-    if (done == 0) s->h_ctl->n_events = 0;
-    QEC_CUDA(cudaMemcpyAsync(s->d_ctl, s->h_ctl, head, cudaMemcpyHostToDevice, s->work));
+    if (done == 0) h->n_events = 0;
+    QEC_CUDA(cudaMemcpyAsync(s->d_ctl, h, head, cudaMemcpyHostToDevice, s->work));
+    QEC_CUDA(cudaEventRecord(s->ctl_ev[slot], s->work));
     for (uint32_t t = 0; t < chunk; ++t) {
       st = launch_trajectory(s);
       if (st) return st;
@@ -497,6 +524,41 @@ qec_status qec_get_events(qec_sim* s, int32_t* host_events, uint32_t max_events,
   if (n > max_events) n = max_events;
   *count = n;
   if (n && host_events) QEC_CUDA(cudaMemcpy(host_events, s->d_events, (size_t)n * 5 * sizeof(int32_t), cudaMemcpyDeviceToHost));
+  return QEC_OK;
+}
+
+qec_status qec_reconfigure(qec_sim* s, const qec_params* params) {
+  if (!s || !params) return fail(QEC_EINVAL, "null argument");
+  std::string err;
+  if (!validate_params(*params, err)) return fail(QEC_EINVAL, err);
+  if (params->d != s->p.d || params->gates != s->p.gates || params->precision != s->p.precision ||
+      params->layout != s->p.layout)
+    return fail(QEC_EINVAL, "qec_reconfigure keeps d, gate set, precision and layout");
+  Program P;
+  if (!build_program(*params, true, P, err)) return fail(QEC_EINVAL, err);
+  if (params->rounds > kMaxRounds) return fail(QEC_EINVAL, "rounds exceed the simulator's capacity");
+  if (P.ops.size() + 1 > s->ops_cap) return fail(QEC_EINVAL, "program larger than the simulator's capacity");
+  QEC_CUDA(cudaStreamSynchronize(s->work));   // in-flight work still reads the old program
+  drop_graph(s);
+  const int S = s->nstab * params->rounds;
+  s->prog = P;
+  if (!P.ops.empty())
+    QEC_CUDA(cudaMemcpyAsync(s->d_ops[1], s->prog.ops.data(), sizeof(ProgOp) * P.ops.size(), cudaMemcpyHostToDevice,
+                             s->work));
+  QEC_CUDA(cudaMemcpyAsync(s->d_blocks[1], s->prog.blocks.data(), sizeof(BlockInfo) * P.blocks.size(),
+                           cudaMemcpyHostToDevice, s->work));
+  QEC_CUDA(cudaMemcpyAsync(s->d_mats[1], s->prog.mats, sizeof(P.mats), cudaMemcpyHostToDevice, s->work));
+  QEC_CUDA(cudaStreamSynchronize(s->work));   // the host copies in s->prog must outlive the uploads
+  s->p = *params;
+  s->R = params->rounds;
+  s->S = S;
+  s->timed_block = -1;
+  if (s->R > 0) {
+    const int rnd = (s->R + 1) / 2;
+    for (int k = 0; k < s->nstab && s->timed_block < 0; ++k)
+      if (s->prog.blocks[k].w == 4) s->timed_block = (rnd - 1) * s->nstab + k;
+  }
+  s->ran = false;
   return QEC_OK;
 }
 

@@ -780,8 +780,11 @@ cudaError_t launch_set_basis0(int precision, void* psi, int D, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// Function attributes are per process, not per simulator: always set the ceiling for the
+// largest supported register (d = 5), so simulators of different sizes can coexist.
 cudaError_t setup_kernels(int precision, int D) {
-  const int smem = (int)sample_smem(D);
+  (void)D;
+  const int smem = (int)sample_smem(25);
   if (precision == QEC_C128) {
     cudaError_t e = cudaFuncSetAttribute(k_sample<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     return e != cudaSuccess ? e : fused_attrs<double>();

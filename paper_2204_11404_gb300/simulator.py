@@ -19,6 +19,14 @@ class Simulator:
         self.params = capi.make_params(d, rounds, gates, precision, **noise)
         self.h = capi.qec_create(self.params, ctypes.c_void_p(stream) if stream else None)
 
+    def reconfigure(self, rounds, **noise):
+        """New noise parameters and round count; d, gate set and precision stay."""
+        g = {capi.QEC_GATES_CNOT: "cnot", capi.QEC_GATES_CR: "cr"}[self.params.gates]
+        pr = {capi.QEC_C128: "c128", capi.QEC_C64: "c64"}[self.params.precision]
+        params = capi.make_params(self.d, rounds, g, pr, **noise)
+        capi.qec_reconfigure(self.h, params)
+        self.params, self.rounds = params, int(rounds)
+
     def run(self, seed, first_traj, n):
         """Host outputs: syndromes [n][rounds+1][d^2-1], data_bits [n][d^2], raw_logical [n] (uint8)."""
         syn = np.zeros((n, self.rounds + 1, self.nstab), dtype=np.uint8)

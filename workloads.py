@@ -45,3 +45,21 @@ def batched_mix(n=8192, seed=4000, rounds=3):
     kinds = ["c128" if i % 2 == 0 else "c64" for i in range(n)]
     noise = [dict(p1=float(p[i]), p2=float(p[i]), p_idle=float(p[i]), theta_rx=float(th[i])) for i in range(n)]
     return list(range(n)), kinds, noise, rounds, seed
+
+
+def serving_trace(n_req=64, rate=50.0, seed=5000, max_traj=8, d_choices=(3, 5), precisions=("c64", "c128")):
+    """Poisson arrivals (mean `rate` per second) of jobs: d from d_choices, rounds U{1..10},
+    trajectories U{1..max_traj}, precision from `precisions`, noise p ~ U[1e-4, 1e-2] on every
+    step and theta_rx ~ U[0, 0.1] rad, cross-resonance gate set.  Returns a list of dicts."""
+    import numpy as np
+
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(1.0 / rate, n_req))
+    jobs = []
+    for i in range(n_req):
+        p = float(rng.uniform(1e-4, 1e-2))
+        jobs.append(dict(jid=i, d=int(rng.choice(d_choices)), rounds=int(rng.integers(1, 11)),
+                         n_traj=int(rng.integers(1, max_traj + 1)), precision=str(rng.choice(precisions)),
+                         noise=dict(p1=p, p2=p, p_idle=p, theta_rx=float(rng.uniform(0, 0.1))),
+                         seed=seed + i, first_traj=0, arrival=float(t[i])))
+    return jobs

@@ -39,7 +39,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=9)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--precision", default="c128", choices=["c128", "c64"])
+    ap.add_argument("--precision", default="c128", choices=["c128", "c64", "c64tc"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--points", type=int, default=9, help="noise points used (1..9); fewer = smaller device footprint")
     ap.add_argument("--workload", default="d5", choices=["d5", "batched", "serve"],
@@ -284,8 +284,10 @@ def native_arm(args, rank, world, local):
                 "unit": "GB/s"}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["traffic"] = traffic_record(args.precision)
-    roof["kernel"] = ("k_apply<double,4> (weight-4 block, 2^25 amplitudes)" if args.precision == "c128" else
-                      "k_fused<float,4,4> (apply weight-4 block + next block's probability, 2^25 amplitudes)")
+    roof["kernel"] = {"c128": "k_apply<double,4> (weight-4 block, 2^25 amplitudes)",
+                      "c64": "k_fused<float,4,4> (apply weight-4 block + next block's probability, 2^25 amplitudes)",
+                      "c64tc": "k_fused_tc (tcgen05 3xTF32: apply weight-4 block + next probability, 2^25 amplitudes)",
+                      }[args.precision]
     roof["ms_apply"] = ms_apply
     roof["ms_prob"] = ms_prob
     roof["apply_hbm_gbs"] = bytes_apply / (ms_apply * 1e-3) / 1e9
@@ -295,7 +297,7 @@ def native_arm(args, rank, world, local):
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "c128" else "f32",
+        "scaling": "weak", "vs_baseline": None, "dtype": {"c128": "f64", "c64": "f32", "c64tc": "tf32x3"}[args.precision],
         "data": "synthetic", "config": workload_config(args, world), "clocks": clk.summary(),
         "e2e": e2e, "gpu_launches": launches_per_traj * args.steps, "roofline": roof,
     }

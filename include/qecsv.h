@@ -36,8 +36,10 @@ typedef enum { QEC_LAYOUT_REDUCED = 0, QEC_LAYOUT_UNREDUCED = 1 } qec_layout;
 typedef enum { QEC_GATES_CNOT = 0, QEC_GATES_CR = 1 } qec_gateset;
 
 /* Amplitude storage / arithmetic.  C128: complex128 state, FP64 arithmetic.
- * C64: complex64 state, FP32 gate arithmetic, FP64 probability reductions. */
-typedef enum { QEC_C128 = 0, QEC_C64 = 1 } qec_precision;
+ * C64: complex64 state, FP32 gate arithmetic, FP64 probability reductions.
+ * C64_TC: complex64 state; weight-4 block contractions on the tensor cores
+ * (3xTF32 split, FP32 accumulation), FP64 probability reductions. */
+typedef enum { QEC_C128 = 0, QEC_C64 = 1, QEC_C64_TC = 2 } qec_precision;
 
 /* Noise (Sec. III.A).  Probabilities in [0, 1]; angles in radians, |angle| <= 4. */
 typedef struct {

@@ -183,7 +183,7 @@ PassArgs traj_pass(const qec_sim* s, int b) {
 // The complex64 form fuses block b's apply pass with block b+1's probability pass (one HBM
 // read + write per stabilizer); complex128 keeps them separate (both passes are FP64-ALU
 // bound, so fusing saves nothing there).
-bool fused_mode(const qec_sim* s) { return s->p.precision == QEC_C64; }
+bool fused_mode(const qec_sim* s) { return s->p.precision != QEC_C128; }
 
 qec_status enqueue_prob(qec_sim* s, int b) {
   PassArgs a = traj_pass(s, b);
@@ -438,7 +438,12 @@ qec_status run_impl(qec_sim* s, uint64_t seed, uint64_t first, uint32_t n, uint8
     QEC_CUDA(cudaEventRecord(s->ev_out, s->work));
     QEC_CUDA(cudaStreamWaitEvent(s->user, s->ev_out, 0));
   }
-  if (host_out) QEC_CUDA(cudaStreamSynchronize(s->work));
+  if (host_out) {
+    QEC_CUDA(cudaStreamSynchronize(s->work));
+    unsigned int status = 0;
+    QEC_CUDA(cudaMemcpy(&status, &s->d_ctl->status, sizeof(status), cudaMemcpyDeviceToHost));
+    if (status) return fail(QEC_ETIMEOUT, "a bounded device wait gave up; results are invalid");
+  }
   QEC_CUDA(cudaGetLastError());
   if (n) s->ran = true;
   return QEC_OK;

@@ -475,6 +475,266 @@ __global__ void __launch_bounds__(256) k_fused(FusedArgs f) {
   finish_prob(f.pr, accA, accN, sred, &s_last);
 }
 
+// ---- tensor-core complex64 fused pass (tcgen05, 3xTF32, FP32 accumulation in TMEM) --------
+// A weight-4 block's 16x16 complex matrix acts on every 16-amplitude group of a tile as a real
+// GEMM: rows = groups (M = 256 per tile, two M = 128 MMAs), K = 32 input reals (re, im
+// interleaved), N = 32 output reals, B[n][k] = real embedding of the matrix.  Operands are
+// split x = hi + lo in TF32 and D = Ahi.Bhi + Ahi.Blo + Alo.Bhi, accumulated in FP32 in
+// tensor memory.  The probability pass of the next block is the same GEMM with its K1 on
+// the regrouped tile, reduced as sum |D|^2.
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor: K-major, no swizzle, 8-row x 16-byte core matrices.
+__device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = (uint64_t)((addr & 0x3FFFF) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+  d |= 1ull << 46;   // descriptor version of sm_100-class tensor cores
+  return d;
+}
+
+// Float index of element (row r, k) of a K = 32 operand: core matrix (r/8, k/4) of 32 floats.
+__device__ __forceinline__ int core_off32(int r, int k) { return ((r >> 3) * 8 + (k >> 2)) * 32 + (r & 7) * 4 + (k & 3); }
+
+__device__ __forceinline__ float tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// TF32 MMA M = 128, N = 32, D = F32, A and B K-major.
+constexpr uint32_t kIdescTf32 = (1u << 4) | (2u << 7) | (2u << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
+
+__device__ __forceinline__ void umma_tf32(uint32_t d_tmem, uint64_t ad, uint64_t bd, uint32_t acc) {
+  asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+               " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
+               ::"r"(d_tmem), "l"(ad), "l"(bd), "r"(kIdescTf32), "r"(acc));
+}
+
+// Bounded wait for an mbarrier phase; false if it gave up.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+  for (long it = 0; it < 40000000; ++it) {
+    uint32_t done;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(done) : "r"(mbar), "r"(parity) : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+               "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                 "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+                 "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+                 "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// Writes the 3xTF32-split real embedding of a 16x16 complex matrix (times scale) as B operands.
+__device__ void build_b(const float2* Kg, double scale, float* Bhi, float* Blo) {
+  for (int idx = threadIdx.x; idx < 32 * 32; idx += blockDim.x) {
+    const int n = idx >> 5, k = idx & 31, r = n >> 1, c = k >> 1;
+    const float2 kv = Kg[r * 16 + c];
+    const double re = (double)kv.x * scale, im = (double)kv.y * scale;
+    const float v = (float)((n & 1) ? ((k & 1) ? re : im) : ((k & 1) ? -im : re));
+    const float hi = tf32_rna(v);
+    Bhi[core_off32(n, k)] = hi;
+    Blo[core_off32(n, k)] = tf32_rna(v - hi);
+  }
+}
+
+// Two complex amplitudes = reals k .. k+3 of one row (k % 4 == 0): one 16-byte store per operand.
+__device__ __forceinline__ void put_a4(float* Ahi, float* Alo, int row, int k, float2 a, float2 b) {
+  float4 h, l;
+  h.x = tf32_rna(a.x); l.x = tf32_rna(a.x - h.x);
+  h.y = tf32_rna(a.y); l.y = tf32_rna(a.y - h.y);
+  h.z = tf32_rna(b.x); l.z = tf32_rna(b.x - h.z);
+  h.w = tf32_rna(b.y); l.w = tf32_rna(b.y - h.w);
+  *reinterpret_cast<float4*>(Ahi + core_off32(row, k)) = h;
+  *reinterpret_cast<float4*>(Alo + core_off32(row, k)) = l;
+}
+
+// 2 M-halves x 4 K-steps x 3 split terms; commit arrives on mbar.
+__device__ __forceinline__ void issue_gemm(uint32_t tmem, const float* Ahi, const float* Alo, const float* Bhi,
+                                           const float* Blo, uint32_t mbar) {
+  const uint32_t ah = smem_u32(Ahi), al = smem_u32(Alo), bh = smem_u32(Bhi), bl = smem_u32(Blo);
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const uint32_t d = tmem + 32u * h;
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      const uint32_t ko = 256u * s, mo = 16384u * h;
+      umma_tf32(d, umma_desc(ah + mo + ko, 128, 1024), umma_desc(bh + ko, 128, 1024), s > 0);
+      umma_tf32(d, umma_desc(ah + mo + ko, 128, 1024), umma_desc(bl + ko, 128, 1024), 1);
+      umma_tf32(d, umma_desc(al + mo + ko, 128, 1024), umma_desc(bh + ko, 128, 1024), 1);
+    }
+  }
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
+}
+
+__device__ __forceinline__ void tc_sync() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Shared memory: one 32 KiB tile, 3xTF32 A operands (2 x 32 KiB), four 4 KiB B operands,
+// 113 KiB in all, so two CTAs share an SM and one's tensor-core phases overlap the other's
+// memory phases.  Tile addresses are computed from the bit lists (no offset table).
+constexpr int kTcSmem = 8 * 4096 + 2 * 4 * 256 * 32 + 4 * 4 * 32 * 32;
+
+__global__ void __launch_bounds__(256, 2) k_fused_tc(FusedArgs f) {
+  constexpr int C = 16;
+  extern __shared__ __align__(128) unsigned char tsm[];
+  const uint32_t tsz = 1u << f.nt, lmask = (1u << f.lb) - 1u;     // tsz = 4096 (checked by the launcher)
+  float2* tile = reinterpret_cast<float2*>(tsm);
+  float* Ahi = reinterpret_cast<float*>(tile + tsz);
+  float* Alo = Ahi + 256 * 32;
+  float* Bahi = Alo + 256 * 32;
+  float* Balo = Bahi + 32 * 32;
+  float* Bphi = Balo + 32 * 32;
+  float* Bplo = Bphi + 32 * 32;
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_base;
+  __shared__ int s_err;
+  __shared__ double sred[64];
+  __shared__ int s_last;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  {
+    const int m = *f.ap.m;
+    const double scale = 1.0 / sqrt(*f.ap.N);
+    build_b(reinterpret_cast<const float2*>(f.ap.kraus) + (m ? 256 : 0), scale, Bahi, Balo);
+    build_b(reinterpret_cast<const float2*>(f.pr.kraus) + 256, 1.0, Bphi, Bplo);
+    if (tid == 0) {
+      s_err = 0;
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(smem_u32(&tmem_base)));
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  tc_sync();
+  const uint32_t tmem = tmem_base;
+  const uint32_t mb = smem_u32(&mbar);
+  int qa[4], qp[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    qa[j] = f.qa[j];
+    qp[j] = f.qp[j];
+  }
+  uint32_t offa[C], offp[C];
+#pragma unroll
+  for (int l = 0; l < C; ++l) {
+    offa[l] = member_off<4>(l, qa);
+    offp[l] = member_off<4>(l, qp);
+  }
+  // this thread's 16-byte chunks of a tile: chunk e = tid*2 + 512*i, i < 8; register offsets of their
+  // high tile bits are the same for every tile
+  uint32_t coff[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const uint32_t e = (uint32_t)tid * 2 + 512u * i, h = e >> f.lb;
+    uint32_t o = 0;
+    for (int j = 0; j < f.nt - f.lb; ++j) o |= ((h >> j) & 1u) << f.hbits[j];
+    coff[i] = o | (e & lmask);
+  }
+  const int trow = 128 * (warp >> 2) + 32 * (warp & 3) + lane;
+  const uint32_t taddr = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + 32u * (warp >> 2);
+  const float2* src = reinterpret_cast<const float2*>(f.ap.src);
+  float2* dst = reinterpret_cast<float2*>(f.ap.dst);
+  const uint32_t ntile = 1u << f.nout;
+  double accA = 0.0, accN = 0.0;
+  uint32_t phase = 0;
+  auto tile_base = [&](uint32_t tix) {
+    uint32_t tb = 0;
+    for (int j = 0; j < f.nout; ++j) tb |= ((tix >> j) & 1u) << f.obits[j];
+    return tb;
+  };
+  auto load_tile = [&](uint32_t tix) {
+    const uint32_t tb = tile_base(tix);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) cp_async16(tile + tid * 2 + 512 * i, src + (tb | coff[i]));
+    cp_async_commit();
+  };
+  if (blockIdx.x < ntile) load_tile(blockIdx.x);
+  for (uint32_t tix = blockIdx.x; tix < ntile; tix += gridDim.x) {
+    const uint32_t tb = tile_base(tix);
+    cp_async_wait<0>();
+    __syncthreads();
+    {
+      const uint32_t b = local_base<4>((uint32_t)tid, qa);
+#pragma unroll
+      for (int l = 0; l < C; l += 2) put_a4(Ahi, Alo, tid, 2 * l, tile[b + offa[l]], tile[b + offa[l + 1]]);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    tc_sync();
+    if (tid == 0) issue_gemm(tmem, Ahi, Alo, Bahi, Balo, mb);
+    if (!mbar_wait(mb, phase & 1)) s_err = 1;
+    ++phase;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (s_err) break;
+    {
+      float d[32];
+      tmem_ld32(taddr, d);
+      const uint32_t b = local_base<4>((uint32_t)trow, qa);
+#pragma unroll
+      for (int r = 0; r < C; ++r) tile[b + offa[r]] = make_float2(d[2 * r], d[2 * r + 1]);
+    }
+    tc_sync();
+    {
+      const uint32_t b = local_base<4>((uint32_t)tid, qp);
+      float sn = 0.f;
+#pragma unroll
+      for (int l = 0; l < C; l += 2) {
+        const float2 v0 = tile[b + offp[l]], v1 = tile[b + offp[l + 1]];
+        sn = fmaf(v0.x, v0.x, fmaf(v0.y, v0.y, sn));
+        sn = fmaf(v1.x, v1.x, fmaf(v1.y, v1.y, sn));
+        put_a4(Ahi, Alo, tid, 2 * l, v0, v1);
+      }
+      accN += (double)sn;
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    tc_sync();
+    if (tid == 0) issue_gemm(tmem, Ahi, Alo, Bphi, Bplo, mb);
+    // while the tensor cores work on the probability GEMM: write the updated tile out and
+    // start loading the next one into the same buffer
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+      *reinterpret_cast<float4*>(dst + (tb | coff[i])) = *reinterpret_cast<const float4*>(tile + tid * 2 + 512 * i);
+    __syncthreads();
+    if (tix + gridDim.x < ntile) load_tile(tix + gridDim.x);
+    if (!mbar_wait(mb, phase & 1)) s_err = 1;
+    ++phase;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (s_err) break;
+    {
+      float d[32];
+      tmem_ld32(taddr, d);
+      float sa = 0.f;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) sa = fmaf(d[j], d[j], sa);
+      accA += (double)sa;
+    }
+    tc_sync();
+  }
+  cp_async_wait<0>();
+  tc_sync();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tmem));
+  if (s_err && tid == 0) atomicOr(&f.pr.ctl->status, 1u);
+  finish_prob(f.pr, accA, accN, sred, &s_last);
+}
+
 // ---- final Z readout (Sec. III.B): sequential per-qubit sampling -------------------------
 // Qubit j gets outcome [u_j < P(q_j = 1 | outcomes of qubits < j)].  The conditional
 // marginals of the low k1 qubits come from one histogram pass over the register; the
@@ -714,6 +974,7 @@ static cudaError_t fused_attrs() {
                         (const void*)k_fused<T, 4, 4>};
   for (const void* fn : fns) {
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kFusedSmemMax);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -753,6 +1014,16 @@ cudaError_t launch_fused(int precision, const PassArgs& ap, const PassArgs& pr, 
     f.qa[j] = j < ap.w ? tile_pos(ap.q[j], lb, f.hbits, nh) : 0;
     f.qp[j] = j < pr.w ? tile_pos(pr.q[j], lb, f.hbits, nh) : 0;
   }
+  if (precision == QEC_C64_TC && ap.w == 4 && pr.w == 4 && f.nt == 12) {
+    const size_t tsmem = kTcSmem;
+    // sized for two resident CTAs per SM (113 KiB each; the occupancy query under-reports this
+    // shape), capped by the tile count
+    int64_t g = 2ll * num_sms;
+    if (g > (1ll << f.nout)) g = 1ll << f.nout;
+    f.grid = (int)(g < MAX_PASS_GRID ? g : MAX_PASS_GRID);
+    k_fused_tc<<<f.grid, 256, tsmem, s>>>(f);
+    return cudaGetLastError();
+  }
   const size_t smem = 2 * amp * ((size_t)1 << f.nt) + sizeof(uint32_t) * ((size_t)1 << nh);
   if (smem > (size_t)kFusedSmemMax) return cudaErrorInvalidValue;
   const int key = (ap.w == 4 ? 2 : 0) + (pr.w == 4 ? 1 : 0);
@@ -790,7 +1061,10 @@ cudaError_t setup_kernels(int precision, int D) {
     return e != cudaSuccess ? e : fused_attrs<double>();
   }
   cudaError_t e = cudaFuncSetAttribute(k_sample<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  return e != cudaSuccess ? e : fused_attrs<float>();
+  if (e == cudaSuccess) e = fused_attrs<float>();
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fused_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kFusedSmemMax);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fused_tc, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  return e;
 }
 
 // ---- host instantiation (test hook; same op arithmetic as inst_block) -------------------

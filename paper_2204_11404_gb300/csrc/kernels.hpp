@@ -19,6 +19,8 @@ struct Ctl {
   unsigned int ev_cap;
   unsigned int pad;
   double final_norm;            // sum |psi|^2 of the state the readout sampled
+  unsigned int status;          // bit 0: a bounded device wait gave up (results invalid)
+  unsigned int pad2;
 };
 
 constexpr int KRAUS_STRIDE = 768;   // per block: K0, K1, M = K1^dagger K1, 16x16 each

@@ -115,7 +115,10 @@ bool validate_params(const qec_params& p, std::string& err) {
   if (p.rounds < 0 || p.rounds > 64) { err = "rounds must be in [0, 64]"; return false; }
   if (p.layout != QEC_LAYOUT_REDUCED && p.layout != QEC_LAYOUT_UNREDUCED) { err = "bad layout"; return false; }
   if (p.gates != QEC_GATES_CNOT && p.gates != QEC_GATES_CR) { err = "bad gate set"; return false; }
-  if (p.precision != QEC_C128 && p.precision != QEC_C64) { err = "bad precision"; return false; }
+  if (p.precision != QEC_C128 && p.precision != QEC_C64 && p.precision != QEC_C64_TC) {
+    err = "bad precision";
+    return false;
+  }
   if (p.reserved != 0) { err = "reserved must be 0"; return false; }
   const qec_noise& n = p.noise;
   if (!finite_in(n.p1, 0, 1) || !finite_in(n.p2, 0, 1) || !finite_in(n.p_idle, 0, 1)) {

@@ -120,7 +120,7 @@ def _d5_oracle():
     return _D5["o"]
 
 
-@pytest.mark.parametrize("prec", ["c128", "c64"])
+@pytest.mark.parametrize("prec", ["c128", "c64", "c64tc"])
 def test_d5_full_size_trajectory_matches_oracle(prec):
     pt, seed, o = _d5_oracle()
     with Simulator(5, 5, "cr", prec, **pt) as sim:
@@ -131,6 +131,7 @@ def test_d5_full_size_trajectory_matches_oracle(prec):
             assert kind == "exact"
         if kind == "exact":
             ref = o["state"][: 1 << 25]
+            _D5["err_" + prec] = float(np.abs(sim.state() - ref).max())
             assert np.abs(o["state"][1 << 25:]).max() == 0
             assert np.abs(sim.state() - ref).max() < AMP_TOL[prec]
             ev = sorted(tuple(int(x) for x in e[1:]) for e in sim.events())

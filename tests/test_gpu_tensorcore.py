@@ -1,0 +1,41 @@
+"""Tensor-core complex64 form: weight-4 block contractions on tcgen05 (3xTF32, FP32
+accumulation).  Checked against the FP64 oracle and against the CUDA-core complex64 form
+on d=5 trajectories (the tensor-core pass needs 4096-amplitude tiles, so d=5)."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import run_trajectory
+from parity_util import AMP_TOL, TAU, compare_trajectory
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2204_11404_gb300.simulator import Simulator  # noqa: E402
+
+
+def test_tensor_core_form_matches_oracle_two_rounds():
+    pt = dict(W.STRESS)
+    o = run_trajectory(5, 2, "cr", "reduced", pt, seed=42, traj=3, want_state=True)
+    with Simulator(5, 2, "cr", "c64tc", **pt) as sim:
+        syn, bits, log = sim.run(42, 3, 1)
+        kind = compare_trajectory(syn[0], bits[0], o, TAU["c64tc"])
+        if kind == "exact":
+            err = np.abs(sim.state() - o["state"][: 1 << 25]).max()
+            assert err < AMP_TOL["c64tc"], err
+
+
+def test_tensor_core_form_agrees_with_cuda_core_form():
+    pts = W.D5_CR["points"]
+    agree = 0
+    for i in (2, 5, 8):
+        with Simulator(5, 5, "cr", "c64tc", **pts[i]) as a, Simulator(5, 5, "cr", "c64", **pts[i]) as b:
+            ra = a.run(2000 + i, 0, 2)
+            rb = b.run(2000 + i, 0, 2)
+            agree += int(all((x == y).all() for x, y in zip(ra, rb)))
+            sa, sb = a.state(), b.state()
+            assert np.abs(sa - sb).max() < 2 * AMP_TOL["c64"]
+    assert agree >= 2

@@ -1,0 +1,84 @@
+"""Host decoder on oracle trajectories (CPU): detection events, single-error correction, and the
+code-distance scaling of the logical error rate."""
+import numpy as np
+import pytest
+
+from oracle import run_trajectory
+from oracle import gates as G
+from oracle.lattice import stabilizers
+from paper_2204_11404_gb300.decoder import Decoder
+
+
+def test_z_stabilizers_match_table1_order():
+    zs = [s["support"] for s in stabilizers(5) if s["kind"] == "Z"]
+    assert Decoder(5).zs == zs
+
+
+@pytest.mark.parametrize("gates", ["cnot", "cr"])
+def test_noiseless_has_no_events_and_no_failure(gates):
+    dec = Decoder(3)
+    r = run_trajectory(3, 3, gates, "reduced", {}, seed=0, traj=0)
+    assert dec.detection_events(r["syndromes"], r["data_bits"]) == []
+    assert dec.logical_failure(r["syndromes"], r["data_bits"], r["raw_logical"]) == 0
+
+
+@pytest.mark.parametrize("gates", ["cnot", "cr"])
+@pytest.mark.parametrize("rnd", [1, 2])
+def test_any_single_x_error_is_corrected_d3(gates, rnd):
+    dec = Decoder(3)
+    for q in range(9):
+        r = run_trajectory(3, 2, gates, "reduced", {}, seed=0, traj=q, inject=[(rnd, 0, q, G.PX)])
+        ev = dec.detection_events(r["syndromes"], r["data_bits"])
+        assert 1 <= len(ev) <= 2
+        assert dec.logical_failure(r["syndromes"], r["data_bits"], r["raw_logical"]) == 0
+
+
+def test_single_x_error_before_readout_is_corrected_d5():
+    # an X on a data qubit right before readout shows only in the final (data-derived) events;
+    # d=5 state vectors are large for the CPU suite, so the record is built directly
+    dec = Decoder(5)
+    syn = np.zeros((3, 24), dtype=np.uint8)
+    for q in range(25):
+        bits = np.zeros(25, dtype=np.uint8)
+        bits[q] = 1
+        raw = int(bits[:5].sum() % 2)
+        ev = dec.detection_events(syn, bits)
+        assert all(r == 2 for r, _ in ev) and 1 <= len(ev) <= 2
+        assert dec.logical_failure(syn, bits, raw) == 0
+
+
+def test_measurement_error_pairs_in_time():
+    dec = Decoder(3)
+    syn = np.zeros((4, 8), dtype=np.uint8)
+    syn[2, 5] = 1                                   # one Z-stabilizer misread in round 2 only
+    bits = np.zeros(9, dtype=np.uint8)
+    assert dec.detection_events(syn, bits) == [(1, 1), (2, 1)]
+    assert dec.logical_failure(syn, bits, 0) == 0
+
+
+def test_distance_three_corrects_one_error_but_not_two_on_a_column():
+    # X on two of the three qubits of the first column: the minimal completion is the third qubit,
+    # which makes logical X (a column), so the decoder fails; one error is corrected
+    dec = Decoder(3)
+    syn = np.zeros((2, 8), dtype=np.uint8)
+    one = np.array([1, 0, 0, 0, 0, 0, 0, 0, 0], dtype=np.uint8)
+    two = np.array([1, 0, 0, 1, 0, 0, 0, 0, 0], dtype=np.uint8)
+    assert dec.logical_failure(syn, one, int(one[:3].sum() % 2)) == 0
+    assert dec.logical_failure(syn, two, int(two[:3].sum() % 2)) == 1
+    # X on two qubits of the top row is the X-stabilizer X1X2 of Table I's rule: no failure
+    stab = np.array([1, 1, 0, 0, 0, 0, 0, 0, 0], dtype=np.uint8)
+    assert dec.detection_events(syn, stab) == []
+    assert dec.logical_failure(syn, stab, int(stab[:3].sum() % 2)) == 0
+
+
+def test_logical_error_rate_grows_with_p_d3():
+    dec = Decoder(3)
+    rates = []
+    for p in (0.004, 0.03):
+        nz = dict(p1=p, p2=p, p_idle=p)
+        f = []
+        for t in range(60):
+            r = run_trajectory(3, 2, "cr", "reduced", nz, seed=21, traj=t)
+            f.append(dec.logical_failure(r["syndromes"], r["data_bits"], r["raw_logical"]))
+        rates.append(np.mean(f))
+    assert rates[0] < rates[1]

@@ -42,7 +42,7 @@ def parse():
     ap.add_argument("--precision", default="c128", choices=["c128", "c64", "c64tc"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--points", type=int, default=9, help="noise points used (1..9); fewer = smaller device footprint")
-    ap.add_argument("--workload", default="d5", choices=["d5", "batched", "serve"],
+    ap.add_argument("--workload", default="d5", choices=["d5", "batched", "serve", "precision", "sweep"],
                     help="d5: the d=5 26-qubit trajectories (default); batched: 8192 d=3 trajectories per "
                          "launch; serve: Poisson trace of mixed jobs through the continuous-batching server")
     ap.add_argument("--requests", type=int, default=64, help="serve: requests in the trace")
@@ -397,6 +397,72 @@ def serve_arm(args, rank, world, local):
         print(json.dumps(out))
 
 
+def precision_arm(args, rank, world, local):
+    """Per noise point of the d=5 workload: the same trajectories in complex128 (which matches the FP64
+    oracle bit for bit and to 1e-12), complex64 and complex64/tensor-core; reports syndrome agreement,
+    max amplitude deviation of the last trajectory's state, and decoded logical error rates."""
+    import numpy as np
+    import torch
+
+    from paper_2204_11404_gb300.decoder import Decoder
+    from paper_2204_11404_gb300.simulator import Simulator
+
+    torch.cuda.set_device(local)
+    n = max(1, args.steps)
+    dec = Decoder(5)
+    rows = []
+    for i, pt in enumerate(W.D5_CR["points"]):
+        seed = W.D5_CR["seed_base"] + i
+        res = {}
+        for prec in ("c128", "c64", "c64tc"):
+            with Simulator(5, W.D5_CR["rounds"], "cr", prec, **pt) as sim:
+                syn, bits, log = sim.run(seed, 0, n)
+                res[prec] = (syn, bits, log, sim.state())
+        ref = res["c128"]
+        row = {"p": pt["p1"], "theta_rx": pt["theta_rx"], "trajectories": n,
+               "pL_c128": dec.logical_error_rate(*ref[:3])}
+        for prec in ("c64", "c64tc"):
+            s, b, l, st = res[prec]
+            same = [bool((s[t] == ref[0][t]).all() and (b[t] == ref[1][t]).all()) for t in range(n)]
+            row[prec] = {"identical_trajectories": int(sum(same)), "pL": dec.logical_error_rate(s, b, l),
+                         "amp_maxabs_dev_last_traj": float(np.abs(st - ref[3]).max()) if same[-1] else None}
+        rows.append(row)
+    if rank == 0:
+        print(json.dumps({"metric": "precision forms vs complex128 per noise point (d=5, 5 rounds)",
+                          "unit": "per-point report", "data": "synthetic", "points": rows,
+                          "decoder_fallbacks": dec.fallbacks}))
+
+
+def sweep_arm(args, rank, world, local):
+    """Logical error rate p_L over (p, c) at d=5, 5 rounds (Sec. III.B-C): over-rotation
+    theta = 2 c sqrt(p) after every rotation gate (Rx/Rx^dagger and Rz), p on every step, decoded by
+    the host matcher; complex64 tensor-core form, --steps trajectories per point."""
+    import numpy as np
+    import torch
+
+    from paper_2204_11404_gb300.decoder import Decoder
+    from paper_2204_11404_gb300.simulator import Simulator
+
+    torch.cuda.set_device(local)
+    n = max(1, args.steps)
+    dec = Decoder(5)
+    rows = []
+    for c in (0.0, 0.5, 1.0):
+        for p in (1e-3, 2e-3, 3e-3, 5e-3):
+            th = 2 * c * np.sqrt(p)
+            nz = dict(p1=p, p2=p, p_idle=p, theta_rx=th, theta_rz=th)
+            with Simulator(5, 5, "cr", "c64tc", **nz) as sim:
+                syn, bits, log = sim.run(7000, rank * n, n)
+            f = [dec.logical_failure(a, b, l) for a, b, l in zip(syn, bits, log)]
+            k = int(np.sum(f))
+            rows.append({"c": c, "p": p, "trajectories": n, "failures": k, "pL": k / n,
+                         "pL_err": float(np.sqrt(max(k, 1) * (1 - k / n)) / n),
+                         "paper_fit_c0": 6.5e5 * p ** 2.92 if c == 0 else None})
+    if rank == 0:
+        print(json.dumps({"metric": "logical error rate p_L(p, c), d=5, 5 rounds", "unit": "per-point report",
+                          "data": "synthetic", "points": rows, "decoder_fallbacks": dec.fallbacks}))
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -406,6 +472,10 @@ def main():
         batched_arm(args, rank, world, local)
     elif args.workload == "serve":
         serve_arm(args, rank, world, local)
+    elif args.workload == "precision":
+        precision_arm(args, rank, world, local)
+    elif args.workload == "sweep":
+        sweep_arm(args, rank, world, local)
     else:
         native_arm(args, rank, world, local)
 

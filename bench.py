@@ -339,17 +339,19 @@ def batched_arm(args, rank, world, local):
     dev = sum(dev_ms) / 1e3
     n = len(traj)
     out = {
-        "metric": "batched d=3 trajectories/s (one persistent launch, c128+c64 mix)", "value": world * n * args.steps / dev,
+        "metric": "batched d=3 trajectories/s (one persistent launch: 10q/17q x c128/c64 mix)",
+        "value": world * n * args.steps / dev,
         "unit": "trajectories/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * dev / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64+f32", "data": "synthetic",
-        "config": {"workload": "8192 d=3 reduced 10-qubit trajectories per step, 3 rounds, cr gates, "
-                               "alternating complex128/complex64, p~U[1e-4,1e-2], theta_rx~U[0,0.1]",
+        "config": {"workload": "8192 d=3 trajectories per step in equal quarters: reduced 10-qubit and "
+                               "unreduced 17-qubit registers x complex128/complex64; 3 rounds, cr gates, "
+                               "p~U[1e-4,1e-2], theta_rx~U[0,0.1]",
                    "autotuned_warps_per_cta": warps, "rounds_per_s": world * n * rounds * args.steps / dev},
         "clocks": clk.summary(),
         "e2e": {"value": world * n * args.steps / wall, "unit": "trajectories/s",
                 "h2d_bytes_per_step": n * (8 + 4 + 72) + 16, "d2h_bytes_per_step": n * ((rounds + 1) * 8 + 9 + 1)},
-        "gpu_launches": args.steps,
+        "gpu_launches": 2 * args.steps,   # per step: the 10-qubit and the 17-qubit persistent kernels
     }
     if rank == 0:
         print(json.dumps(out))

@@ -187,8 +187,12 @@ qec_status qec_batch_create(int32_t d, int32_t rounds, int32_t gates, uint32_t m
 
 /*
  * Run n trajectories (Sec. III.B protocol, as qec_run_trajectories), each with
- * its own trajectory index traj[i], precision kind[i] (QEC_C128 or QEC_C64)
- * and noise parameters noise[i] (Sec. III.A).  Inputs and outputs are HOST
+ * its own trajectory index traj[i], kind[i] = precision (QEC_C128 or QEC_C64)
+ * + 2 * layout, and noise parameters noise[i] (Sec. III.A).  Layout
+ * QEC_LAYOUT_REDUCED runs the 10-qubit delayed register (one warp, Sec. II.B);
+ * QEC_LAYOUT_UNREDUCED runs all 17 qubits time-ordered, every ancilla of a part
+ * active at once (one CTA; the other part's ancillas are |0>, so a
+ * 2^13-amplitude slab holds the exact state).  Inputs and outputs are HOST
  * arrays: syndromes [n][rounds+1][8], data_bits [n][9], raw_logical [n] (any
  * output may be NULL).  Trajectory i equals qec_run_trajectories for
  * (noise[i], kind[i], seed, traj[i]).  Blocks until the outputs are on the host.

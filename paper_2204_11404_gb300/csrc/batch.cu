@@ -40,8 +40,10 @@ template <> struct C2<float> { using t = float2; };
 
 struct BatchCtl {
   uint64_t seed;
-  uint32_t n;                 // trajectories in this run
-  unsigned int counter;       // work queue head (zeroed before every run)
+  uint32_t n;                 // reduced-register (10-qubit) trajectories in this run
+  unsigned int counter;       // their work queue head (zeroed before every run)
+  uint32_t n_u;               // unreduced-register (17-qubit) trajectories in this run
+  unsigned int counter_u;     // their work queue head
 };
 
 struct BatchArgs {
@@ -51,7 +53,16 @@ struct BatchArgs {
   const BlockInfo* iblocks;
   const double* mats;         // static matrices [M_COUNT][16][2] (coherent entries overwritten per trajectory)
   const qec_noise* noise;     // [n]
-  const int32_t* kind;        // [n]: 0 = complex128, 1 = complex64
+  const int32_t* kind;        // [n]: bit 0 = complex64 (else complex128), bit 1 = unreduced register
+  const uint32_t* idx;        // reduced-register items of this run
+  const uint32_t* idx_u;      // unreduced-register items of this run
+  const ProgOp* uops;         // unreduced time-ordered program (one round)
+  const UItem* uitems;
+  int n_uitems;
+  const ProgOp* iuops;        // its noise-free init round
+  const UItem* iuitems;
+  int n_iuitems;
+  const void* psi0_u[2];      // unreduced init slab per precision
   const uint64_t* traj;       // [n]
   BatchCtl* ctl;
   int rounds;
@@ -246,7 +257,7 @@ __device__ void run_warp(const BatchArgs& a, unsigned char* wsm, uint32_t item) 
   if (init) {
     for (int i = lane; i < kNAmp; i += 32) psi[i] = mk<T2>(i == 0 ? 1.0 : 0.0, 0.0);
   } else {
-    const T2* p0 = reinterpret_cast<const T2*>(a.psi0[a.kind[item]]);
+    const T2* p0 = reinterpret_cast<const T2*>(a.psi0[a.kind[item] & 1]);
     for (int i = lane; i < kNAmp; i += 32) psi[i] = p0[i];
   }
   __syncwarp();
@@ -329,12 +340,249 @@ __global__ void k_batch(BatchArgs a) {
     return;
   }
   for (;;) {
-    uint32_t item = 0;
-    if ((threadIdx.x & 31) == 0) item = atomicAdd(&a.ctl->counter, 1u);
-    item = __shfl_sync(0xffffffffu, item, 0);
-    if (item >= a.ctl->n) return;
-    if (a.kind[item] == 0) run_warp<double>(a, wsm, item);
+    uint32_t pos = 0;
+    if ((threadIdx.x & 31) == 0) pos = atomicAdd(&a.ctl->counter, 1u);
+    pos = __shfl_sync(0xffffffffu, pos, 0);
+    if (pos >= a.ctl->n) return;
+    const uint32_t item = a.idx[pos];
+    if ((a.kind[item] & 1) == 0) run_warp<double>(a, wsm, item);
     else run_warp<float>(a, wsm, item);
+  }
+}
+
+// ---- unreduced register: one CTA per 17-qubit trajectory --------------------------------
+constexpr int kUBits = kND + kNStab / 2;      // 13 slab bits: 9 data + the active part's 4 ancillas
+constexpr int kUAmp = 1 << kUBits;            // 8192 amplitudes
+constexpr int kUSmem = kUAmp * 16 + M_COUNT * 16 * 16 + 16 * 16 + 64 * 8 + 16;   // slab, mats, F, reduction, flag
+
+template <typename T>
+__device__ void block_sum2_u(double& x, double& y, double* sh) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  x = wsum(x);
+  y = wsum(y);
+  __syncthreads();
+  if (lane == 0) { sh[w] = x; sh[32 + w] = y; }
+  __syncthreads();
+  x = 0.0;
+  y = 0.0;
+  for (int i = 0; i < nw; ++i) { x += sh[i]; y += sh[32 + i]; }   // fixed order, same in every thread
+  __syncthreads();
+}
+
+// One trajectory (or the noise-free init round) of the unreduced register on one CTA.
+template <typename T>
+__device__ void run_cta_u(const BatchArgs& a, unsigned char* sm, uint32_t item) {
+  using T2 = typename C2<T>::t;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  T2* slab = reinterpret_cast<T2*>(sm);
+  T2 (*mats)[16] = reinterpret_cast<T2 (*)[16]>(slab + kUAmp);
+  double2* F = reinterpret_cast<double2*>(mats + M_COUNT);         // fused unit matrix (FP64, 16 entries)
+  double* sh = reinterpret_cast<double*>(F + 16);                  // 64 doubles
+  int* sflag = reinterpret_cast<int*>(sh + 64);
+  const bool init = a.init_mode != 0;
+  const qec_noise nz = init ? qec_noise{} : a.noise[item];
+  const uint64_t traj = init ? 0ull : a.traj[item];
+  const uint64_t seed = a.ctl->seed;
+  const ProgOp* ops = init ? a.iuops : a.uops;
+  const UItem* items = init ? a.iuitems : a.uitems;
+  const int nitems = init ? a.n_iuitems : a.n_uitems;
+  const double prob[3] = {nz.p1, nz.p2, nz.p_idle};
+  for (int i = tid; i < M_COUNT * 16; i += nt) {
+    const int id = i / 16, e = i % 16;
+    mats[id][e] = mk<T2>(a.mats[(id * 16 + e) * 2], a.mats[(id * 16 + e) * 2 + 1]);
+  }
+  __syncthreads();
+  if (!init && tid < 32) coherent_mats(mats, nz, tid & 31);
+  if (init) {
+    for (int i = tid; i < kUAmp; i += nt) slab[i] = mk<T2>(i == 0 ? 1.0 : 0.0, 0.0);
+  } else {
+    const T2* p0 = reinterpret_cast<const T2*>(a.psi0_u[a.kind[item] & 1]);
+    for (int i = tid; i < kUAmp; i += nt) slab[i] = p0[i];
+  }
+  __syncthreads();
+  uint8_t* syn = init ? nullptr : a.syn + (size_t)item * (a.rounds + 1) * kNStab;
+  if (syn)
+    for (int k = tid; k < kNStab; k += nt) syn[k] = 0;
+  const int r_first = init ? 0 : 1, r_last = init ? 0 : a.rounds;
+  for (int rnd = r_first; rnd <= r_last; ++rnd) {
+    for (int it = 0; it < nitems; ++it) {
+      const UItem u = items[it];
+      if (u.kind == 0) {
+        // thread 0 fuses the unit: F = (Pauli) (coherent) (gate), applied in op order
+        if (tid == 0) {
+          const int dim = u.nq == 1 ? 2 : 4;
+          double2 M[16];
+          for (int i = 0; i < 16; ++i) M[i] = make_double2((i / 4 == i % 4) ? 1.0 : 0.0, 0.0);
+          int any = 0;
+          for (int oi = u.op_begin; oi < u.op_end; ++oi) {
+            const ProgOp op = ops[oi];
+            int code = 0;
+            if (op.kind == OP_N1 || op.kind == OP_N2) {
+              code = noise_code(op, prob[op.pidx], seed, traj, (uint64_t)rnd);
+              if (!code) continue;
+            }
+            // left-multiply M by this op's matrix G (dim x dim, embedded in the unit's local qubits)
+            double2 G[16];
+            for (int i = 0; i < 16; ++i) G[i] = make_double2(0.0, 0.0);
+            auto from_tab = [&](int id, int r, int c) {
+              return make_double2((double)mats[id][r * 4 + c].x, (double)mats[id][r * 4 + c].y);
+            };
+            if (dim == 2) {
+              const int id = op.kind == OP_U1 ? op.mat : code;
+              for (int r = 0; r < 2; ++r)
+                for (int c = 0; c < 2; ++c) G[r * 4 + c] = from_tab(id, r, c);
+            } else if (op.kind == OP_U2) {
+              for (int r = 0; r < 4; ++r)
+                for (int c = 0; c < 4; ++c) G[r * 4 + c] = from_tab(op.mat, r, c);
+            } else {
+              // one-qubit op or Pauli pair on a 2-qubit unit: local index 2*bit(qa) + bit(qb)
+              int ida = 0, idb = 0;
+              if (op.kind == OP_N2) { ida = code >> 2; idb = code & 3; }
+              else {
+                const int id = op.kind == OP_U1 ? op.mat : code;
+                if (op.q0 == u.qa) ida = id; else idb = id;
+              }
+              if (op.kind == OP_N2 && op.q0 != u.qa) { const int t = ida; ida = idb; idb = t; }
+              for (int ra = 0; ra < 2; ++ra)
+                for (int rb = 0; rb < 2; ++rb)
+                  for (int ca = 0; ca < 2; ++ca)
+                    for (int cb = 0; cb < 2; ++cb) {
+                      const double2 x = from_tab(ida, ra, ca), y = from_tab(idb, rb, cb);
+                      G[(2 * ra + rb) * 4 + 2 * ca + cb] = make_double2(x.x * y.x - x.y * y.y, x.x * y.y + x.y * y.x);
+                    }
+            }
+            double2 R[16];
+            for (int r = 0; r < dim; ++r)
+              for (int c = 0; c < dim; ++c) {
+                double re = 0.0, im = 0.0;
+                for (int k = 0; k < dim; ++k) {
+                  const double2 g = G[r * 4 + k], m = M[k * 4 + c];
+                  re += g.x * m.x - g.y * m.y;
+                  im += g.x * m.y + g.y * m.x;
+                }
+                R[r * 4 + c] = make_double2(re, im);
+              }
+            for (int r = 0; r < dim; ++r)
+              for (int c = 0; c < dim; ++c) M[r * 4 + c] = R[r * 4 + c];
+            any = 1;
+          }
+          for (int i = 0; i < 16; ++i) F[i] = M[i];
+          *sflag = any;
+        }
+        __syncthreads();
+        if (*sflag) {
+          T2 f[16];
+          for (int i = 0; i < 16; ++i) f[i] = mk<T2>(F[i].x, F[i].y);
+          if (u.nq == 1) {
+            const int b = u.qa;
+            for (int pr = tid; pr < kUAmp / 2; pr += nt) {
+              const int i0 = (int)ins0(pr, b), i1 = i0 | (1 << b);
+              const T2 x = slab[i0], y = slab[i1];
+              T2 o0 = mk<T2>(0, 0), o1 = mk<T2>(0, 0);
+              o0 = cmul_add<T>(o0, f[0], x); o0 = cmul_add<T>(o0, f[1], y);
+              o1 = cmul_add<T>(o1, f[4], x); o1 = cmul_add<T>(o1, f[5], y);
+              slab[i0] = o0;
+              slab[i1] = o1;
+            }
+          } else {
+            const int qa = u.qa, qb = u.qb, lo = qa < qb ? qa : qb, hi = qa < qb ? qb : qa;
+            for (int qd = tid; qd < kUAmp / 4; qd += nt) {
+              const int base = (int)ins0(ins0(qd, lo), hi);
+              int idx[4];
+              T2 x[4];
+              for (int l = 0; l < 4; ++l) {
+                idx[l] = base | ((l >> 1) << qa) | ((l & 1) << qb);
+                x[l] = slab[idx[l]];
+              }
+              for (int r = 0; r < 4; ++r) {
+                T2 acc = mk<T2>(0, 0);
+                for (int k = 0; k < 4; ++k) acc = cmul_add<T>(acc, f[r * 4 + k], x[k]);
+                slab[idx[r]] = acc;
+              }
+            }
+          }
+        }
+        __syncthreads();
+      } else {
+        // measurement of the ancilla at slab bit u.qa: Born rule, collapse, renormalise, reset
+        const int b = u.qa;
+        double s0 = 0.0, s1 = 0.0;
+        for (int pr = tid; pr < kUAmp / 2; pr += nt) {
+          const int i0 = (int)ins0(pr, b), i1 = i0 | (1 << b);
+          s0 += (double)slab[i0].x * slab[i0].x + (double)slab[i0].y * slab[i0].y;
+          s1 += (double)slab[i1].x * slab[i1].x + (double)slab[i1].y * slab[i1].y;
+        }
+        block_sum2_u<T>(s0, s1, sh);
+        int m;
+        if (init) {
+          m = u.offset;
+        } else {
+          const double uu = uniform53(draw(seed, traj, (uint64_t)rnd, 0u, (uint32_t)(kND + u.stab), TAG_MEASURE).v[0]);
+          m = uu < s1 / (s0 + s1) ? 1 : 0;
+        }
+        const double sc = 1.0 / sqrt(m ? s1 : s0);
+        for (int pr = tid; pr < kUAmp / 2; pr += nt) {
+          const int i0 = (int)ins0(pr, b), i1 = i0 | (1 << b);
+          const T2 kept = m ? slab[i1] : slab[i0];
+          slab[i0] = mk<T2>((double)kept.x * sc, (double)kept.y * sc);
+          slab[i1] = mk<T2>(0, 0);
+        }
+        __syncthreads();
+        if (syn && tid == 0) syn[rnd * kNStab + u.stab] = (uint8_t)(m ^ u.offset);
+      }
+    }
+  }
+  if (init) {
+    T2* out = reinterpret_cast<T2*>(a.init_out);
+    for (int i = tid; i < kUAmp; i += nt) out[i] = slab[i];
+    return;
+  }
+  // final Z readout of the data qubits (the ancillas are all |0>: slab entries 0..511)
+  uint8_t* bits = a.bits + (size_t)item * kND;
+  uint32_t prefix = 0;
+  for (int j = 0; j < kND; ++j) {
+    const uint32_t mask = (1u << j) - 1u;
+    double s_all = 0.0, s_one = 0.0;
+    for (int x = tid; x < kNAmp; x += nt) {
+      if ((x & mask) == prefix) {
+        const double pp = (double)slab[x].x * slab[x].x + (double)slab[x].y * slab[x].y;
+        s_all += pp;
+        if ((x >> j) & 1) s_one += pp;
+      }
+    }
+    block_sum2_u<T>(s_all, s_one, sh);
+    const double uu = uniform53(draw(seed, traj, (uint64_t)a.rounds + 1, 0u, (uint32_t)j, TAG_READOUT).v[0]);
+    const int bb = uu < s_one / s_all ? 1 : 0;
+    prefix |= (uint32_t)bb << j;
+    if (tid == 0) bits[j] = (uint8_t)bb;
+  }
+  if (tid == 0) {
+    int par = 0;
+    for (int c = 0; c < kD; ++c) par ^= (int)((prefix >> c) & 1u);
+    a.logical[item] = (uint8_t)par;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_batch_u(BatchArgs a) {
+  extern __shared__ __align__(16) unsigned char usm[];
+  __shared__ uint32_t s_pos;
+  if (a.init_mode) {
+    if (blockIdx.x == 0) {
+      if (a.init_prec == 0) run_cta_u<double>(a, usm, 0);
+      else run_cta_u<float>(a, usm, 0);
+    }
+    return;
+  }
+  for (;;) {
+    if (threadIdx.x == 0) s_pos = atomicAdd(&a.ctl->counter_u, 1u);
+    __syncthreads();
+    const uint32_t pos = s_pos;
+    __syncthreads();
+    if (pos >= a.ctl->n_u) return;
+    const uint32_t item = a.idx_u[pos];
+    if ((a.kind[item] & 1) == 0) run_cta_u<double>(a, usm, item);
+    else run_cta_u<float>(a, usm, item);
+    __syncthreads();
   }
 }
 
@@ -353,6 +601,18 @@ struct qec_batch {
   BlockInfo* d_iblocks = nullptr;
   double* d_mats = nullptr;
   void* d_psi0[2] = {nullptr, nullptr};
+  UProgram uprog, iuprog;
+  ProgOp* d_uops = nullptr;
+  UItem* d_uitems = nullptr;
+  ProgOp* d_iuops = nullptr;
+  UItem* d_iuitems = nullptr;
+  void* d_psi0_u[2] = {nullptr, nullptr};
+  uint32_t* d_idx = nullptr;
+  uint32_t* d_idx_u = nullptr;
+  std::vector<uint32_t> h_idx, h_idx_u;
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+  int u_ctas_per_sm = 1;
   qec_noise* d_noise = nullptr;
   int32_t* d_kind = nullptr;
   uint64_t* d_traj = nullptr;
@@ -393,8 +653,13 @@ void drop_batch_graph(qec_batch* b) {
 void batch_free(qec_batch* b) {
   drop_batch_graph(b);
   void* ptrs[] = {b->d_ops, b->d_blocks, b->d_iops, b->d_iblocks, b->d_mats, b->d_psi0[0], b->d_psi0[1],
-                  b->d_noise, b->d_kind, b->d_traj, b->d_ctl, b->d_syn, b->d_bits, b->d_log};
+                  b->d_noise, b->d_kind, b->d_traj, b->d_ctl, b->d_syn, b->d_bits, b->d_log,
+                  b->d_uops, b->d_uitems, b->d_iuops, b->d_iuitems, b->d_psi0_u[0], b->d_psi0_u[1],
+                  b->d_idx, b->d_idx_u};
   for (void* p : ptrs) if (p) cudaFree(p);
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->join) cudaEventDestroy(b->join);
+  if (b->side) cudaStreamDestroy(b->side);
   if (b->h_ctl) cudaFreeHost(b->h_ctl);
   cudaEvent_t evs[] = {b->ev_in, b->ev_out, b->t0, b->t1};
   for (cudaEvent_t e : evs) if (e) cudaEventDestroy(e);
@@ -415,6 +680,16 @@ BatchArgs batch_args(const qec_batch* b) {
   a.rounds = b->rounds;
   a.psi0[0] = b->d_psi0[0];
   a.psi0[1] = b->d_psi0[1];
+  a.idx = b->d_idx;
+  a.idx_u = b->d_idx_u;
+  a.uops = b->d_uops;
+  a.uitems = b->d_uitems;
+  a.n_uitems = (int)b->uprog.items.size();
+  a.iuops = b->d_iuops;
+  a.iuitems = b->d_iuitems;
+  a.n_iuitems = (int)b->iuprog.items.size();
+  a.psi0_u[0] = b->d_psi0_u[0];
+  a.psi0_u[1] = b->d_psi0_u[1];
   a.syn = b->d_syn;
   a.bits = b->d_bits;
   a.logical = b->d_log;
@@ -432,8 +707,19 @@ qec_status ensure_batch_graph(qec_batch* b) {
   if (b->gexec) return QEC_OK;
   QEC_BCUDA(cudaStreamBeginCapture(b->work, cudaStreamCaptureModeThreadLocal));
   BatchArgs a = batch_args(b);
-  k_batch<<<b->num_sms * b->ctas_per_sm, 32 * b->warps_per_cta, smem_for(b->warps_per_cta), b->work>>>(a);
-  cudaError_t le = cudaGetLastError();
+  // reduced-register warps on the main branch, unreduced-register CTAs on a parallel branch
+  cudaError_t le = cudaEventRecord(b->fork, b->work);
+  if (le == cudaSuccess) le = cudaStreamWaitEvent(b->side, b->fork, 0);
+  if (le == cudaSuccess) {
+    k_batch<<<b->num_sms * b->ctas_per_sm, 32 * b->warps_per_cta, smem_for(b->warps_per_cta), b->work>>>(a);
+    le = cudaGetLastError();
+  }
+  if (le == cudaSuccess) {
+    k_batch_u<<<b->num_sms * b->u_ctas_per_sm, 256, kUSmem, b->side>>>(a);
+    le = cudaGetLastError();
+  }
+  if (le == cudaSuccess) le = cudaEventRecord(b->join, b->side);
+  if (le == cudaSuccess) le = cudaStreamWaitEvent(b->work, b->join, 0);
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamEndCapture(b->work, &g);
   if (le != cudaSuccess || e != cudaSuccess) {
@@ -483,7 +769,8 @@ qec_status qec_batch_create(int32_t d, int32_t rounds, int32_t gates, uint32_t m
   b->gates = gates;
   b->cap = max_traj;
   b->user = static_cast<cudaStream_t>(cuda_stream);
-  if (!build_program(p, true, b->prog, err) || !build_program(p, false, b->iprog, err))
+  if (!build_program(p, true, b->prog, err) || !build_program(p, false, b->iprog, err) ||
+      !build_unreduced_program(p, true, b->uprog, err) || !build_unreduced_program(p, false, b->iuprog, err))
     return bail(bfail(QEC_EINVAL, err));
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -493,17 +780,26 @@ qec_status qec_batch_create(int32_t d, int32_t rounds, int32_t gates, uint32_t m
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreate(&b->t0);
   if (e == cudaSuccess) e = cudaEventCreate(&b->t1);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming);
   if (e != cudaSuccess) return bail(bfail(QEC_ECUDA, std::string("CUDA setup: ") + cudaGetErrorString(e)));
   const size_t syn_bytes = (size_t)max_traj * (rounds + 1) * kNStab;
   void** allocs[] = {(void**)&b->d_ops, (void**)&b->d_blocks, (void**)&b->d_iops, (void**)&b->d_iblocks,
                      (void**)&b->d_mats, &b->d_psi0[0], &b->d_psi0[1], (void**)&b->d_noise, (void**)&b->d_kind,
                      (void**)&b->d_traj, (void**)&b->d_ctl, (void**)&b->d_syn, (void**)&b->d_bits,
-                     (void**)&b->d_log};
+                     (void**)&b->d_log, (void**)&b->d_uops, (void**)&b->d_uitems, (void**)&b->d_iuops,
+                     (void**)&b->d_iuitems, &b->d_psi0_u[0], &b->d_psi0_u[1], (void**)&b->d_idx,
+                     (void**)&b->d_idx_u};
   const size_t sizes[] = {sizeof(ProgOp) * (b->prog.ops.size() + 1), sizeof(BlockInfo) * kNStab,
                           sizeof(ProgOp) * (b->iprog.ops.size() + 1), sizeof(BlockInfo) * kNStab,
                           sizeof(b->prog.mats), (size_t)kNAmp * 16, (size_t)kNAmp * 8,
                           sizeof(qec_noise) * max_traj, sizeof(int32_t) * max_traj, sizeof(uint64_t) * max_traj,
-                          sizeof(BatchCtl), syn_bytes, (size_t)max_traj * kND, (size_t)max_traj};
+                          sizeof(BatchCtl), syn_bytes, (size_t)max_traj * kND, (size_t)max_traj,
+                          sizeof(ProgOp) * (b->uprog.ops.size() + 1), sizeof(UItem) * (b->uprog.items.size() + 1),
+                          sizeof(ProgOp) * (b->iuprog.ops.size() + 1), sizeof(UItem) * (b->iuprog.items.size() + 1),
+                          (size_t)kUAmp * 16, (size_t)kUAmp * 8, sizeof(uint32_t) * max_traj,
+                          sizeof(uint32_t) * max_traj};
   for (size_t i = 0; i < sizeof(sizes) / sizeof(sizes[0]); ++i) {
     e = cudaMalloc(allocs[i], sizes[i]);
     if (e != cudaSuccess) return bail(bfail(QEC_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e)));
@@ -514,6 +810,14 @@ qec_status qec_batch_create(int32_t d, int32_t rounds, int32_t gates, uint32_t m
     e = cudaMemcpy(b->d_iops, b->iprog.ops.data(), sizeof(ProgOp) * b->iprog.ops.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(b->d_iblocks, b->iprog.blocks.data(), sizeof(BlockInfo) * kNStab, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(b->d_mats, b->prog.mats, sizeof(b->prog.mats), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !b->uprog.ops.empty())
+    e = cudaMemcpy(b->d_uops, b->uprog.ops.data(), sizeof(ProgOp) * b->uprog.ops.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(b->d_uitems, b->uprog.items.data(), sizeof(UItem) * b->uprog.items.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !b->iuprog.ops.empty())
+    e = cudaMemcpy(b->d_iuops, b->iuprog.ops.data(), sizeof(ProgOp) * b->iuprog.ops.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(b->d_iuitems, b->iuprog.items.data(), sizeof(UItem) * b->iuprog.items.size(), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return bail(bfail(QEC_ECUDA, std::string("upload: ") + cudaGetErrorString(e)));
   e = cudaMallocHost((void**)&b->h_ctl, sizeof(BatchCtl));
   if (e != cudaSuccess) return bail(bfail(QEC_ENOMEM, "pinned allocation failed"));
@@ -522,12 +826,20 @@ qec_status qec_batch_create(int32_t d, int32_t rounds, int32_t gates, uint32_t m
   if (e != cudaSuccess) return bail(bfail(QEC_ECUDA, cudaGetErrorString(e)));
   qec_status st = set_shape(b, 8);
   if (st) return bail(st);
+  e = cudaFuncSetAttribute(k_batch_u, cudaFuncAttributeMaxDynamicSharedMemorySize, kUSmem);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b->u_ctas_per_sm, k_batch_u, 256, kUSmem);
+  if (e != cudaSuccess || b->u_ctas_per_sm < 1)
+    return bail(bfail(QEC_ECUDA, "unreduced batched kernel does not fit an SM"));
   for (int prec = 0; prec < 2; ++prec) {   // the noise-free init round, once per precision
     BatchArgs a = batch_args(b);
     a.init_mode = 1;
     a.init_prec = prec;
     a.init_out = b->d_psi0[prec];
     k_batch<<<1, 32, smem_for(1), b->work>>>(a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return bail(bfail(QEC_ECUDA, std::string("init round: ") + cudaGetErrorString(e)));
+    a.init_out = b->d_psi0_u[prec];   // and of the unreduced register
+    k_batch_u<<<1, 256, kUSmem, b->work>>>(a);
     e = cudaGetLastError();
     if (e != cudaSuccess) return bail(bfail(QEC_ECUDA, std::string("init round: ") + cudaGetErrorString(e)));
   }
@@ -544,7 +856,8 @@ qec_status qec_batch_run(qec_batch* b, uint64_t seed, uint32_t n, const uint64_t
   if (n == 0) return QEC_OK;
   if (!traj || !kind || !noise) return bfail(QEC_EINVAL, "null input array");
   for (uint32_t i = 0; i < n; ++i) {
-    if (kind[i] != QEC_C128 && kind[i] != QEC_C64) return bfail(QEC_EINVAL, "kind must be QEC_C128 or QEC_C64");
+    if (kind[i] < 0 || kind[i] > 3)
+      return bfail(QEC_EINVAL, "kind must be precision (QEC_C128 or QEC_C64) | 2 * layout (QEC_LAYOUT_*)");
     const qec_noise& z = noise[i];
     const double pr[3] = {z.p1, z.p2, z.p_idle};
     for (double v : pr)
@@ -560,12 +873,22 @@ qec_status qec_batch_run(qec_batch* b, uint64_t seed, uint32_t n, const uint64_t
   QEC_BCUDA(cudaMemcpyAsync(b->d_traj, traj, sizeof(uint64_t) * n, cudaMemcpyHostToDevice, b->work));
   QEC_BCUDA(cudaMemcpyAsync(b->d_kind, kind, sizeof(int32_t) * n, cudaMemcpyHostToDevice, b->work));
   QEC_BCUDA(cudaMemcpyAsync(b->d_noise, noise, sizeof(qec_noise) * n, cudaMemcpyHostToDevice, b->work));
+  b->h_idx.clear();
+  b->h_idx_u.clear();
+  for (uint32_t i = 0; i < n; ++i) ((kind[i] & 2) ? b->h_idx_u : b->h_idx).push_back(i);
+  if (!b->h_idx.empty())
+    QEC_BCUDA(cudaMemcpyAsync(b->d_idx, b->h_idx.data(), sizeof(uint32_t) * b->h_idx.size(), cudaMemcpyHostToDevice, b->work));
+  if (!b->h_idx_u.empty())
+    QEC_BCUDA(cudaMemcpyAsync(b->d_idx_u, b->h_idx_u.data(), sizeof(uint32_t) * b->h_idx_u.size(),
+                              cudaMemcpyHostToDevice, b->work));
   qec_status st = ensure_batch_graph(b);
   if (st) return st;
   QEC_BCUDA(cudaStreamSynchronize(b->work));   // h_ctl is reused
   b->h_ctl->seed = seed;
-  b->h_ctl->n = n;
+  b->h_ctl->n = (uint32_t)b->h_idx.size();
   b->h_ctl->counter = 0;
+  b->h_ctl->n_u = (uint32_t)b->h_idx_u.size();
+  b->h_ctl->counter_u = 0;
   QEC_BCUDA(cudaMemcpyAsync(b->d_ctl, b->h_ctl, sizeof(BatchCtl), cudaMemcpyHostToDevice, b->work));
   QEC_BCUDA(cudaEventRecord(b->t0, b->work));
   QEC_BCUDA(cudaGraphLaunch(b->gexec, b->work));

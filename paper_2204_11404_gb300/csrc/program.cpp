@@ -3,6 +3,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <tuple>
 
 namespace qec {
@@ -259,6 +260,115 @@ bool build_program(const qec_params& p, bool noisy, Program& P, std::string& err
     for (auto& e : post[k]) data_event(e.first, e.second);
     bi.op_end = (int)P.ops.size();
     P.blocks.push_back(bi);
+  }
+  return true;
+}
+
+bool build_unreduced_program(const qec_params& p, bool noisy, UProgram& U, std::string& err) {
+  if (!validate_params(p, err)) return false;
+  const int d = p.d, nd = d * d;
+  const bool cr = p.gates == QEC_GATES_CR;
+  const qec_noise& nz = p.noise;
+  std::vector<Stab> S = make_stabilizers(d);
+  const int nst = (int)S.size(), half = nst / 2;
+  U = UProgram();
+  U.d = d;
+  U.nd = nd;
+  U.nstab = nst;
+  U.nbits = nd + half;
+  {
+    Program tmp;
+    tmp.d = d;
+    fill_mats(tmp, nz, noisy);
+    std::memcpy(U.mats, tmp.mats, sizeof(U.mats));
+  }
+  U.prob[PR_P1] = noisy ? nz.p1 : 0.0;
+  U.prob[PR_P2] = noisy ? nz.p2 : 0.0;
+  U.prob[PR_IDLE] = noisy ? nz.p_idle : 0.0;
+  std::vector<int> nx(nd, 0), nzc(nd, 0);
+  for (const Stab& s : S)
+    for (int i = 0; i < 4; ++i)
+      if (s.slots[i] >= 0) (s.kind == 'X' ? nx : nzc)[s.slots[i]]++;
+  auto u1 = [&](int q, uint16_t m) { U.ops.push_back({OP_U1, (uint8_t)q, 0, 0, m, 0, 0}); };
+  auto u2 = [&](int a, int b, uint16_t m) { U.ops.push_back({OP_U2, (uint8_t)a, (uint8_t)b, 0, m, 0, 0}); };
+  auto n1 = [&](int q, int step, uint32_t site, uint8_t pid) {
+    if (U.prob[pid] > 0.0) U.ops.push_back({OP_N1, (uint8_t)q, 0, pid, 0, (uint16_t)step, site});
+  };
+  auto n2 = [&](int a, int b, int step, uint32_t site) {
+    if (U.prob[PR_P2] > 0.0) U.ops.push_back({OP_N2, (uint8_t)a, (uint8_t)b, PR_P2, 0, (uint16_t)step, site});
+  };
+  auto unit = [&](int nq, int qa, int qb, int begin) {
+    if ((int)U.ops.size() > begin) U.items.push_back({0, begin, (int32_t)U.ops.size(), nq, qa, qb, -1, 0});
+  };
+  for (int part = 0; part < 2; ++part) {
+    const char kind = part == 0 ? 'X' : 'Z';
+    const int k0 = part == 0 ? 0 : half;
+    const int t0 = part == 0 ? 1 : 7, t1 = part == 0 ? 6 : 11;
+    for (int t = (part == 0 ? 0 : t0); t <= t1; ++t) {
+      std::vector<int> busy(nd, 0);
+      for (int j = 0; j < half; ++j) {   // ancilla units of this step
+        const Stab& s = S[k0 + j];
+        const int a = nd + j;
+        const uint32_t site_a = (uint32_t)(nd + k0 + j);
+        if (t == 0) continue;
+        const int begin = (int)U.ops.size();
+        if (kind == 'X' && (t == 1 || t == 6)) {
+          if (!cr) {
+            u1(a, M_H);
+          } else {
+            u1(a, t == 1 ? M_RX90DG : M_RX90);
+            if (noisy && nz.theta_rx != 0.0) u1(a, M_ROT_RX);
+          }
+          n1(a, t, site_a, PR_P1);
+          unit(1, a, 0, begin);
+          continue;
+        }
+        if (kind == 'Z' && t == 11) {
+          n1(a, t, site_a, PR_IDLE);
+          unit(1, a, 0, begin);
+          continue;
+        }
+        const int q = s.slots[kind == 'X' ? t - 2 : t - 7];
+        if (q < 0) {
+          n1(a, t, site_a, PR_IDLE);
+          unit(1, a, 0, begin);
+          continue;
+        }
+        busy[q] = 1;
+        const int first = kind == 'X' ? a : q, second = kind == 'X' ? q : a;
+        if (!cr) {
+          u2(first, second, M_CNOT);
+        } else {
+          u2(first, second, M_RZX90);
+          if (noisy && nz.theta_rzx != 0.0) u2(first, second, M_ROT_RZX);
+        }
+        if (noisy && nz.phi_zz != 0.0) u2(first, second, M_ZZ);
+        n2(a, q, t, (uint32_t)q);
+        unit(2, first, second, begin);
+      }
+      for (int q = 0; q < nd; ++q) {     // data qubits not in a two-qubit gate
+        if (busy[q]) continue;
+        const int begin = (int)U.ops.size();
+        if (t == 0) {
+          if (noisy && nz.round_rz != 0.0) u1(q, M_ROUND_RZ);
+          if (noisy && nz.round_rx != 0.0) u1(q, M_ROUND_RX);
+        } else if (cr && (t == 6 || t == 11)) {
+          const int nfac = t == 6 ? nx[q] : nzc[q];
+          for (int f = 0; f < nfac; ++f) {
+            u1(q, t == 6 ? M_RX90 : M_RZ90);
+            if (noisy && (t == 6 ? nz.theta_rx : nz.theta_rz) != 0.0) u1(q, t == 6 ? M_ROT_RX : M_ROT_RZ);
+          }
+          n1(q, t, (uint32_t)q, PR_P1);
+        } else {
+          n1(q, t, (uint32_t)q, PR_IDLE);
+        }
+        unit(1, q, 0, begin);
+      }
+    }
+    for (int j = 0; j < half; ++j) {     // measurements of this part's ancillas, serial order
+      const Stab& s = S[k0 + j];
+      U.items.push_back({1, 0, 0, 1, nd + j, 0, k0 + j, (cr && s.w == 2) ? 1 : 0});
+    }
   }
   return true;
 }

@@ -57,6 +57,31 @@ struct Stab {
   int w;
 };
 
+// Time-ordered program of the unreduced register (all 2d^2-1 qubits, Sec. II.B), on a slab of
+// d^2 + (d^2-1)/2 qubits: data q -> bit q; the active part's ancilla j -> bit d^2 + j.  The four (at
+// d=3) ancillas of the part not in progress are |0> (reset after their measurement, untouched
+// until their part starts), so the slab holds the exact 2d^2-1 qubit state.  A round is a list of
+// items in execution order: fused units (one qubit, or one two-qubit gate pair, at one step; their
+// ops in order gate, coherent terms, Pauli) and ancilla measurements (after steps 6 and 11).
+struct UItem {
+  int32_t kind;           // 0: unit, 1: measurement
+  int32_t op_begin, op_end;   // unit ops (ProgOp, q0/q1 = slab bits)
+  int32_t nq;             // unit: 1 or 2 qubits
+  int32_t qa, qb;         // unit: slab bits (qa = first-listed); measurement: qa = slab bit
+  int32_t stab;           // measurement: stabilizer index (serial order)
+  int32_t offset;         // measurement: syndrome = raw ^ offset
+};
+
+struct UProgram {
+  int d = 0, nd = 0, nstab = 0, nbits = 0;
+  std::vector<ProgOp> ops;
+  std::vector<UItem> items;         // one round
+  double mats[M_COUNT][16][2];
+  double prob[3];
+};
+
+bool build_unreduced_program(const qec_params& p, bool noisy, UProgram& out, std::string& err);
+
 std::vector<Stab> make_stabilizers(int d);
 bool validate_params(const qec_params& p, std::string& err);
 // noisy = false: the noise-free init round (no noise sites, no coherent terms).

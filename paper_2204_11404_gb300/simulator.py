@@ -74,7 +74,9 @@ class Simulator:
 
 
 class BatchSimulator:
-    """qec_batch handle: d = 3 trajectories with per-trajectory precision and noise in one launch."""
+    """qec_batch handle: d = 3 trajectories with per-trajectory register (reduced 10-qubit or
+    unreduced 17-qubit), precision and noise in one launch.  kind strings: "c128", "c64" (reduced),
+    "c128u", "c64u" (unreduced)."""
 
     def __init__(self, rounds, gates="cr", max_traj=8192, stream=None, d=3):
         self.d, self.rounds, self.nstab = d, rounds, d * d - 1
@@ -85,7 +87,9 @@ class BatchSimulator:
     def _inputs(traj, kind, noise):
         n = len(traj)
         t = np.ascontiguousarray(traj, dtype=np.uint64)
-        k = np.ascontiguousarray([{"c128": capi.QEC_C128, "c64": capi.QEC_C64}.get(x, x) for x in kind], dtype=np.int32)
+        # kind: precision, plus 2 for the unreduced (2d^2-1 qubit, time-ordered) register
+        codes = {"c128": 0, "c64": 1, "c128u": 2, "c64u": 3}
+        k = np.ascontiguousarray([codes.get(x, x) for x in kind], dtype=np.int32)
         nz = (capi.qec_noise * max(n, 1))()
         for i, d in enumerate(noise):
             for f in capi.NOISE_FIELDS:

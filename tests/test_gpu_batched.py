@@ -45,7 +45,7 @@ def test_batched_mix_matches_oracle(gates):
 
 
 def test_batched_equals_single_trajectory_path_and_autotune():
-    traj, kinds, noise, rounds, seed = W.batched_mix(n=512)
+    traj, kinds, noise, rounds, seed = W.batched_mix(n=512, unreduced=False)
     with BatchSimulator(rounds, "cr", max_traj=512) as b:
         w, ms = b.autotune(seed, traj, kinds, noise)
         assert w > 0 and ms > 0
@@ -57,3 +57,25 @@ def test_batched_equals_single_trajectory_path_and_autotune():
             s1, b1, l1 = sim.run(seed, traj[i], 1)
         if kinds[i] == "c128":
             assert (s1[0] == syn[i]).all() and (b1[0] == bits[i]).all() and l1[0] == log[i]
+
+
+@pytest.mark.parametrize("gates", ["cr", "cnot"])
+def test_batched_unreduced_register_matches_oracle_and_reduced(gates):
+    # 17-qubit time-ordered register in the same launch as 10-qubit trajectories
+    n = 40
+    traj = [300 + i for i in range(n)]
+    kinds = ["c128u", "c64u", "c128", "c64"] * (n // 4)
+    noise = [dict(W.STRESS) if i % 2 else dict(p1=0.02, p2=0.02, p_idle=0.01, theta_rx=0.08, phi_zz=0.03)
+             for i in range(n)]
+    with BatchSimulator(3, gates, max_traj=64) as b:
+        syn, bits, log = b.run(91, traj, kinds, noise)
+    amb = 0
+    for i in range(n):
+        layout = "unreduced" if kinds[i].endswith("u") else "reduced"
+        prec = kinds[i].rstrip("u")
+        o = run_trajectory(3, 3, gates, layout, noise[i], seed=91, traj=traj[i])
+        kind = compare_trajectory(syn[i], bits[i], o, TAU[prec])
+        if prec == "c128":
+            assert kind == "exact", (i, kinds[i])
+        amb += kind == "ambiguous"
+    assert amb <= 2

@@ -32,17 +32,20 @@ STRESS = dict(p1=0.03, p2=0.03, p_idle=0.02, theta_rx=0.1, theta_rz=0.07, theta_
               phi_zz=0.08, round_rz=0.1, round_rx=0.05)
 
 
-def batched_mix(n=8192, seed=4000, rounds=3):
-    """Config of the batched form: n trajectories of the d=3 reduced register, a 50/50 mix of
-    complex128 and complex64 (alternating), each with its own noise: p ~ U[1e-4, 1e-2] on every
-    step (Eqs. 1-2) and an Rx over-rotation theta ~ U[0, 0.1] rad, drawn with numpy's seeded
-    generator.  Returns (traj indices, kinds, noise dicts, rounds, seed)."""
+def batched_mix(n=8192, seed=4000, rounds=3, unreduced=True):
+    """Config of the batched form: n trajectories of the d=3 register in equal quarters of
+    reduced 10-qubit complex128, reduced complex64, unreduced 17-qubit complex128 and unreduced
+    complex64 (interleaved), each with its own noise: p ~ U[1e-4, 1e-2] on every step (Eqs. 1-2)
+    and an Rx over-rotation theta ~ U[0, 0.1] rad, drawn with numpy's seeded generator.
+    unreduced=False keeps only the reduced register.  Returns (traj indices, kinds, noise dicts,
+    rounds, seed)."""
     import numpy as np
 
     rng = np.random.default_rng(seed)
     p = rng.uniform(1e-4, 1e-2, n)
     th = rng.uniform(0.0, 0.1, n)
-    kinds = ["c128" if i % 2 == 0 else "c64" for i in range(n)]
+    cycle = ["c128", "c64", "c128u", "c64u"] if unreduced else ["c128", "c64"]
+    kinds = [cycle[i % len(cycle)] for i in range(n)]
     noise = [dict(p1=float(p[i]), p2=float(p[i]), p_idle=float(p[i]), theta_rx=float(th[i])) for i in range(n)]
     return list(range(n)), kinds, noise, rounds, seed
 

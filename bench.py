@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--rate", type=float, default=50.0, help="serve: mean arrival rate (requests/s)")
     ap.add_argument("--max-traj", type=int, default=8, help="serve: trajectories per request drawn from 1..max")
     ap.add_argument("--mem-gib", type=float, default=32.0, help="serve: device memory budget for state vectors")
+    ap.add_argument("--noise", default="full", choices=["full", "idle"],
+                    help="sweep: full = p on every step (Eqs. 1-2); idle = p on waiting qubits only")
     return ap.parse_args()
 
 
@@ -449,10 +451,11 @@ def sweep_arm(args, rank, world, local):
     n = max(1, args.steps)
     dec = Decoder(5)
     rows = []
-    for c in (0.0, 0.5, 1.0):
+    for c in ((0.0, 0.5, 1.0) if args.noise == "full" else (0.0,)):
         for p in (1e-3, 2e-3, 3e-3, 5e-3):
             th = 2 * c * np.sqrt(p)
-            nz = dict(p1=p, p2=p, p_idle=p, theta_rx=th, theta_rz=th)
+            g = p if args.noise == "full" else 0.0
+            nz = dict(p1=g, p2=g, p_idle=p, theta_rx=th, theta_rz=th)
             with Simulator(5, 5, "cr", "c64tc", **nz) as sim:
                 syn, bits, log = sim.run(7000, rank * n, n)
             f = [dec.logical_failure(a, b, l) for a, b, l in zip(syn, bits, log)]
@@ -461,7 +464,8 @@ def sweep_arm(args, rank, world, local):
                          "pL_err": float(np.sqrt(max(k, 1) * (1 - k / n)) / n),
                          "paper_fit_c0": 6.5e5 * p ** 2.92 if c == 0 else None})
     if rank == 0:
-        print(json.dumps({"metric": "logical error rate p_L(p, c), d=5, 5 rounds", "unit": "per-point report",
+        print(json.dumps({"metric": "logical error rate p_L(p, c), d=5, 5 rounds, noise=" + args.noise,
+                          "unit": "per-point report",
                           "data": "synthetic", "points": rows, "decoder_fallbacks": dec.fallbacks}))
 
 

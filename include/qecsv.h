@@ -23,7 +23,7 @@ typedef enum {
   QEC_ENOMEM = -2,       /* device or host allocation failed */
   QEC_ECUDA = -3,        /* a CUDA runtime call failed (message has the CUDA error string) */
   QEC_ETIMEOUT = -4,     /* a bounded device wait gave up */
-  QEC_EUNSUPPORTED = -6  /* valid request this build does not implement */
+  QEC_EUNSUPPORTED = -6  /* valid request the library does not implement (e.g. unreduced layout in a qec_sim) */
 } qec_status;
 
 /* Register layout (Sec. II.B).  REDUCED: d^2 data qubits + one reused ancilla
@@ -144,6 +144,15 @@ qec_status qec_get_events(qec_sim* sim, int32_t* host_events, uint32_t max_event
  * sim has no noisy round.
  */
 qec_status qec_kernel_times(qec_sim* sim, float* ms, int32_t* block);
+
+/*
+ * Self-test of failure detection: runs, on the sim's stream, the bounded
+ * mbarrier wait used by the tensor-core pass on a barrier that nothing ever
+ * arrives on, giving up after `polls` polls (1..1e7).  Returns QEC_ETIMEOUT
+ * when the wait ran out and was reported through the device status word
+ * (the expected result); the sim stays usable afterwards.
+ */
+qec_status qec_selftest_wait(qec_sim* sim, uint32_t polls);
 
 /*
  * Trajectories without any device allocation (the paper has no counterpart;

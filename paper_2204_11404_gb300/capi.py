@@ -47,6 +47,7 @@ SIGNATURES = {
     "qec_record_events": ([_P, ctypes.c_uint32], ctypes.c_int),
     "qec_get_events": ([_P, _P, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32)], ctypes.c_int),
     "qec_kernel_times": ([_P, _P, _P], ctypes.c_int),
+    "qec_selftest_wait": ([_P, ctypes.c_uint32], ctypes.c_int),
     "qec_run_trajectories_noalloc": ([ctypes.POINTER(qec_params), ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32,
                                       _P, _P, _P, _P], ctypes.c_int),
     "qec_destroy": ([_P], ctypes.c_int),
@@ -174,6 +175,11 @@ def qec_batch_last_ms(b):
 
 def qec_batch_destroy(b):
     return check(lib().qec_batch_destroy(b))
+
+
+def qec_selftest_wait(sim, polls):
+    """Returns the raw status (QEC_ETIMEOUT expected) without raising."""
+    return int(lib().qec_selftest_wait(sim, polls))
 
 
 def qec_destroy(sim):

@@ -567,6 +567,21 @@ qec_status qec_reconfigure(qec_sim* s, const qec_params* params) {
   return QEC_OK;
 }
 
+qec_status qec_selftest_wait(qec_sim* s, uint32_t polls) {
+  if (!s) return fail(QEC_EINVAL, "null handle");
+  if (polls == 0 || polls > 10000000) return fail(QEC_EINVAL, "polls must be in [1, 1e7]");
+  QEC_CUDA(cudaStreamSynchronize(s->work));
+  QEC_CUDA(cudaMemsetAsync(&s->d_ctl->status, 0, sizeof(unsigned int), s->work));
+  QEC_CUDA(launch_wait_selftest(&s->d_ctl->status, (long)polls, s->work));
+  QEC_CUDA(cudaStreamSynchronize(s->work));
+  unsigned int status = 0;
+  QEC_CUDA(cudaMemcpy(&status, &s->d_ctl->status, sizeof(status), cudaMemcpyDeviceToHost));
+  QEC_CUDA(cudaMemsetAsync(&s->d_ctl->status, 0, sizeof(unsigned int), s->work));   // leave the sim usable
+  QEC_CUDA(cudaStreamSynchronize(s->work));
+  if (status) return fail(QEC_ETIMEOUT, "bounded device wait gave up (self-test)");
+  return QEC_OK;
+}
+
 qec_status qec_kernel_times(qec_sim* s, float* ms, int32_t* block) {
   if (!s || !ms || !block) return fail(QEC_EINVAL, "null argument");
   if (!s->ran || s->timed_block < 0) return fail(QEC_EINVAL, "no instrumented trajectory has run");

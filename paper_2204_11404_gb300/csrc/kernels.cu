@@ -28,6 +28,21 @@ __device__ __forceinline__ double2 lds_v2(const double2* p) {
   asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(r.x), "=d"(r.y) : "r"((unsigned)__cvta_generic_to_shared(p)));
   return r;
 }
+// Two consecutive complex entries p[0], p[1]: one 16-byte load for float (p 16-byte aligned),
+// two for double.
+__device__ __forceinline__ void lds_pair(const float2* p, float2& a, float2& b) {
+  float4 r;
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w) : "r"((unsigned)__cvta_generic_to_shared(p)));
+  a = make_float2(r.x, r.y);
+  b = make_float2(r.z, r.w);
+}
+__device__ __forceinline__ double2 lds_v2(const double2* p);
+__device__ __forceinline__ void lds_pair(const double2* p, double2& a, double2& b) {
+  a = lds_v2(p);
+  b = lds_v2(p + 1);
+}
+
 __device__ __forceinline__ float2 lds_v2(const float2* p) {
   float2 r;
   asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(r.x), "=f"(r.y) : "r"((unsigned)__cvta_generic_to_shared(p)));
@@ -84,7 +99,7 @@ __device__ void inst_block(const InstArgs& a, double2* U, double (*sm)[16][2], i
           if (e < a.ctl->ev_cap) {
             int32_t* ev = a.events + 5 * (size_t)e;
             ev[0] = (int32_t)traj; ev[1] = rnd; ev[2] = op.step; ev[3] = (int32_t)op.site;
-            ev[4] = op.kind == OP_N1 ? code : code;
+            ev[4] = code;
           }
         }
       }
@@ -356,8 +371,8 @@ __global__ void __launch_bounds__(256) k_fused(FusedArgs f) {
   T2* buf0 = reinterpret_cast<T2*>(fsm);
   T2* buf1 = buf0 + tsz;
   uint32_t* hoff = reinterpret_cast<uint32_t*>(buf1 + tsz);
-  __shared__ T2 sK[C * C];
-  __shared__ T2 sM[C2 * C2];
+  __shared__ __align__(16) T2 sK[C * C];
+  __shared__ __align__(16) T2 sM[C2 * C2];
   __shared__ double sred[64];
   __shared__ int s_last;
   {
@@ -425,12 +440,17 @@ __global__ void __launch_bounds__(256) k_fused(FusedArgs f) {
       for (int r = 0; r < C; ++r) {
         T sr = 0, si = 0;
 #pragma unroll
-        for (int c = 0; c < C; ++c) {
-          const T2 k = lds_v2(&sK[r * C + c]);
-          sr = fma_t(k.x, v[c].x, sr);
-          sr = fma_t(-k.y, v[c].y, sr);
-          si = fma_t(k.x, v[c].y, si);
-          si = fma_t(k.y, v[c].x, si);
+        for (int c = 0; c < C; c += 2) {
+          T2 k0, k1;
+          lds_pair(&sK[r * C + c], k0, k1);
+          sr = fma_t(k0.x, v[c].x, sr);
+          sr = fma_t(-k0.y, v[c].y, sr);
+          si = fma_t(k0.x, v[c].y, si);
+          si = fma_t(k0.y, v[c].x, si);
+          sr = fma_t(k1.x, v[c + 1].x, sr);
+          sr = fma_t(-k1.y, v[c + 1].y, sr);
+          si = fma_t(k1.x, v[c + 1].y, si);
+          si = fma_t(k1.y, v[c + 1].x, si);
         }
         T2 o;
         o.x = sr;
@@ -448,13 +468,29 @@ __global__ void __launch_bounds__(256) k_fused(FusedArgs f) {
 #pragma unroll
       for (int i = 0; i < C2; ++i) {
         T tr = 0, ti = 0;
+        int j = i + 1;
+        if (j & 1) {               // reach an even column, then take pairs
+          if (j < C2) {
+            const T2 m = lds_v2(&sM[i * C2 + j]);
+            tr = fma_t(m.x, v[j].x, tr);
+            tr = fma_t(-m.y, v[j].y, tr);
+            ti = fma_t(m.x, v[j].y, ti);
+            ti = fma_t(m.y, v[j].x, ti);
+          }
+          ++j;
+        }
 #pragma unroll
-        for (int j = i + 1; j < C2; ++j) {
-          const T2 m = lds_v2(&sM[i * C2 + j]);
-          tr = fma_t(m.x, v[j].x, tr);
-          tr = fma_t(-m.y, v[j].y, tr);
-          ti = fma_t(m.x, v[j].y, ti);
-          ti = fma_t(m.y, v[j].x, ti);
+        for (; j < C2; j += 2) {
+          T2 m0, m1;
+          lds_pair(&sM[i * C2 + j], m0, m1);
+          tr = fma_t(m0.x, v[j].x, tr);
+          tr = fma_t(-m0.y, v[j].y, tr);
+          ti = fma_t(m0.x, v[j].y, ti);
+          ti = fma_t(m0.y, v[j].x, ti);
+          tr = fma_t(m1.x, v[j + 1].x, tr);
+          tr = fma_t(-m1.y, v[j + 1].y, tr);
+          ti = fma_t(m1.x, v[j + 1].y, ti);
+          ti = fma_t(m1.y, v[j + 1].x, ti);
         }
         cross = fma_t(v[i].x, tr, cross);
         cross = fma_t(v[i].y, ti, cross);
@@ -512,14 +548,26 @@ __device__ __forceinline__ void umma_tf32(uint32_t d_tmem, uint64_t ad, uint64_t
 }
 
 // Bounded wait for an mbarrier phase; false if it gave up.
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
-  for (long it = 0; it < 40000000; ++it) {
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, long limit = 40000000) {
+  for (long it = 0; it < limit; ++it) {
     uint32_t done;
     asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
                  : "=r"(done) : "r"(mbar), "r"(parity) : "memory");
     if (done) return true;
   }
   return false;
+}
+
+// Self-test of the bounded-wait path: waits on an mbarrier that nothing arrives on, gives up
+// after `limit` polls and records the timeout in *status (bit 0), as the tensor-core pass does.
+__global__ void k_wait_selftest(unsigned int* status, long limit) {
+  __shared__ __align__(8) uint64_t mbar;
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (!mbar_wait(smem_u32(&mbar), 0, limit) && threadIdx.x == 0) atomicOr(status, 1u);
 }
 
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
@@ -1041,6 +1089,11 @@ cudaError_t launch_fused(int precision, const PassArgs& ap, const PassArgs& pr, 
     case 2: return fused_t<float, 4, 2>(f, smem, num_sms, s);
     default: return fused_t<float, 4, 4>(f, smem, num_sms, s);
   }
+}
+
+cudaError_t launch_wait_selftest(unsigned int* status, long limit, cudaStream_t s) {
+  k_wait_selftest<<<1, 32, 0, s>>>(status, limit);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_set_basis0(int precision, void* psi, int D, cudaStream_t s) {

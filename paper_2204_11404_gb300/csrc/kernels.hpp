@@ -97,7 +97,8 @@ cudaError_t launch_readout(int precision, const ReadArgs& a, cudaStream_t s);
 // Builds the tile for (apply block ap, probability block pr) and launches the fused pass.
 cudaError_t launch_fused(int precision, const PassArgs& ap, const PassArgs& pr, int num_sms, cudaStream_t s);
 cudaError_t launch_set_basis0(int precision, void* psi, int D, cudaStream_t s);
-cudaError_t setup_kernels(int precision, int D);   // once per process/device, before any capture
+cudaError_t setup_kernels(int precision, int D);
+cudaError_t launch_wait_selftest(unsigned int* status, long limit, cudaStream_t s);   // once per process/device, before any capture
 int pass_grid(int D, int w, int num_sms);
 // One wave of resident CTAs for the probability (prob = true) or apply pass kernel.
 int pass_grid_for(int precision, bool prob, int D, int w, int num_sms);

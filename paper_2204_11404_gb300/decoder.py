@@ -4,11 +4,16 @@ Sec. III.B: detection events are the XOR of the syndromes of adjacent rounds;
 the error positions are estimated by minimum-weight perfect matching; the
 logical value after correction decides failure.  The paper does not give the
 graph or weights, so this module uses the plain reading.
-- The space-time graph has one node per (round, Z-stabilizer).
-- Unit-weight edges join stabilizers that share a data qubit (one X error), or
-  the same stabilizer in consecutive rounds (one measurement error).
+- The space-time graph has one node per (event layer, Z-stabilizer).
+- Unit-weight space edges join stabilizers that share a data qubit (one X error
+  before both of their gates on it).
+- Unit-weight diagonal edges join the later-gated stabilizer in one layer with
+  the earlier-gated one in the next layer (one X error between their two gates
+  on that qubit: the later gate sees it this round, the earlier one next round).
+- Unit-weight time edges join the same stabilizer in consecutive layers (one
+  measurement error).
 - A data qubit in only one Z-stabilizer is an edge to the boundary.
-- The last round of events compares the last measured syndrome with the
+- The last layer of events compares the last measured syndrome with the
   Z-stabilizer parities of the final data readout.
 
 Only Z-stabilizers are decoded, because the experiment measures logical Z.
@@ -28,23 +33,28 @@ MAX_EXACT = 16
 
 
 def _stabilizers(d):
-    """Z-stabilizer supports in serial order (same rule as the library's program builder)."""
+    """Z-stabilizers in serial order (same rule as the library's program builder): list of
+    (support sorted, {data qubit: gate slot}) with slots clockwise from the top-right corner."""
     zs = []
     for r in range(-1, d):
         for c in range(-1, d):
-            cells = [(a, b) for (a, b) in ((r, c), (r, c + 1), (r + 1, c), (r + 1, c + 1)) if 0 <= a < d and 0 <= b < d]
             if (r + c) % 2:
                 continue
+            corners = [(r, c + 1), (r + 1, c + 1), (r + 1, c), (r, c)]   # TR, BR, BL, TL
+            cells = [(a, b) for (a, b) in corners if 0 <= a < d and 0 <= b < d]
             if len(cells) == 4 or (len(cells) == 2 and (c == -1 or c == d - 1) and not (r == -1 or r == d - 1)):
-                zs.append(((c, -r), sorted(a * d + b for (a, b) in cells)))
+                slots = {a * d + b: i for i, (a, b) in enumerate(corners) if 0 <= a < d and 0 <= b < d}
+                zs.append(((c, -r), sorted(slots), slots))
     zs.sort(key=lambda t: t[0])
-    return [s for _, s in zs]
+    return [(sup, slots) for _, sup, slots in zs]
 
 
 class Decoder:
     def __init__(self, d):
         self.d = d
-        self.zs = _stabilizers(d)
+        st = _stabilizers(d)
+        self.zs = [sup for sup, _ in st]
+        self.slots = [sl for _, sl in st]
         self.nz = len(self.zs)
         self.nx = self.nz                      # X-stabilizers come first in the syndrome rows
         nd = d * d
@@ -52,61 +62,80 @@ class Decoder:
         for k, sup in enumerate(self.zs):
             for q in sup:
                 owners[q].append(k)
-        B = self.nz                            # boundary node
-        adj = [[] for _ in range(self.nz + 1)]
-        for q, ks in enumerate(owners):
-            if len(ks) == 2:
-                adj[ks[0]].append((ks[1], q))
-                adj[ks[1]].append((ks[0], q))
-            elif len(ks) == 1:
-                adj[ks[0]].append((B, q))
-                adj[B].append((ks[0], q))
-        row = set(range(d))                    # logical Z support
-        n = self.nz + 1
-        self.dist = np.zeros((n, n), dtype=np.int64)
-        self.par = np.zeros((n, n), dtype=np.uint8)
-        for s in range(n):
-            dist = [-1] * n
-            par = [0] * n
-            dist[s] = 0
-            dq = deque([s])
-            while dq:
-                u = dq.popleft()
-                if u == B and s != B:
-                    continue                   # paths do not pass through the boundary
-                for v, q in adj[u]:
-                    if dist[v] < 0:
-                        dist[v] = dist[u] + 1
-                        par[v] = par[u] ^ (1 if q in row else 0)
-                        dq.append(v)
-            self.dist[s] = dist
-            self.par[s] = par
-        self.boundary = B
-        self.z_of_data = owners
+        self.owners = owners
+        self.row = set(range(d))               # logical Z support
         self.fallbacks = 0
+        self._graphs = {}
+
+    def _graph(self, layers):
+        """Space-time graph of `layers` event layers: adjacency (node -> [(node, parity)]), node
+        (e, k) = e * nz + k, boundary = layers * nz."""
+        if layers in self._graphs:
+            return self._graphs[layers]
+        nz, B = self.nz, layers * self.nz
+        adj = [[] for _ in range(B + 1)]
+
+        def edge(u, v, par):
+            adj[u].append((v, par))
+            adj[v].append((u, par))
+
+        for q, ks in enumerate(self.owners):
+            par = 1 if q in self.row else 0
+            for e in range(layers):
+                if len(ks) == 2:
+                    edge(e * nz + ks[0], e * nz + ks[1], par)
+                    if e + 1 < layers:
+                        early, late = sorted(ks, key=lambda k: self.slots[k][q])
+                        edge(e * nz + late, (e + 1) * nz + early, par)
+                elif len(ks) == 1:
+                    edge(e * nz + ks[0], B, par)
+        for e in range(layers - 1):
+            for k in range(nz):
+                edge(e * nz + k, (e + 1) * nz + k, 0)
+        self._graphs[layers] = (adj, B)
+        return adj, B
+
+    def _bfs(self, adj, B, src):
+        n = len(adj)
+        dist = [-1] * n
+        par = [0] * n
+        dist[src] = 0
+        dq = deque([src])
+        while dq:
+            u = dq.popleft()
+            if u == B and src != B:
+                continue                       # a chain ends at the boundary
+            for v, pq in adj[u]:
+                if dist[v] < 0:
+                    dist[v] = dist[u] + 1
+                    par[v] = par[u] ^ pq
+                    dq.append(v)
+        return dist, par
 
     def detection_events(self, syndromes, data_bits):
         """syndromes [R+1][d^2-1] (row 0 = init), data_bits [d^2] -> list of (round, z index)."""
-        s = np.asarray(syndromes, dtype=np.uint8)[:, self.nx:]
+        s = np.asarray(syndromes, dtype=np.uint8)[:, self.nx:]     # rows 0 (init) .. R
         final = np.array([np.bitwise_xor.reduce(np.asarray(data_bits, dtype=np.uint8)[sup]) for sup in self.zs],
                          dtype=np.uint8)
         full = np.vstack([s, final[None, :]])
         ev = full[1:] ^ full[:-1]
         return [(int(r), int(k)) for r, k in zip(*np.nonzero(ev))]
 
-    def _match(self, defects):
+    def _match(self, defects, layers):
         n = len(defects)
         if n == 0:
             return 0
-        B = self.boundary
+        adj, B = self._graph(layers)
+        nodes = [e * self.nz + k for e, k in defects]
         w = np.zeros((n, n), dtype=np.int64)
         p = np.zeros((n, n), dtype=np.uint8)
-        for i, (ri, ki) in enumerate(defects):
-            for j, (rj, kj) in enumerate(defects):
-                w[i, j] = self.dist[ki, kj] + abs(ri - rj)
-                p[i, j] = self.par[ki, kj]
-        wb = np.array([self.dist[k, B] for _, k in defects], dtype=np.int64)
-        pb = np.array([self.par[k, B] for _, k in defects], dtype=np.uint8)
+        wb = np.zeros(n, dtype=np.int64)
+        pb = np.zeros(n, dtype=np.uint8)
+        for i, u in enumerate(nodes):
+            dist, par = self._bfs(adj, B, u)
+            for j, v in enumerate(nodes):
+                w[i, j], p[i, j] = dist[v], par[v]
+            wb[i], pb[i] = dist[B], par[B]
         if n > MAX_EXACT:
             self.fallbacks += 1
             return self._greedy(w, p, wb, pb)
@@ -149,7 +178,8 @@ class Decoder:
 
     def logical_failure(self, syndromes, data_bits, raw_logical):
         """1 if the decoded logical Z differs from the prepared |0_L> (Sec. III.B)."""
-        return int(raw_logical) ^ self._match(self.detection_events(syndromes, data_bits))
+        layers = len(syndromes)                # event layers: rounds 1..R and the final readout
+        return int(raw_logical) ^ self._match(self.detection_events(syndromes, data_bits), layers)
 
     def logical_error_rate(self, syndromes, data_bits, raw_logical):
         f = [self.logical_failure(s, b, l) for s, b, l in zip(syndromes, data_bits, raw_logical)]

@@ -82,3 +82,20 @@ def test_logical_error_rate_grows_with_p_d3():
             f.append(dec.logical_failure(r["syndromes"], r["data_bits"], r["raw_logical"]))
         rates.append(np.mean(f))
     assert rates[0] < rates[1]
+
+
+@pytest.mark.parametrize("gates", ["cnot", "cr"])
+def test_error_between_two_z_gates_is_one_diagonal_edge(gates):
+    # data qubit 4 (centre, d=3) is BR of Z{0,1,3,4} (gate at step 8) and TL of Z{4,5,7,8}
+    # (gate at step 10); an X error at step 9 is seen by the later-gated stabilizer in round 1
+    # and by the earlier-gated one only in round 2
+    dec = Decoder(3)
+    r = run_trajectory(3, 2, gates, "reduced", {}, seed=0, traj=0, inject=[(1, 9, 4, G.PX)])
+    ev = dec.detection_events(r["syndromes"], r["data_bits"])
+    zs = dec.zs
+    k_early, k_late = zs.index([0, 1, 3, 4]), zs.index([4, 5, 7, 8])
+    assert sorted(ev) == sorted([(0, k_late), (1, k_early)])
+    adj, B = dec._graph(len(r["syndromes"]))
+    dist, _ = dec._bfs(adj, B, 0 * dec.nz + k_late)
+    assert dist[1 * dec.nz + k_early] == 1
+    assert dec.logical_failure(r["syndromes"], r["data_bits"], r["raw_logical"]) == 0

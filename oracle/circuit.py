@@ -37,6 +37,15 @@ ancillas (bits d^2 + k) and runs the circuit step by step.  Both consume the
 same random draws: noise sites are keyed by (round, step, physical qubit) with
 ancilla k numbered d^2 + k, a two-qubit gate's site is its data qubit.
 
+Twirled variant (twirl = 1; Sec. III.A: a coherent term whose coherence is
+destroyed, e.g. by twirling, acts as a stochastic Pauli error): every
+coherent term R_A(theta) is replaced by the Pauli A with probability
+sin^2(theta/2), and the crosstalk exp(-i phi Z(x)Z) by Z(x)Z with probability
+sin^2(phi).  Each such term is a draw of its own (tag 4, site field
+factor << 24 | site, factor = index of the term on that site in that step:
+0..3 the one-qubit terms after Rx/Rz factors, 4 the Rzx term, 5 the ZZ term,
+6 / 7 the round-start R_Z / R_X).
+
 Draws (Philox4x64-10, counter (trajectory, round, step<<32 | site, tag)):
 occurrence iff (w0 >> 11) 2^-53 < p; Eq. 1 Pauli index = ((w1 >> 32) * 3 >> 32)
 -> X, Y, Z; Eq. 2 pair index k = ((w1 >> 32) * 15 >> 32) + 1, ancilla Pauli
@@ -48,9 +57,9 @@ import numpy as np
 
 from . import gates as G
 from .lattice import stabilizers, logical_z_support
-from .philox import draw, uniform53, TAG_NOISE, TAG_MEASURE, TAG_READOUT
+from .philox import draw, uniform53, TAG_NOISE, TAG_MEASURE, TAG_READOUT, TAG_TWIRL
 
-NOISE_KEYS = ("p1", "p2", "p_idle", "theta_rx", "theta_rz", "theta_rzx", "phi_zz", "round_rz", "round_rx")
+NOISE_KEYS = ("p1", "p2", "p_idle", "theta_rx", "theta_rz", "theta_rzx", "phi_zz", "round_rz", "round_rx", "twirl")
 
 
 def noise_dict(**kw):
@@ -78,6 +87,7 @@ class Trajectory:
         self.inject = inject or []        # (round, step, data qubit, 2x2 matrix), applied after that step's ops
         self.ops = []
         self.events = []                  # sampled Paulis: (round, step, site, pauli code)
+        self.twirls = []                  # fired twirled terms: (round, step, site, factor)
         self.meas = []                    # measurement records, in op order
         nx = [0] * self.nd
         nz = [0] * self.nd
@@ -105,6 +115,32 @@ class Trajectory:
             self.events.append((rnd, t, site, code))
             self.u1(q, G.PAULI[code])
 
+    def coherent1(self, rnd, t, site, factor, q, pauli, theta):
+        """R_P(theta) on q, or (twirled) the Pauli P with probability sin^2(theta/2)."""
+        if not theta:
+            return
+        if not self.noise["twirl"]:
+            self.u1(q, G.rot(pauli, theta))
+            return
+        w = draw(self.seed, self.traj, rnd, t, (factor << 24) | site, TAG_TWIRL)
+        if uniform53(w[0]) < np.sin(theta / 2) ** 2:
+            self.twirls.append((rnd, t, site, factor))
+            self.u1(q, pauli)
+
+    def coherent2(self, rnd, t, site, factor, qa, qb, pauli2, angle, zz):
+        """exp(-i angle/2 P) (Rzx term) or exp(-i angle P) (ZZ term, zz=True) on (qa, qb); twirled:
+        the Pauli product with probability sin^2(angle/2) / sin^2(angle)."""
+        if not angle:
+            return
+        if not self.noise["twirl"]:
+            self.u2(qa, qb, G.zz_crosstalk(angle) if zz else G.rot(pauli2, angle))
+            return
+        w = draw(self.seed, self.traj, rnd, t, (factor << 24) | site, TAG_TWIRL)
+        prob = np.sin(angle) ** 2 if zz else np.sin(angle / 2) ** 2
+        if uniform53(w[0]) < prob:
+            self.twirls.append((rnd, t, site, factor))
+            self.u2(qa, qb, pauli2)
+
     def e2(self, rnd, t, site, qa, qd, p):
         if rnd == 0 or p <= 0.0:
             return
@@ -124,19 +160,18 @@ class Trajectory:
         nz = self.noise
         noisy = rnd > 0
         if t == 0:
-            if noisy and nz["round_rz"]:
-                self.u1(q, G.rot(G.PZ, nz["round_rz"]))
-            if noisy and nz["round_rx"]:
-                self.u1(q, G.rot(G.PX, nz["round_rx"]))
+            if noisy:
+                self.coherent1(rnd, t, q, 6, q, G.PZ, nz["round_rz"])
+                self.coherent1(rnd, t, q, 7, q, G.PX, nz["round_rx"])
         elif self.gates == "cr" and t in (6, 11):
             n_fact = self.nx[q] if t == 6 else self.nz[q]
             base = G.RX90 if t == 6 else G.RZ90
             over = nz["theta_rx"] if t == 6 else nz["theta_rz"]
             pauli = G.PX if t == 6 else G.PZ
-            for _ in range(n_fact):
+            for f in range(n_fact):
                 self.u1(q, base)
-                if noisy and over:
-                    self.u1(q, G.rot(pauli, over))
+                if noisy:
+                    self.coherent1(rnd, t, q, f, q, pauli, over)
             self.e1(rnd, t, q, q, nz["p1"])
         else:
             self.e1(rnd, t, q, q, nz["p_idle"])
@@ -157,8 +192,8 @@ class Trajectory:
                     self.u1(a, G.H)
                 else:
                     self.u1(a, G.RX90DG if t == 1 else G.RX90)
-                    if noisy and nz["theta_rx"]:
-                        self.u1(a, G.rot(G.PX, nz["theta_rx"]))
+                    if noisy:
+                        self.coherent1(rnd, t, site_a, 0, a, G.PX, nz["theta_rx"])
                 self.e1(rnd, t, site_a, a, nz["p1"])
                 return
             slot = t - 2
@@ -178,10 +213,10 @@ class Trajectory:
             self.u2(first, second, G.CNOT)
         else:
             self.u2(first, second, G.RZX90)
-            if noisy and nz["theta_rzx"]:
-                self.u2(first, second, G.rot(G.ZX, nz["theta_rzx"]))
-        if noisy and nz["phi_zz"]:
-            self.u2(first, second, G.zz_crosstalk(nz["phi_zz"]))
+            if noisy:
+                self.coherent2(rnd, t, q, 4, first, second, G.ZX, nz["theta_rzx"], zz=False)
+        if noisy:
+            self.coherent2(rnd, t, q, 5, first, second, G.ZZ, nz["phi_zz"], zz=True)
         self.e2(rnd, t, q, a, q, nz["p2"])
 
     def measure_anc(self, rnd, k):

@@ -23,6 +23,7 @@ PHILOX_W1 = 0xBB67AE8584CAA73B
 TAG_NOISE = 0      # Pauli occurrence and type at one noise site
 TAG_MEASURE = 1    # uniform for one ancilla measurement
 TAG_READOUT = 3    # uniform for one final data-qubit Z measurement
+TAG_TWIRL = 4      # occurrence of one twirled coherent term (site field: factor << 24 | site)
 
 
 def philox4x64_10(counter, key):

@@ -122,6 +122,14 @@ def apply_op(tab, op):
             raise ValueError("non-Clifford one-qubit op")
     elif kind == "U2":
         a, b, m = op[1], op[2], op[3]
+        for ca in range(4):                  # a product of Paulis (twirled two-qubit terms)
+            for cb in range(4):
+                if (ca or cb) and _close_up_to_phase(m, np.kron(G.PAULI[ca], G.PAULI[cb])):
+                    if ca:
+                        tab.pauli(a, ca)
+                    if cb:
+                        tab.pauli(b, cb)
+                    return
         if _close_up_to_phase(m, G.CNOT):
             tab.cnot(a, b)
         elif _close_up_to_phase(m, G.RZX90):

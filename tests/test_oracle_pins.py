@@ -387,3 +387,39 @@ def test_two_qubit_pauli_pairs_uniform():
 def test_norm_conserved_with_coherent_noise():
     r = run_trajectory(3, 4, "cr", "reduced", NOISY, seed=3, traj=5, want_state=True)
     assert abs(np.linalg.norm(r["state"]) - 1) < 1e-13
+
+
+# ---- twirled variant (Sec. III.A: decohered coherent terms act as Pauli errors) -------------
+TWIRLED = dict(NOISY, twirl=1, theta_rx=0.4, theta_rz=0.3, theta_rzx=0.3, phi_zz=0.2, round_rz=0.3, round_rx=0.25)
+
+
+@pytest.mark.parametrize("gates", ["cnot", "cr"])
+@pytest.mark.parametrize("layout", ["reduced", "unreduced"])
+def test_twirled_noise_is_clifford_and_matches_tableau(gates, layout):
+    for traj in range(6):
+        T = Trajectory(3, 3, gates, layout, TWIRLED, 13, traj).build()
+        assert T.twirls                      # the twirled terms do fire at these angles
+        outs, _ = TB.run_ops(TB.Tableau(T.n), T.ops)
+        sv = run_trajectory(3, 3, gates, layout, TWIRLED, seed=13, traj=traj)
+        sv_outs = [rec[4] for rec in sv["anc_records"]] + [rec[3] for rec in sv["readout_records"]]
+        assert outs == sv_outs
+
+
+@pytest.mark.parametrize("gates", ["cnot", "cr"])
+def test_twirled_reduced_register_equals_unreduced(gates):
+    for traj in range(8):
+        a = Trajectory(3, 3, gates, "reduced", TWIRLED, 5, traj).build()
+        b = Trajectory(3, 3, gates, "unreduced", TWIRLED, 5, traj).build()
+        assert sorted(a.twirls) == sorted(b.twirls) and sorted(a.events) == sorted(b.events)
+
+
+def test_twirl_probability_is_sin2_half_angle():
+    # round_rx alone, twirled: every data qubit gets X with probability sin^2(theta/2) per round
+    th = 0.5
+    fired = trials = 0
+    for traj in range(40):
+        T = Trajectory(3, 10, "cr", "reduced", dict(round_rx=th, twirl=1), 3, traj).build()
+        fired += sum(1 for (r, t, s, f) in T.twirls if f == 7)
+        trials += 10 * 9
+    p = np.sin(th / 2) ** 2
+    assert abs(fired / trials - p) < 4 * np.sqrt(p * (1 - p) / trials)

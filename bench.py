@@ -49,8 +49,9 @@ def parse():
     ap.add_argument("--rate", type=float, default=50.0, help="serve: mean arrival rate (requests/s)")
     ap.add_argument("--max-traj", type=int, default=8, help="serve: trajectories per request drawn from 1..max")
     ap.add_argument("--mem-gib", type=float, default=32.0, help="serve: device memory budget for state vectors")
-    ap.add_argument("--noise", default="full", choices=["full", "idle"],
-                    help="sweep: full = p on every step (Eqs. 1-2); idle = p on waiting qubits only")
+    ap.add_argument("--noise", default="full", choices=["full", "idle", "twirl"],
+                    help="sweep: full = p on every step (Eqs. 1-2); idle = p on waiting qubits only; "
+                         "twirl = full with the coherent terms replaced by their Pauli twirl")
     return ap.parse_args()
 
 
@@ -451,11 +452,11 @@ def sweep_arm(args, rank, world, local):
     n = max(1, args.steps)
     dec = Decoder(5)
     rows = []
-    for c in ((0.0, 0.5, 1.0) if args.noise == "full" else (0.0,)):
+    for c in ((0.0,) if args.noise == "idle" else (0.0, 0.5, 1.0)):
         for p in (1e-3, 2e-3, 3e-3, 5e-3):
             th = 2 * c * np.sqrt(p)
-            g = p if args.noise == "full" else 0.0
-            nz = dict(p1=g, p2=g, p_idle=p, theta_rx=th, theta_rz=th)
+            g = 0.0 if args.noise == "idle" else p
+            nz = dict(p1=g, p2=g, p_idle=p, theta_rx=th, theta_rz=th, twirl=1.0 if args.noise == "twirl" else 0.0)
             with Simulator(5, 5, "cr", "c64tc", **nz) as sim:
                 syn, bits, log = sim.run(7000, rank * n, n)
             f = [dec.logical_failure(a, b, l) for a, b, l in zip(syn, bits, log)]

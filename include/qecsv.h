@@ -52,6 +52,8 @@ typedef struct {
   double phi_zz;    /* ZZ crosstalk exp(-i phi Z(x)Z) after every two-qubit gate */
   double round_rz;  /* R_Z(angle) on every data qubit at the start of each noisy round */
   double round_rx;  /* R_X(angle) on every data qubit at the start of each noisy round */
+  double twirl;     /* 0: coherent terms as unitaries; 1: each replaced by its Pauli twirl, the
+                       generator Pauli A with probability sin^2(theta/2) (ZZ: sin^2(phi)) (Sec. III.A) */
 } qec_noise;
 
 typedef struct {

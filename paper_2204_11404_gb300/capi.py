@@ -14,7 +14,7 @@ QEC_LAYOUT_REDUCED, QEC_LAYOUT_UNREDUCED = 0, 1
 QEC_GATES_CNOT, QEC_GATES_CR = 0, 1
 QEC_C128, QEC_C64, QEC_C64_TC = 0, 1, 2
 
-NOISE_FIELDS = ("p1", "p2", "p_idle", "theta_rx", "theta_rz", "theta_rzx", "phi_zz", "round_rz", "round_rx")
+NOISE_FIELDS = ("p1", "p2", "p_idle", "theta_rx", "theta_rz", "theta_rzx", "phi_zz", "round_rz", "round_rx", "twirl")
 
 
 class qec_noise(ctypes.Structure):

@@ -99,9 +99,27 @@ __device__ __forceinline__ T2 cmul_add(T2 acc, T2 a, T2 b) {
 }
 
 // Per-trajectory coherent matrices (same conventions as the program builder).
+// Per-trajectory probabilities: p1, p2, p_idle and the twirl probabilities (0 unless twirled).
+__device__ void traj_probs(const qec_noise& nz, double* prob) {
+  const bool on = nz.twirl != 0.0;
+  prob[PR_P1] = nz.p1;
+  prob[PR_P2] = nz.p2;
+  prob[PR_IDLE] = nz.p_idle;
+  auto half = [&](double th) { const double s = sin(th / 2); return on ? s * s : 0.0; };
+  prob[PR_TW_RX] = half(nz.theta_rx);
+  prob[PR_TW_RZ] = half(nz.theta_rz);
+  prob[PR_TW_RZX] = half(nz.theta_rzx);
+  prob[PR_TW_ZZ] = on ? sin(nz.phi_zz) * sin(nz.phi_zz) : 0.0;
+  prob[PR_TW_ROUND_RZ] = half(nz.round_rz);
+  prob[PR_TW_ROUND_RX] = half(nz.round_rx);
+}
+
+// Per-trajectory coherent matrices; identities when the trajectory's coherent terms are twirled
+// (the program holds both forms of every term).
 template <typename T2>
-__device__ void coherent_mats(T2 (*m)[16], const qec_noise& nz, int lane) {
+__device__ void coherent_mats(T2 (*m)[16], qec_noise nz, int lane) {
   if (lane != 0) return;
+  if (nz.twirl != 0.0) nz.theta_rx = nz.theta_rz = nz.theta_rzx = nz.phi_zz = nz.round_rz = nz.round_rx = 0.0;
   auto clear = [&](int id) { for (int i = 0; i < 16; ++i) m[id][i] = mk<T2>(0, 0); };
   auto rot1 = [&](int id, bool x, double th) {
     clear(id);
@@ -253,7 +271,8 @@ __device__ void run_warp(const BatchArgs& a, unsigned char* wsm, uint32_t item) 
   }
   __syncwarp();
   if (!init) coherent_mats(mats, nz, lane);
-  const double prob[3] = {nz.p1, nz.p2, nz.p_idle};
+  double prob[PR_COUNT];
+  traj_probs(nz, prob);
   if (init) {
     for (int i = lane; i < kNAmp; i += 32) psi[i] = mk<T2>(i == 0 ? 1.0 : 0.0, 0.0);
   } else {
@@ -273,6 +292,15 @@ __device__ void run_warp(const BatchArgs& a, unsigned char* wsm, uint32_t item) 
       __syncwarp();
       for (int oi = bi.op_begin; oi < bi.op_end; ++oi) {
         const ProgOp op = ops[oi];
+        if (op.kind == OP_T1 || op.kind == OP_T2) {
+          int fire = 0;
+          if (lane == 0) fire = twirl_fires(op, prob[op.pidx], a.ctl->seed, traj, (uint64_t)rnd) ? 1 : 0;
+          fire = __shfl_sync(0xffffffffu, fire, 0);
+          if (!fire) continue;
+          if (op.kind == OP_T1) apply1_w<T>(U, w, op.q0, mats[op.mat], lane);
+          else apply2_w<T>(U, w, op.q0, op.q1, mats[op.mat], lane);
+          continue;
+        }
         if (op.kind == OP_N1 || op.kind == OP_N2) {
           int code = 0;
           if (lane == 0) code = noise_code(op, prob[op.pidx], a.ctl->seed, traj, (uint64_t)rnd);
@@ -386,7 +414,8 @@ __device__ void run_cta_u(const BatchArgs& a, unsigned char* sm, uint32_t item) 
   const ProgOp* ops = init ? a.iuops : a.uops;
   const UItem* items = init ? a.iuitems : a.uitems;
   const int nitems = init ? a.n_iuitems : a.n_uitems;
-  const double prob[3] = {nz.p1, nz.p2, nz.p_idle};
+  double prob[PR_COUNT];
+  traj_probs(nz, prob);
   for (int i = tid; i < M_COUNT * 16; i += nt) {
     const int id = i / 16, e = i % 16;
     mats[id][e] = mk<T2>(a.mats[(id * 16 + e) * 2], a.mats[(id * 16 + e) * 2 + 1]);
@@ -421,6 +450,8 @@ __device__ void run_cta_u(const BatchArgs& a, unsigned char* sm, uint32_t item) 
               code = noise_code(op, prob[op.pidx], seed, traj, (uint64_t)rnd);
               if (!code) continue;
             }
+            if ((op.kind == OP_T1 || op.kind == OP_T2) && !twirl_fires(op, prob[op.pidx], seed, traj, (uint64_t)rnd))
+              continue;
             // left-multiply M by this op's matrix G (dim x dim, embedded in the unit's local qubits)
             double2 G[16];
             for (int i = 0; i < 16; ++i) G[i] = make_double2(0.0, 0.0);
@@ -428,10 +459,10 @@ __device__ void run_cta_u(const BatchArgs& a, unsigned char* sm, uint32_t item) 
               return make_double2((double)mats[id][r * 4 + c].x, (double)mats[id][r * 4 + c].y);
             };
             if (dim == 2) {
-              const int id = op.kind == OP_U1 ? op.mat : code;
+              const int id = (op.kind == OP_U1 || op.kind == OP_T1) ? op.mat : code;
               for (int r = 0; r < 2; ++r)
                 for (int c = 0; c < 2; ++c) G[r * 4 + c] = from_tab(id, r, c);
-            } else if (op.kind == OP_U2) {
+            } else if (op.kind == OP_U2 || op.kind == OP_T2) {
               for (int r = 0; r < 4; ++r)
                 for (int c = 0; c < 4; ++c) G[r * 4 + c] = from_tab(op.mat, r, c);
             } else {
@@ -760,7 +791,7 @@ qec_status qec_batch_create(int32_t d, int32_t rounds, int32_t gates, uint32_t m
   p.gates = gates;
   p.precision = QEC_C128;
   // every noise site and coherent op present; the per-trajectory values decide what they do
-  p.noise = qec_noise{1, 1, 1, 1, 1, 1, 1, 1, 1};
+  p.noise = qec_noise{1, 1, 1, 1, 1, 1, 1, 1, 1, 0};
   std::string err;
   qec_batch* b = new (std::nothrow) qec_batch();
   if (!b) return bfail(QEC_ENOMEM, "host allocation failed");
@@ -769,8 +800,8 @@ qec_status qec_batch_create(int32_t d, int32_t rounds, int32_t gates, uint32_t m
   b->gates = gates;
   b->cap = max_traj;
   b->user = static_cast<cudaStream_t>(cuda_stream);
-  if (!build_program(p, true, b->prog, err) || !build_program(p, false, b->iprog, err) ||
-      !build_unreduced_program(p, true, b->uprog, err) || !build_unreduced_program(p, false, b->iuprog, err))
+  if (!build_program(p, true, b->prog, err, true) || !build_program(p, false, b->iprog, err) ||
+      !build_unreduced_program(p, true, b->uprog, err, true) || !build_unreduced_program(p, false, b->iuprog, err))
     return bail(bfail(QEC_EINVAL, err));
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -865,6 +896,7 @@ qec_status qec_batch_run(qec_batch* b, uint64_t seed, uint32_t n, const uint64_t
     const double an[6] = {z.theta_rx, z.theta_rz, z.theta_rzx, z.phi_zz, z.round_rz, z.round_rx};
     for (double v : an)
       if (!(std::fabs(v) <= 4.0)) return bfail(QEC_EINVAL, "angles must be finite with |angle| <= 4");
+    if (z.twirl != 0.0 && z.twirl != 1.0) return bfail(QEC_EINVAL, "twirl must be 0 or 1");
   }
   if (b->user) {
     QEC_BCUDA(cudaEventRecord(b->ev_in, b->user));

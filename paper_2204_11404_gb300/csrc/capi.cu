@@ -104,10 +104,10 @@ qec_status upload_program(qec_sim* s, int which, const Program& P) {
   size_t cap = P.ops.size() + 1;
   if (which == 1) {   // room for every noise site and coherent op, so qec_reconfigure never reallocates
     qec_params full = s->p;
-    full.noise = qec_noise{1, 1, 1, 1, 1, 1, 1, 1, 1};
+    full.noise = qec_noise{1, 1, 1, 1, 1, 1, 1, 1, 1, 0};
     Program F;
     std::string err;
-    if (build_program(full, true, F, err) && F.ops.size() + 1 > cap) cap = F.ops.size() + 1;
+    if (build_program(full, true, F, err, true) && F.ops.size() + 1 > cap) cap = F.ops.size() + 1;
     s->ops_cap = cap;
   }
   if ((st = dmalloc(&s->d_ops[which], sizeof(ProgOp) * cap)) != QEC_OK) return st;
@@ -126,7 +126,7 @@ InstArgs inst_args(const qec_sim* s, int which, int round_base, int nblk, bool w
   a.ops = s->d_ops[which];
   a.blocks = s->d_blocks[which];
   a.mats = s->d_mats[which];
-  for (int i = 0; i < 3; ++i) a.prob[i] = P.prob[i];
+  for (int i = 0; i < PR_COUNT; ++i) a.prob[i] = P.prob[i];
   a.nstab = s->nstab;
   a.nd = s->D;
   a.round_base = round_base;
@@ -637,7 +637,7 @@ qec_status qec_debug_blocks(const qec_params* params, uint64_t seed, uint64_t tr
   a.ops = P.ops.data();
   a.blocks = P.blocks.data();
   a.mats = &P.mats[0][0][0];
-  for (int i = 0; i < 3; ++i) a.prob[i] = P.prob[i];
+  for (int i = 0; i < PR_COUNT; ++i) a.prob[i] = P.prob[i];
   a.nstab = P.nstab;
   a.nd = P.nd;
   a.round_base = round;

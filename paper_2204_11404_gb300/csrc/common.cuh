@@ -43,7 +43,7 @@ QEC_HD U64x4 philox4x64_10(uint64_t c0, uint64_t c1, uint64_t c2, uint64_t c3, u
   return o;
 }
 
-enum : uint64_t { TAG_NOISE = 0, TAG_MEASURE = 1, TAG_READOUT = 3 };
+enum : uint64_t { TAG_NOISE = 0, TAG_MEASURE = 1, TAG_READOUT = 3, TAG_TWIRL = 4 };
 
 // Counter (trajectory, round, step << 32 | site, tag), key (seed, 0).
 QEC_HD U64x4 draw(uint64_t seed, uint64_t traj, uint64_t rnd, uint32_t step, uint32_t site, uint64_t tag) {
@@ -59,6 +59,12 @@ QEC_HD int noise_code(const ProgOp& op, double p, uint64_t seed, uint64_t traj, 
   uint64_t hi = w.v[1] >> 32;
   if (op.kind == OP_N1) return (int)((hi * 3ull) >> 32) + 1;
   return (int)((hi * 15ull) >> 32) + 1;
+}
+
+// Twirled coherent term (OP_T1 / OP_T2): fires with probability p (site field factor << 24 | site).
+QEC_HD bool twirl_fires(const ProgOp& op, double p, uint64_t seed, uint64_t traj, uint64_t rnd) {
+  U64x4 w = draw(seed, traj, rnd, op.step, op.site, TAG_TWIRL);
+  return uniform53(w.v[0]) < p;
 }
 
 // ---- block fusion -----------------------------------------------------------------------

@@ -90,6 +90,20 @@ __device__ void inst_block(const InstArgs& a, double2* U, double (*sm)[16][2], i
   __syncthreads();
   for (int oi = bi.op_begin; oi < bi.op_end; ++oi) {
     const ProgOp op = a.ops[oi];
+    if (op.kind == OP_T1 || op.kind == OP_T2) {
+      if (tid == 0) *scode = twirl_fires(op, a.prob[op.pidx], seed, traj, rnd) ? 1 : 0;
+      __syncthreads();
+      const int fire = *scode;
+      __syncthreads();
+      if (!fire) continue;
+      if (op.kind == OP_T1) {
+        for (int it = tid; it < items_1q(w); it += nt) apply1_item(U, w, op.q0, sm[op.mat], it);
+      } else {
+        for (int it = tid; it < items_2q(w); it += nt) apply2_item(U, w, op.q0, op.q1, sm[op.mat], it);
+      }
+      __syncthreads();
+      continue;
+    }
     if (op.kind == OP_N1 || op.kind == OP_N2) {
       if (tid == 0) {
         int code = noise_code(op, a.prob[op.pidx], seed, traj, rnd);
@@ -1135,6 +1149,15 @@ void instantiate_block_host(const InstArgs& a, int blk, uint64_t seed, uint64_t 
   }
   for (int oi = bi.op_begin; oi < bi.op_end; ++oi) {
     const ProgOp op = a.ops[oi];
+    if (op.kind == OP_T1 || op.kind == OP_T2) {
+      if (!twirl_fires(op, a.prob[op.pidx], seed, traj, rnd)) continue;
+      if (op.kind == OP_T1) {
+        for (int it = 0; it < items_1q(w); ++it) apply1_item(U, w, op.q0, sm[op.mat], it);
+      } else {
+        for (int it = 0; it < items_2q(w); ++it) apply2_item(U, w, op.q0, op.q1, sm[op.mat], it);
+      }
+      continue;
+    }
     if (op.kind == OP_N1 || op.kind == OP_N2) {
       const int code = noise_code(op, a.prob[op.pidx], seed, traj, rnd);
       if (!code) continue;

@@ -30,7 +30,7 @@ struct InstArgs {
   const ProgOp* ops;
   const BlockInfo* blocks;
   const double* mats;     // [M_COUNT][16][2]
-  double prob[3];
+  double prob[PR_COUNT];
   int nstab, nd;
   int round_base;         // round of block 0 of this launch
   int nblk;               // blocks in this launch (nstab x rounds)

@@ -145,7 +145,7 @@ extern "C" qec_status qec_run_trajectories_noalloc(const qec_params* params, uin
     a.ops = ops[which];
     a.blocks = blks[which];
     a.mats = mats[which];
-    for (int i = 0; i < 3; ++i) a.prob[i] = P.prob[i];
+    for (int i = 0; i < PR_COUNT; ++i) a.prob[i] = P.prob[i];
     a.nstab = nstab;
     a.nd = D;
     a.round_base = round_base;

@@ -69,6 +69,13 @@ void fill_mats(Program& P, const qec_noise& nz, bool noisy) {
   }
   rot1(P.mats[M_ROUND_RZ], 'Z', g * nz.round_rz);
   rot1(P.mats[M_ROUND_RX], 'X', g * nz.round_rx);
+  // Pauli products Z(x)X and Z(x)Z (twirled Rzx and ZZ terms), local index 2*a + b
+  for (int i = 0; i < 16; ++i) P.mats[M_PZX][i][0] = P.mats[M_PZX][i][1] = P.mats[M_PZZ][i][0] = P.mats[M_PZZ][i][1] = 0.0;
+  for (int r = 0; r < 4; ++r) {
+    const int a = r >> 1, b = r & 1;
+    P.mats[M_PZX][4 * r + ((a << 1) | (b ^ 1))][0] = a ? -1.0 : 1.0;
+    P.mats[M_PZZ][5 * r][0] = (a ^ b) ? -1.0 : 1.0;
+  }
 }
 
 bool finite_in(double v, double lo, double hi) { return std::isfinite(v) && v >= lo && v <= hi; }
@@ -130,10 +137,22 @@ bool validate_params(const qec_params& p, std::string& err) {
   for (double v : a) {
     if (!finite_in(v, -4.0, 4.0)) { err = "angles must be finite with |angle| <= 4"; return false; }
   }
+  if (n.twirl != 0.0 && n.twirl != 1.0) { err = "twirl must be 0 or 1"; return false; }
   return true;
 }
 
-bool build_program(const qec_params& p, bool noisy, Program& P, std::string& err) {
+void twirl_probs(const qec_noise& nz, double* prob) {
+  const bool on = nz.twirl != 0.0;
+  auto half = [&](double th) { return on ? std::sin(th / 2) * std::sin(th / 2) : 0.0; };
+  prob[PR_TW_RX] = half(nz.theta_rx);
+  prob[PR_TW_RZ] = half(nz.theta_rz);
+  prob[PR_TW_RZX] = half(nz.theta_rzx);
+  prob[PR_TW_ZZ] = on ? std::sin(nz.phi_zz) * std::sin(nz.phi_zz) : 0.0;   // exp(-i phi ZZ) = R_ZZ(2 phi)
+  prob[PR_TW_ROUND_RZ] = half(nz.round_rz);
+  prob[PR_TW_ROUND_RX] = half(nz.round_rx);
+}
+
+bool build_program(const qec_params& p, bool noisy, Program& P, std::string& err, bool all_slots) {
   if (!validate_params(p, err)) return false;
   const int d = p.d, nd = d * d;
   const bool cr = p.gates == QEC_GATES_CR;
@@ -147,6 +166,10 @@ bool build_program(const qec_params& p, bool noisy, Program& P, std::string& err
   P.prob[PR_P1] = noisy ? nz.p1 : 0.0;
   P.prob[PR_P2] = noisy ? nz.p2 : 0.0;
   P.prob[PR_IDLE] = noisy ? nz.p_idle : 0.0;
+  twirl_probs(nz, P.prob);
+  if (!noisy)
+    for (int i = PR_TW_RX; i < PR_COUNT; ++i) P.prob[i] = 0.0;
+  const bool twirl = noisy && nz.twirl != 0.0;
 
   // Gate steps of each data qubit, in serial (block) order.
   std::vector<int> nx(nd, 0), nzc(nd, 0);
@@ -203,21 +226,37 @@ bool build_program(const qec_params& p, bool noisy, Program& P, std::string& err
     auto u1 = [&](uint8_t q, uint16_t m) { P.ops.push_back({OP_U1, q, 0, 0, m, 0, 0}); };
     auto u2 = [&](uint8_t a, uint8_t b, uint16_t m) { P.ops.push_back({OP_U2, a, b, 0, m, 0, 0}); };
     auto n1 = [&](uint8_t q, int step, uint32_t site, uint8_t pid) {
-      if (P.prob[pid] > 0.0) P.ops.push_back({OP_N1, q, 0, pid, 0, (uint16_t)step, site});
+      if (all_slots || P.prob[pid] > 0.0) P.ops.push_back({OP_N1, q, 0, pid, 0, (uint16_t)step, site});
     };
     auto n2 = [&](uint8_t a, uint8_t b, int step, uint32_t site) {
-      if (P.prob[PR_P2] > 0.0) P.ops.push_back({OP_N2, a, b, PR_P2, 0, (uint16_t)step, site});
+      if (all_slots || P.prob[PR_P2] > 0.0) P.ops.push_back({OP_N2, a, b, PR_P2, 0, (uint16_t)step, site});
+    };
+    // A coherent term: the unitary `um` (angle != 0), or twirled, the Pauli `tm` with
+    // probability prob[pid], drawn at (step, factor << 24 | site).
+    auto coh1 = [&](uint8_t q, int step, uint32_t site, int factor, uint16_t um, uint16_t tm, double angle, uint8_t pid) {
+      if (!noisy) return;
+      if (all_slots || (!twirl && angle != 0.0)) u1(q, um);
+      if (all_slots || (twirl && P.prob[pid] > 0.0))
+        P.ops.push_back({OP_T1, q, 0, pid, tm, (uint16_t)step, ((uint32_t)factor << 24) | site});
+    };
+    auto coh2 = [&](uint8_t a, uint8_t b, int step, uint32_t site, int factor, uint16_t um, uint16_t tm, double angle,
+                    uint8_t pid) {
+      if (!noisy) return;
+      if (all_slots || (!twirl && angle != 0.0)) u2(a, b, um);
+      if (all_slots || (twirl && P.prob[pid] > 0.0))
+        P.ops.push_back({OP_T2, a, b, pid, tm, (uint16_t)step, ((uint32_t)factor << 24) | site});
     };
     auto data_event = [&](int q, int t) {
       uint8_t lq = local(q);
       if (t == 0) {
-        if (noisy && nz.round_rz != 0.0) u1(lq, M_ROUND_RZ);
-        if (noisy && nz.round_rx != 0.0) u1(lq, M_ROUND_RX);
+        coh1(lq, t, (uint32_t)q, 6, M_ROUND_RZ, M_Z, nz.round_rz, PR_TW_ROUND_RZ);
+        coh1(lq, t, (uint32_t)q, 7, M_ROUND_RX, M_X, nz.round_rx, PR_TW_ROUND_RX);
       } else if (cr && (t == 6 || t == 11)) {
         int nfac = t == 6 ? nx[q] : nzc[q];
         for (int f = 0; f < nfac; ++f) {
           u1(lq, t == 6 ? M_RX90 : M_RZ90);
-          if (noisy && (t == 6 ? nz.theta_rx : nz.theta_rz) != 0.0) u1(lq, t == 6 ? M_ROT_RX : M_ROT_RZ);
+          if (t == 6) coh1(lq, t, (uint32_t)q, f, M_ROT_RX, M_X, nz.theta_rx, PR_TW_RX);
+          else coh1(lq, t, (uint32_t)q, f, M_ROT_RZ, M_Z, nz.theta_rz, PR_TW_RZ);
         }
         n1(lq, t, (uint32_t)q, PR_P1);
       } else {
@@ -232,7 +271,7 @@ bool build_program(const qec_params& p, bool noisy, Program& P, std::string& err
           u1(anc, M_H);
         } else {
           u1(anc, t == 1 ? M_RX90DG : M_RX90);
-          if (noisy && nz.theta_rx != 0.0) u1(anc, M_ROT_RX);
+          coh1(anc, t, site_a, 0, M_ROT_RX, M_X, nz.theta_rx, PR_TW_RX);
         }
         n1(anc, t, site_a, PR_P1);
         continue;
@@ -252,9 +291,9 @@ bool build_program(const qec_params& p, bool noisy, Program& P, std::string& err
         u2(first, second, M_CNOT);
       } else {
         u2(first, second, M_RZX90);
-        if (noisy && nz.theta_rzx != 0.0) u2(first, second, M_ROT_RZX);
+        coh2(first, second, t, (uint32_t)q, 4, M_ROT_RZX, M_PZX, nz.theta_rzx, PR_TW_RZX);
       }
-      if (noisy && nz.phi_zz != 0.0) u2(first, second, M_ZZ);
+      coh2(first, second, t, (uint32_t)q, 5, M_ZZ, M_PZZ, nz.phi_zz, PR_TW_ZZ);
       n2(anc, lq, t, (uint32_t)q);
     }
     for (auto& e : post[k]) data_event(e.first, e.second);
@@ -264,7 +303,7 @@ bool build_program(const qec_params& p, bool noisy, Program& P, std::string& err
   return true;
 }
 
-bool build_unreduced_program(const qec_params& p, bool noisy, UProgram& U, std::string& err) {
+bool build_unreduced_program(const qec_params& p, bool noisy, UProgram& U, std::string& err, bool all_slots) {
   if (!validate_params(p, err)) return false;
   const int d = p.d, nd = d * d;
   const bool cr = p.gates == QEC_GATES_CR;
@@ -285,6 +324,10 @@ bool build_unreduced_program(const qec_params& p, bool noisy, UProgram& U, std::
   U.prob[PR_P1] = noisy ? nz.p1 : 0.0;
   U.prob[PR_P2] = noisy ? nz.p2 : 0.0;
   U.prob[PR_IDLE] = noisy ? nz.p_idle : 0.0;
+  twirl_probs(nz, U.prob);
+  if (!noisy)
+    for (int i = PR_TW_RX; i < PR_COUNT; ++i) U.prob[i] = 0.0;
+  const bool twirl = noisy && nz.twirl != 0.0;
   std::vector<int> nx(nd, 0), nzc(nd, 0);
   for (const Stab& s : S)
     for (int i = 0; i < 4; ++i)
@@ -292,10 +335,24 @@ bool build_unreduced_program(const qec_params& p, bool noisy, UProgram& U, std::
   auto u1 = [&](int q, uint16_t m) { U.ops.push_back({OP_U1, (uint8_t)q, 0, 0, m, 0, 0}); };
   auto u2 = [&](int a, int b, uint16_t m) { U.ops.push_back({OP_U2, (uint8_t)a, (uint8_t)b, 0, m, 0, 0}); };
   auto n1 = [&](int q, int step, uint32_t site, uint8_t pid) {
-    if (U.prob[pid] > 0.0) U.ops.push_back({OP_N1, (uint8_t)q, 0, pid, 0, (uint16_t)step, site});
+    if (all_slots || U.prob[pid] > 0.0) U.ops.push_back({OP_N1, (uint8_t)q, 0, pid, 0, (uint16_t)step, site});
   };
   auto n2 = [&](int a, int b, int step, uint32_t site) {
-    if (U.prob[PR_P2] > 0.0) U.ops.push_back({OP_N2, (uint8_t)a, (uint8_t)b, PR_P2, 0, (uint16_t)step, site});
+    if (all_slots || U.prob[PR_P2] > 0.0)
+      U.ops.push_back({OP_N2, (uint8_t)a, (uint8_t)b, PR_P2, 0, (uint16_t)step, site});
+  };
+  auto coh1 = [&](int q, int step, uint32_t site, int factor, uint16_t um, uint16_t tm, double angle, uint8_t pid) {
+    if (!noisy) return;
+    if (all_slots || (!twirl && angle != 0.0)) u1(q, um);
+    if (all_slots || (twirl && U.prob[pid] > 0.0))
+      U.ops.push_back({OP_T1, (uint8_t)q, 0, pid, tm, (uint16_t)step, ((uint32_t)factor << 24) | site});
+  };
+  auto coh2 = [&](int a, int b, int step, uint32_t site, int factor, uint16_t um, uint16_t tm, double angle,
+                  uint8_t pid) {
+    if (!noisy) return;
+    if (all_slots || (!twirl && angle != 0.0)) u2(a, b, um);
+    if (all_slots || (twirl && U.prob[pid] > 0.0))
+      U.ops.push_back({OP_T2, (uint8_t)a, (uint8_t)b, pid, tm, (uint16_t)step, ((uint32_t)factor << 24) | site});
   };
   auto unit = [&](int nq, int qa, int qb, int begin) {
     if ((int)U.ops.size() > begin) U.items.push_back({0, begin, (int32_t)U.ops.size(), nq, qa, qb, -1, 0});
@@ -317,7 +374,7 @@ bool build_unreduced_program(const qec_params& p, bool noisy, UProgram& U, std::
             u1(a, M_H);
           } else {
             u1(a, t == 1 ? M_RX90DG : M_RX90);
-            if (noisy && nz.theta_rx != 0.0) u1(a, M_ROT_RX);
+            coh1(a, t, site_a, 0, M_ROT_RX, M_X, nz.theta_rx, PR_TW_RX);
           }
           n1(a, t, site_a, PR_P1);
           unit(1, a, 0, begin);
@@ -340,9 +397,9 @@ bool build_unreduced_program(const qec_params& p, bool noisy, UProgram& U, std::
           u2(first, second, M_CNOT);
         } else {
           u2(first, second, M_RZX90);
-          if (noisy && nz.theta_rzx != 0.0) u2(first, second, M_ROT_RZX);
+          coh2(first, second, t, (uint32_t)q, 4, M_ROT_RZX, M_PZX, nz.theta_rzx, PR_TW_RZX);
         }
-        if (noisy && nz.phi_zz != 0.0) u2(first, second, M_ZZ);
+        coh2(first, second, t, (uint32_t)q, 5, M_ZZ, M_PZZ, nz.phi_zz, PR_TW_ZZ);
         n2(a, q, t, (uint32_t)q);
         unit(2, first, second, begin);
       }
@@ -350,13 +407,14 @@ bool build_unreduced_program(const qec_params& p, bool noisy, UProgram& U, std::
         if (busy[q]) continue;
         const int begin = (int)U.ops.size();
         if (t == 0) {
-          if (noisy && nz.round_rz != 0.0) u1(q, M_ROUND_RZ);
-          if (noisy && nz.round_rx != 0.0) u1(q, M_ROUND_RX);
+          coh1(q, t, (uint32_t)q, 6, M_ROUND_RZ, M_Z, nz.round_rz, PR_TW_ROUND_RZ);
+          coh1(q, t, (uint32_t)q, 7, M_ROUND_RX, M_X, nz.round_rx, PR_TW_ROUND_RX);
         } else if (cr && (t == 6 || t == 11)) {
           const int nfac = t == 6 ? nx[q] : nzc[q];
           for (int f = 0; f < nfac; ++f) {
             u1(q, t == 6 ? M_RX90 : M_RZ90);
-            if (noisy && (t == 6 ? nz.theta_rx : nz.theta_rz) != 0.0) u1(q, t == 6 ? M_ROT_RX : M_ROT_RZ);
+            if (t == 6) coh1(q, t, (uint32_t)q, f, M_ROT_RX, M_X, nz.theta_rx, PR_TW_RX);
+            else coh1(q, t, (uint32_t)q, f, M_ROT_RZ, M_Z, nz.theta_rz, PR_TW_RZ);
           }
           n1(q, t, (uint32_t)q, PR_P1);
         } else {

@@ -16,8 +16,14 @@
 
 namespace qec {
 
-enum OpKind : uint8_t { OP_U1 = 0, OP_U2 = 1, OP_N1 = 2, OP_N2 = 3 };
-enum ProbId : uint8_t { PR_P1 = 0, PR_P2 = 1, PR_IDLE = 2 };
+// OP_T1 / OP_T2: a twirled coherent term: the Pauli (product) `mat` with probability prob[pidx]
+// (site field = factor << 24 | physical site, drawn with its own stream tag).
+enum OpKind : uint8_t { OP_U1 = 0, OP_U2 = 1, OP_N1 = 2, OP_N2 = 3, OP_T1 = 4, OP_T2 = 5 };
+enum ProbId : uint8_t {
+  PR_P1 = 0, PR_P2 = 1, PR_IDLE = 2,
+  PR_TW_RX = 3, PR_TW_RZ = 4, PR_TW_RZX = 5, PR_TW_ZZ = 6, PR_TW_ROUND_RZ = 7, PR_TW_ROUND_RX = 8,
+  PR_COUNT = 9
+};
 
 // Local qubits of a block: data j = 0..w-1 (ascending global bit), ancilla = w.
 struct ProgOp {
@@ -40,7 +46,7 @@ struct BlockInfo {
 
 enum MatId : uint16_t {
   M_I = 0, M_X, M_Y, M_Z, M_H, M_RX90, M_RX90DG, M_RZ90, M_CNOT, M_RZX90,
-  M_ROT_RX, M_ROT_RZ, M_ROT_RZX, M_ZZ, M_ROUND_RZ, M_ROUND_RX, M_COUNT
+  M_ROT_RX, M_ROT_RZ, M_ROT_RZX, M_ZZ, M_ROUND_RZ, M_ROUND_RX, M_PZX, M_PZZ, M_COUNT
 };
 
 struct Program {
@@ -48,7 +54,7 @@ struct Program {
   std::vector<ProgOp> ops;
   std::vector<BlockInfo> blocks;    // nstab blocks, serial order
   double mats[M_COUNT][16][2];      // 4x4 complex row-major; one-qubit gates in the top-left 2x2
-  double prob[3];                   // p1, p2, p_idle (0 in the init program)
+  double prob[PR_COUNT];            // p1, p2, p_idle, twirl probabilities (0 in the init program)
 };
 
 struct Stab {
@@ -77,14 +83,19 @@ struct UProgram {
   std::vector<ProgOp> ops;
   std::vector<UItem> items;         // one round
   double mats[M_COUNT][16][2];
-  double prob[3];
+  double prob[PR_COUNT];
 };
 
-bool build_unreduced_program(const qec_params& p, bool noisy, UProgram& out, std::string& err);
+// all_slots: emit every noise site and both the unitary and the twirled form of every coherent
+// term (probabilities and angles then decide per trajectory) -- the batched form's template.
+bool build_unreduced_program(const qec_params& p, bool noisy, UProgram& out, std::string& err,
+                             bool all_slots = false);
 
 std::vector<Stab> make_stabilizers(int d);
 bool validate_params(const qec_params& p, std::string& err);
 // noisy = false: the noise-free init round (no noise sites, no coherent terms).
-bool build_program(const qec_params& p, bool noisy, Program& out, std::string& err);
+bool build_program(const qec_params& p, bool noisy, Program& out, std::string& err, bool all_slots = false);
+// The twirl probabilities prob[PR_TW_*] of a noise setting (0 when twirl is off).
+void twirl_probs(const qec_noise& nz, double* prob);
 
 }  // namespace qec

@@ -67,6 +67,8 @@ def test_batched_unreduced_register_matches_oracle_and_reduced(gates):
     kinds = ["c128u", "c64u", "c128", "c64"] * (n // 4)
     noise = [dict(W.STRESS) if i % 2 else dict(p1=0.02, p2=0.02, p_idle=0.01, theta_rx=0.08, phi_zz=0.03)
              for i in range(n)]
+    for i in range(0, n, 3):                 # a third of them with twirled coherent terms
+        noise[i] = dict(noise[i], twirl=1, theta_rx=0.4, phi_zz=0.2, round_rz=0.3)
     with BatchSimulator(3, gates, max_traj=64) as b:
         syn, bits, log = b.run(91, traj, kinds, noise)
     amb = 0

@@ -143,3 +143,17 @@ def test_d5_full_size_trajectory_matches_oracle(prec):
 def sim_kernel_times(sim):
     from paper_2204_11404_gb300 import capi
     return capi.qec_kernel_times(sim.h)
+
+
+TWIRLED = dict(W.STRESS, twirl=1, theta_rx=0.4, theta_rz=0.3, theta_rzx=0.3, phi_zz=0.2, round_rz=0.3, round_rx=0.25)
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+def test_d3_twirled_matches_oracle(prec):
+    with Simulator(3, 3, "cr", prec, **TWIRLED) as sim:
+        kinds = check_batch(sim, 3, 3, "cr", TWIRLED, 47, 0, 40, prec)
+        assert kinds.count("ambiguous") <= (0 if prec == "c128" else 2)
+        syn, bits, log = sim.run(47, 5, 1)
+        o = oracle_traj(3, 3, "cr", TWIRLED, 47, 5, want_state=True)
+        if compare_trajectory(syn[0], bits[0], o, TAU[prec]) == "exact":
+            assert np.abs(sim.state() - o["state"][: 1 << 9]).max() < AMP_TOL[prec]

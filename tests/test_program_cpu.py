@@ -50,3 +50,16 @@ def test_invalid_params_rejected():
     p = capi.make_params(3, 3, p1=1.5)
     with pytest.raises(capi.QecError):
         capi.qec_debug_program(p, n.ctypes.data, 0, n.ctypes.data, 0)
+
+
+TWIRLED = dict(NOISY, twirl=1, theta_rx=0.4, theta_rz=0.3, theta_rzx=0.3, phi_zz=0.2, round_rz=0.3, round_rx=0.25)
+
+
+@pytest.mark.parametrize("gates", ["cnot", "cr"])
+def test_host_blocks_match_oracle_twirled(gates):
+    params = capi.make_params(3, 3, gates, **TWIRLED)
+    for traj in range(6):
+        syn, psi = kraus_run(params, 23, traj)
+        o = run_trajectory(3, 3, gates, "reduced", TWIRLED, seed=23, traj=traj, want_state=True)
+        assert (syn == o["syndromes"]).all()
+        assert np.abs(psi - o["state"][: 1 << 9]).max() < 1e-13

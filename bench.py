@@ -39,7 +39,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=9)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--precision", default="c128", choices=["c128", "c64", "c64tc"])
+    ap.add_argument("--precision", default="c128", choices=["c128", "c64", "c64tc", "c128tc"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--points", type=int, default=9, help="noise points used (1..9); fewer = smaller device footprint")
     ap.add_argument("--workload", default="d5", choices=["d5", "batched", "serve", "precision", "sweep"],
@@ -276,7 +276,7 @@ def native_arm(args, rank, world, local):
     ms_apply = float(np.mean([k[1] for k in kt]))
     amps = 1 << 25
     flops_apply = amps * 16 * 8            # 16x16 complex mat-vec per 16 amplitudes: 16 cmacs/amp
-    bytes_apply = amps * (32 if args.precision == "c128" else 16)
+    bytes_apply = amps * (32 if args.precision in ("c128", "c128tc") else 16)
     flops_prob = amps * (16 * 8 * 136 // 256 + 4)
     if args.precision == "c128":
         roof = {"bound": "alu", "achieved": flops_apply / (ms_apply * 1e-3) / 1e12, "peak": FP64_PEAK_TFLOPS,
@@ -290,6 +290,7 @@ def native_arm(args, rank, world, local):
     roof["kernel"] = {"c128": "k_apply<double,4> (weight-4 block, 2^25 amplitudes)",
                       "c64": "k_fused<float,4,4> (apply weight-4 block + next block's probability, 2^25 amplitudes)",
                       "c64tc": "k_fused_tc (tcgen05 3xTF32: apply weight-4 block + next probability, 2^25 amplitudes)",
+                      "c128tc": "k_apply_oz (tcgen05 FP16 8-bit slices, FP64-exact: weight-4 block, 2^25 amplitudes)",
                       }[args.precision]
     roof["ms_apply"] = ms_apply
     roof["ms_prob"] = ms_prob
@@ -300,7 +301,8 @@ def native_arm(args, rank, world, local):
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": {"c128": "f64", "c64": "f32", "c64tc": "tf32x3"}[args.precision],
+        "scaling": "weak", "vs_baseline": None, "dtype": {"c128": "f64", "c64": "f32", "c64tc": "tf32x3",
+                                                                 "c128tc": "f64 (fp16 slices)"}[args.precision],
         "data": "synthetic", "config": workload_config(args, world), "clocks": clk.summary(),
         "e2e": e2e, "gpu_launches": launches_per_traj * args.steps, "roofline": roof,
     }
@@ -419,14 +421,14 @@ def precision_arm(args, rank, world, local):
     for i, pt in enumerate(W.D5_CR["points"]):
         seed = W.D5_CR["seed_base"] + i
         res = {}
-        for prec in ("c128", "c64", "c64tc"):
+        for prec in ("c128", "c128tc", "c64", "c64tc"):
             with Simulator(5, W.D5_CR["rounds"], "cr", prec, **pt) as sim:
                 syn, bits, log = sim.run(seed, 0, n)
                 res[prec] = (syn, bits, log, sim.state())
         ref = res["c128"]
         row = {"p": pt["p1"], "theta_rx": pt["theta_rx"], "trajectories": n,
                "pL_c128": dec.logical_error_rate(*ref[:3])}
-        for prec in ("c64", "c64tc"):
+        for prec in ("c128tc", "c64", "c64tc"):
             s, b, l, st = res[prec]
             same = [bool((s[t] == ref[0][t]).all() and (b[t] == ref[1][t]).all()) for t in range(n)]
             row[prec] = {"identical_trajectories": int(sum(same)), "pL": dec.logical_error_rate(s, b, l),

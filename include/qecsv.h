@@ -38,8 +38,14 @@ typedef enum { QEC_GATES_CNOT = 0, QEC_GATES_CR = 1 } qec_gateset;
 /* Amplitude storage / arithmetic.  C128: complex128 state, FP64 arithmetic.
  * C64: complex64 state, FP32 gate arithmetic, FP64 probability reductions.
  * C64_TC: complex64 state; weight-4 block contractions on the tensor cores
- * (3xTF32 split, FP32 accumulation), FP64 probability reductions. */
-typedef enum { QEC_C128 = 0, QEC_C64 = 1, QEC_C64_TC = 2 } qec_precision;
+ * (3xTF32 split, FP32 accumulation), FP64 probability reductions.
+ * C128_TC: complex128 state; weight-4 block applications (tiles of 2^11
+ * amplitudes, so d >= 5) as emulated FP64 products on the FP16 tensor cores:
+ * each operand row split into 7 signed 8-bit slices under one exponent,
+ * slice products accumulated exactly, recombined in integers and rounded
+ * once (Ozaki scheme); everything else FP64.  Same amplitudes as C128 to
+ * within a few FP64 roundings. */
+typedef enum { QEC_C128 = 0, QEC_C64 = 1, QEC_C64_TC = 2, QEC_C128_TC = 3 } qec_precision;
 
 /* Noise (Sec. III.A).  Probabilities in [0, 1]; angles in radians, |angle| <= 4. */
 typedef struct {
@@ -245,6 +251,18 @@ qec_status qec_debug_program(const qec_params* params, int32_t* ops, uint32_t ca
  */
 qec_status qec_debug_blocks(const qec_params* params, uint64_t seed, uint64_t traj, int32_t round,
                             double* kraus, double* u);
+
+/*
+ * Host-only test hook (no GPU needed): the FP64-exact emulated product that the tensor-core
+ * complex128 pass computes, run on the CPU with the same slicing and recombination code.
+ * out[m][32] = A[m][32] . B[32][32]^T (row-major FP64); each entry is the dot product of
+ * the 56-bit truncated inputs (truncation relative to each row's largest exponent) with
+ * slice products of weight below 2^-56 dropped, rounded once to FP64: absolute error at
+ * most 2^-44 * max|A[r]| * max|B[n]| + 2^-53 * |exact|.  The paper has no counterpart
+ * (an arithmetic form of the gate application of Sec. III).  Returns QEC_EINVAL on null
+ * pointers or m <= 0.
+ */
+qec_status qec_debug_ozaki_gemm(const double* A, const double* B, int32_t m, double* out);
 
 #ifdef __cplusplus
 }

@@ -9,7 +9,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libqecsv.so")
 SOURCES = ["program.cpp", "kernels.cu", "capi.cu", "noalloc.cu", "batch.cu"]
-HEADERS = ["program.hpp", "common.cuh", "kernels.hpp"]
+HEADERS = ["program.hpp", "common.cuh", "kernels.hpp", "ozaki.cuh"]
 NVCC_FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-gencode", "arch=compute_103a,code=sm_103a",
               "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall"]
 

@@ -12,7 +12,7 @@ from .build import LIB, build
 QEC_OK, QEC_EINVAL, QEC_ENOMEM, QEC_ECUDA, QEC_ETIMEOUT, QEC_EUNSUPPORTED = 0, -1, -2, -3, -4, -6
 QEC_LAYOUT_REDUCED, QEC_LAYOUT_UNREDUCED = 0, 1
 QEC_GATES_CNOT, QEC_GATES_CR = 0, 1
-QEC_C128, QEC_C64, QEC_C64_TC = 0, 1, 2
+QEC_C128, QEC_C64, QEC_C64_TC, QEC_C128_TC = 0, 1, 2, 3
 
 NOISE_FIELDS = ("p1", "p2", "p_idle", "theta_rx", "theta_rz", "theta_rzx", "phi_zz", "round_rz", "round_rx", "twirl")
 
@@ -62,6 +62,7 @@ SIGNATURES = {
                            _P, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32)], ctypes.c_int),
     "qec_debug_blocks": ([ctypes.POINTER(qec_params), ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int32, _P, _P],
                          ctypes.c_int),
+    "qec_debug_ozaki_gemm": ([_P, _P, ctypes.c_int32, _P], ctypes.c_int),
 }
 
 
@@ -90,7 +91,7 @@ def make_params(d, rounds, gates="cr", precision="c128", layout="reduced", **noi
     p.d, p.rounds = int(d), int(rounds)
     p.layout = {"reduced": QEC_LAYOUT_REDUCED, "unreduced": QEC_LAYOUT_UNREDUCED}[layout]
     p.gates = {"cnot": QEC_GATES_CNOT, "cr": QEC_GATES_CR}[gates]
-    p.precision = {"c128": QEC_C128, "c64": QEC_C64, "c64tc": QEC_C64_TC}[precision]
+    p.precision = {"c128": QEC_C128, "c64": QEC_C64, "c64tc": QEC_C64_TC, "c128tc": QEC_C128_TC}[precision]
     p.reserved = 0
     for k, v in noise.items():
         if k not in NOISE_FIELDS:
@@ -199,3 +200,7 @@ def qec_debug_program(params, ops_ptr, cap, block_ptr, block_cap):
 
 def qec_debug_blocks(params, seed, traj, rnd, kraus_ptr, u_ptr):
     return check(lib().qec_debug_blocks(ctypes.byref(params), seed, traj, rnd, kraus_ptr, u_ptr))
+
+
+def qec_debug_ozaki_gemm(A_ptr, B_ptr, m, out_ptr):
+    return check(lib().qec_debug_ozaki_gemm(A_ptr, B_ptr, m, out_ptr))

@@ -2,6 +2,7 @@
 // round, the per-trajectory CUDA graph, and the host-side test hooks.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstddef>
 #include <cstdio>
@@ -13,6 +14,7 @@
 #include "../../include/qecsv.h"
 #include "common.cuh"
 #include "kernels.hpp"
+#include "ozaki.cuh"
 #include "program.hpp"
 
 using namespace qec;
@@ -183,12 +185,18 @@ PassArgs traj_pass(const qec_sim* s, int b) {
 // The complex64 form fuses block b's apply pass with block b+1's probability pass (one HBM
 // read + write per stabilizer); complex128 keeps them separate (both passes are FP64-ALU
 // bound, so fusing saves nothing there).
-bool fused_mode(const qec_sim* s) { return s->p.precision != QEC_C128; }
+bool fused_mode(const qec_sim* s) { return !is_f64(s->p.precision); }
 
 qec_status enqueue_prob(qec_sim* s, int b) {
   PassArgs a = traj_pass(s, b);
   QEC_CUDA(launch_prob(s->p.precision, a, pass_grid_for(s->p.precision, true, s->D, a.w, s->num_sms), s->work));
   return QEC_OK;
+}
+
+// One apply pass of block b (complex128 forms): on the tensor cores for QEC_C128_TC weight-4 blocks.
+cudaError_t apply_pass(qec_sim* s, const PassArgs& a) {
+  if (s->p.precision == QEC_C128_TC && apply_oz_applies(a)) return launch_apply_oz(a, s->num_sms, s->work);
+  return launch_apply(s->p.precision, a, pass_grid_for(s->p.precision, false, s->D, a.w, s->num_sms), s->work);
 }
 
 // The pass(es) that apply block b: apply(b) + prob(b+1) fused, or apply(b) then prob(b+1).
@@ -201,7 +209,7 @@ qec_status enqueue_apply(qec_sim* s, int b) {
     QEC_CUDA(launch_fused(s->p.precision, a, n, s->num_sms, s->work));
     return QEC_OK;
   }
-  QEC_CUDA(launch_apply(s->p.precision, a, pass_grid_for(s->p.precision, false, s->D, a.w, s->num_sms), s->work));
+  QEC_CUDA(apply_pass(s, a));
   return (fused_mode(s) || last) ? QEC_OK : enqueue_prob(s, b + 1);
 }
 
@@ -254,7 +262,7 @@ qec_status enqueue_part(qec_sim* s, int part) {
       if (fused_mode(s)) {
         st = enqueue_apply(s, b);
       } else {
-        QEC_CUDA(launch_apply(s->p.precision, a, pass_grid_for(s->p.precision, false, s->D, a.w, s->num_sms), s->work));
+        QEC_CUDA(apply_pass(s, a));
         if (b + 1 < tb) st = enqueue_prob(s, b + 1);
       }
     }
@@ -304,7 +312,7 @@ qec_status launch_trajectory(qec_sim* s) {
     n.src = s->psi;
     QEC_CUDA(launch_fused(s->p.precision, a, n, s->num_sms, s->work));
   } else {
-    QEC_CUDA(launch_apply(s->p.precision, a, pass_grid_for(s->p.precision, false, s->D, a.w, s->num_sms), s->work));
+    QEC_CUDA(apply_pass(s, a));
   }
   QEC_CUDA(cudaEventRecord(s->kev[2], s->work));
   QEC_CUDA(cudaGraphLaunch(s->gexec[1], s->work));
@@ -353,7 +361,7 @@ qec_status create_impl(const qec_params* params, void* stream, qec_sim** out) {
   s->nstab = s->prog.nstab;
   s->R = s->p.rounds;
   s->S = s->nstab * s->R;
-  s->amp = s->p.precision == QEC_C128 ? 16 : 8;
+  s->amp = is_f64(s->p.precision) ? 16 : 8;
   if (s->R > 0) {   // first weight-4 block of the middle noisy round
     const int rnd = (s->R + 1) / 2;
     for (int k = 0; k < s->nstab && s->timed_block < 0; ++k)
@@ -492,7 +500,7 @@ qec_status qec_get_state(qec_sim* s, void* host_buf, size_t bytes) {
   const void* src = s->S > 0 ? s->psi : s->psi0;
   double* out = static_cast<double*>(host_buf);
   const double scale = 1.0 / std::sqrt(c.final_norm);
-  if (s->p.precision == QEC_C128) {
+  if (is_f64(s->p.precision)) {
     QEC_CUDA(cudaMemcpy(out, src, 16 * n, cudaMemcpyDeviceToHost));
     for (size_t i = 0; i < 2 * n; ++i) out[i] *= scale;
   } else {
@@ -622,6 +630,38 @@ qec_status qec_debug_program(const qec_params* params, int32_t* ops, uint32_t ca
         int32_t* o = ops + 6 * i;
         o[0] = (int32_t)b; o[1] = op.kind; o[2] = op.q0; o[3] = op.q1; o[4] = op.step; o[5] = (int32_t)op.site;
       }
+    }
+  }
+  return QEC_OK;
+}
+
+qec_status qec_debug_ozaki_gemm(const double* A, const double* B, int32_t m, double* out) {
+  if (!A || !B || !out || m <= 0) return fail(QEC_EINVAL, "bad argument");
+  std::vector<int> ea(m), eb(32);
+  std::vector<int> da((size_t)m * 32 * oz::kSlices), db(32 * 32 * oz::kSlices);
+  for (int r = 0; r < m; ++r) {
+    int E = 0;
+    for (int k = 0; k < 32; ++k) E = std::max(E, oz::bexp(A[r * 32 + k]));
+    ea[r] = E;
+    for (int k = 0; k < 32; ++k) oz::split7(A[r * 32 + k], E, &da[((size_t)r * 32 + k) * oz::kSlices]);
+  }
+  for (int n = 0; n < 32; ++n) {
+    int E = 0;
+    for (int k = 0; k < 32; ++k) E = std::max(E, oz::bexp(B[n * 32 + k]));
+    eb[n] = E;
+    for (int k = 0; k < 32; ++k) oz::split7(B[n * 32 + k], E, &db[((size_t)n * 32 + k) * oz::kSlices]);
+  }
+  for (int r = 0; r < m; ++r) {
+    for (int n = 0; n < 32; ++n) {
+      float D[oz::kSlices];
+      for (int t = 0; t < oz::kSlices; ++t) {
+        float acc = 0.f;   // exact: every partial sum is an integer below 2^24
+        for (int p = 0; p <= t; ++p)
+          for (int k = 0; k < 32; ++k)
+            acc += (float)(da[((size_t)r * 32 + k) * oz::kSlices + p] * db[((size_t)n * 32 + k) * oz::kSlices + (t - p)]);
+        D[t] = acc;
+      }
+      out[r * 32 + n] = oz::assemble7(D, ea[r], eb[n]);
     }
   }
   return QEC_OK;

@@ -12,6 +12,7 @@
 
 #include "common.cuh"
 #include "kernels.hpp"
+#include "ozaki.cuh"
 
 namespace qec {
 
@@ -797,6 +798,207 @@ __global__ void __launch_bounds__(256, 2) k_fused_tc(FusedArgs f) {
   finish_prob(f.pr, accA, accN, sred, &s_last);
 }
 
+// ---- complex128 apply pass, FP64-exact on the FP16 tensor cores (Ozaki slices) -----------------
+// A weight-4 block's 16x16 complex matrix (times 1/sqrt(N)) on the 128 groups of a 2048-amplitude
+// tile is a real product y = x . B^T (x: 128 x 32 reals, B: 32 x 32).  Each row of x and of B is
+// split into 7 signed 8-bit slices under its own exponent (ozaki.cuh); the 28 slice products with
+// p + q <= 6 run as FP16 MMAs (M = 128, N = 32, K = 16) accumulating each diagonal p + q = t exactly
+// in its own FP32 TMEM accumulator; the epilogue recombines the 7 diagonals in integers and rounds
+// once to FP64.  Two CTAs per SM (103 KiB of shared memory and 256 TMEM columns each) overlap one
+// tile's copies with the other's slicing, MMAs and recombination.
+constexpr uint32_t kIdescF16 = (1u << 4) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
+constexpr int kOzTileBits = 11;
+constexpr int kOzSlab = 128 * 32;                    // fp16 elements per A slice
+constexpr int kOzSmem = 16 * (1 << kOzTileBits) + 2 * oz::kSlices * kOzSlab + 2 * oz::kSlices * 32 * 32 + 4 * 256 + 4 * 32;
+
+__device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t ad, uint64_t bd, uint32_t acc) {
+  asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+               " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+               ::"r"(d_tmem), "l"(ad), "l"(bd), "r"(kIdescF16), "r"(acc));
+}
+
+// Element offset of (row r, k) of a K = 32 16-bit operand: core matrix (r/8, k/8) of 64 elements.
+__device__ __forceinline__ int core_off16(int r, int k) { return ((r >> 3) * 4 + (k >> 3)) * 64 + (r & 7) * 8 + (k & 7); }
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// FP16x2 of (digit P of a, digit P of b): the byte is placed in the mantissa of 1024 (0x6400),
+// and one fma with (+-1, -+1024) removes the offset and applies each value's sign, exactly.
+template <int P>
+__device__ __forceinline__ uint32_t digit_pair(uint64_t Xa, uint64_t Xb, uint32_t sg, uint32_t nsg) {
+  constexpr int j = P < 3 ? 2 - P : 6 - P;           // byte of the 32-bit word holding bits 48-8P..55-8P
+  const uint32_t wa = P < 3 ? (uint32_t)(Xa >> 32) : (uint32_t)Xa;
+  const uint32_t wb = P < 3 ? (uint32_t)(Xb >> 32) : (uint32_t)Xb;
+  const uint32_t t = (__byte_perm(wa, wb, j | (j << 4) | ((4 + j) << 8) | ((4 + j) << 12)) & 0x00FF00FFu) | 0x64006400u;
+  uint32_t r;
+  asm("fma.rn.f16x2 %0, %1, %2, %3;" : "=r"(r) : "r"(t), "r"(sg), "r"(nsg));
+  return r;
+}
+
+// Writes the 7 FP16 slices of 8 consecutive reals x[0..7] (row `row`, k0 % 8 == 0) under exponent E.
+__device__ __forceinline__ void put_slices8(uint16_t* S, int slab, int row, int k0, const double* x, int E) {
+  uint64_t X[8];
+  uint32_t sg[4], nsg[4];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) X[j] = E ? oz::mag56(x[j], E) : 0ull;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const uint32_t sb = (uint32_t)(oz::d2u(x[2 * i]) >> 63) << 15 | (uint32_t)(oz::d2u(x[2 * i + 1]) >> 63) << 31;
+    sg[i] = 0x3C003C00u | sb;
+    nsg[i] = 0xE400E400u ^ sb;
+  }
+  uint16_t* base = S + core_off16(row, k0);
+#define QEC_OZ_SLICE(P)                                                                    \
+  *reinterpret_cast<uint4*>(base + (P) * slab) =                                         \
+      make_uint4(digit_pair<P>(X[0], X[1], sg[0], nsg[0]), digit_pair<P>(X[2], X[3], sg[1], nsg[1]), \
+                 digit_pair<P>(X[4], X[5], sg[2], nsg[2]), digit_pair<P>(X[6], X[7], sg[3], nsg[3]));
+  QEC_OZ_SLICE(0) QEC_OZ_SLICE(1) QEC_OZ_SLICE(2) QEC_OZ_SLICE(3) QEC_OZ_SLICE(4) QEC_OZ_SLICE(5) QEC_OZ_SLICE(6)
+#undef QEC_OZ_SLICE
+}
+
+__global__ void __launch_bounds__(256, 2) k_apply_oz(FusedArgs f) {
+  constexpr int TS = 1 << kOzTileBits;
+  extern __shared__ __align__(128) unsigned char osm[];
+  const uint32_t lmask = (1u << f.lb) - 1u;
+  double2* tile = reinterpret_cast<double2*>(osm);
+  uint16_t* A = reinterpret_cast<uint16_t*>(tile + TS);            // 7 slices x 128 rows x 32
+  uint16_t* B = A + oz::kSlices * kOzSlab;                         // 7 slices x 32 rows x 32
+  int* rowE = reinterpret_cast<int*>(B + oz::kSlices * 32 * 32);   // [2][128]: per half row
+  int* colE = rowE + 256;
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_base;
+  __shared__ int s_err;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  if (tid < 32) {   // B: real embedding of K_m / sqrt(N), one row per thread, sliced
+    const int n = tid, r = n >> 1;
+    const int m = *f.ap.m;
+    const double scale = 1.0 / sqrt(*f.ap.N);
+    const double2* Kg = reinterpret_cast<const double2*>(f.ap.kraus) + (m ? 256 : 0);
+    double b[32];
+    int E = 0;
+#pragma unroll
+    for (int l = 0; l < 16; ++l) {
+      const double2 kv = Kg[r * 16 + l];
+      const double re = kv.x * scale, im = kv.y * scale;
+      b[2 * l] = (n & 1) ? im : re;
+      b[2 * l + 1] = (n & 1) ? re : -im;
+      E = max(E, max(oz::bexp(b[2 * l]), oz::bexp(b[2 * l + 1])));
+    }
+    colE[n] = E;
+#pragma unroll
+    for (int kc = 0; kc < 4; ++kc) put_slices8(B, 32 * 32, n, 8 * kc, b + 8 * kc, E);
+  }
+  if (tid == 0) {
+    s_err = 0;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(smem_u32(&tmem_base)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  tc_sync();
+  const uint32_t tmem = tmem_base;
+  const uint32_t mb = smem_u32(&mbar);
+  int qa[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) qa[j] = f.qa[j];
+  // thread = (row r, half hf): amplitudes 8hf..8hf+7 of group r, reals 16hf..16hf+15
+  const int r = tid & 127, hf = tid >> 7;
+  const uint32_t gbase = local_base<4>((uint32_t)r, qa);
+  uint32_t offa[8];
+#pragma unroll
+  for (int l = 0; l < 8; ++l) offa[l] = gbase + member_off<4>(8 * hf + l, qa);
+  uint32_t coff[TS / 256];   // this thread's amplitudes of a tile for the copies: e = tid + 256 i
+#pragma unroll
+  for (int i = 0; i < TS / 256; ++i) {
+    const uint32_t e = (uint32_t)tid + 256u * i, h = e >> f.lb;
+    uint32_t o = 0;
+    for (int j = 0; j < f.nt - f.lb; ++j) o |= ((h >> j) & 1u) << f.hbits[j];
+    coff[i] = o | (e & lmask);
+  }
+  const uint32_t tlane = (uint32_t)(32 * (warp & 3)) << 16;
+  const double2* src = reinterpret_cast<const double2*>(f.ap.src);
+  double2* dst = reinterpret_cast<double2*>(f.ap.dst);
+  const uint32_t ntile = 1u << f.nout;
+  uint32_t phase = 0;
+  for (uint32_t tix = blockIdx.x; tix < ntile; tix += gridDim.x) {
+    uint32_t tb = 0;
+    for (int j = 0; j < f.nout; ++j) tb |= ((tix >> j) & 1u) << f.obits[j];
+#pragma unroll
+    for (int i = 0; i < TS / 256; ++i) cp_async16(tile + tid + 256 * i, src + (tb | coff[i]));
+    cp_async_commit();
+    cp_async_wait<0>();
+    __syncthreads();
+    double x[16];
+    int E = 0;
+#pragma unroll
+    for (int l = 0; l < 8; ++l) {
+      const double2 v = tile[offa[l]];
+      x[2 * l] = v.x;
+      x[2 * l + 1] = v.y;
+      E = max(E, max(oz::bexp(v.x), oz::bexp(v.y)));
+    }
+    rowE[128 * hf + r] = E;
+    __syncthreads();
+    E = max(rowE[r], rowE[128 + r]);
+    put_slices8(A, kOzSlab, r, 16 * hf, x, E);
+    put_slices8(A, kOzSlab, r, 16 * hf + 8, x + 8, E);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    tc_sync();
+    if (tid == 0) {
+      const uint32_t a0 = smem_u32(A), b0 = smem_u32(B);
+      for (int t = 0; t < oz::kSlices; ++t)
+        for (int p = 0; p <= t; ++p)
+          for (int ks = 0; ks < 2; ++ks) {
+            const uint64_t ad = umma_desc(a0 + 2u * kOzSlab * p + 256u * ks, 128, 512);
+            const uint64_t bd = umma_desc(b0 + 2u * 32 * 32 * (t - p) + 256u * ks, 128, 512);
+            umma_f16(tmem + 32u * t, ad, bd, (p > 0 || ks > 0) ? 1u : 0u);
+          }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mb) : "memory");
+    }
+    if (!mbar_wait(mb, phase & 1)) s_err = 1;
+    ++phase;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (s_err) break;
+    // outputs 16hf..16hf+15 of row r: amplitudes 8hf..8hf+7, recombined and written into the tile
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      float D[oz::kSlices][8];
+#pragma unroll
+      for (int t = 0; t < oz::kSlices; ++t) tmem_ld8(tmem + tlane + 32u * t + 16u * hf + 8u * c, D[t]);
+#pragma unroll
+      for (int j = 0; j < 8; j += 2) {
+        float d0[oz::kSlices], d1[oz::kSlices];
+#pragma unroll
+        for (int t = 0; t < oz::kSlices; ++t) {
+          d0[t] = D[t][j];
+          d1[t] = D[t][j + 1];
+        }
+        const int n = 16 * hf + 8 * c + j;
+        tile[offa[4 * c + j / 2]] = make_double2(oz::assemble7(d0, E, colE[n]), oz::assemble7(d1, E, colE[n + 1]));
+      }
+    }
+    tc_sync();
+#pragma unroll
+    for (int i = 0; i < TS / 256; ++i) dst[tb | coff[i]] = tile[tid + 256 * i];
+    tc_sync();
+  }
+  tc_sync();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem));
+  if (s_err && tid == 0) atomicOr(&f.ap.ctl->status, 1u);
+}
+
 // ---- final Z readout (Sec. III.B): sequential per-qubit sampling -------------------------
 // Qubit j gets outcome [u_j < P(q_j = 1 | outcomes of qubits < j)].  The conditional
 // marginals of the low k1 qubits come from one histogram pass over the register; the
@@ -953,7 +1155,7 @@ int hist_grid(int D, int num_sms) {
 }
 
 cudaError_t launch_instantiate(int precision, const InstArgs& a, cudaStream_t s) {
-  if (precision == QEC_C128) k_instantiate<double><<<a.nblk, 256, 0, s>>>(a);
+  if (is_f64(precision)) k_instantiate<double><<<a.nblk, 256, 0, s>>>(a);
   else k_instantiate<float><<<a.nblk, 256, 0, s>>>(a);
   return cudaGetLastError();
 }
@@ -972,7 +1174,7 @@ static void apply_t(const PassArgs& a, int grid, cudaStream_t s) {
 
 int pass_grid_for(int precision, bool prob, int D, int w, int num_sms) {
   const void* fn;
-  if (precision == QEC_C128)
+  if (is_f64(precision))
     fn = prob ? (w == 4 ? (const void*)k_prob<double, 4> : (const void*)k_prob<double, 2>)
               : (w == 4 ? (const void*)k_apply<double, 4> : (const void*)k_apply<double, 2>);
   else
@@ -983,14 +1185,14 @@ int pass_grid_for(int precision, bool prob, int D, int w, int num_sms) {
 
 cudaError_t launch_prob(int precision, const PassArgs& a, int grid, cudaStream_t s) {
   if (a.w != 2 && a.w != 4) return cudaErrorInvalidValue;
-  if (precision == QEC_C128) prob_t<double>(a, grid, s);
+  if (is_f64(precision)) prob_t<double>(a, grid, s);
   else prob_t<float>(a, grid, s);
   return cudaGetLastError();
 }
 
 cudaError_t launch_apply(int precision, const PassArgs& a, int grid, cudaStream_t s) {
   if (a.w != 2 && a.w != 4) return cudaErrorInvalidValue;
-  if (precision == QEC_C128) apply_t<double>(a, grid, s);
+  if (is_f64(precision)) apply_t<double>(a, grid, s);
   else apply_t<float>(a, grid, s);
   return cudaGetLastError();
 }
@@ -1004,7 +1206,7 @@ static size_t sample_smem(int D) {
 cudaError_t launch_readout(int precision, const ReadArgs& a, cudaStream_t s) {
   const int B = 1 << a.k1;
   const size_t smem = sample_smem(a.D);
-  if (precision == QEC_C128) {
+  if (is_f64(precision)) {
     k_hist<double><<<a.grid_hist, 256, 0, s>>>(a);
     k_hist_reduce<<<(B + 255) / 256, 256, 0, s>>>(a);
     k_sample<double><<<1, 256, smem, s>>>(a);
@@ -1044,7 +1246,7 @@ static cudaError_t fused_attrs() {
 
 cudaError_t launch_fused(int precision, const PassArgs& ap, const PassArgs& pr, int num_sms, cudaStream_t s) {
   if ((ap.w != 2 && ap.w != 4) || (pr.w != 2 && pr.w != 4)) return cudaErrorInvalidValue;
-  const size_t amp = precision == QEC_C128 ? 16 : 8;
+  const size_t amp = is_f64(precision) ? 16 : 8;
   FusedArgs f;
   f.ap = ap;
   f.pr = pr;
@@ -1089,7 +1291,7 @@ cudaError_t launch_fused(int precision, const PassArgs& ap, const PassArgs& pr, 
   const size_t smem = 2 * amp * ((size_t)1 << f.nt) + sizeof(uint32_t) * ((size_t)1 << nh);
   if (smem > (size_t)kFusedSmemMax) return cudaErrorInvalidValue;
   const int key = (ap.w == 4 ? 2 : 0) + (pr.w == 4 ? 1 : 0);
-  if (precision == QEC_C128) {
+  if (is_f64(precision)) {
     switch (key) {
       case 0: return fused_t<double, 2, 2>(f, smem, num_sms, s);
       case 1: return fused_t<double, 2, 4>(f, smem, num_sms, s);
@@ -1105,6 +1307,48 @@ cudaError_t launch_fused(int precision, const PassArgs& ap, const PassArgs& pr, 
   }
 }
 
+// Tile of one block's qubits plus low bits, >= 2^12 amplitudes (shared with the fused launchers).
+static void block_tile(const PassArgs& ap, const PassArgs& pr, int lb0, int bits, FusedArgs& f) {
+  uint32_t mask = 0;
+  for (int j = 0; j < ap.w; ++j) mask |= 1u << ap.q[j];
+  for (int j = 0; j < pr.w; ++j) mask |= 1u << pr.q[j];
+  int lb = lb0 > ap.D ? ap.D : lb0;
+  while (__builtin_popcount(mask | ((1u << lb) - 1u)) < bits && lb < ap.D) ++lb;
+  const uint32_t tmask = mask | ((1u << lb) - 1u);
+  f.lb = lb;
+  int nh = 0, no = 0;
+  for (int q = lb; q < ap.D; ++q)
+    if (tmask & (1u << q)) f.hbits[nh++] = q;
+  for (int q = 0; q < ap.D; ++q)
+    if (!(tmask & (1u << q))) f.obits[no++] = q;
+  f.nt = lb + nh;
+  f.nout = no;
+  for (int j = 0; j < 4; ++j) {
+    f.qa[j] = j < ap.w ? tile_pos(ap.q[j], lb, f.hbits, nh) : 0;
+    f.qp[j] = j < pr.w ? tile_pos(pr.q[j], lb, f.hbits, nh) : 0;
+  }
+}
+
+bool apply_oz_applies(const PassArgs& ap) {
+  if (ap.w != 4) return false;
+  FusedArgs f;
+  block_tile(ap, ap, 3, kOzTileBits, f);
+  return f.nt == kOzTileBits;
+}
+
+cudaError_t launch_apply_oz(const PassArgs& ap, int num_sms, cudaStream_t s) {
+  FusedArgs f;
+  f.ap = ap;
+  f.pr = ap;
+  block_tile(ap, ap, 3, kOzTileBits, f);
+  if (ap.w != 4 || f.nt != kOzTileBits) return cudaErrorInvalidValue;
+  int64_t g = 2ll * num_sms;   // two CTAs per SM: 103 KiB of shared memory and 256 TMEM columns each
+  if (g > (1ll << f.nout)) g = 1ll << f.nout;
+  f.grid = (int)g;
+  k_apply_oz<<<f.grid, 256, kOzSmem, s>>>(f);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_wait_selftest(unsigned int* status, long limit, cudaStream_t s) {
   k_wait_selftest<<<1, 32, 0, s>>>(status, limit);
   return cudaGetLastError();
@@ -1113,7 +1357,7 @@ cudaError_t launch_wait_selftest(unsigned int* status, long limit, cudaStream_t 
 cudaError_t launch_set_basis0(int precision, void* psi, int D, cudaStream_t s) {
   const int64_t n = 1ll << D;
   int grid = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
-  if (precision == QEC_C128) k_set_basis0<double><<<grid, 256, 0, s>>>(psi, n);
+  if (is_f64(precision)) k_set_basis0<double><<<grid, 256, 0, s>>>(psi, n);
   else k_set_basis0<float><<<grid, 256, 0, s>>>(psi, n);
   return cudaGetLastError();
 }
@@ -1123,9 +1367,12 @@ cudaError_t launch_set_basis0(int precision, void* psi, int D, cudaStream_t s) {
 cudaError_t setup_kernels(int precision, int D) {
   (void)D;
   const int smem = (int)sample_smem(25);
-  if (precision == QEC_C128) {
+  if (is_f64(precision)) {
     cudaError_t e = cudaFuncSetAttribute(k_sample<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    return e != cudaSuccess ? e : fused_attrs<double>();
+    if (e == cudaSuccess) e = fused_attrs<double>();
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_apply_oz, cudaFuncAttributeMaxDynamicSharedMemorySize, kOzSmem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_apply_oz, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    return e;
   }
   cudaError_t e = cudaFuncSetAttribute(k_sample<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e == cudaSuccess) e = fused_attrs<float>();

@@ -23,7 +23,10 @@ struct Ctl {
   unsigned int pad2;
 };
 
-constexpr int KRAUS_STRIDE = 768;   // per block: K0, K1, M = K1^dagger K1, 16x16 each
+constexpr int KRAUS_STRIDE = 768;
+
+// complex128 storage (QEC_C128, QEC_C128_TC) vs complex64.
+inline bool is_f64(int precision) { return precision == QEC_C128 || precision == QEC_C128_TC; }   // per block: K0, K1, M = K1^dagger K1, 16x16 each
 constexpr int MAX_PASS_GRID = 2048;
 
 struct InstArgs {
@@ -98,7 +101,10 @@ cudaError_t launch_readout(int precision, const ReadArgs& a, cudaStream_t s);
 cudaError_t launch_fused(int precision, const PassArgs& ap, const PassArgs& pr, int num_sms, cudaStream_t s);
 cudaError_t launch_set_basis0(int precision, void* psi, int D, cudaStream_t s);
 cudaError_t setup_kernels(int precision, int D);
-cudaError_t launch_wait_selftest(unsigned int* status, long limit, cudaStream_t s);   // once per process/device, before any capture
+cudaError_t launch_wait_selftest(unsigned int* status, long limit, cudaStream_t s);
+// complex128 apply pass on the tensor cores (weight-4 blocks whose tile has 2^12 amplitudes).
+bool apply_oz_applies(const PassArgs& ap);
+cudaError_t launch_apply_oz(const PassArgs& ap, int num_sms, cudaStream_t s);   // once per process/device, before any capture
 int pass_grid(int D, int w, int num_sms);
 // One wave of resident CTAs for the probability (prob = true) or apply pass kernel.
 int pass_grid_for(int precision, bool prob, int D, int w, int num_sms);

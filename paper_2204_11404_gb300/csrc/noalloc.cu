@@ -75,7 +75,7 @@ extern "C" qec_status qec_run_trajectories_noalloc(const qec_params* params, uin
     return nfail(QEC_EINVAL, err);
   const int D = prog.nd, nstab = prog.nstab, R = params->rounds, S = nstab * R;
   const int prec = params->precision;
-  const size_t amp = prec == QEC_C128 ? 16 : 8;
+  const size_t amp = is_f64(prec) ? 16 : 8;
 
   int dev = 0, sms = 0;
   cudaError_t e = cudaGetDevice(&dev);

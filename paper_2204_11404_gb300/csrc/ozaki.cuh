@@ -1,0 +1,134 @@
+// Error-free splitting of FP64 values into 8-bit slices and exact recombination (Ozaki scheme:
+// Ozaki, Ogita, Oishi, Rump, "Error-free transformations of matrix multiplication by using fast
+// routines of matrix multiplication and its applications", Numer. Algorithms 59 (2012)).
+//
+// A row of FP64 values x_k (|x_k| < 2^(E-1022), E = the row's largest biased exponent) is
+// written as x_k = 2^(E-1022-56) * X_k, X_k a signed 56-bit integer (truncated: error below
+// 2^-56 of the row's scale), and X_k = sum_p d_pk 2^(48-8p), p = 0..6, with signed digits
+// |d_pk| <= 255.  Digits are exact in FP16 and BF16, products of two digits are exact, and sums
+// of up to 7 x 32 such products stay below 2^24, so a tensor core with FP32 accumulation
+// computes every diagonal D_t = sum_{p+q=t} sum_k d_pk e_qk exactly.  The dot product is then
+// 2^(Ea+Eb-2044-64) * sum_{t<=6} D_t 2^(8(6-t)) (terms with p+q > 6 are below 2^-56 of the
+// scales and dropped), recombined in integers and rounded once to FP64.
+#pragma once
+#include <stdint.h>
+#include <string.h>
+
+#if defined(__CUDACC__)
+#define OZ_HD __host__ __device__ __forceinline__
+#else
+#define OZ_HD inline
+#endif
+
+namespace qec {
+namespace oz {
+
+constexpr int kSlices = 7;
+
+OZ_HD uint64_t d2u(double x) {
+#if defined(__CUDA_ARCH__)
+  return (uint64_t)__double_as_longlong(x);
+#else
+  uint64_t u;
+  memcpy(&u, &x, 8);
+  return u;
+#endif
+}
+
+OZ_HD double u2d(uint64_t u) {
+#if defined(__CUDA_ARCH__)
+  return __longlong_as_double((long long)u);
+#else
+  double x;
+  memcpy(&x, &u, 8);
+  return x;
+#endif
+}
+
+OZ_HD uint32_t f2u(float x) {
+#if defined(__CUDA_ARCH__)
+  return __float_as_uint(x);
+#else
+  uint32_t u;
+  memcpy(&u, &x, 4);
+  return u;
+#endif
+}
+
+OZ_HD float u2f(uint32_t u) {
+#if defined(__CUDA_ARCH__)
+  return __uint_as_float(u);
+#else
+  float x;
+  memcpy(&x, &u, 4);
+  return x;
+#endif
+}
+
+// Biased exponent field of x (0 for zero and subnormals, which are treated as zero).
+OZ_HD int bexp(double x) { return (int)((d2u(x) >> 52) & 0x7FF); }
+
+// BF16 bit pattern of the signed integer d, |d| <= 255 (exact).
+OZ_HD uint16_t bf16_of_int(int d) {
+  if (d == 0) return 0;
+  const uint32_t a = (uint32_t)(d < 0 ? -d : d);
+  const float f = u2f(0x4B000000u | a) - 8388608.0f;   // exact: a < 2^23
+  return (uint16_t)((f2u(f) >> 16) | (d < 0 ? 0x8000u : 0u));
+}
+
+// The 56-bit magnitude X of x relative to the row exponent E: x = 2^(E-1022-56) * (-1)^s * X.
+OZ_HD uint64_t mag56(double x, int E) {
+  const uint64_t u = d2u(x);
+  const int ex = (int)((u >> 52) & 0x7FF);
+  const int k = E - ex;                                                       // >= 0
+  const uint64_t m = ((u & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull) << 3;   // 56 bits
+  return (ex == 0 || k > 55) ? 0ull : (m >> k);
+}
+
+// The 7 signed digits of x relative to the row exponent E (x == 0 or E == 0: all zero).
+OZ_HD void split7(double x, int E, int* d) {
+  const uint64_t X = E ? mag56(x, E) : 0ull;
+  const int neg = (int)(d2u(x) >> 63);
+  for (int p = 0; p < kSlices; ++p) {
+    const int v = (int)((X >> (48 - 8 * p)) & 0xFF);
+    d[p] = neg ? -v : v;
+  }
+}
+
+// Recombination: y = 2^(Ea + Eb - 2044 - 64) * sum_t D_t 2^(8(6-t)), D_t FP32 values holding exact
+// integers (|D_t| <= (t+1) * 32 * 255^2 < 2^24).  The sum is formed in 64-bit integers with its
+// lowest 10 bits truncated (|sum| < 2^70, so the truncation is below 2^-59 of the largest possible
+// sum) and rounded once to FP64 (nearest, ties away from zero).
+OZ_HD double assemble7(const float* D, int Ea, int Eb) {
+  if (Ea == 0 || Eb == 0) return 0.0;
+  int64_t d[kSlices];
+  for (int t = 0; t < kSlices; ++t) d[t] = (int64_t)(int32_t)D[t];
+  const int64_t Z = d[0] * (1ll << 38) + d[1] * (1ll << 30) + d[2] * (1ll << 22) + d[3] * (1ll << 14) +
+                    d[4] * (1ll << 6) + ((d[5] * 256 + d[6]) >> 10);
+  if (Z == 0) return 0.0;
+  const uint64_t neg = Z < 0 ? 1ull : 0ull;
+  const uint64_t mag = neg ? (uint64_t)(-Z) : (uint64_t)Z;
+#if defined(__CUDA_ARCH__)
+  int lead = 63 - __clzll((long long)mag);
+#else
+  int lead = 63 - __builtin_clzll(mag);
+#endif
+  uint64_t mant;
+  if (lead <= 52) {
+    mant = mag << (52 - lead);
+  } else {
+    const int s = lead - 52;
+    mant = (mag + (1ull << (s - 1))) >> s;
+    if (mant >> 53) {
+      mant >>= 1;
+      ++lead;
+    }
+  }
+  const int be = lead + Ea + Eb - 2098 + 1023;       // value = mag * 2^(Ea + Eb - 2098)
+  if (be <= 0) return neg ? -0.0 : 0.0;              // below the normal range: flush
+  if (be >= 2047) return u2d((neg << 63) | 0x7FF0000000000000ull);
+  return u2d((neg << 63) | ((uint64_t)be << 52) | (mant & 0xFFFFFFFFFFFFFull));
+}
+
+}  // namespace oz
+}  // namespace qec

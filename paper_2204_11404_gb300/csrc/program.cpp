@@ -123,7 +123,7 @@ bool validate_params(const qec_params& p, std::string& err) {
   if (p.rounds < 0 || p.rounds > 64) { err = "rounds must be in [0, 64]"; return false; }
   if (p.layout != QEC_LAYOUT_REDUCED && p.layout != QEC_LAYOUT_UNREDUCED) { err = "bad layout"; return false; }
   if (p.gates != QEC_GATES_CNOT && p.gates != QEC_GATES_CR) { err = "bad gate set"; return false; }
-  if (p.precision != QEC_C128 && p.precision != QEC_C64 && p.precision != QEC_C64_TC) {
+  if (p.precision != QEC_C128 && p.precision != QEC_C64 && p.precision != QEC_C64_TC && p.precision != QEC_C128_TC) {
     err = "bad precision";
     return false;
   }

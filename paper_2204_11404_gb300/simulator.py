@@ -22,7 +22,8 @@ class Simulator:
     def reconfigure(self, rounds, **noise):
         """New noise parameters and round count; d, gate set and precision stay."""
         g = {capi.QEC_GATES_CNOT: "cnot", capi.QEC_GATES_CR: "cr"}[self.params.gates]
-        pr = {capi.QEC_C128: "c128", capi.QEC_C64: "c64", capi.QEC_C64_TC: "c64tc"}[self.params.precision]
+        pr = {capi.QEC_C128: "c128", capi.QEC_C64: "c64", capi.QEC_C64_TC: "c64tc",
+              capi.QEC_C128_TC: "c128tc"}[self.params.precision]
         params = capi.make_params(self.d, rounds, g, pr, **noise)
         capi.qec_reconfigure(self.h, params)
         self.params, self.rounds = params, int(rounds)

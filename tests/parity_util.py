@@ -4,8 +4,8 @@ import numpy as np
 # Near-threshold rule: a measurement whose oracle probability is within TAU of its uniform may
 # legitimately come out differently under another summation order; such a trajectory is
 # compared only up to that measurement.
-TAU = {"c128": 1e-9, "c64": 1e-4, "c64tc": 1e-4}
-AMP_TOL = {"c128": 1e-12, "c64": 2e-5, "c64tc": 2e-5}
+TAU = {"c128": 1e-9, "c64": 1e-4, "c64tc": 1e-4, "c128tc": 1e-9}
+AMP_TOL = {"c128": 1e-12, "c64": 2e-5, "c64tc": 2e-5, "c128tc": 1e-12}
 
 
 def measurement_sequence(o):

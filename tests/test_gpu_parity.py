@@ -120,14 +120,14 @@ def _d5_oracle():
     return _D5["o"]
 
 
-@pytest.mark.parametrize("prec", ["c128", "c64", "c64tc"])
+@pytest.mark.parametrize("prec", ["c128", "c64", "c64tc", "c128tc"])
 def test_d5_full_size_trajectory_matches_oracle(prec):
     pt, seed, o = _d5_oracle()
     with Simulator(5, 5, "cr", prec, **pt) as sim:
         sim.record_events(1 << 16)
         syn, bits, log = sim.run(seed, 0, 1)
         kind = compare_trajectory(syn[0], bits[0], o, TAU[prec])
-        if prec == "c128":
+        if prec in ("c128", "c128tc"):
             assert kind == "exact"
         if kind == "exact":
             ref = o["state"][: 1 << 25]

@@ -1,6 +1,7 @@
-"""Tensor-core complex64 form: weight-4 block contractions on tcgen05 (3xTF32, FP32
-accumulation).  Checked against the FP64 oracle and against the CUDA-core complex64 form
-on d=5 trajectories (the tensor-core pass needs 4096-amplitude tiles, so d=5)."""
+"""Tensor-core forms on d=5 trajectories (the tensor-core passes need 4096-amplitude tiles):
+complex64 with weight-4 contractions in 3xTF32, and complex128 with weight-4 applications as
+FP64-exact 8-bit-slice products on the BF16 tensor cores.  Checked against the FP64 oracle and
+against the CUDA-core forms of the same storage."""
 import numpy as np
 import pytest
 
@@ -39,3 +40,36 @@ def test_tensor_core_form_agrees_with_cuda_core_form():
             sa, sb = a.state(), b.state()
             assert np.abs(sa - sb).max() < 2 * AMP_TOL["c64"]
     assert agree >= 2
+
+
+def test_emulated_fp64_form_matches_oracle_two_rounds():
+    pt = dict(W.STRESS)
+    o = run_trajectory(5, 2, "cr", "reduced", pt, seed=42, traj=3, want_state=True)
+    with Simulator(5, 2, "cr", "c128tc", **pt) as sim:
+        syn, bits, log = sim.run(42, 3, 1)
+        assert compare_trajectory(syn[0], bits[0], o, TAU["c128tc"]) == "exact"
+        err = np.abs(sim.state() - o["state"][: 1 << 25]).max()
+        assert err < AMP_TOL["c128tc"], err
+
+
+def test_emulated_fp64_form_agrees_with_fp64_form():
+    """Same outcomes bit for bit, and states within a few FP64 roundings of each other."""
+    pts = W.D5_CR["points"]
+    for i in (0, 4, 8):
+        with Simulator(5, 3, "cr", "c128tc", **pts[i]) as a, Simulator(5, 3, "cr", "c128", **pts[i]) as b:
+            ra = a.run(2000 + i, 0, 2)
+            rb = b.run(2000 + i, 0, 2)
+            for x, y in zip(ra, rb):
+                assert (x == y).all()
+            assert np.abs(a.state() - b.state()).max() < 1e-13
+
+
+def test_emulated_fp64_form_on_d3_uses_fp64_passes():
+    """d=3 tiles are below 2^12 amplitudes: the form falls back to the FP64 passes, bit-identical."""
+    pt = dict(W.STRESS)
+    with Simulator(3, 3, "cr", "c128tc", **pt) as a, Simulator(3, 3, "cr", "c128", **pt) as b:
+        ra = a.run(7, 0, 20)
+        rb = b.run(7, 0, 20)
+        for x, y in zip(ra, rb):
+            assert (x == y).all()
+        assert np.array_equal(a.state(), b.state())

@@ -441,35 +441,55 @@ def precision_arm(args, rank, world, local):
 
 
 def sweep_arm(args, rank, world, local):
-    """Logical error rate p_L over (p, c) at d=5, 5 rounds (Sec. III.B-C): over-rotation
-    theta = 2 c sqrt(p) after every rotation gate (Rx/Rx^dagger and Rz), p on every step, decoded by
-    the host matcher; complex64 tensor-core form, --steps trajectories per point."""
+    """Logical error rate p_L over (p, c) at d=5, 5 rounds (Sec. III.B-C) and the effective-model fit
+    p_eff = (1 + alpha c^2) p.  Over-rotation theta = 2 c sqrt(p) after every rotation gate (Rx, Rx^dagger,
+    Rz and the two-qubit Rzx, each about its own generator), p on every step, decoded by the host
+    matcher; complex64 tensor-core form.  --steps trajectories at p = 3e-3, scaled by 3e-3 / p below
+    it so that each point sees a similar number of failures."""
     import numpy as np
     import torch
 
     from paper_2204_11404_gb300.decoder import Decoder
+    from paper_2204_11404_gb300.effective import fit_effective_model
     from paper_2204_11404_gb300.simulator import Simulator
 
     torch.cuda.set_device(local)
-    n = max(1, args.steps)
+    n0 = max(1, args.steps)
     dec = Decoder(5)
     rows = []
-    for c in ((0.0,) if args.noise == "idle" else (0.0, 0.5, 1.0)):
+    cs = (0.0,) if args.noise == "idle" else (0.0, 0.25, 0.5, 0.75, 1.0)
+    for c in cs:
         for p in (1e-3, 2e-3, 3e-3, 5e-3):
+            n = n0 * max(1, int(round(3e-3 / p)))
             th = 2 * c * np.sqrt(p)
             g = 0.0 if args.noise == "idle" else p
-            nz = dict(p1=g, p2=g, p_idle=p, theta_rx=th, theta_rz=th, twirl=1.0 if args.noise == "twirl" else 0.0)
+            nz = dict(p1=g, p2=g, p_idle=p, theta_rx=th, theta_rz=th, theta_rzx=th,
+                      twirl=1.0 if args.noise == "twirl" else 0.0)
             with Simulator(5, 5, "cr", "c64tc", **nz) as sim:
                 syn, bits, log = sim.run(7000, rank * n, n)
             f = [dec.logical_failure(a, b, l) for a, b, l in zip(syn, bits, log)]
             k = int(np.sum(f))
-            rows.append({"c": c, "p": p, "trajectories": n, "failures": k, "pL": k / n,
-                         "pL_err": float(np.sqrt(max(k, 1) * (1 - k / n)) / n),
+            if world > 1:
+                import torch.distributed as dist
+                t = torch.tensor([k], dtype=torch.int64, device="cuda")
+                dist.all_reduce(t)
+                k = int(t.item())
+            nt = n * world
+            rows.append({"c": c, "p": p, "trajectories": nt, "failures": k, "pL": k / nt,
+                         "pL_err": float(np.sqrt(max(k, 1) * (1 - k / nt)) / nt),
                          "paper_fit_c0": 6.5e5 * p ** 2.92 if c == 0 else None})
+    out = {"metric": "logical error rate p_L(p, c), d=5, 5 rounds, noise=" + args.noise, "unit": "per-point report",
+           "data": "synthetic", "points": rows, "decoder_fallbacks": dec.fallbacks}
+    if len(cs) > 1:
+        try:
+            fit = fit_effective_model(rows)
+            out["effective_model"] = {"fit_range_p": [1e-3, 3e-3], "A": fit.A, "xi": fit.xi,
+                                      "B": {str(c): b for c, b in fit.B.items()}, "alpha": fit.alpha,
+                                      "paper": {"A": 6.5e5, "xi": 2.92, "alpha": 0.872}}
+        except ValueError as e:
+            out["effective_model"] = {"error": str(e)}
     if rank == 0:
-        print(json.dumps({"metric": "logical error rate p_L(p, c), d=5, 5 rounds, noise=" + args.noise,
-                          "unit": "per-point report",
-                          "data": "synthetic", "points": rows, "decoder_fallbacks": dec.fallbacks}))
+        print(json.dumps(out))
 
 
 def main():

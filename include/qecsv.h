@@ -60,6 +60,10 @@ typedef struct {
   double round_rx;  /* R_X(angle) on every data qubit at the start of each noisy round */
   double twirl;     /* 0: coherent terms as unitaries; 1: each replaced by its Pauli twirl, the
                        generator Pauli A with probability sin^2(theta/2) (ZZ: sin^2(phi)) (Sec. III.A) */
+  double overrot_follows; /* 0: the extra rotation has the same sign after every gate (Sec. III.A
+                       read literally); 1: after Rx^dagger(pi/2), the X-ancilla preparation and the
+                       schedule's only negative-angle rotation, it is R_X(-theta_rx) (the angle's
+                       magnitude grows).  Must be 0 or 1. */
 } qec_noise;
 
 typedef struct {

@@ -46,6 +46,12 @@ factor << 24 | site, factor = index of the term on that site in that step:
 0..3 the one-qubit terms after Rx/Rz factors, 4 the Rzx term, 5 the ZZ term,
 6 / 7 the round-start R_Z / R_X).
 
+Over-rotation sign (Sec. III.A gives exp(-i c sqrt(p) A) for every rotation gate): by default
+the extra rotation has the same sign after every gate, Rx^dagger included.  With
+overrot_follows = 1 (a flagged variant) the extra rotation after Rx^dagger(pi/2), the only
+negative-angle rotation gate of the schedule (X-ancilla preparation at step 1), is R_X(-theta_rx):
+the magnitude of every gate's angle grows.
+
 Draws (Philox4x64-10, counter (trajectory, round, step<<32 | site, tag)):
 occurrence iff (w0 >> 11) 2^-53 < p; Eq. 1 Pauli index = ((w1 >> 32) * 3 >> 32)
 -> X, Y, Z; Eq. 2 pair index k = ((w1 >> 32) * 15 >> 32) + 1, ancilla Pauli
@@ -59,7 +65,8 @@ from . import gates as G
 from .lattice import stabilizers, logical_z_support
 from .philox import draw, uniform53, TAG_NOISE, TAG_MEASURE, TAG_READOUT, TAG_TWIRL
 
-NOISE_KEYS = ("p1", "p2", "p_idle", "theta_rx", "theta_rz", "theta_rzx", "phi_zz", "round_rz", "round_rx", "twirl")
+NOISE_KEYS = ("p1", "p2", "p_idle", "theta_rx", "theta_rz", "theta_rzx", "phi_zz", "round_rz", "round_rx", "twirl",
+              "overrot_follows")
 
 
 def noise_dict(**kw):
@@ -193,7 +200,9 @@ class Trajectory:
                 else:
                     self.u1(a, G.RX90DG if t == 1 else G.RX90)
                     if noisy:
-                        self.coherent1(rnd, t, site_a, 0, a, G.PX, nz["theta_rx"])
+                        # sign-follows variant: the over-rotation of Rx^dagger turns the same way
+                        sgn = -1.0 if (t == 1 and nz["overrot_follows"]) else 1.0
+                        self.coherent1(rnd, t, site_a, 0, a, G.PX, sgn * nz["theta_rx"])
                 self.e1(rnd, t, site_a, a, nz["p1"])
                 return
             slot = t - 2

@@ -14,7 +14,8 @@ QEC_LAYOUT_REDUCED, QEC_LAYOUT_UNREDUCED = 0, 1
 QEC_GATES_CNOT, QEC_GATES_CR = 0, 1
 QEC_C128, QEC_C64, QEC_C64_TC, QEC_C128_TC = 0, 1, 2, 3
 
-NOISE_FIELDS = ("p1", "p2", "p_idle", "theta_rx", "theta_rz", "theta_rzx", "phi_zz", "round_rz", "round_rx", "twirl")
+NOISE_FIELDS = ("p1", "p2", "p_idle", "theta_rx", "theta_rz", "theta_rzx", "phi_zz", "round_rz", "round_rx", "twirl",
+                "overrot_follows")
 
 
 class qec_noise(ctypes.Structure):

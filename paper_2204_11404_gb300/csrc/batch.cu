@@ -128,6 +128,7 @@ __device__ void coherent_mats(T2 (*m)[16], qec_noise nz, int lane) {
     else { m[id][0] = mk<T2>(c, -s); m[id][5] = mk<T2>(c, s); }
   };
   rot1(M_ROT_RX, true, nz.theta_rx);
+  rot1(M_ROT_RXP, true, nz.overrot_follows != 0.0 ? -nz.theta_rx : nz.theta_rx);
   rot1(M_ROT_RZ, false, nz.theta_rz);
   rot1(M_ROUND_RZ, false, nz.round_rz);
   rot1(M_ROUND_RX, true, nz.round_rx);
@@ -897,6 +898,7 @@ qec_status qec_batch_run(qec_batch* b, uint64_t seed, uint32_t n, const uint64_t
     for (double v : an)
       if (!(std::fabs(v) <= 4.0)) return bfail(QEC_EINVAL, "angles must be finite with |angle| <= 4");
     if (z.twirl != 0.0 && z.twirl != 1.0) return bfail(QEC_EINVAL, "twirl must be 0 or 1");
+    if (z.overrot_follows != 0.0 && z.overrot_follows != 1.0) return bfail(QEC_EINVAL, "overrot_follows must be 0 or 1");
   }
   if (b->user) {
     QEC_BCUDA(cudaEventRecord(b->ev_in, b->user));

@@ -187,16 +187,21 @@ PassArgs traj_pass(const qec_sim* s, int b) {
 // bound, so fusing saves nothing there).
 bool fused_mode(const qec_sim* s) { return !is_f64(s->p.precision); }
 
-qec_status enqueue_prob(qec_sim* s, int b) {
-  PassArgs a = traj_pass(s, b);
-  QEC_CUDA(launch_prob(s->p.precision, a, pass_grid_for(s->p.precision, true, s->D, a.w, s->num_sms), s->work));
-  return QEC_OK;
+// One probability / apply pass of a block outside the fused complex64 path: on the tensor cores
+// for QEC_C128_TC weight-4 blocks, else the CUDA-core pass of the precision.
+cudaError_t prob_pass(qec_sim* s, const PassArgs& a) {
+  if (s->p.precision == QEC_C128_TC && apply_oz_applies(a)) return launch_prob_oz(a, s->num_sms, s->work);
+  return launch_prob(s->p.precision, a, pass_grid_for(s->p.precision, true, s->D, a.w, s->num_sms), s->work);
 }
 
-// One apply pass of block b (complex128 forms): on the tensor cores for QEC_C128_TC weight-4 blocks.
 cudaError_t apply_pass(qec_sim* s, const PassArgs& a) {
   if (s->p.precision == QEC_C128_TC && apply_oz_applies(a)) return launch_apply_oz(a, s->num_sms, s->work);
   return launch_apply(s->p.precision, a, pass_grid_for(s->p.precision, false, s->D, a.w, s->num_sms), s->work);
+}
+
+qec_status enqueue_prob(qec_sim* s, int b) {
+  QEC_CUDA(prob_pass(s, traj_pass(s, b)));
+  return QEC_OK;
 }
 
 // The pass(es) that apply block b: apply(b) + prob(b+1) fused, or apply(b) then prob(b+1).
@@ -305,7 +310,7 @@ qec_status launch_trajectory(qec_sim* s) {
   const int b = s->timed_block;
   PassArgs a = traj_pass(s, b);
   QEC_CUDA(cudaEventRecord(s->kev[0], s->work));
-  if (!fused_mode(s)) QEC_CUDA(launch_prob(s->p.precision, a, pass_grid_for(s->p.precision, true, s->D, a.w, s->num_sms), s->work));
+  if (!fused_mode(s)) QEC_CUDA(prob_pass(s, a));
   QEC_CUDA(cudaEventRecord(s->kev[1], s->work));
   if (fused_mode(s)) {
     PassArgs n = traj_pass(s, b + 1);

@@ -200,6 +200,41 @@ __device__ __forceinline__ uint32_t member_off(int l, const int (&q)[4]) {
   return o;
 }
 
+// End of a probability pass: block sums of (A, N) into per-CTA partials; the last CTA to finish
+// (ticket) sums the partials in a fixed order, draws the outcome m (u < A/N, or the forced value),
+// stores A, N, m and the syndrome bit, and resets the ticket.  Deterministic for a fixed grid.
+__device__ void prob_finish(const PassArgs& a, double accA, double accN, double* sred, int* s_last) {
+  block_sum2(accA, accN, sred);
+  if (threadIdx.x == 0) {
+    a.partials[2 * blockIdx.x] = accA;
+    a.partials[2 * blockIdx.x + 1] = accN;
+    __threadfence();
+    const unsigned int t = atomicAdd(&a.ctl->ticket, 1u);
+    *s_last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!*s_last) return;
+  __threadfence();
+  double sA = 0.0, sN = 0.0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
+    sA += __ldcg(&a.partials[2 * i]);
+    sN += __ldcg(&a.partials[2 * i + 1]);
+  }
+  block_sum2(sA, sN, sred);
+  if (threadIdx.x == 0) {
+    const double p1 = sA / sN;
+    const int m = a.forced >= 0 ? a.forced : (*a.u < p1 ? 1 : 0);
+    *a.A = sA;
+    *a.N = sN;
+    *a.m = m;
+    if (a.syn) {
+      const unsigned long long t = a.ctl->traj - a.ctl->first;
+      a.syn[t * (unsigned long long)a.syn_stride + a.syn_idx] = (uint8_t)(m ^ a.offset);
+    }
+    a.ctl->ticket = 0u;
+  }
+}
+
 template <typename T, int W>
 __global__ void __launch_bounds__(256) k_prob(PassArgs a) {
   using T2 = typename V2<T>::t;
@@ -246,35 +281,7 @@ __global__ void __launch_bounds__(256) k_prob(PassArgs a) {
     accA += (double)(2 * cross + diag);
     accN += (double)sn;
   }
-  block_sum2(accA, accN, sred);
-  if (threadIdx.x == 0) {
-    a.partials[2 * blockIdx.x] = accA;
-    a.partials[2 * blockIdx.x + 1] = accN;
-    __threadfence();
-    const unsigned int t = atomicAdd(&a.ctl->ticket, 1u);
-    s_last = (t == gridDim.x - 1);
-  }
-  __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-  double sA = 0.0, sN = 0.0;
-  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
-    sA += __ldcg(&a.partials[2 * i]);
-    sN += __ldcg(&a.partials[2 * i + 1]);
-  }
-  block_sum2(sA, sN, sred);
-  if (threadIdx.x == 0) {
-    const double p1 = sA / sN;
-    const int m = a.forced >= 0 ? a.forced : (*a.u < p1 ? 1 : 0);
-    *a.A = sA;
-    *a.N = sN;
-    *a.m = m;
-    if (a.syn) {
-      const unsigned long long t = a.ctl->traj - a.ctl->first;
-      a.syn[t * (unsigned long long)a.syn_stride + a.syn_idx] = (uint8_t)(m ^ a.offset);
-    }
-    a.ctl->ticket = 0u;
-  }
+  prob_finish(a, accA, accN, sred, &s_last);
 }
 
 // ---- apply pass: psi <- K_m psi / sqrt(N) ---------------------------------------------
@@ -331,39 +338,6 @@ __device__ __forceinline__ uint32_t local_base(uint32_t g, const int (&q)[4]) {
 #pragma unroll
   for (int j = 0; j < W; ++j) g = ((g >> q[j]) << (q[j] + 1)) | (g & ((1u << q[j]) - 1u));
   return g;
-}
-
-// Last-CTA reduction of (A, N) into the result slots of a probability block; shared with k_prob.
-__device__ __forceinline__ void finish_prob(const PassArgs& a, double accA, double accN, double* sred, int* s_last) {
-  block_sum2(accA, accN, sred);
-  if (threadIdx.x == 0) {
-    a.partials[2 * blockIdx.x] = accA;
-    a.partials[2 * blockIdx.x + 1] = accN;
-    __threadfence();
-    const unsigned int t = atomicAdd(&a.ctl->ticket, 1u);
-    *s_last = (t == gridDim.x - 1);
-  }
-  __syncthreads();
-  if (!*s_last) return;
-  __threadfence();
-  double sA = 0.0, sN = 0.0;
-  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
-    sA += __ldcg(&a.partials[2 * i]);
-    sN += __ldcg(&a.partials[2 * i + 1]);
-  }
-  block_sum2(sA, sN, sred);
-  if (threadIdx.x == 0) {
-    const double p1 = sA / sN;
-    const int m = a.forced >= 0 ? a.forced : (*a.u < p1 ? 1 : 0);
-    *a.A = sA;
-    *a.N = sN;
-    *a.m = m;
-    if (a.syn) {
-      const unsigned long long t = a.ctl->traj - a.ctl->first;
-      a.syn[t * (unsigned long long)a.syn_stride + a.syn_idx] = (uint8_t)(m ^ a.offset);
-    }
-    a.ctl->ticket = 0u;
-  }
 }
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
@@ -523,7 +497,7 @@ __global__ void __launch_bounds__(256) k_fused(FusedArgs f) {
     cur ^= 1;
   }
   cp_async_wait<0>();
-  finish_prob(f.pr, accA, accN, sred, &s_last);
+  prob_finish(f.pr, accA, accN, sred, &s_last);
 }
 
 // ---- tensor-core complex64 fused pass (tcgen05, 3xTF32, FP32 accumulation in TMEM) --------
@@ -795,7 +769,7 @@ __global__ void __launch_bounds__(256, 2) k_fused_tc(FusedArgs f) {
   tc_sync();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tmem));
   if (s_err && tid == 0) atomicOr(&f.pr.ctl->status, 1u);
-  finish_prob(f.pr, accA, accN, sred, &s_last);
+  prob_finish(f.pr, accA, accN, sred, &s_last);
 }
 
 // ---- complex128 apply pass, FP64-exact on the FP16 tensor cores (Ozaki slices) -----------------
@@ -864,7 +838,11 @@ __device__ __forceinline__ void put_slices8(uint16_t* S, int slab, int row, int 
 #undef QEC_OZ_SLICE
 }
 
-__global__ void __launch_bounds__(256, 2) k_apply_oz(FusedArgs f) {
+// PROB = false: psi <- K_m psi / sqrt(N) (apply pass).  PROB = true: A = sum |K_1 psi_g|^2 and
+// N = sum |psi|^2 over all groups, then the outcome (probability pass; K_1^dagger K_1 is the
+// projector-side operator M of the FP64 pass, so A is the same quantity).
+template <bool PROB>
+__global__ void __launch_bounds__(256, 2) k_oz(FusedArgs f) {
   constexpr int TS = 1 << kOzTileBits;
   extern __shared__ __align__(128) unsigned char osm[];
   const uint32_t lmask = (1u << f.lb) - 1u;
@@ -876,11 +854,13 @@ __global__ void __launch_bounds__(256, 2) k_apply_oz(FusedArgs f) {
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t tmem_base;
   __shared__ int s_err;
+  __shared__ double sred[64];
+  __shared__ int s_last;
   const int tid = threadIdx.x, warp = tid >> 5;
-  if (tid < 32) {   // B: real embedding of K_m / sqrt(N), one row per thread, sliced
+  if (tid < 32) {   // B: real embedding of K_m / sqrt(N) (apply) or K_1 (probability), sliced
     const int n = tid, r = n >> 1;
-    const int m = *f.ap.m;
-    const double scale = 1.0 / sqrt(*f.ap.N);
+    const int m = PROB ? 1 : *f.ap.m;
+    const double scale = PROB ? 1.0 : 1.0 / sqrt(*f.ap.N);
     const double2* Kg = reinterpret_cast<const double2*>(f.ap.kraus) + (m ? 256 : 0);
     double b[32];
     int E = 0;
@@ -929,8 +909,10 @@ __global__ void __launch_bounds__(256, 2) k_apply_oz(FusedArgs f) {
   const uint32_t tlane = (uint32_t)(32 * (warp & 3)) << 16;
   const double2* src = reinterpret_cast<const double2*>(f.ap.src);
   double2* dst = reinterpret_cast<double2*>(f.ap.dst);
+  (void)dst;
   const uint32_t ntile = 1u << f.nout;
   uint32_t phase = 0;
+  double accA[4] = {0.0, 0.0, 0.0, 0.0}, accN[2] = {0.0, 0.0};   // independent FMA chains
   for (uint32_t tix = blockIdx.x; tix < ntile; tix += gridDim.x) {
     uint32_t tb = 0;
     for (int j = 0; j < f.nout; ++j) tb |= ((tix >> j) & 1u) << f.obits[j];
@@ -947,6 +929,10 @@ __global__ void __launch_bounds__(256, 2) k_apply_oz(FusedArgs f) {
       x[2 * l] = v.x;
       x[2 * l + 1] = v.y;
       E = max(E, max(oz::bexp(v.x), oz::bexp(v.y)));
+      if (PROB) {
+        accN[0] = fma(v.x, v.x, accN[0]);
+        accN[1] = fma(v.y, v.y, accN[1]);
+      }
     }
     rowE[128 * hf + r] = E;
     __syncthreads();
@@ -986,17 +972,25 @@ __global__ void __launch_bounds__(256, 2) k_apply_oz(FusedArgs f) {
           d1[t] = D[t][j + 1];
         }
         const int n = 16 * hf + 8 * c + j;
-        tile[offa[4 * c + j / 2]] = make_double2(oz::assemble7(d0, E, colE[n]), oz::assemble7(d1, E, colE[n + 1]));
+        const double y0 = oz::assemble7(d0, E, colE[n]), y1 = oz::assemble7(d1, E, colE[n + 1]);
+        if (PROB) {
+          accA[j >> 1] = fma(y0, y0, accA[j >> 1]);
+          accA[j >> 1] = fma(y1, y1, accA[j >> 1]);
+        }
+        else tile[offa[4 * c + j / 2]] = make_double2(y0, y1);
       }
     }
     tc_sync();
+    if (!PROB) {
 #pragma unroll
-    for (int i = 0; i < TS / 256; ++i) dst[tb | coff[i]] = tile[tid + 256 * i];
-    tc_sync();
+      for (int i = 0; i < TS / 256; ++i) dst[tb | coff[i]] = tile[tid + 256 * i];
+      tc_sync();
+    }
   }
   tc_sync();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem));
   if (s_err && tid == 0) atomicOr(&f.ap.ctl->status, 1u);
+  if (PROB) prob_finish(f.ap, (accA[0] + accA[1]) + (accA[2] + accA[3]), accN[0] + accN[1], sred, &s_last);
 }
 
 // ---- final Z readout (Sec. III.B): sequential per-qubit sampling -------------------------
@@ -1336,7 +1330,7 @@ bool apply_oz_applies(const PassArgs& ap) {
   return f.nt == kOzTileBits;
 }
 
-cudaError_t launch_apply_oz(const PassArgs& ap, int num_sms, cudaStream_t s) {
+static cudaError_t launch_oz(bool prob, const PassArgs& ap, int num_sms, cudaStream_t s) {
   FusedArgs f;
   f.ap = ap;
   f.pr = ap;
@@ -1344,10 +1338,15 @@ cudaError_t launch_apply_oz(const PassArgs& ap, int num_sms, cudaStream_t s) {
   if (ap.w != 4 || f.nt != kOzTileBits) return cudaErrorInvalidValue;
   int64_t g = 2ll * num_sms;   // two CTAs per SM: 103 KiB of shared memory and 256 TMEM columns each
   if (g > (1ll << f.nout)) g = 1ll << f.nout;
+  if (g > MAX_PASS_GRID) g = MAX_PASS_GRID;
   f.grid = (int)g;
-  k_apply_oz<<<f.grid, 256, kOzSmem, s>>>(f);
+  if (prob) k_oz<true><<<f.grid, 256, kOzSmem, s>>>(f);
+  else k_oz<false><<<f.grid, 256, kOzSmem, s>>>(f);
   return cudaGetLastError();
 }
+
+cudaError_t launch_apply_oz(const PassArgs& ap, int num_sms, cudaStream_t s) { return launch_oz(false, ap, num_sms, s); }
+cudaError_t launch_prob_oz(const PassArgs& ap, int num_sms, cudaStream_t s) { return launch_oz(true, ap, num_sms, s); }
 
 cudaError_t launch_wait_selftest(unsigned int* status, long limit, cudaStream_t s) {
   k_wait_selftest<<<1, 32, 0, s>>>(status, limit);
@@ -1370,8 +1369,10 @@ cudaError_t setup_kernels(int precision, int D) {
   if (is_f64(precision)) {
     cudaError_t e = cudaFuncSetAttribute(k_sample<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess) e = fused_attrs<double>();
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_apply_oz, cudaFuncAttributeMaxDynamicSharedMemorySize, kOzSmem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_apply_oz, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_oz<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kOzSmem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_oz<false>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_oz<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kOzSmem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_oz<true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     return e;
   }
   cudaError_t e = cudaFuncSetAttribute(k_sample<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);

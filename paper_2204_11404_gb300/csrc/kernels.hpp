@@ -102,9 +102,11 @@ cudaError_t launch_fused(int precision, const PassArgs& ap, const PassArgs& pr, 
 cudaError_t launch_set_basis0(int precision, void* psi, int D, cudaStream_t s);
 cudaError_t setup_kernels(int precision, int D);
 cudaError_t launch_wait_selftest(unsigned int* status, long limit, cudaStream_t s);
-// complex128 apply pass on the tensor cores (weight-4 blocks whose tile has 2^12 amplitudes).
+// complex128 apply / probability passes on the tensor cores (weight-4 blocks, tiles of 2^11
+// amplitudes: registers of at least 11 qubits).
 bool apply_oz_applies(const PassArgs& ap);
-cudaError_t launch_apply_oz(const PassArgs& ap, int num_sms, cudaStream_t s);   // once per process/device, before any capture
+cudaError_t launch_apply_oz(const PassArgs& ap, int num_sms, cudaStream_t s);
+cudaError_t launch_prob_oz(const PassArgs& ap, int num_sms, cudaStream_t s);   // once per process/device, before any capture
 int pass_grid(int D, int w, int num_sms);
 // One wave of resident CTAs for the probability (prob = true) or apply pass kernel.
 int pass_grid_for(int precision, bool prob, int D, int w, int num_sms);

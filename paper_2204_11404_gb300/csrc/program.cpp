@@ -59,6 +59,7 @@ void fill_mats(Program& P, const qec_noise& nz, bool noisy) {
   rot_zx(P.mats[M_RZX90], M_PI / 2);
   double g = noisy ? 1.0 : 0.0;
   rot1(P.mats[M_ROT_RX], 'X', g * nz.theta_rx);
+  rot1(P.mats[M_ROT_RXP], 'X', (nz.overrot_follows != 0.0 ? -g : g) * nz.theta_rx);   // after the Rx^dagger prep
   rot1(P.mats[M_ROT_RZ], 'Z', g * nz.theta_rz);
   rot_zx(P.mats[M_ROT_RZX], g * nz.theta_rzx);
   for (int i = 0; i < 16; ++i) P.mats[M_ZZ][i][0] = P.mats[M_ZZ][i][1] = 0.0;
@@ -138,6 +139,7 @@ bool validate_params(const qec_params& p, std::string& err) {
     if (!finite_in(v, -4.0, 4.0)) { err = "angles must be finite with |angle| <= 4"; return false; }
   }
   if (n.twirl != 0.0 && n.twirl != 1.0) { err = "twirl must be 0 or 1"; return false; }
+  if (n.overrot_follows != 0.0 && n.overrot_follows != 1.0) { err = "overrot_follows must be 0 or 1"; return false; }
   return true;
 }
 
@@ -271,7 +273,7 @@ bool build_program(const qec_params& p, bool noisy, Program& P, std::string& err
           u1(anc, M_H);
         } else {
           u1(anc, t == 1 ? M_RX90DG : M_RX90);
-          coh1(anc, t, site_a, 0, M_ROT_RX, M_X, nz.theta_rx, PR_TW_RX);
+          coh1(anc, t, site_a, 0, t == 1 ? M_ROT_RXP : M_ROT_RX, M_X, nz.theta_rx, PR_TW_RX);
         }
         n1(anc, t, site_a, PR_P1);
         continue;
@@ -374,7 +376,7 @@ bool build_unreduced_program(const qec_params& p, bool noisy, UProgram& U, std::
             u1(a, M_H);
           } else {
             u1(a, t == 1 ? M_RX90DG : M_RX90);
-            coh1(a, t, site_a, 0, M_ROT_RX, M_X, nz.theta_rx, PR_TW_RX);
+            coh1(a, t, site_a, 0, t == 1 ? M_ROT_RXP : M_ROT_RX, M_X, nz.theta_rx, PR_TW_RX);
           }
           n1(a, t, site_a, PR_P1);
           unit(1, a, 0, begin);

@@ -46,7 +46,7 @@ struct BlockInfo {
 
 enum MatId : uint16_t {
   M_I = 0, M_X, M_Y, M_Z, M_H, M_RX90, M_RX90DG, M_RZ90, M_CNOT, M_RZX90,
-  M_ROT_RX, M_ROT_RZ, M_ROT_RZX, M_ZZ, M_ROUND_RZ, M_ROUND_RX, M_PZX, M_PZZ, M_COUNT
+  M_ROT_RX, M_ROT_RZ, M_ROT_RZX, M_ZZ, M_ROUND_RZ, M_ROUND_RX, M_PZX, M_PZZ, M_ROT_RXP, M_COUNT
 };
 
 struct Program {

@@ -81,3 +81,23 @@ def test_batched_unreduced_register_matches_oracle_and_reduced(gates):
             assert kind == "exact", (i, kinds[i])
         amb += kind == "ambiguous"
     assert amb <= 2
+
+
+def test_batched_sign_follows_variant_matches_oracle():
+    """Per-trajectory over-rotation sign variant, all four kinds in one launch."""
+    n = 32
+    traj = [500 + i for i in range(n)]
+    kinds = ["c128u", "c64u", "c128", "c64"] * (n // 4)
+    noise = [dict(p1=0.01, p2=0.01, p_idle=0.01, theta_rx=0.3, overrot_follows=i % 2) for i in range(n)]
+    with BatchSimulator(3, "cr", max_traj=64) as b:
+        syn, bits, log = b.run(93, traj, kinds, noise)
+    amb = 0
+    for i in range(n):
+        layout = "unreduced" if kinds[i].endswith("u") else "reduced"
+        prec = kinds[i].rstrip("u")
+        o = run_trajectory(3, 3, "cr", layout, noise[i], seed=93, traj=traj[i])
+        kind = compare_trajectory(syn[i], bits[i], o, TAU[prec])
+        if prec == "c128":
+            assert kind == "exact", (i, kinds[i])
+        amb += kind == "ambiguous"
+    assert amb <= 2

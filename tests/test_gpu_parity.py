@@ -157,3 +157,14 @@ def test_d3_twirled_matches_oracle(prec):
         o = oracle_traj(3, 3, "cr", TWIRLED, 47, 5, want_state=True)
         if compare_trajectory(syn[0], bits[0], o, TAU[prec]) == "exact":
             assert np.abs(sim.state() - o["state"][: 1 << 9]).max() < AMP_TOL[prec]
+
+
+SIGN_FOLLOWS = dict(W.STRESS, theta_rx=0.35, overrot_follows=1)
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+def test_d3_sign_follows_variant_matches_oracle(prec):
+    """Over-rotation R_X(-theta) after the Rx^dagger preparation (the flagged sign variant)."""
+    with Simulator(3, 3, "cr", prec, **SIGN_FOLLOWS) as sim:
+        kinds = check_batch(sim, 3, 3, "cr", SIGN_FOLLOWS, 53, 0, 40, prec)
+        assert kinds.count("ambiguous") <= (0 if prec == "c128" else 2)

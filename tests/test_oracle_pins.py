@@ -346,6 +346,26 @@ def test_over_rotation_flip_probability(gates):
             assert min(x[3], 1 - x[3]) < 1e-14
 
 
+@pytest.mark.parametrize("d", [3, 5])
+def test_over_rotation_sign_closed_form(d):
+    """X-stabilizer readout of the code state under theta_rx alone (Sec. III.A, CR compile of Sec. II.C).
+
+    The ancilla sees Rx(pi/2 + theta) U Rx(-pi/2 + s theta)|0>, s = +1 with the same-sign reading and
+    -1 with the sign-follows variant.  On the +1 eigenspace of a weight-4 X stabilizer the four Rzx
+    gates multiply to a phase, so P(1) = sin^2((1 + s) theta / 2); for weight 2 they multiply to
+    -+i Z_anc, so P(1) = cos^2((1 - s) theta / 2).  Data over-rotations commute with X stabilizers."""
+    S = stabilizers(d)
+    th = 0.31
+    for fol, s in ((0, 1.0), (1, -1.0)):
+        r = run_trajectory(d, 1, "cr", "reduced", {"theta_rx": th, "overrot_follows": fol}, 0, 0)
+        for k, st in enumerate(S):
+            if st["kind"] != "X":
+                continue
+            (x,) = [x for x in r["anc_records"] if x[0] == 1 and x[1] == k]
+            want = np.sin((1 + s) * th / 2) ** 2 if st["weight"] == 4 else np.cos((1 - s) * th / 2) ** 2
+            assert abs(x[3] - want) < 1e-13, (fol, k, x[3], want)   # FP64 sums over 2^26 amplitudes
+
+
 def _n_sites(d, rounds):
     # per round: every data qubit at each of the 11 steps, plus each ancilla's own steps
     # (X: 6 - weight, Z: 5 - weight; its gate steps share the data qubit's site)

@@ -63,3 +63,27 @@ def test_host_blocks_match_oracle_twirled(gates):
         o = run_trajectory(3, 3, gates, "reduced", TWIRLED, seed=23, traj=traj, want_state=True)
         assert (syn == o["syndromes"]).all()
         assert np.abs(psi - o["state"][: 1 << 9]).max() < 1e-13
+
+
+SIGN_FOLLOWS = dict(NOISY, theta_rx=0.35, overrot_follows=1)
+
+
+@pytest.mark.parametrize("noise", [SIGN_FOLLOWS, dict(SIGN_FOLLOWS, twirl=1)])
+def test_host_blocks_match_oracle_sign_follows(noise):
+    """The sign-follows over-rotation variant (R_X(-theta) after the Rx^dagger preparation)."""
+    params = capi.make_params(3, 3, "cr", **noise)
+    for traj in range(6):
+        syn, psi = kraus_run(params, 29, traj)
+        o = run_trajectory(3, 3, "cr", "reduced", noise, seed=29, traj=traj, want_state=True)
+        assert (syn == o["syndromes"]).all()
+        assert np.abs(psi - o["state"][: 1 << 9]).max() < 1e-13
+
+
+def test_sign_follows_changes_the_blocks():
+    base = capi.make_params(3, 3, "cr", theta_rx=0.35)
+    var = capi.make_params(3, 3, "cr", theta_rx=0.35, overrot_follows=1)
+    (s0, p0), (s1, p1) = kraus_run(base, 3, 0), kraus_run(var, 3, 0)
+    assert np.abs(p0 - p1).max() > 1e-3
+    with pytest.raises(capi.QecError):
+        capi.qec_debug_program(capi.make_params(3, 3, "cr", overrot_follows=0.5),
+                               np.zeros(8, dtype=np.int32).ctypes.data, 0, np.zeros(8, dtype=np.int32).ctypes.data, 0)

@@ -262,11 +262,16 @@ qec_status qec_debug_blocks(const qec_params* params, uint64_t seed, uint64_t tr
  * out[m][32] = A[m][32] . B[32][32]^T (row-major FP64); each entry is the dot product of
  * the 56-bit truncated inputs (truncation relative to each row's largest exponent) with
  * slice products of weight below 2^-56 dropped, rounded once to FP64: absolute error at
- * most 2^-44 * max|A[r]| * max|B[n]| + 2^-53 * |exact|.  The paper has no counterpart
+ * most 2^-44 * max|A[r]| * max|B[n]| + 2^-53 * |exact|.  variant 0: recombination in
+ * integers with rounding to nearest, ties away (the probability pass); 1: through one
+ * int64 -> FP64 conversion, ties to even (the apply pass); 2: the probability pass's sums,
+ * with one exponent for all of B: out[r][0] = sum_n (A[r] . B[n])^2, out[r][1] =
+ * sum_k A[r][k]^2 (each half-row's squares summed in integers, converted once), the rest
+ * untouched.  Returns QEC_EINVAL for any other variant.  The paper has no counterpart
  * (an arithmetic form of the gate application of Sec. III).  Returns QEC_EINVAL on null
  * pointers or m <= 0.
  */
-qec_status qec_debug_ozaki_gemm(const double* A, const double* B, int32_t m, double* out);
+qec_status qec_debug_ozaki_gemm(const double* A, const double* B, int32_t m, int32_t variant, double* out);
 
 #ifdef __cplusplus
 }

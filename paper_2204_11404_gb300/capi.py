@@ -63,7 +63,7 @@ SIGNATURES = {
                            _P, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32)], ctypes.c_int),
     "qec_debug_blocks": ([ctypes.POINTER(qec_params), ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int32, _P, _P],
                          ctypes.c_int),
-    "qec_debug_ozaki_gemm": ([_P, _P, ctypes.c_int32, _P], ctypes.c_int),
+    "qec_debug_ozaki_gemm": ([_P, _P, ctypes.c_int32, ctypes.c_int32, _P], ctypes.c_int),
 }
 
 
@@ -203,5 +203,5 @@ def qec_debug_blocks(params, seed, traj, rnd, kraus_ptr, u_ptr):
     return check(lib().qec_debug_blocks(ctypes.byref(params), seed, traj, rnd, kraus_ptr, u_ptr))
 
 
-def qec_debug_ozaki_gemm(A_ptr, B_ptr, m, out_ptr):
-    return check(lib().qec_debug_ozaki_gemm(A_ptr, B_ptr, m, out_ptr))
+def qec_debug_ozaki_gemm(A_ptr, B_ptr, m, variant, out_ptr):
+    return check(lib().qec_debug_ozaki_gemm(A_ptr, B_ptr, m, variant, out_ptr))

@@ -640,8 +640,8 @@ qec_status qec_debug_program(const qec_params* params, int32_t* ops, uint32_t ca
   return QEC_OK;
 }
 
-qec_status qec_debug_ozaki_gemm(const double* A, const double* B, int32_t m, double* out) {
-  if (!A || !B || !out || m <= 0) return fail(QEC_EINVAL, "bad argument");
+qec_status qec_debug_ozaki_gemm(const double* A, const double* B, int32_t m, int32_t variant, double* out) {
+  if (!A || !B || !out || m <= 0 || variant < 0 || variant > 2) return fail(QEC_EINVAL, "bad argument");
   std::vector<int> ea(m), eb(32);
   std::vector<int> da((size_t)m * 32 * oz::kSlices), db(32 * 32 * oz::kSlices);
   for (int r = 0; r < m; ++r) {
@@ -650,13 +650,17 @@ qec_status qec_debug_ozaki_gemm(const double* A, const double* B, int32_t m, dou
     ea[r] = E;
     for (int k = 0; k < 32; ++k) oz::split7(A[r * 32 + k], E, &da[((size_t)r * 32 + k) * oz::kSlices]);
   }
+  int EB = 0;   // variant 2 (probability pass): one exponent for all of B
+  for (int i = 0; i < 32 * 32; ++i) EB = std::max(EB, oz::bexp(B[i]));
   for (int n = 0; n < 32; ++n) {
     int E = 0;
     for (int k = 0; k < 32; ++k) E = std::max(E, oz::bexp(B[n * 32 + k]));
-    eb[n] = E;
-    for (int k = 0; k < 32; ++k) oz::split7(B[n * 32 + k], E, &db[((size_t)n * 32 + k) * oz::kSlices]);
+    eb[n] = variant == 2 ? EB : E;
+    for (int k = 0; k < 32; ++k) oz::split7(B[n * 32 + k], eb[n], &db[((size_t)n * 32 + k) * oz::kSlices]);
   }
   for (int r = 0; r < m; ++r) {
+    oz::SqAcc sa, sn;   // variant 2: the two halves of a row, as two threads of the pass hold them
+    double A2 = 0.0, N2 = 0.0;
     for (int n = 0; n < 32; ++n) {
       float D[oz::kSlices];
       for (int t = 0; t < oz::kSlices; ++t) {
@@ -666,7 +670,21 @@ qec_status qec_debug_ozaki_gemm(const double* A, const double* B, int32_t m, dou
             acc += (float)(da[((size_t)r * 32 + k) * oz::kSlices + p] * db[((size_t)n * 32 + k) * oz::kSlices + (t - p)]);
         D[t] = acc;
       }
-      out[r * 32 + n] = oz::assemble7(D, ea[r], eb[n]);
+      if (variant == 2) {
+        const int64_t z = oz::combine7(D);
+        sa.add((uint64_t)(z < 0 ? -z : z));
+        sn.add(ea[r] ? oz::mag56(A[r * 32 + n], ea[r]) : 0ull);
+        if ((n & 15) == 15) {
+          A2 += (ea[r] && EB) ? sa.take(2 * (ea[r] + EB - 2098)) : sa.take(-4000);
+          N2 += sn.take(2 * (ea[r] - 1078));
+        }
+        continue;
+      }
+      out[r * 32 + n] = variant ? oz::assemble7_cvt(D, ea[r], eb[n]) : oz::assemble7(D, ea[r], eb[n]);
+    }
+    if (variant == 2) {
+      out[r * 32] = A2;
+      out[r * 32 + 1] = N2;
     }
   }
   return QEC_OK;

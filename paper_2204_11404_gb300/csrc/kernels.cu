@@ -794,6 +794,17 @@ __device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t ad, uint64_t 
 // Element offset of (row r, k) of a K = 32 16-bit operand: core matrix (r/8, k/8) of 64 elements.
 __device__ __forceinline__ int core_off16(int r, int k) { return ((r >> 3) * 4 + (k >> 3)) * 64 + (r & 7) * 8 + (k & 7); }
 
+__device__ __forceinline__ void tmem_ld8_nowait(uint32_t taddr, uint32_t (&r)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+// Orders every later use of r after the preceding tcgen05.wait::ld.
+__device__ __forceinline__ void reg_fence8(uint32_t (&r)[8]) {
+  asm volatile("" : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]));
+}
+
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
   uint32_t r[8];
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
@@ -817,9 +828,10 @@ __device__ __forceinline__ uint32_t digit_pair(uint64_t Xa, uint64_t Xb, uint32_
   return r;
 }
 
-// Writes the 7 FP16 slices of 8 consecutive reals x[0..7] (row `row`, k0 % 8 == 0) under exponent E.
-__device__ __forceinline__ void put_slices8(uint16_t* S, int slab, int row, int k0, const double* x, int E) {
-  uint64_t X[8];
+// Writes the 7 FP16 slices of 8 consecutive reals x[0..7] (row `row`, k0 % 8 == 0) under exponent E;
+// X[0..7] receives their 56-bit magnitudes.
+__device__ __forceinline__ void put_slices8(uint16_t* S, int slab, int row, int k0, const double* x, int E,
+                                            uint64_t (&X)[8]) {
   uint32_t sg[4], nsg[4];
 #pragma unroll
   for (int j = 0; j < 8; ++j) X[j] = E ? oz::mag56(x[j], E) : 0ull;
@@ -872,9 +884,11 @@ __global__ void __launch_bounds__(256, 2) k_oz(FusedArgs f) {
       b[2 * l + 1] = (n & 1) ? re : -im;
       E = max(E, max(oz::bexp(b[2 * l]), oz::bexp(b[2 * l + 1])));
     }
+    if (PROB) E = __reduce_max_sync(0xffffffffu, E);   // one exponent for all of K_1: the outputs share a scale
     colE[n] = E;
+    uint64_t Xb[8];
 #pragma unroll
-    for (int kc = 0; kc < 4; ++kc) put_slices8(B, 32 * 32, n, 8 * kc, b + 8 * kc, E);
+    for (int kc = 0; kc < 4; ++kc) put_slices8(B, 32 * 32, n, 8 * kc, b + 8 * kc, E, Xb);
   }
   if (tid == 0) {
     s_err = 0;
@@ -898,27 +912,39 @@ __global__ void __launch_bounds__(256, 2) k_oz(FusedArgs f) {
   uint32_t offa[8];
 #pragma unroll
   for (int l = 0; l < 8; ++l) offa[l] = gbase + member_off<4>(8 * hf + l, qa);
-  uint32_t coff[TS / 256];   // this thread's amplitudes of a tile for the copies: e = tid + 256 i
-#pragma unroll
-  for (int i = 0; i < TS / 256; ++i) {
-    const uint32_t e = (uint32_t)tid + 256u * i, h = e >> f.lb;
+  auto t2g = [&](uint32_t e) {   // tile index -> offset within the register (tile bits)
+    const uint32_t h = e >> f.lb;
     uint32_t o = 0;
     for (int j = 0; j < f.nt - f.lb; ++j) o |= ((h >> j) & 1u) << f.hbits[j];
-    coff[i] = o | (e & lmask);
-  }
+    return o | (e & lmask);
+  };
+  uint32_t coff[TS / 256];   // this thread's amplitudes of a tile for the copies: e = tid + 256 i
+#pragma unroll
+  for (int i = 0; i < TS / 256; ++i) coff[i] = t2g((uint32_t)tid + 256u * i);
+  uint32_t goff[8];          // this thread's 8 outputs (apply): written straight to the register
+#pragma unroll
+  for (int l = 0; l < 8; ++l) goff[l] = t2g(offa[l]);
   const uint32_t tlane = (uint32_t)(32 * (warp & 3)) << 16;
   const double2* src = reinterpret_cast<const double2*>(f.ap.src);
   double2* dst = reinterpret_cast<double2*>(f.ap.dst);
-  (void)dst;
   const uint32_t ntile = 1u << f.nout;
-  uint32_t phase = 0;
-  double accA[4] = {0.0, 0.0, 0.0, 0.0}, accN[2] = {0.0, 0.0};   // independent FMA chains
-  for (uint32_t tix = blockIdx.x; tix < ntile; tix += gridDim.x) {
+  auto tile_base = [&](uint32_t tix) {
     uint32_t tb = 0;
     for (int j = 0; j < f.nout; ++j) tb |= ((tix >> j) & 1u) << f.obits[j];
+    return tb;
+  };
+  auto load_tile = [&](uint32_t tb) {
 #pragma unroll
     for (int i = 0; i < TS / 256; ++i) cp_async16(tile + tid + 256 * i, src + (tb | coff[i]));
     cp_async_commit();
+  };
+  uint32_t phase = 0;
+  double accA = 0.0, accN = 0.0;
+  oz::SqAcc sq;   // probability pass: integer sums of squares, one FP64 conversion per tile and sum
+  uint32_t tix = blockIdx.x;
+  uint32_t tb = tix < ntile ? tile_base(tix) : 0u;
+  if (tix < ntile) load_tile(tb);
+  for (; tix < ntile; tix += gridDim.x) {
     cp_async_wait<0>();
     __syncthreads();
     double x[16];
@@ -929,16 +955,26 @@ __global__ void __launch_bounds__(256, 2) k_oz(FusedArgs f) {
       x[2 * l] = v.x;
       x[2 * l + 1] = v.y;
       E = max(E, max(oz::bexp(v.x), oz::bexp(v.y)));
-      if (PROB) {
-        accN[0] = fma(v.x, v.x, accN[0]);
-        accN[1] = fma(v.y, v.y, accN[1]);
-      }
     }
     rowE[128 * hf + r] = E;
-    __syncthreads();
+    __syncthreads();   // every thread holds its inputs: the tile buffer takes the next tile's copy
+    const uint32_t tnext = tix + gridDim.x;
+    const uint32_t tbn = tnext < ntile ? tile_base(tnext) : 0u;
+    if (tnext < ntile) load_tile(tbn);
     E = max(rowE[r], rowE[128 + r]);
-    put_slices8(A, kOzSlab, r, 16 * hf, x, E);
-    put_slices8(A, kOzSlab, r, 16 * hf + 8, x + 8, E);
+    {
+      uint64_t X0[8], X1[8];
+      put_slices8(A, kOzSlab, r, 16 * hf, x, E, X0);
+      put_slices8(A, kOzSlab, r, 16 * hf + 8, x + 8, E, X1);
+      if (PROB) {   // N: sum of x^2 with x = X 2^(E - 1078)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          sq.add(X0[j]);
+          sq.add(X1[j]);
+        }
+        accN += sq.take(2 * (E - 1078));
+      }
+    }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     tc_sync();
     if (tid == 0) {
@@ -957,40 +993,42 @@ __global__ void __launch_bounds__(256, 2) k_oz(FusedArgs f) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     __syncthreads();
     if (s_err) break;
-    // outputs 16hf..16hf+15 of row r: amplitudes 8hf..8hf+7, recombined and written into the tile
+    // outputs 16hf..16hf+15 of row r: amplitudes 8hf..8hf+7
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
-      float D[oz::kSlices][8];
+      uint32_t R[oz::kSlices][8];
 #pragma unroll
-      for (int t = 0; t < oz::kSlices; ++t) tmem_ld8(tmem + tlane + 32u * t + 16u * hf + 8u * c, D[t]);
+      for (int t = 0; t < oz::kSlices; ++t) tmem_ld8_nowait(tmem + tlane + 32u * t + 16u * hf + 8u * c, R[t]);
+      tmem_wait_ld();
+#pragma unroll
+      for (int t = 0; t < oz::kSlices; ++t) reg_fence8(R[t]);
 #pragma unroll
       for (int j = 0; j < 8; j += 2) {
         float d0[oz::kSlices], d1[oz::kSlices];
 #pragma unroll
         for (int t = 0; t < oz::kSlices; ++t) {
-          d0[t] = D[t][j];
-          d1[t] = D[t][j + 1];
+          d0[t] = __uint_as_float(R[t][j]);
+          d1[t] = __uint_as_float(R[t][j + 1]);
         }
         const int n = 16 * hf + 8 * c + j;
-        const double y0 = oz::assemble7(d0, E, colE[n]), y1 = oz::assemble7(d1, E, colE[n + 1]);
-        if (PROB) {
-          accA[j >> 1] = fma(y0, y0, accA[j >> 1]);
-          accA[j >> 1] = fma(y1, y1, accA[j >> 1]);
+        if (PROB) {   // A: sum of y^2 with y = Z 2^(E + E_B - 2098)
+          const int64_t z0 = oz::combine7(d0), z1 = oz::combine7(d1);
+          sq.add((uint64_t)(z0 < 0 ? -z0 : z0));
+          sq.add((uint64_t)(z1 < 0 ? -z1 : z1));
+        } else {
+          dst[tb | goff[4 * c + j / 2]] = make_double2(oz::assemble7_cvt(d0, E, colE[n]), oz::assemble7_cvt(d1, E, colE[n + 1]));
         }
-        else tile[offa[4 * c + j / 2]] = make_double2(y0, y1);
       }
     }
-    tc_sync();
-    if (!PROB) {
-#pragma unroll
-      for (int i = 0; i < TS / 256; ++i) dst[tb | coff[i]] = tile[tid + 256 * i];
-      tc_sync();
-    }
+    if (PROB) accA += (E && colE[0]) ? sq.take(2 * (E + colE[0] - 2098)) : sq.take(-4000);
+    tc_sync();         // TMEM read out before the next tile's MMAs overwrite it
+    tb = tbn;
   }
+  cp_async_wait<0>();  // a copy still in flight after an early exit
   tc_sync();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem));
   if (s_err && tid == 0) atomicOr(&f.ap.ctl->status, 1u);
-  if (PROB) prob_finish(f.ap, (accA[0] + accA[1]) + (accA[2] + accA[3]), accN[0] + accN[1], sred, &s_last);
+  if (PROB) prob_finish(f.ap, accA, accN, sred, &s_last);
 }
 
 // ---- final Z readout (Sec. III.B): sequential per-qubit sampling -------------------------

@@ -99,12 +99,17 @@ OZ_HD void split7(double x, int E, int* d) {
 // integers (|D_t| <= (t+1) * 32 * 255^2 < 2^24).  The sum is formed in 64-bit integers with its
 // lowest 10 bits truncated (|sum| < 2^70, so the truncation is below 2^-59 of the largest possible
 // sum) and rounded once to FP64 (nearest, ties away from zero).
-OZ_HD double assemble7(const float* D, int Ea, int Eb) {
-  if (Ea == 0 || Eb == 0) return 0.0;
+// Z = floor(sum_t D_t 2^(8(6-t)) / 2^10) in 64 bits (|Z| < 2^60).
+OZ_HD int64_t combine7(const float* D) {
   int64_t d[kSlices];
   for (int t = 0; t < kSlices; ++t) d[t] = (int64_t)(int32_t)D[t];
-  const int64_t Z = d[0] * (1ll << 38) + d[1] * (1ll << 30) + d[2] * (1ll << 22) + d[3] * (1ll << 14) +
-                    d[4] * (1ll << 6) + ((d[5] * 256 + d[6]) >> 10);
+  return d[0] * (1ll << 38) + d[1] * (1ll << 30) + d[2] * (1ll << 22) + d[3] * (1ll << 14) + d[4] * (1ll << 6) +
+         ((d[5] * 256 + d[6]) >> 10);
+}
+
+OZ_HD double assemble7(const float* D, int Ea, int Eb) {
+  if (Ea == 0 || Eb == 0) return 0.0;
+  const int64_t Z = combine7(D);
   if (Z == 0) return 0.0;
   const uint64_t neg = Z < 0 ? 1ull : 0ull;
   const uint64_t mag = neg ? (uint64_t)(-Z) : (uint64_t)Z;
@@ -129,6 +134,42 @@ OZ_HD double assemble7(const float* D, int Ea, int Eb) {
   if (be >= 2047) return u2d((neg << 63) | 0x7FF0000000000000ull);
   return u2d((neg << 63) | ((uint64_t)be << 52) | (mant & 0xFFFFFFFFFFFFFull));
 }
+
+// The same value through one int64 -> FP64 conversion (round to nearest even) and an exact
+// power-of-two scaling of the exponent field: fewer integer operations, one conversion.
+// v * 2^s for a finite v by its exponent field (flush to zero below the normal range).
+OZ_HD double scale2(double v, int s) {
+  const uint64_t u = d2u(v);
+  const int be = (int)((u >> 52) & 0x7FF) + s;
+  if (v == 0.0 || be <= 0) return 0.0;
+  if (be >= 2047) return u2d((u & 0x8000000000000000ull) | 0x7FF0000000000000ull);
+  return u2d(u + ((uint64_t)(int64_t)s << 52));
+}
+
+OZ_HD double assemble7_cvt(const float* D, int Ea, int Eb) {
+  if (Ea == 0 || Eb == 0) return 0.0;
+  const int64_t Z = combine7(D);
+  return scale2((double)Z, Ea + Eb - 2098);          // one rounding (the conversion), exact scaling
+}
+
+// Exact sums of squares of up to 16 integers below 2^60 without FP64 work per term:
+// v = h 2^30 + l (h, l < 2^30), v^2 = h^2 2^60 + 2 h l 2^30 + l^2, the three partial sums each
+// below 16 * 2^60 = 2^64.  take() converts once (three roundings, relative error below 2^-51).
+struct SqAcc {
+  uint64_t hh = 0, hl = 0, ll = 0;
+  OZ_HD void add(uint64_t v) {
+    const uint64_t h = v >> 30, l = v & 0x3FFFFFFFull;
+    hh += h * h;
+    hl += h * l;
+    ll += l * l;
+  }
+  // sum * 2^s as FP64 (scaled exactly), then the accumulators restart
+  OZ_HD double take(int s) {
+    const double v = (double)hh * 0x1p60 + ((double)hl * 0x1p31 + (double)ll);
+    hh = hl = ll = 0;
+    return scale2(v, s);
+  }
+};
 
 }  // namespace oz
 }  // namespace qec

@@ -27,8 +27,9 @@ def _exact(A, B):
     return out
 
 
+@pytest.mark.parametrize("variant", [0, 1])
 @pytest.mark.parametrize("seed", [0, 1])
-def test_emulated_product_is_fp64_accurate(seed):
+def test_emulated_product_is_fp64_accurate(seed, variant):
     rng = np.random.default_rng(seed)
     m = 24
     A = _rows(rng, m)
@@ -37,7 +38,7 @@ def test_emulated_product_is_fp64_accurate(seed):
     B[0::2, 0::2], B[0::2, 1::2] = q.real, -q.imag
     B[1::2, 0::2], B[1::2, 1::2] = q.imag, q.real
     out = np.zeros((m, 32))
-    capi.qec_debug_ozaki_gemm(A.ctypes.data, np.ascontiguousarray(B).ctypes.data, m, out.ctypes.data)
+    capi.qec_debug_ozaki_gemm(A.ctypes.data, np.ascontiguousarray(B).ctypes.data, m, variant, out.ctypes.data)
     ex = _exact(A, B)
     ref = A @ B.T
     for r in range(m):
@@ -53,11 +54,45 @@ def test_emulated_product_is_fp64_accurate(seed):
     assert err <= max(4 * err_np, 1e-300)       # as accurate as numpy's FP64 product
 
 
-def test_zero_and_single_term_rows_are_exact():
+@pytest.mark.parametrize("variant", [0, 1])
+def test_zero_and_single_term_rows_are_exact(variant):
     A = np.zeros((2, 32))
     A[1, 5] = 0.123456789012345678
     B = np.eye(32)
     out = np.zeros((2, 32))
-    capi.qec_debug_ozaki_gemm(A.ctypes.data, B.ctypes.data, 2, out.ctypes.data)
+    capi.qec_debug_ozaki_gemm(A.ctypes.data, B.ctypes.data, 2, variant, out.ctypes.data)
     assert not out[0].any()
     assert out[1, 5] == A[1, 5] and np.count_nonzero(out[1]) == 1
+
+
+def test_bad_variant_rejected():
+    a = np.zeros((1, 32))
+    with pytest.raises(capi.QecError):
+        capi.qec_debug_ozaki_gemm(a.ctypes.data, np.zeros((32, 32)).ctypes.data, 1, 3, a.ctypes.data)
+
+
+@pytest.mark.parametrize("seed", [0, 3])
+def test_probability_sums_are_fp64_accurate(seed):
+    """Variant 2: A_r = sum_n (A[r] . B[n])^2 and N_r = sum_k A[r][k]^2 with integer sums of squares."""
+    rng = np.random.default_rng(seed)
+    m = 12
+    A = _rows(rng, m)
+    q, _ = np.linalg.qr(rng.standard_normal((16, 16)) + 1j * rng.standard_normal((16, 16)))
+    q[3] = 0.0                                   # a zero output row, as projector-like Kraus operators have
+    B = np.zeros((32, 32))
+    B[0::2, 0::2], B[0::2, 1::2] = q.real, -q.imag
+    B[1::2, 0::2], B[1::2, 1::2] = q.imag, q.real
+    out = np.zeros((m, 32))
+    capi.qec_debug_ozaki_gemm(A.ctypes.data, np.ascontiguousarray(B).ctypes.data, m, 2, out.ctypes.data)
+    ex = _exact(A, B)
+    sb = float(np.abs(B).max())
+    tiny = Fraction(2.0 ** -1074)                # sums below the FP64 range flush to zero
+    for r in range(m):
+        sa = float(np.abs(A[r]).max())
+        a_ex = sum((v * v for v in ex[r]), Fraction(0))
+        n_ex = sum((Fraction(float(v)) ** 2 for v in A[r]), Fraction(0))
+        # per product: the 2^-44 sa sb bound of the emulated product, squared into the sum
+        ea = abs(Fraction(out[r, 0]) - a_ex)
+        assert ea <= Fraction(2.0 ** -42) * (Fraction(sa) * Fraction(sb)) ** 2 * 32 + a_ex * Fraction(2.0 ** -50) + tiny, (r, float(ea))
+        en = abs(Fraction(out[r, 1]) - n_ex)
+        assert en <= Fraction(2.0 ** -50) * n_ex + Fraction(2.0 ** -52) * Fraction(sa) ** 2 + tiny, (r, float(en))

@@ -39,12 +39,13 @@ typedef enum { QEC_GATES_CNOT = 0, QEC_GATES_CR = 1 } qec_gateset;
  * C64: complex64 state, FP32 gate arithmetic, FP64 probability reductions.
  * C64_TC: complex64 state; weight-4 block contractions on the tensor cores
  * (3xTF32 split, FP32 accumulation), FP64 probability reductions.
- * C128_TC: complex128 state; weight-4 block applications (tiles of 2^11
- * amplitudes, so d >= 5) as emulated FP64 products on the FP16 tensor cores:
- * each operand row split into 7 signed 8-bit slices under one exponent,
- * slice products accumulated exactly, recombined in integers and rounded
- * once (Ozaki scheme); everything else FP64.  Same amplitudes as C128 to
- * within a few FP64 roundings. */
+ * C128_TC: complex128 state; the apply and probability passes of every
+ * stabilizer block (tiles of 2^11 amplitudes, so d >= 5) as emulated FP64
+ * products on the FP16 tensor cores: each operand row split into 7 signed
+ * 8-bit slices under one exponent, slice products accumulated exactly,
+ * recombined in integers and rounded once (Ozaki scheme); sums of squares
+ * in exact integers; init and readout in FP64.  Same outcomes and, to
+ * within a few FP64 roundings, the same amplitudes as C128. */
 typedef enum { QEC_C128 = 0, QEC_C64 = 1, QEC_C64_TC = 2, QEC_C128_TC = 3 } qec_precision;
 
 /* Noise (Sec. III.A).  Probabilities in [0, 1]; angles in radians, |angle| <= 4. */

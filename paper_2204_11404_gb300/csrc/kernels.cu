@@ -10,6 +10,8 @@
 // renormalises and resets in one go.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.hpp"
 #include "ozaki.cuh"
@@ -774,7 +776,9 @@ __global__ void __launch_bounds__(256, 2) k_fused_tc(FusedArgs f) {
 
 // ---- complex128 apply pass, FP64-exact on the FP16 tensor cores (Ozaki slices) -----------------
 // A weight-4 block's 16x16 complex matrix (times 1/sqrt(N)) on the 128 groups of a 2048-amplitude
-// tile is a real product y = x . B^T (x: 128 x 32 reals, B: 32 x 32).  Each row of x and of B is
+// tile is a real product y = x . B^T (x: 128 x 32 reals, B: 32 x 32).  A weight-2 block's 4x4
+// matrix K runs as K (x) I on 16-amplitude groups made of its two qubits and two spectator qubits
+// of the tile: the same product with a block-diagonal B.  Each row of x and of B is
 // split into 7 signed 8-bit slices under its own exponent (ozaki.cuh); the 28 slice products with
 // p + q <= 6 run as FP16 MMAs (M = 128, N = 32, K = 16) accumulating each diagonal p + q = t exactly
 // in its own FP32 TMEM accumulator; the epilogue recombines the 7 diagonals in integers and rounds
@@ -874,11 +878,12 @@ __global__ void __launch_bounds__(256, 2) k_oz(FusedArgs f) {
     const int m = PROB ? 1 : *f.ap.m;
     const double scale = PROB ? 1.0 : 1.0 / sqrt(*f.ap.N);
     const double2* Kg = reinterpret_cast<const double2*>(f.ap.kraus) + (m ? 256 : 0);
+    const bool w2 = f.ap.w == 2;
     double b[32];
     int E = 0;
 #pragma unroll
     for (int l = 0; l < 16; ++l) {
-      const double2 kv = Kg[r * 16 + l];
+      const double2 kv = !w2 ? Kg[r * 16 + l] : ((r >> 2) == (l >> 2) ? Kg[(r & 3) * 16 + (l & 3)] : make_double2(0.0, 0.0));
       const double re = kv.x * scale, im = kv.y * scale;
       b[2 * l] = (n & 1) ? im : re;
       b[2 * l + 1] = (n & 1) ? re : -im;
@@ -903,12 +908,15 @@ __global__ void __launch_bounds__(256, 2) k_oz(FusedArgs f) {
   tc_sync();
   const uint32_t tmem = tmem_base;
   const uint32_t mb = smem_u32(&mbar);
-  int qa[4];
+  int qa[4], qs[4];
 #pragma unroll
-  for (int j = 0; j < 4; ++j) qa[j] = f.qa[j];
+  for (int j = 0; j < 4; ++j) {
+    qa[j] = f.qa[j];
+    qs[j] = f.qp[j];
+  }
   // thread = (row r, half hf): amplitudes 8hf..8hf+7 of group r, reals 16hf..16hf+15
   const int r = tid & 127, hf = tid >> 7;
-  const uint32_t gbase = local_base<4>((uint32_t)r, qa);
+  const uint32_t gbase = local_base<4>((uint32_t)r, qs);
   uint32_t offa[8];
 #pragma unroll
   for (int l = 0; l < 8; ++l) offa[l] = gbase + member_off<4>(8 * hf + l, qa);
@@ -977,15 +985,16 @@ __global__ void __launch_bounds__(256, 2) k_oz(FusedArgs f) {
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     tc_sync();
-    if (tid == 0) {
-      const uint32_t a0 = smem_u32(A), b0 = smem_u32(B);
+    if (tid == 0) {   // 56 MMAs, descriptors as constant offsets from two bases (address field: bytes / 16)
+      const uint64_t da = umma_desc(smem_u32(A), 128, 512), db = umma_desc(smem_u32(B), 128, 512);
+#pragma unroll
       for (int t = 0; t < oz::kSlices; ++t)
+#pragma unroll
         for (int p = 0; p <= t; ++p)
-          for (int ks = 0; ks < 2; ++ks) {
-            const uint64_t ad = umma_desc(a0 + 2u * kOzSlab * p + 256u * ks, 128, 512);
-            const uint64_t bd = umma_desc(b0 + 2u * 32 * 32 * (t - p) + 256u * ks, 128, 512);
-            umma_f16(tmem + 32u * t, ad, bd, (p > 0 || ks > 0) ? 1u : 0u);
-          }
+#pragma unroll
+          for (int ks = 0; ks < 2; ++ks)
+            umma_f16(tmem + 32u * t, da + ((2u * kOzSlab * p + 256u * ks) >> 4),
+                     db + ((2u * 32 * 32 * (t - p) + 256u * ks) >> 4), (p > 0 || ks > 0) ? 1u : 0u);
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mb) : "memory");
     }
     if (!mbar_wait(mb, phase & 1)) s_err = 1;
@@ -1362,7 +1371,7 @@ static void block_tile(const PassArgs& ap, const PassArgs& pr, int lb0, int bits
 }
 
 bool apply_oz_applies(const PassArgs& ap) {
-  if (ap.w != 4) return false;
+  if (ap.w != 2 && ap.w != 4) return false;
   FusedArgs f;
   block_tile(ap, ap, 3, kOzTileBits, f);
   return f.nt == kOzTileBits;
@@ -1373,7 +1382,14 @@ static cudaError_t launch_oz(bool prob, const PassArgs& ap, int num_sms, cudaStr
   f.ap = ap;
   f.pr = ap;
   block_tile(ap, ap, 3, kOzTileBits, f);
-  if (ap.w != 4 || f.nt != kOzTileBits) return cudaErrorInvalidValue;
+  if ((ap.w != 2 && ap.w != 4) || f.nt != kOzTileBits) return cudaErrorInvalidValue;
+  if (ap.w == 2) {   // spectators: the two lowest tile bits outside the block
+    int k = 2;
+    for (int b = 0; b < f.nt && k < 4; ++b)
+      if (b != f.qa[0] && b != f.qa[1]) f.qa[k++] = b;
+  }
+  for (int j = 0; j < 4; ++j) f.qp[j] = f.qa[j];
+  std::sort(f.qp, f.qp + 4);
   int64_t g = 2ll * num_sms;   // two CTAs per SM: 103 KiB of shared memory and 256 TMEM columns each
   if (g > (1ll << f.nout)) g = 1ll << f.nout;
   if (g > MAX_PASS_GRID) g = MAX_PASS_GRID;

@@ -73,8 +73,10 @@ struct FusedArgs {
   int hbits[16];
   int nout;
   int obits[32];          // register bits outside the tile, ascending
-  int qa[4];              // apply block's qubits as tile-index bits (ascending)
-  int qp[4];              // probability block's qubits as tile-index bits (ascending)
+  int qa[4];              // apply block's qubits as tile-index bits (ascending; the tensor-core
+                          // complex128 passes: a weight-2 block's two qubits, then two spectators)
+  int qp[4];              // probability block's qubits as tile-index bits (ascending; the
+                          // tensor-core complex128 passes: qa sorted)
   int grid;
 };
 

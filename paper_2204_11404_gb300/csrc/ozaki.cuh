@@ -65,7 +65,7 @@ OZ_HD float u2f(uint32_t u) {
 #endif
 }
 
-// Biased exponent field of x (0 for zero and subnormals, which are treated as zero).
+// Biased exponent field of x (0 for zero and subnormals).
 OZ_HD int bexp(double x) { return (int)((d2u(x) >> 52) & 0x7FF); }
 
 // BF16 bit pattern of the signed integer d, |d| <= 255 (exact).
@@ -79,10 +79,16 @@ OZ_HD uint16_t bf16_of_int(int d) {
 // The 56-bit magnitude X of x relative to the row exponent E: x = 2^(E-1022-56) * (-1)^s * X.
 OZ_HD uint64_t mag56(double x, int E) {
   const uint64_t u = d2u(x);
-  const int ex = (int)((u >> 52) & 0x7FF);
-  const int k = E - ex;                                                       // >= 0
-  const uint64_t m = ((u & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull) << 3;   // 56 bits
-  return (ex == 0 || k > 55) ? 0ull : (m >> k);
+  const int ex = (int)((u >> 52) & 0x7FF);                                    // 0: zero or subnormal
+  const uint64_t m = ((u & 0xFFFFFFFFFFFFFull) | ((uint64_t)(ex != 0) << 52)) << 3;   // 56 bits
+  const unsigned k = (unsigned)(E - (ex ? ex : 1));                           // >= 0 when E >= 1
+#if defined(__CUDA_ARCH__)
+  uint64_t X;
+  asm("shr.b64 %0, %1, %2;" : "=l"(X) : "l"(m), "r"(k));                     // amounts >= 64 give 0
+  return X;
+#else
+  return k > 63 ? 0ull : (m >> k);
+#endif
 }
 
 // The 7 signed digits of x relative to the row exponent E (x == 0 or E == 0: all zero).

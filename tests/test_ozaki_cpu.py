@@ -15,6 +15,8 @@ def _rows(rng, m):
     A[1, :] = 1e-300 * rng.standard_normal(32)                                  # tiny scale
     A[2, :16] = 0.5
     A[2, 16:] = -0.5                                                            # exact ties
+    A[3, :] = 1e-300 * rng.standard_normal(32)
+    A[3, ::4] = 3e-310 * rng.standard_normal(8)                                 # subnormals beside normals
     return A
 
 

@@ -39,7 +39,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=9)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--precision", default="c128", choices=["c128", "c64", "c64tc", "c128tc"])
+    ap.add_argument("--precision", default="c128tc", choices=["c128", "c64", "c64tc", "c128tc"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--points", type=int, default=9, help="noise points used (1..9); fewer = smaller device footprint")
     ap.add_argument("--workload", default="d5", choices=["d5", "batched", "serve", "precision", "sweep"],
@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--rate", type=float, default=50.0, help="serve: mean arrival rate (requests/s)")
     ap.add_argument("--max-traj", type=int, default=8, help="serve: trajectories per request drawn from 1..max")
     ap.add_argument("--mem-gib", type=float, default=32.0, help="serve: device memory budget for state vectors")
-    ap.add_argument("--noise", default="full", choices=["full", "idle", "twirl"],
+    ap.add_argument("--noise", default="full", choices=["full", "idle", "twirl", "follows"],
                     help="sweep: full = p on every step (Eqs. 1-2); idle = p on waiting qubits only; "
                          "twirl = full with the coherent terms replaced by their Pauli twirl")
     return ap.parse_args()
@@ -189,17 +189,23 @@ def workload_config(args, world):
 
 # ---- native arm ------------------------------------------------------------------------------
 def traffic_record(precision):
-    """dram bytes per launch of the apply pass from the committed ncu summary, if it still
-    describes the current kernel source; else None."""
+    """dram bytes per launch of the apply pass from the committed ncu summary, if it was taken
+    on the current kernel source (sha256 of kernels.cu and ozaki.cuh); else None."""
     path = os.path.join(ROOT, "profiles", "apply_pass_traffic.json")
     try:
-        rec = json.load(open(path))
+        rec = json.load(open(path)).get(precision, {})
     except (OSError, ValueError):
         return None
-    src = open(os.path.join(ROOT, "paper_2204_11404_gb300", "csrc", "kernels.cu"), "rb").read()
-    if rec.get("kernels_cu_sha256") != hashlib.sha256(src).hexdigest():
+    if rec.get("source_sha256") != kernel_source_sha():
         return None
-    return rec.get(precision, {}).get("dram_bytes_per_launch")
+    return rec.get("dram_bytes_per_launch")
+
+
+def kernel_source_sha():
+    h = hashlib.sha256()
+    for f in ("kernels.cu", "ozaki.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2204_11404_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
 
 
 def native_arm(args, rank, world, local):
@@ -290,7 +296,7 @@ def native_arm(args, rank, world, local):
     roof["kernel"] = {"c128": "k_apply<double,4> (weight-4 block, 2^25 amplitudes)",
                       "c64": "k_fused<float,4,4> (apply weight-4 block + next block's probability, 2^25 amplitudes)",
                       "c64tc": "k_fused_tc (tcgen05 3xTF32: apply weight-4 block + next probability, 2^25 amplitudes)",
-                      "c128tc": "k_apply_oz (tcgen05 FP16 8-bit slices, FP64-exact: weight-4 block, 2^25 amplitudes)",
+                      "c128tc": "k_oz<false> (apply pass on tcgen05: FP64-exact 8-bit-slice products, weight-4 block, 2^25 amplitudes)",
                       }[args.precision]
     roof["ms_apply"] = ms_apply
     roof["ms_prob"] = ms_prob
@@ -464,7 +470,8 @@ def sweep_arm(args, rank, world, local):
             th = 2 * c * np.sqrt(p)
             g = 0.0 if args.noise == "idle" else p
             nz = dict(p1=g, p2=g, p_idle=p, theta_rx=th, theta_rz=th, theta_rzx=th,
-                      twirl=1.0 if args.noise == "twirl" else 0.0)
+                      twirl=1.0 if args.noise == "twirl" else 0.0,
+                      overrot_follows=1.0 if args.noise == "follows" else 0.0)
             with Simulator(5, 5, "cr", "c64tc", **nz) as sim:
                 syn, bits, log = sim.run(7000, rank * n, n)
             f = [dec.logical_failure(a, b, l) for a, b, l in zip(syn, bits, log)]

@@ -41,6 +41,9 @@ def parse():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--precision", default="c128tc", choices=["c128", "c64", "c64tc", "c128tc"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--code", default="surface", choices=["surface", "repetition"],
+                    help="repetition: the d=25 line code of Fig. 2 (same 25-qubit register, 24 stabilizers); "
+                         "no CPU baseline")
     ap.add_argument("--points", type=int, default=9, help="noise points used (1..9); fewer = smaller device footprint")
     ap.add_argument("--workload", default="d5", choices=["d5", "batched", "serve", "precision", "sweep"],
                     help="d5: the d=5 26-qubit trajectories (default); batched: 8192 d=3 trajectories per "
@@ -179,6 +182,13 @@ def reference_arm(args, rank, world):
 
 
 def workload_config(args, world):
+    if args.code == "repetition":
+        return {"workload": "d=25 one-dimensional repetition code (Fig. 2), reduced 26-qubit register (25 data "
+                            "resident + ancilla), cr gate set, 5 noisy rounds + init + Z readout, 9 noise points "
+                            "(p x theta_rx) with ZZ 0.02",
+                "d": 25, "code": "repetition", "rounds": 5, "precision": args.precision,
+                "trajectories_per_rank": args.steps, "parallelism": "trajectory-sharded x%d" % world,
+                "l2": "state 512 MiB (c128) / 256 MiB (c64) per pass > 129 MB L2, no flush needed"}
     return {"workload": "d=5 rotated surface code, reduced 26-qubit register (25 data resident + ancilla), "
                         "cr gate set, 5 noisy rounds + init + Z readout, 9 noise points "
                         "(p x theta_rx) with ZZ 0.02",
@@ -222,7 +232,8 @@ def native_arm(args, rank, world, local):
         dist.init_process_group("nccl")
     pts = W.D5_CR["points"][: max(1, min(args.points, len(W.D5_CR["points"])))]
     R = W.D5_CR["rounds"]
-    sims = [Simulator(5, R, "cr", args.precision, **pt) for pt in pts]
+    dd = 25 if args.code == "repetition" else 5   # 25 data qubits and 24 stabilizers either way
+    sims = [Simulator(dd, R, "cr", args.precision, code=args.code, **pt) for pt in pts]
     seeds = [W.D5_CR["seed_base"] + i for i in range(len(pts))]
     nst = 24
     syn = torch.empty((1, R + 1, nst), dtype=torch.uint8, device="cuda")
@@ -312,7 +323,7 @@ def native_arm(args, rank, world, local):
         "data": "synthetic", "config": workload_config(args, world), "clocks": clk.summary(),
         "e2e": e2e, "gpu_launches": launches_per_traj * args.steps, "roofline": roof,
     }
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.code == "surface":
         smp = OracleSampler()
         secs_o = smp.run(24)
         out["cpu_baseline"] = {"value": 1.0 / secs_o, "unit": UNIT, "cores": smp.threads, "kind": "oracle",

@@ -29,6 +29,12 @@ typedef enum {
 /* Register layout (Sec. II.B).  REDUCED: d^2 data qubits + one reused ancilla
  * (26 qubits at d=5); UNREDUCED: all 2d^2-1 qubits (only the oracle runs it). */
 typedef enum { QEC_LAYOUT_REDUCED = 0, QEC_LAYOUT_UNREDUCED = 1 } qec_layout;
+/* The code whose memory experiment runs.  SURFACE: the rotated surface code (Sec. II.A,
+ * Table I), d^2 data qubits, d^2 - 1 stabilizers.  REPETITION: the one-dimensional bit-flip
+ * repetition code of Sec. II.B, Fig. 2 (the paper's illustration of the delayed register), d
+ * data qubits on a line, d - 1 stabilizers Z_k Z_{k+1} measured in the Z part of the round
+ * (steps 7-11) with gate order q_{k+1}, q_k; the X part of its round is idle. */
+typedef enum { QEC_CODE_SURFACE = 0, QEC_CODE_REPETITION = 1 } qec_code;
 
 /* Gate set.  CNOT: H + CNOT stabilizer circuits (Fig. 1b/c).  CR: the
  * cross-resonance native set {Rx(pi/2), Rx^dagger(pi/2), Rzx(pi/2), Rz(pi/2)}
@@ -68,12 +74,13 @@ typedef struct {
 } qec_noise;
 
 typedef struct {
-  int32_t d;          /* code distance: odd, 3 <= d <= 5 (2^(d^2) amplitudes resident) */
+  int32_t d;          /* code distance: odd; surface code 3 <= d <= 5 (2^(d^2) amplitudes resident),
+                         repetition code 9 <= d <= 25 (2^d) */
   int32_t rounds;     /* noisy syndrome rounds after the noise-free init round, 0..64 */
   int32_t layout;     /* qec_layout; only QEC_LAYOUT_REDUCED runs on the GPU */
   int32_t gates;      /* qec_gateset */
   int32_t precision;  /* qec_precision */
-  int32_t reserved;   /* must be 0 */
+  int32_t code;       /* qec_code */
   qec_noise noise;
 } qec_params;
 
@@ -99,11 +106,14 @@ qec_status qec_create(const qec_params* params, void* cuda_stream, qec_sim** out
  * trajectory index): noise and measurement draws come from Philox4x64-10 with
  * key (seed, 0) and counter (trajectory, round, step<<32 | physical site, tag).
  * Outputs are caller-owned HOST buffers (may be NULL to skip):
- *   syndromes  [n][rounds+1][d*d-1]  uint8: row 0 is the forced init round
- *              (all 0); stabilizers in Table I order, X then Z
- *   data_bits  [n][d*d]              uint8: final Z outcome of each data qubit
- *   raw_logical[n]                   uint8: parity of data_bits over the first
- *              data row (logical Z), before any decoding
+ *   syndromes  [n][rounds+1][S]  uint8: row 0 is the forced init round (all 0);
+ *              S = d*d-1 stabilizers in Table I order, X then Z (surface
+ *              code), or S = d-1 in line order (repetition code)
+ *   data_bits  [n][Q]            uint8: final Z outcome of each data qubit,
+ *              Q = d*d (surface) or d (repetition)
+ *   raw_logical[n]               uint8: parity of data_bits over data qubits
+ *              0..d-1 (logical Z: the first row of the surface code, the whole
+ *              line of the repetition code), before any decoding
  * Blocks until the results are on the host.
  */
 qec_status qec_run_trajectories(qec_sim* sim, uint64_t seed, uint64_t first_traj, uint32_t n,
@@ -120,13 +130,13 @@ qec_status qec_run_trajectories_device(qec_sim* sim, uint64_t seed, uint64_t fir
 /*
  * Re-point an existing simulator at new noise parameters and round count,
  * keeping its device buffers and its resident init code state (which does not
- * depend on noise or rounds).  d, gate set, precision and layout must match
- * the handle's (QEC_EINVAL otherwise).  Waits for the handle's queued work.
+ * depend on noise or rounds).  d, gate set, precision, layout and code must
+ * match the handle's (QEC_EINVAL otherwise).  Waits for the handle's queued work.
  */
 qec_status qec_reconfigure(qec_sim* sim, const qec_params* params);
 
-/* Number of amplitudes of the resident data register (2^(d*d)); the ancilla
- * of the d^2+1 register is |0> at every point a snapshot can be taken. */
+/* Number of amplitudes of the resident data register (2^Q, Q data qubits); the
+ * reused ancilla is |0> at every point a snapshot can be taken. */
 uint64_t qec_state_len(const qec_sim* sim);
 
 /*

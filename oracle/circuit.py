@@ -62,7 +62,7 @@ rounds+1, site = data qubit).
 import numpy as np
 
 from . import gates as G
-from .lattice import stabilizers, logical_z_support
+from .lattice import code_stabilizers, logical_z_support, n_data
 from .philox import draw, uniform53, TAG_NOISE, TAG_MEASURE, TAG_READOUT, TAG_TWIRL
 
 NOISE_KEYS = ("p1", "p2", "p_idle", "theta_rx", "theta_rz", "theta_rzx", "phi_zz", "round_rz", "round_rx", "twirl",
@@ -81,14 +81,14 @@ def noise_dict(**kw):
 class Trajectory:
     """Builds the op list of one trajectory and records the sampled Pauli events."""
 
-    def __init__(self, d, rounds, gates, layout, noise, seed, traj, inject=None):
+    def __init__(self, d, rounds, gates, layout, noise, seed, traj, inject=None, code="surface"):
         if gates not in ("cnot", "cr") or layout not in ("reduced", "unreduced"):
             raise ValueError("bad gate set or layout")
-        self.d, self.rounds, self.gates, self.layout = d, rounds, gates, layout
+        self.d, self.rounds, self.gates, self.layout, self.code = d, rounds, gates, layout, code
         self.noise = noise_dict(**(noise or {}))
         self.seed, self.traj = seed, traj
-        self.nd = d * d
-        self.stabs = stabilizers(d)
+        self.nd = n_data(d, code)
+        self.stabs = code_stabilizers(d, code)
         self.nstab = len(self.stabs)
         self.n = self.nd + (1 if layout == "reduced" else self.nstab)
         self.inject = inject or []        # (round, step, data qubit, 2x2 matrix), applied after that step's ops
@@ -179,7 +179,8 @@ class Trajectory:
                 self.u1(q, base)
                 if noisy:
                     self.coherent1(rnd, t, q, f, q, pauli, over)
-            self.e1(rnd, t, q, q, nz["p1"])
+            # no correction gate (a code with no stabilizer of that kind on q): the qubit idles
+            self.e1(rnd, t, q, q, nz["p1"] if n_fact else nz["p_idle"])
         else:
             self.e1(rnd, t, q, q, nz["p_idle"])
         for (ri, ti, qi, m) in self.inject:
@@ -298,5 +299,5 @@ class Trajectory:
         return len(self.ops)
 
 
-def logical_parity(d, data_bits):
-    return int(np.bitwise_xor.reduce([int(data_bits[q]) for q in logical_z_support(d)]))
+def logical_parity(d, data_bits, code="surface"):
+    return int(np.bitwise_xor.reduce([int(data_bits[q]) for q in logical_z_support(d, code)]))

@@ -1,4 +1,5 @@
-"""Rotated surface code geometry: data qubits, stabilizers, two-qubit gate order.
+"""Code geometry: data qubits, stabilizers, two-qubit gate order (rotated surface code; the
+one-dimensional repetition code of Fig. 2 as a second workload).
 
 Test infrastructure only (see ``oracle/__init__.py``).
 
@@ -74,8 +75,34 @@ def stabilizers(d):
     return out
 
 
-def logical_z_support(d):
+def logical_z_support(d, code="surface"):
+    """Surface code: the first data row.  Repetition code: all d data qubits (Z on every qubit of
+    the line, equal to Z on one qubit times stabilizers for odd d)."""
+    if code == "repetition":
+        return list(range(d))
     return [data_id(d, 0, c) for c in range(d)]
+
+
+def repetition_stabilizers(d):
+    """One-dimensional bit-flip repetition code (Sec. II.B, Fig. 2): d data qubits on a line,
+    stabilizers Z_k Z_{k+1}, k = 0..d-2, all Z-type.  Gate order q_{k+1} then q_k, so that
+    measuring k = 0, 1, ... one at a time keeps every qubit's gates in time order (qubit k+1 meets
+    stabilizer k at the first gate step and stabilizer k+1 at the second): the time-shifted
+    circuit of Fig. 2(b).  Slots 3 and 4 of the Z part are waits."""
+    return [{"kind": "Z", "slots": [k + 1, k, None, None], "support": [k, k + 1], "weight": 2}
+            for k in range(d - 1)]
+
+
+def code_stabilizers(d, code="surface"):
+    if code == "surface":
+        return stabilizers(d)
+    if code == "repetition":
+        return repetition_stabilizers(d)
+    raise ValueError("code must be 'surface' or 'repetition'")
+
+
+def n_data(d, code="surface"):
+    return d if code == "repetition" else d * d
 
 
 def n_stabilizers(d):

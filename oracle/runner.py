@@ -82,11 +82,11 @@ def run_ops(psi, n, ops):
 
 
 def run_trajectory(d, rounds, gates="cr", layout="reduced", noise=None, seed=0, traj=0,
-                   inject=None, want_state=False):
+                   inject=None, want_state=False, code="surface"):
     """Simulate one trajectory.  Returns a dict with syndromes [rounds+1][d^2-1] (row 0 is the
     forced init round), data_bits [d^2], raw_logical, events (sampled Paulis), the per-measurement
     records (u, P(1), outcome) and, if want_state, the state after the last round (before readout)."""
-    T = Trajectory(d, rounds, gates, layout, noise, seed, traj, inject).build()
+    T = Trajectory(d, rounds, gates, layout, noise, seed, traj, inject, code).build()
     if T.n > 30:
         raise ValueError("register too large for the oracle")
     psi = np.zeros(1 << T.n, dtype=np.complex128)
@@ -106,7 +106,7 @@ def run_trajectory(d, rounds, gates="cr", layout="reduced", noise=None, seed=0, 
     return {
         "syndromes": syn,
         "data_bits": data_bits,
-        "raw_logical": logical_parity(d, data_bits),
+        "raw_logical": logical_parity(d, data_bits, code),
         "events": list(T.events),
         "anc_records": recs,
         "readout_records": ro_recs,

@@ -12,6 +12,7 @@ from .build import LIB, build
 QEC_OK, QEC_EINVAL, QEC_ENOMEM, QEC_ECUDA, QEC_ETIMEOUT, QEC_EUNSUPPORTED = 0, -1, -2, -3, -4, -6
 QEC_LAYOUT_REDUCED, QEC_LAYOUT_UNREDUCED = 0, 1
 QEC_GATES_CNOT, QEC_GATES_CR = 0, 1
+QEC_CODE_SURFACE, QEC_CODE_REPETITION = 0, 1
 QEC_C128, QEC_C64, QEC_C64_TC, QEC_C128_TC = 0, 1, 2, 3
 
 NOISE_FIELDS = ("p1", "p2", "p_idle", "theta_rx", "theta_rz", "theta_rzx", "phi_zz", "round_rz", "round_rx", "twirl",
@@ -24,7 +25,7 @@ class qec_noise(ctypes.Structure):
 
 class qec_params(ctypes.Structure):
     _fields_ = [("d", ctypes.c_int32), ("rounds", ctypes.c_int32), ("layout", ctypes.c_int32),
-                ("gates", ctypes.c_int32), ("precision", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("gates", ctypes.c_int32), ("precision", ctypes.c_int32), ("code", ctypes.c_int32),
                 ("noise", qec_noise)]
 
 
@@ -87,13 +88,13 @@ def check(status):
     return status
 
 
-def make_params(d, rounds, gates="cr", precision="c128", layout="reduced", **noise):
+def make_params(d, rounds, gates="cr", precision="c128", layout="reduced", code="surface", **noise):
     p = qec_params()
     p.d, p.rounds = int(d), int(rounds)
     p.layout = {"reduced": QEC_LAYOUT_REDUCED, "unreduced": QEC_LAYOUT_UNREDUCED}[layout]
     p.gates = {"cnot": QEC_GATES_CNOT, "cr": QEC_GATES_CR}[gates]
     p.precision = {"c128": QEC_C128, "c64": QEC_C64, "c64tc": QEC_C64_TC, "c128tc": QEC_C128_TC}[precision]
-    p.reserved = 0
+    p.code = {"surface": QEC_CODE_SURFACE, "repetition": QEC_CODE_REPETITION}[code]
     for k, v in noise.items():
         if k not in NOISE_FIELDS:
             raise KeyError(k)

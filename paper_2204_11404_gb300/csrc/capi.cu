@@ -550,8 +550,8 @@ qec_status qec_reconfigure(qec_sim* s, const qec_params* params) {
   std::string err;
   if (!validate_params(*params, err)) return fail(QEC_EINVAL, err);
   if (params->d != s->p.d || params->gates != s->p.gates || params->precision != s->p.precision ||
-      params->layout != s->p.layout)
-    return fail(QEC_EINVAL, "qec_reconfigure keeps d, gate set, precision and layout");
+      params->layout != s->p.layout || params->code != s->p.code)
+    return fail(QEC_EINVAL, "qec_reconfigure keeps d, gate set, precision, layout and code");
   Program P;
   if (!build_program(*params, true, P, err)) return fail(QEC_EINVAL, err);
   if (params->rounds > kMaxRounds) return fail(QEC_EINVAL, "rounds exceed the simulator's capacity");

@@ -1117,7 +1117,7 @@ __global__ void __launch_bounds__(256) k_sample(ReadArgs a) {
   const uint64_t seed = a.ctl->seed, traj = a.ctl->traj;
   const unsigned long long t = traj - a.ctl->first;
   const uint64_t rnd = (uint64_t)a.rounds + 1;
-  const int nd = a.d * a.d;
+  const int nd = a.D;   // data qubits = resident register bits
   uint8_t* bits = a.bits + t * (unsigned long long)nd;
   double tot = 0.0, dummy = 0.0;
   for (int i = threadIdx.x; i < B; i += blockDim.x) {
@@ -1141,7 +1141,7 @@ __global__ void __launch_bounds__(256) k_sample(ReadArgs a) {
   __syncthreads();
   if (threadIdx.x == 0) {
     int par = 0;
-    for (int c = 0; c < a.d; ++c) par ^= bits[c];
+    for (int c = 0; c < a.d; ++c) par ^= bits[c];   // Z_L: the first row (surface), the whole line (repetition)
     a.logical[t] = (uint8_t)par;
     for (int k = 0; k < a.nstab; ++k) a.syn[t * (unsigned long long)a.syn_stride + k] = 0;
     a.ctl->traj = traj + 1;

@@ -88,7 +88,7 @@ struct ReadArgs {
   double* hist_part;      // [grid_hist][2^k1]
   double* hist;           // [2^k1]
   Ctl* ctl;
-  uint8_t* bits;          // [traj][d^2]
+  uint8_t* bits;          // [traj][D] (one bit per data qubit)
   uint8_t* logical;       // [traj]
   uint8_t* syn;           // [traj][syn_stride]; round-0 row zeroed here
   int syn_stride;

@@ -83,7 +83,19 @@ bool finite_in(double v, double lo, double hi) { return std::isfinite(v) && v >=
 
 }  // namespace
 
-std::vector<Stab> make_stabilizers(int d) {
+std::vector<Stab> make_stabilizers(int d, int code) {
+  if (code == QEC_CODE_REPETITION) {   // Z_k Z_{k+1} on a line; gate order q_{k+1}, q_k (Fig. 2(b))
+    std::vector<Stab> out;
+    for (int k = 0; k + 1 < d; ++k) {
+      Stab s;
+      s.kind = 'Z';
+      s.w = 2;
+      const int sl[4] = {k + 1, k, -1, -1};
+      std::copy(sl, sl + 4, s.slots);
+      out.push_back(s);
+    }
+    return out;
+  }
   std::vector<std::tuple<int, int, Stab>> xs, zs;
   for (int r = -1; r < d; ++r) {
     for (int c = -1; c < d; ++c) {
@@ -120,7 +132,12 @@ std::vector<Stab> make_stabilizers(int d) {
 }
 
 bool validate_params(const qec_params& p, std::string& err) {
-  if (p.d < 3 || p.d > 5 || (p.d % 2) == 0) { err = "d must be 3 or 5"; return false; }
+  if (p.code != QEC_CODE_SURFACE && p.code != QEC_CODE_REPETITION) { err = "bad code"; return false; }
+  if (p.code == QEC_CODE_SURFACE && (p.d < 3 || p.d > 5 || (p.d % 2) == 0)) { err = "d must be 3 or 5"; return false; }
+  if (p.code == QEC_CODE_REPETITION && (p.d < 9 || p.d > 25 || (p.d % 2) == 0)) {
+    err = "repetition code: d must be odd, 9..25";
+    return false;
+  }
   if (p.rounds < 0 || p.rounds > 64) { err = "rounds must be in [0, 64]"; return false; }
   if (p.layout != QEC_LAYOUT_REDUCED && p.layout != QEC_LAYOUT_UNREDUCED) { err = "bad layout"; return false; }
   if (p.gates != QEC_GATES_CNOT && p.gates != QEC_GATES_CR) { err = "bad gate set"; return false; }
@@ -128,7 +145,6 @@ bool validate_params(const qec_params& p, std::string& err) {
     err = "bad precision";
     return false;
   }
-  if (p.reserved != 0) { err = "reserved must be 0"; return false; }
   const qec_noise& n = p.noise;
   if (!finite_in(n.p1, 0, 1) || !finite_in(n.p2, 0, 1) || !finite_in(n.p_idle, 0, 1)) {
     err = "noise probabilities must be in [0, 1]";
@@ -156,10 +172,10 @@ void twirl_probs(const qec_noise& nz, double* prob) {
 
 bool build_program(const qec_params& p, bool noisy, Program& P, std::string& err, bool all_slots) {
   if (!validate_params(p, err)) return false;
-  const int d = p.d, nd = d * d;
+  const int d = p.d, nd = p.code == QEC_CODE_REPETITION ? d : d * d;
   const bool cr = p.gates == QEC_GATES_CR;
   const qec_noise& nz = p.noise;
-  std::vector<Stab> S = make_stabilizers(d);
+  std::vector<Stab> S = make_stabilizers(d, p.code);
   P = Program();
   P.d = d;
   P.nd = nd;
@@ -260,7 +276,7 @@ bool build_program(const qec_params& p, bool noisy, Program& P, std::string& err
           if (t == 6) coh1(lq, t, (uint32_t)q, f, M_ROT_RX, M_X, nz.theta_rx, PR_TW_RX);
           else coh1(lq, t, (uint32_t)q, f, M_ROT_RZ, M_Z, nz.theta_rz, PR_TW_RZ);
         }
-        n1(lq, t, (uint32_t)q, PR_P1);
+        n1(lq, t, (uint32_t)q, nfac ? PR_P1 : PR_IDLE);   // no correction gate: the qubit idles
       } else {
         n1(lq, t, (uint32_t)q, PR_IDLE);
       }
@@ -307,10 +323,11 @@ bool build_program(const qec_params& p, bool noisy, Program& P, std::string& err
 
 bool build_unreduced_program(const qec_params& p, bool noisy, UProgram& U, std::string& err, bool all_slots) {
   if (!validate_params(p, err)) return false;
+  if (p.code != QEC_CODE_SURFACE) { err = "the unreduced register is built for the surface code"; return false; }
   const int d = p.d, nd = d * d;
   const bool cr = p.gates == QEC_GATES_CR;
   const qec_noise& nz = p.noise;
-  std::vector<Stab> S = make_stabilizers(d);
+  std::vector<Stab> S = make_stabilizers(d, p.code);
   const int nst = (int)S.size(), half = nst / 2;
   U = UProgram();
   U.d = d;

@@ -91,7 +91,9 @@ struct UProgram {
 bool build_unreduced_program(const qec_params& p, bool noisy, UProgram& out, std::string& err,
                              bool all_slots = false);
 
-std::vector<Stab> make_stabilizers(int d);
+// Serial-order stabilizers of the code (qec_code): the rotated surface code (Table I order, X then
+// Z) or the repetition code's Z_k Z_{k+1}.
+std::vector<Stab> make_stabilizers(int d, int code);
 bool validate_params(const qec_params& p, std::string& err);
 // noisy = false: the noise-free init round (no noise sites, no coherent terms).
 bool build_program(const qec_params& p, bool noisy, Program& out, std::string& err, bool all_slots = false);

@@ -17,8 +17,9 @@ graph or weights, so this module uses the plain reading.
   Z-stabilizer parities of the final data readout.
 
 Only Z-stabilizers are decoded, because the experiment measures logical Z.
-Logical Z is Z on the first data row.  A correction chain flips the logical
-when it crosses that row an odd number of times.
+Logical Z is Z on the first data row (surface code) or on the whole line
+(repetition code, Fig. 2).  A correction chain flips the logical when it
+crosses that support an odd number of times.
 
 The matching is exact (dynamic programming over subsets of defects) up to
 MAX_EXACT defects.  Beyond that it falls back to greedy pairing of the closest
@@ -49,15 +50,21 @@ def _stabilizers(d):
     return [(sup, slots) for _, sup, slots in zs]
 
 
+def _repetition_stabilizers(d):
+    """Z_k Z_{k+1} in line order, gate order q_{k+1} then q_k (as the library builds them)."""
+    return [([k, k + 1], {k + 1: 0, k: 1}) for k in range(d - 1)]
+
+
 class Decoder:
-    def __init__(self, d):
-        self.d = d
-        st = _stabilizers(d)
+    def __init__(self, d, code="surface"):
+        self.d, self.code = d, code
+        st = _repetition_stabilizers(d) if code == "repetition" else _stabilizers(d)
         self.zs = [sup for sup, _ in st]
         self.slots = [sl for _, sl in st]
         self.nz = len(self.zs)
-        self.nx = self.nz                      # X-stabilizers come first in the syndrome rows
-        nd = d * d
+        # X-stabilizers come first in the syndrome rows (the repetition code has none)
+        self.nx = 0 if code == "repetition" else self.nz
+        nd = d if code == "repetition" else d * d
         owners = [[] for _ in range(nd)]
         for k, sup in enumerate(self.zs):
             for q in sup:

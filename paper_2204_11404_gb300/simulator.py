@@ -7,16 +7,19 @@ from . import capi
 
 
 class Simulator:
-    """One qec_sim handle: d, rounds, gate set, precision and noise are fixed at creation.
+    """One qec_sim handle: d, rounds, gate set, precision, code and noise are fixed at creation.
 
     ``stream``: an integer cudaStream_t (e.g. ``torch.cuda.current_stream().cuda_stream``)
     that the simulator's work is ordered after/before, or None.
+    ``code``: "surface" (rotated surface code, d^2 data qubits) or "repetition" (Fig. 2's
+    one-dimensional code, d data qubits).
     """
 
-    def __init__(self, d, rounds, gates="cr", precision="c128", stream=None, **noise):
-        self.d, self.rounds = int(d), int(rounds)
-        self.nstab = self.d * self.d - 1
-        self.params = capi.make_params(d, rounds, gates, precision, **noise)
+    def __init__(self, d, rounds, gates="cr", precision="c128", stream=None, code="surface", **noise):
+        self.d, self.rounds, self.code = int(d), int(rounds), code
+        self.nd = self.d if code == "repetition" else self.d * self.d
+        self.nstab = self.nd - 1
+        self.params = capi.make_params(d, rounds, gates, precision, code=code, **noise)
         self.h = capi.qec_create(self.params, ctypes.c_void_p(stream) if stream else None)
 
     def reconfigure(self, rounds, **noise):
@@ -24,14 +27,15 @@ class Simulator:
         g = {capi.QEC_GATES_CNOT: "cnot", capi.QEC_GATES_CR: "cr"}[self.params.gates]
         pr = {capi.QEC_C128: "c128", capi.QEC_C64: "c64", capi.QEC_C64_TC: "c64tc",
               capi.QEC_C128_TC: "c128tc"}[self.params.precision]
-        params = capi.make_params(self.d, rounds, g, pr, **noise)
+        params = capi.make_params(self.d, rounds, g, pr, code=self.code, **noise)
         capi.qec_reconfigure(self.h, params)
         self.params, self.rounds = params, int(rounds)
 
     def run(self, seed, first_traj, n):
-        """Host outputs: syndromes [n][rounds+1][d^2-1], data_bits [n][d^2], raw_logical [n] (uint8)."""
+        """Host outputs: syndromes [n][rounds+1][stabilizers], data_bits [n][data qubits], raw_logical [n]
+        (uint8)."""
         syn = np.zeros((n, self.rounds + 1, self.nstab), dtype=np.uint8)
-        bits = np.zeros((n, self.d * self.d), dtype=np.uint8)
+        bits = np.zeros((n, self.nd), dtype=np.uint8)
         log = np.zeros(n, dtype=np.uint8)
         capi.qec_run_trajectories(self.h, seed, first_traj, n, syn.ctypes.data, bits.ctypes.data, log.ctypes.data)
         return syn, bits, log

@@ -12,9 +12,13 @@ import numpy as np
 from paper_2204_11404_gb300 import capi
 
 
+def ndata(params):
+    """Data qubits of the code: d^2 (surface) or d (repetition)."""
+    return params.d if params.code == capi.QEC_CODE_REPETITION else params.d * params.d
+
+
 def blocks(params, seed, traj, rnd):
-    d = params.d
-    nst = d * d - 1
+    nst = ndata(params) - 1
     kr = np.zeros((nst, 2, 16, 16), dtype=np.complex128)
     u = np.zeros(nst, dtype=np.float64)
     capi.qec_debug_blocks(params, seed, traj, rnd, kr.ctypes.data, u.ctypes.data)
@@ -22,7 +26,7 @@ def blocks(params, seed, traj, rnd):
 
 
 def block_meta(params):
-    nst = params.d * params.d - 1
+    nst = ndata(params) - 1
     ops = np.zeros((4096, 6), dtype=np.int32)
     info = np.zeros((nst, 6), dtype=np.int32)
     capi.qec_debug_program(params, ops.ctypes.data, 4096, info.ctypes.data, nst)
@@ -41,8 +45,8 @@ def apply_block(psi, D, qs, K):
 
 
 def run(params, seed, traj):
-    d, R = params.d, params.rounds
-    D = d * d
+    R = params.rounds
+    D = ndata(params)
     nst = D - 1
     info = block_meta(params)
     psi = np.zeros(1 << D, dtype=np.complex128)

@@ -99,3 +99,32 @@ def test_error_between_two_z_gates_is_one_diagonal_edge(gates):
     dist, _ = dec._bfs(adj, B, 0 * dec.nz + k_late)
     assert dist[1 * dec.nz + k_early] == 1
     assert dec.logical_failure(r["syndromes"], r["data_bits"], r["raw_logical"]) == 0
+
+
+def test_repetition_code_corrects_up_to_four_flips_d9():
+    """Fig. 2's repetition code at d = 9: any (d-1)/2 = 4 X errors in one round are corrected; the
+    stabilizer list matches the oracle's line order."""
+    from oracle.lattice import code_stabilizers
+    d = 9
+    dec = Decoder(d, "repetition")
+    assert dec.zs == [s["support"] for s in code_stabilizers(d, "repetition")]
+    rng = np.random.default_rng(3)
+    for trial in range(6):
+        qs = sorted(rng.choice(d, size=1 + trial % 4, replace=False).tolist())
+        inject = [(1, 0, q, G.PX) for q in qs]
+        r = run_trajectory(d, 2, "cr", "reduced", {}, seed=0, traj=trial, inject=inject, code="repetition")
+        assert r["raw_logical"] == len(qs) % 2
+        assert dec.logical_failure(r["syndromes"], r["data_bits"], r["raw_logical"]) == 0
+    # five flips on a distance-9 line are a logical error after decoding
+    r = run_trajectory(d, 2, "cr", "reduced", {}, seed=0, traj=9, inject=[(1, 0, q, G.PX) for q in range(5)],
+                       code="repetition")
+    assert dec.logical_failure(r["syndromes"], r["data_bits"], r["raw_logical"]) == 1
+
+
+def test_repetition_code_measurement_error_is_a_time_pair():
+    d = 9
+    dec = Decoder(d, "repetition")
+    syn = np.zeros((4, d - 1), dtype=np.uint8)
+    syn[2, 3] = 1                      # one wrong outcome in round 2: events in layers 2 and 3
+    assert dec.logical_failure(syn, np.zeros(d, dtype=np.uint8), 0) == 0
+    assert len(dec.detection_events(syn, np.zeros(d, dtype=np.uint8))) == 2

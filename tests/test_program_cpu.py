@@ -87,3 +87,25 @@ def test_sign_follows_changes_the_blocks():
     with pytest.raises(capi.QecError):
         capi.qec_debug_program(capi.make_params(3, 3, "cr", overrot_follows=0.5),
                                np.zeros(8, dtype=np.int32).ctypes.data, 0, np.zeros(8, dtype=np.int32).ctypes.data, 0)
+
+
+@pytest.mark.parametrize("gates", ["cnot", "cr"])
+def test_host_blocks_match_oracle_repetition_code(gates):
+    """The one-dimensional repetition code of Fig. 2 (d = 9, Z_k Z_{k+1}), every noise term on."""
+    params = capi.make_params(9, 3, gates, code="repetition", **NOISY)
+    for traj in range(6):
+        syn, psi = kraus_run(params, 31, traj)
+        o = run_trajectory(9, 3, gates, "reduced", NOISY, seed=31, traj=traj, want_state=True, code="repetition")
+        assert (syn == o["syndromes"]).all()
+        assert np.abs(psi - o["state"][: 1 << 9]).max() < 1e-13
+
+
+def test_repetition_code_params_validated():
+    n = np.zeros(8, dtype=np.int32)
+    for d in (7, 10, 27):
+        with pytest.raises(capi.QecError):
+            capi.qec_debug_program(capi.make_params(d, 2, code="repetition"), n.ctypes.data, 0, n.ctypes.data, 0)
+    p = capi.make_params(9, 2)
+    p.code = 2
+    with pytest.raises(capi.QecError):
+        capi.qec_debug_program(p, n.ctypes.data, 0, n.ctypes.data, 0)

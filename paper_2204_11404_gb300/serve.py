@@ -58,7 +58,7 @@ class Job:
 
 def state_bytes(d, precision):
     """Device bytes of one slot: working state + resident init state."""
-    return 2 * (1 << (d * d)) * (16 if precision == "c128" else 8)
+    return 2 * (1 << (d * d)) * (16 if precision.startswith("c128") else 8)
 
 
 @dataclass
@@ -74,7 +74,11 @@ class Slot:
 
 
 class Server:
-    def __init__(self, mem_budget_bytes, device=0, max_heavy=2, heavy_d=5):
+    """fp64_on_tensor_cores: complex128 jobs with d >= 5 run on the tensor-core complex128 engine
+    ("c128tc": the same outcomes, amplitudes within a few FP64 roundings, about 5x faster); False
+    keeps them on the FP64 CUDA-core engine."""
+
+    def __init__(self, mem_budget_bytes, device=0, max_heavy=2, heavy_d=5, fp64_on_tensor_cores=True):
         import torch
 
         self.torch = torch
@@ -82,6 +86,7 @@ class Server:
         self.budget = int(mem_budget_bytes)
         self.max_heavy = int(max_heavy)
         self.heavy_d = int(heavy_d)
+        self.fp64_on_tensor_cores = bool(fp64_on_tensor_cores)
         lo, hi = torch.cuda.Stream.priority_range() if hasattr(torch.cuda.Stream, "priority_range") else (0, -1)
         self.prio_light = min(lo, hi)      # numerically lower = higher priority
         self.prio_heavy = max(lo, hi)
@@ -95,12 +100,19 @@ class Server:
         self.slots.remove(slot)
         self.used -= slot.nbytes
 
+    def engine(self, job):
+        """The simulator precision that serves a job's requested precision."""
+        if job.precision == "c128" and job.d >= 5 and self.fp64_on_tensor_cores:
+            return "c128tc"
+        return job.precision
+
     def _acquire(self, job):
-        key = (job.d, job.gates, job.precision)
+        eng = self.engine(job)
+        key = (job.d, job.gates, eng)
         for s in self.slots:
             if s.key == key and s.job is None:
                 return s
-        need = state_bytes(job.d, job.precision)
+        need = state_bytes(job.d, eng)
         if need > self.budget:
             raise ValueError("job %d needs %d bytes, more than the whole budget" % (job.jid, need))
         if self.used + need > self.budget:
@@ -118,7 +130,7 @@ class Server:
                 self._free_slot(s)
         light = job.d < self.heavy_d
         stream = self.torch.cuda.Stream(device=self.device, priority=self.prio_light if light else self.prio_heavy)
-        sim = Simulator(job.d, job.rounds, job.gates, job.precision, stream=stream.cuda_stream, **job.noise)
+        sim = Simulator(job.d, job.rounds, job.gates, eng, stream=stream.cuda_stream, **job.noise)
         slot = Slot(key, sim, stream, need)
         self.slots.append(slot)
         self.used += need

@@ -26,6 +26,10 @@ def test_continuous_batching_results_equal_solo_runs():
     jobs = [Job(**j) for j in trace]
     budget = 2 * state_bytes(5, "c64") + state_bytes(5, "c128") // 2 + 64 * 2**20   # forces waiting
     srv = Server(budget)
+    # complex128 at d=5 is served by the tensor-core complex128 engine; the solo runs below use the
+    # FP64 CUDA-core engine, so the equality checks cover the two engines against each other
+    assert [srv.engine(j) for j in jobs if j.d == 5 and j.precision == "c128"] == \
+        ["c128tc"] * sum(j.d == 5 and j.precision == "c128" for j in jobs)
     try:
         srv.run(jobs)
     finally:

@@ -309,6 +309,8 @@ def native_arm(args, rank, world, local):
                       "c64tc": "k_fused_tc (tcgen05 3xTF32: apply weight-4 block + next probability, 2^25 amplitudes)",
                       "c128tc": "k_oz<false> (apply pass on tcgen05: FP64-exact 8-bit-slice products, weight-4 block, 2^25 amplitudes)",
                       }[args.precision]
+    if args.code == "repetition":
+        roof["kernel"] = roof["kernel"].replace("weight-4 block", "weight-2 block Z_k Z_(k+1)")
     roof["ms_apply"] = ms_apply
     roof["ms_prob"] = ms_prob
     roof["apply_hbm_gbs"] = bytes_apply / (ms_apply * 1e-3) / 1e9

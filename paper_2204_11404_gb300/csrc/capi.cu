@@ -176,6 +176,15 @@ qec_status run_init_round(qec_sim* s) {
   return QEC_OK;   // no host wait: every later call is ordered after it on the same stream
 }
 
+// The instrumented block: the first weight-4 block of the middle noisy round, or its first block
+// when the code has none (the repetition code).
+int pick_timed_block(const qec_sim* s) {
+  const int rnd = (s->R + 1) / 2;
+  for (int k = 0; k < s->nstab; ++k)
+    if (s->prog.blocks[k].w == 4) return (rnd - 1) * s->nstab + k;
+  return (rnd - 1) * s->nstab;
+}
+
 PassArgs traj_pass(const qec_sim* s, int b) {
   const void* src = b == 0 ? s->psi0 : s->psi;
   const int rnd = 1 + b / s->nstab, k = b % s->nstab;
@@ -367,11 +376,7 @@ qec_status create_impl(const qec_params* params, void* stream, qec_sim** out) {
   s->R = s->p.rounds;
   s->S = s->nstab * s->R;
   s->amp = is_f64(s->p.precision) ? 16 : 8;
-  if (s->R > 0) {   // first weight-4 block of the middle noisy round
-    const int rnd = (s->R + 1) / 2;
-    for (int k = 0; k < s->nstab && s->timed_block < 0; ++k)
-      if (s->prog.blocks[k].w == 4) s->timed_block = (rnd - 1) * s->nstab + k;
-  }
+  if (s->R > 0) s->timed_block = pick_timed_block(s);
   cudaError_t e = cudaGetDevice(&s->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, s->device);
   int prio = 0;   // the work stream inherits the caller's stream priority
@@ -570,12 +575,7 @@ qec_status qec_reconfigure(qec_sim* s, const qec_params* params) {
   s->p = *params;
   s->R = params->rounds;
   s->S = S;
-  s->timed_block = -1;
-  if (s->R > 0) {
-    const int rnd = (s->R + 1) / 2;
-    for (int k = 0; k < s->nstab && s->timed_block < 0; ++k)
-      if (s->prog.blocks[k].w == 4) s->timed_block = (rnd - 1) * s->nstab + k;
-  }
+  s->timed_block = s->R > 0 ? pick_timed_block(s) : -1;
   s->ran = false;
   return QEC_OK;
 }

@@ -784,15 +784,16 @@ __global__ void __launch_bounds__(256, 2) k_fused_tc(FusedArgs f) {
 // in its own FP32 TMEM accumulator; the epilogue recombines the 7 diagonals in integers and rounds
 // once to FP64.  Two CTAs per SM (103 KiB of shared memory and 256 TMEM columns each) overlap one
 // tile's copies with the other's slicing, MMAs and recombination.
-constexpr uint32_t kIdescF16 = (1u << 4) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
+// FP16 inputs, FP32 accumulator, K-major A and B, M = 128, N = n
+__host__ __device__ constexpr uint32_t idesc_f16(uint32_t n) { return (1u << 4) | ((n >> 3) << 17) | ((128u >> 4) << 24); }
 constexpr int kOzTileBits = 11;
 constexpr int kOzSlab = 128 * 32;                    // fp16 elements per A slice
 constexpr int kOzSmem = 16 * (1 << kOzTileBits) + 2 * oz::kSlices * kOzSlab + 2 * oz::kSlices * 32 * 32 + 4 * 256 + 4 * 32;
 
-__device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t ad, uint64_t bd, uint32_t acc) {
+__device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
   asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
-               ::"r"(d_tmem), "l"(ad), "l"(bd), "r"(kIdescF16), "r"(acc));
+               ::"r"(d_tmem), "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
 }
 
 // Element offset of (row r, k) of a K = 32 16-bit operand: core matrix (r/8, k/8) of 64 elements.
@@ -985,16 +986,19 @@ __global__ void __launch_bounds__(256, 2) k_oz(FusedArgs f) {
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     tc_sync();
-    if (tid == 0) {   // 56 MMAs, descriptors as constant offsets from two bases (address field: bytes / 16)
+    if (tid == 0) {
+      // 14 MMAs.  The B slices are contiguous 32-row blocks with one row-group stride, so slices
+      // 0..6-p form a single N = 32(7-p) operand; written at TMEM column 32p, its product (p, q)
+      // lands in the columns of diagonal t = p + q.  Slice 0 (p = 0, first K step) initialises
+      // every diagonal; the rest accumulate.  Descriptors: constant offsets (address field:
+      // bytes / 16) from two bases.
       const uint64_t da = umma_desc(smem_u32(A), 128, 512), db = umma_desc(smem_u32(B), 128, 512);
 #pragma unroll
-      for (int t = 0; t < oz::kSlices; ++t)
+      for (int p = 0; p < oz::kSlices; ++p)
 #pragma unroll
-        for (int p = 0; p <= t; ++p)
-#pragma unroll
-          for (int ks = 0; ks < 2; ++ks)
-            umma_f16(tmem + 32u * t, da + ((2u * kOzSlab * p + 256u * ks) >> 4),
-                     db + ((2u * 32 * 32 * (t - p) + 256u * ks) >> 4), (p > 0 || ks > 0) ? 1u : 0u);
+        for (int ks = 0; ks < 2; ++ks)
+          umma_f16(tmem + 32u * p, da + ((2u * kOzSlab * p + 256u * ks) >> 4), db + ((256u * ks) >> 4),
+                   idesc_f16(32u * (oz::kSlices - p)), (p > 0 || ks > 0) ? 1u : 0u);
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mb) : "memory");
     }
     if (!mbar_wait(mb, phase & 1)) s_err = 1;

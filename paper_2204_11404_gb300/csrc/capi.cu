@@ -680,7 +680,17 @@ qec_status qec_debug_ozaki_gemm(const double* A, const double* B, int32_t m, int
         }
         continue;
       }
-      out[r * 32 + n] = variant ? oz::assemble7_cvt(D, ea[r], eb[n]) : oz::assemble7(D, ea[r], eb[n]);
+      if (variant == 1) {   // the apply pass's choice: checked only when the row may leave the range
+        int cmin = 4095, cmax = 0;
+        for (int j = 0; j < 32; ++j) {
+          if (eb[j]) cmin = std::min(cmin, eb[j]);
+          cmax = std::max(cmax, eb[j]);
+        }
+        const bool in_range = ea[r] == 0 || (ea[r] + cmin >= 1076 && ea[r] + cmax <= 2980);
+        out[r * 32 + n] = in_range ? oz::assemble7_cvt_inrange(D, ea[r], eb[n]) : oz::assemble7_cvt(D, ea[r], eb[n]);
+      } else {
+        out[r * 32 + n] = oz::assemble7(D, ea[r], eb[n]);
+      }
     }
     if (variant == 2) {
       out[r * 32] = A2;

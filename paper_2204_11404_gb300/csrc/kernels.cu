@@ -934,6 +934,13 @@ __global__ void __launch_bounds__(256, 2) k_oz(FusedArgs f) {
 #pragma unroll
   for (int l = 0; l < 8; ++l) goff[l] = t2g(offa[l]);
   const uint32_t tlane = (uint32_t)(32 * (warp & 3)) << 16;
+  int cmin = 4095, cmax = 0;   // exponents of this thread's 16 outputs' B rows (nonzero rows for cmin)
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    const int e = colE[16 * hf + j];
+    if (e) cmin = min(cmin, e);
+    cmax = max(cmax, e);
+  }
   const double2* src = reinterpret_cast<const double2*>(f.ap.src);
   double2* dst = reinterpret_cast<double2*>(f.ap.dst);
   const uint32_t ntile = 1u << f.nout;
@@ -1006,7 +1013,9 @@ __global__ void __launch_bounds__(256, 2) k_oz(FusedArgs f) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     __syncthreads();
     if (s_err) break;
-    // outputs 16hf..16hf+15 of row r: amplitudes 8hf..8hf+7
+    // outputs 16hf..16hf+15 of row r: amplitudes 8hf..8hf+7; in range: no output can leave the
+    // normal FP64 range, so the recombination skips its range checks
+    const bool in_range = E == 0 || (E + cmin >= 1076 && E + cmax <= 2980);
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
       uint32_t R[oz::kSlices][8];
@@ -1029,7 +1038,9 @@ __global__ void __launch_bounds__(256, 2) k_oz(FusedArgs f) {
           sq.add((uint64_t)(z0 < 0 ? -z0 : z0));
           sq.add((uint64_t)(z1 < 0 ? -z1 : z1));
         } else {
-          dst[tb | goff[4 * c + j / 2]] = make_double2(oz::assemble7_cvt(d0, E, colE[n]), oz::assemble7_cvt(d1, E, colE[n + 1]));
+          const double y0 = in_range ? oz::assemble7_cvt_inrange(d0, E, colE[n]) : oz::assemble7_cvt(d0, E, colE[n]);
+          const double y1 = in_range ? oz::assemble7_cvt_inrange(d1, E, colE[n + 1]) : oz::assemble7_cvt(d1, E, colE[n + 1]);
+          dst[tb | goff[4 * c + j / 2]] = make_double2(y0, y1);
         }
       }
     }

@@ -105,12 +105,14 @@ OZ_HD void split7(double x, int E, int* d) {
 // integers (|D_t| <= (t+1) * 32 * 255^2 < 2^24).  The sum is formed in 64-bit integers with its
 // lowest 10 bits truncated (|sum| < 2^70, so the truncation is below 2^-59 of the largest possible
 // sum) and rounded once to FP64 (nearest, ties away from zero).
-// Z = floor(sum_t D_t 2^(8(6-t)) / 2^10) in 64 bits (|Z| < 2^60).
+// Z = sum_t D_t 2^(8(6-t)) / 2^10 in 64 bits (|Z| < 2^60), the two lowest diagonals truncated
+// separately in 32 bits: floor(D_5 / 4) + floor(D_6 / 1024), within 2 units of the exact quotient.
 OZ_HD int64_t combine7(const float* D) {
-  int64_t d[kSlices];
-  for (int t = 0; t < kSlices; ++t) d[t] = (int64_t)(int32_t)D[t];
-  return d[0] * (1ll << 38) + d[1] * (1ll << 30) + d[2] * (1ll << 22) + d[3] * (1ll << 14) + d[4] * (1ll << 6) +
-         ((d[5] * 256 + d[6]) >> 10);
+  int32_t d[kSlices];
+  for (int t = 0; t < kSlices; ++t) d[t] = (int32_t)D[t];
+  const int32_t tail = (d[5] >> 2) + (d[6] >> 10);   // arithmetic shifts: floor division
+  return (int64_t)d[0] * (1ll << 38) + (int64_t)d[1] * (1ll << 30) + (int64_t)d[2] * (1ll << 22) +
+         (int64_t)d[3] * (1ll << 14) + (int64_t)d[4] * (1ll << 6) + (int64_t)tail;
 }
 
 OZ_HD double assemble7(const float* D, int Ea, int Eb) {
@@ -156,6 +158,13 @@ OZ_HD double assemble7_cvt(const float* D, int Ea, int Eb) {
   if (Ea == 0 || Eb == 0) return 0.0;
   const int64_t Z = combine7(D);
   return scale2((double)Z, Ea + Eb - 2098);          // one rounding (the conversion), exact scaling
+}
+
+// assemble7_cvt when the caller has checked that Z * 2^(Ea + Eb - 2098) stays in the normal range
+// for any Z with |Z| < 2^60 (Ea + Eb >= 1076 and Ea + Eb <= 2980) or that Eb = 0 gives Z = 0.
+OZ_HD double assemble7_cvt_inrange(const float* D, int Ea, int Eb) {
+  const int64_t Z = combine7(D);
+  return Z ? u2d(d2u((double)Z) + ((uint64_t)(int64_t)(Ea + Eb - 2098) << 52)) : 0.0;
 }
 
 // Exact sums of squares of up to 16 integers below 2^60 without FP64 work per term:

@@ -307,7 +307,7 @@ def native_arm(args, rank, world, local):
     roof["kernel"] = {"c128": "k_apply<double,4> (weight-4 block, 2^25 amplitudes)",
                       "c64": "k_fused<float,4,4> (apply weight-4 block + next block's probability, 2^25 amplitudes)",
                       "c64tc": "k_fused_tc (tcgen05 3xTF32: apply weight-4 block + next probability, 2^25 amplitudes)",
-                      "c128tc": "k_oz<false> (apply pass on tcgen05: FP64-exact 8-bit-slice products, weight-4 block, 2^25 amplitudes)",
+                      "c128tc": "k_oz<OZ_APPLY> (apply pass on tcgen05: FP64-exact 8-bit-slice products, weight-4 block, 2^25 amplitudes)",
                       }[args.precision]
     if args.code == "repetition":
         roof["kernel"] = roof["kernel"].replace("weight-4 block", "weight-2 block Z_k Z_(k+1)")

@@ -278,11 +278,25 @@ qec_status qec_debug_blocks(const qec_params* params, uint64_t seed, uint64_t tr
  * int64 -> FP64 conversion, ties to even (the apply pass); 2: the probability pass's sums,
  * with one exponent for all of B: out[r][0] = sum_n (A[r] . B[n])^2, out[r][1] =
  * sum_k A[r][k]^2 (each half-row's squares summed in integers, converted once), the rest
- * untouched.  Returns QEC_EINVAL for any other variant.  The paper has no counterpart
+ * untouched; 3: the bounded probability pass: out[r][0] = sum_n y^_n^2 from the top 3
+ * slices of each operand, out[r][1] = its error bound (|sum_n (A[r] . B[n])^2 - out[r][0]|
+ * <= out[r][1]).  Returns QEC_EINVAL for any other variant.  The paper has no counterpart
  * (an arithmetic form of the gate application of Sec. III).  Returns QEC_EINVAL on null
  * pointers or m <= 0.
  */
 qec_status qec_debug_ozaki_gemm(const double* A, const double* B, int32_t m, int32_t variant, double* out);
+
+/*
+ * Test hook for QEC_C128_TC (the paper has no counterpart: an evaluation order of Sec. II.B's
+ * measurement probability).  Its probability pass first computes A = |K_1 psi|^2 from the top
+ * 3 of the 7 slices of each operand together with a rigorous bound on the error, and N exactly;
+ * it decides the outcome on the device when |u N - A| exceeds twice the bound plus
+ * 1e-10 (A + N), where the exact pass must decide the same way, and otherwise runs the exact
+ * pass.  force = 1: every outcome goes through the exact pass; 0: the default; -1: unchanged.
+ * *fallbacks (may be NULL) receives the number of exact passes run on this handle so far.
+ * Waits for the handle's queued work.  QEC_EINVAL on a null handle or force outside -1..1.
+ */
+qec_status qec_debug_exact_probability(qec_sim* sim, int32_t force, uint64_t* fallbacks);
 
 #ifdef __cplusplus
 }

@@ -65,6 +65,7 @@ SIGNATURES = {
     "qec_debug_blocks": ([ctypes.POINTER(qec_params), ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int32, _P, _P],
                          ctypes.c_int),
     "qec_debug_ozaki_gemm": ([_P, _P, ctypes.c_int32, ctypes.c_int32, _P], ctypes.c_int),
+    "qec_debug_exact_probability": ([_P, ctypes.c_int32, _P], ctypes.c_int),
 }
 
 
@@ -202,6 +203,13 @@ def qec_debug_program(params, ops_ptr, cap, block_ptr, block_cap):
 
 def qec_debug_blocks(params, seed, traj, rnd, kraus_ptr, u_ptr):
     return check(lib().qec_debug_blocks(ctypes.byref(params), seed, traj, rnd, kraus_ptr, u_ptr))
+
+
+def qec_debug_exact_probability(sim, force):
+    """Set the exact-probability mode (1, 0, or -1 = unchanged); returns the exact passes run so far."""
+    c = ctypes.c_uint64(0)
+    check(lib().qec_debug_exact_probability(sim, force, ctypes.byref(c)))
+    return int(c.value)
 
 
 def qec_debug_ozaki_gemm(A_ptr, B_ptr, m, variant, out_ptr):

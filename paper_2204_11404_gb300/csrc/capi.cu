@@ -439,7 +439,7 @@ qec_status run_impl(qec_sim* s, uint64_t seed, uint64_t first, uint32_t n, uint8
     h->traj = first + done;
     h->ticket = 0;
     h->ev_cap = s->ev_cap;
-    const size_t head = done == 0 ? offsetof(Ctl, pad) : offsetof(Ctl, ticket);   // events reset per call
+    const size_t head = done == 0 ? offsetof(Ctl, prob_uncertain) : offsetof(Ctl, ticket);   // events reset per call
     if (done == 0) h->n_events = 0;
     QEC_CUDA(cudaMemcpyAsync(s->d_ctl, h, head, cudaMemcpyHostToDevice, s->work));
     QEC_CUDA(cudaEventRecord(s->ctl_ev[slot], s->work));
@@ -641,7 +641,7 @@ qec_status qec_debug_program(const qec_params* params, int32_t* ops, uint32_t ca
 }
 
 qec_status qec_debug_ozaki_gemm(const double* A, const double* B, int32_t m, int32_t variant, double* out) {
-  if (!A || !B || !out || m <= 0 || variant < 0 || variant > 2) return fail(QEC_EINVAL, "bad argument");
+  if (!A || !B || !out || m <= 0 || variant < 0 || variant > 3) return fail(QEC_EINVAL, "bad argument");
   std::vector<int> ea(m), eb(32);
   std::vector<int> da((size_t)m * 32 * oz::kSlices), db(32 * 32 * oz::kSlices);
   for (int r = 0; r < m; ++r) {
@@ -655,13 +655,34 @@ qec_status qec_debug_ozaki_gemm(const double* A, const double* B, int32_t m, int
   for (int n = 0; n < 32; ++n) {
     int E = 0;
     for (int k = 0; k < 32; ++k) E = std::max(E, oz::bexp(B[n * 32 + k]));
-    eb[n] = variant == 2 ? EB : E;
+    eb[n] = variant >= 2 ? EB : E;
     for (int k = 0; k < 32; ++k) oz::split7(B[n * 32 + k], eb[n], &db[((size_t)n * 32 + k) * oz::kSlices]);
   }
   for (int r = 0; r < m; ++r) {
-    oz::SqAcc sa, sn;   // variant 2: the two halves of a row, as two threads of the pass hold them
-    double A2 = 0.0, N2 = 0.0;
+    oz::SqAcc sa, sn;   // variants 2, 3: the two halves of a row, as two threads of the pass hold them
+    double A2 = 0.0, N2 = 0.0, E3 = 0.0;
     for (int n = 0; n < 32; ++n) {
+      if (variant == 3) {   // the bounded pass: 3 slices each, every product, diagonals 0..4
+        float D5[5];
+        for (int t = 0; t < 5; ++t) {
+          float acc = 0.f;
+          for (int p = 0; p < 3; ++p) {
+            const int q = t - p;
+            if (q < 0 || q > 2) continue;
+            for (int k = 0; k < 32; ++k)
+              acc += (float)(da[((size_t)r * 32 + k) * oz::kSlices + p] * db[((size_t)n * 32 + k) * oz::kSlices + q]);
+          }
+          D5[t] = acc;
+        }
+        const int64_t z = oz::combine5(D5);
+        sa.add((uint64_t)(z < 0 ? -z : z));
+        if ((n & 15) == 15) {
+          const double ah = (ea[r] && EB) ? sa.take(2 * (ea[r] + EB - 2092)) : sa.take(-4000);
+          A2 += ah;
+          if (ea[r] && EB) E3 += oz::half_row_bound(ah, ea[r] + EB);
+        }
+        continue;
+      }
       float D[oz::kSlices];
       for (int t = 0; t < oz::kSlices; ++t) {
         float acc = 0.f;   // exact: every partial sum is an integer below 2^24
@@ -696,6 +717,27 @@ qec_status qec_debug_ozaki_gemm(const double* A, const double* B, int32_t m, int
       out[r * 32] = A2;
       out[r * 32 + 1] = N2;
     }
+    if (variant == 3) {
+      out[r * 32] = A2;
+      out[r * 32 + 1] = E3;
+    }
+  }
+  return QEC_OK;
+}
+
+qec_status qec_debug_exact_probability(qec_sim* sim, int32_t force, uint64_t* fallbacks) {
+  if (!sim || force < -1 || force > 1) return fail(QEC_EINVAL, "bad argument");
+  QEC_CUDA(cudaStreamSynchronize(sim->work));
+  if (force >= 0) {
+    const unsigned int v = (unsigned int)force;
+    QEC_CUDA(cudaMemcpy(reinterpret_cast<char*>(sim->d_ctl) + offsetof(Ctl, prob_force_exact), &v, sizeof(v),
+                        cudaMemcpyHostToDevice));
+  }
+  if (fallbacks) {
+    unsigned long long c = 0;
+    QEC_CUDA(cudaMemcpy(&c, reinterpret_cast<char*>(sim->d_ctl) + offsetof(Ctl, prob_fallbacks), sizeof(c),
+                        cudaMemcpyDeviceToHost));
+    *fallbacks = c;
   }
   return QEC_OK;
 }

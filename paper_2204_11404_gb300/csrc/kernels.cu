@@ -237,6 +237,59 @@ __device__ void prob_finish(const PassArgs& a, double accA, double accN, double*
   }
 }
 
+// The bounded probability pass's end: block sums of (A^, N, bound) into 3 partials per CTA; the last
+// CTA sums them in a fixed order and decides the outcome only if |u N - A^| exceeds twice the bound
+// plus 1e-10 (A^ + N) (the exact pass's own rounding, with room), where the exact pass must decide
+// the same way; it then stores A^, N (bit-identical to the exact pass's N), m and the syndrome bit.
+// Otherwise (or with ctl->prob_force_exact) it sets ctl->prob_uncertain and stores nothing.
+__device__ void prob_finish_bounded(const PassArgs& a, double accA, double accN, double accE, double* sred,
+                                    int* s_last) {
+  double dummy = 0.0;
+  block_sum2(accA, accN, sred);
+  __syncthreads();
+  block_sum2(accE, dummy, sred);
+  if (threadIdx.x == 0) {
+    a.partials[3 * blockIdx.x] = accA;
+    a.partials[3 * blockIdx.x + 1] = accN;
+    a.partials[3 * blockIdx.x + 2] = accE;
+    __threadfence();
+    const unsigned int t = atomicAdd(&a.ctl->ticket, 1u);
+    *s_last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!*s_last) return;
+  __threadfence();
+  double sA = 0.0, sN = 0.0, sE = 0.0, d2 = 0.0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
+    sA += __ldcg(&a.partials[3 * i]);
+    sN += __ldcg(&a.partials[3 * i + 1]);
+    sE += __ldcg(&a.partials[3 * i + 2]);
+  }
+  block_sum2(sA, sN, sred);
+  __syncthreads();
+  block_sum2(sE, d2, sred);
+  if (threadIdx.x == 0) {
+    bool decided = true;
+    int m = a.forced;
+    if (m < 0) {
+      const double u = *a.u;
+      decided = !a.ctl->prob_force_exact && fabs(u * sN - sA) > 2.0 * sE + 1e-10 * (sA + sN);
+      m = u < sA / sN ? 1 : 0;
+    }
+    a.ctl->prob_uncertain = decided ? 0u : 1u;
+    if (decided) {
+      *a.A = sA;
+      *a.N = sN;
+      *a.m = m;
+      if (a.syn) {
+        const unsigned long long t = a.ctl->traj - a.ctl->first;
+        a.syn[t * (unsigned long long)a.syn_stride + a.syn_idx] = (uint8_t)(m ^ a.offset);
+      }
+    }
+    a.ctl->ticket = 0u;
+  }
+}
+
 template <typename T, int W>
 __global__ void __launch_bounds__(256) k_prob(PassArgs a) {
   using T2 = typename V2<T>::t;
@@ -775,6 +828,7 @@ __global__ void __launch_bounds__(256, 2) k_fused_tc(FusedArgs f) {
 }
 
 // ---- complex128 apply pass, FP64-exact on the FP16 tensor cores (Ozaki slices) -----------------
+enum OzMode { OZ_APPLY = 0, OZ_PROB = 1, OZ_PROB_BOUND = 2 };
 // A weight-4 block's 16x16 complex matrix (times 1/sqrt(N)) on the 128 groups of a 2048-amplitude
 // tile is a real product y = x . B^T (x: 128 x 32 reals, B: 32 x 32).  A weight-2 block's 4x4
 // matrix K runs as K (x) I on 16-amplitude groups made of its two qubits and two spectator qubits
@@ -833,8 +887,9 @@ __device__ __forceinline__ uint32_t digit_pair(uint64_t Xa, uint64_t Xb, uint32_
   return r;
 }
 
-// Writes the 7 FP16 slices of 8 consecutive reals x[0..7] (row `row`, k0 % 8 == 0) under exponent E;
-// X[0..7] receives their 56-bit magnitudes.
+// Writes the first NS FP16 slices of 8 consecutive reals x[0..7] (row `row`, k0 % 8 == 0) under
+// exponent E; X[0..7] receives their 56-bit magnitudes.
+template <int NS = oz::kSlices>
 __device__ __forceinline__ void put_slices8(uint16_t* S, int slab, int row, int k0, const double* x, int E,
                                             uint64_t (&X)[8]) {
   uint32_t sg[4], nsg[4];
@@ -848,6 +903,7 @@ __device__ __forceinline__ void put_slices8(uint16_t* S, int slab, int row, int 
   }
   uint16_t* base = S + core_off16(row, k0);
 #define QEC_OZ_SLICE(P)                                                                    \
+  if ((P) < NS)                                                                          \
   *reinterpret_cast<uint4*>(base + (P) * slab) =                                         \
       make_uint4(digit_pair<P>(X[0], X[1], sg[0], nsg[0]), digit_pair<P>(X[2], X[3], sg[1], nsg[1]), \
                  digit_pair<P>(X[4], X[5], sg[2], nsg[2]), digit_pair<P>(X[6], X[7], sg[3], nsg[3]));
@@ -855,11 +911,21 @@ __device__ __forceinline__ void put_slices8(uint16_t* S, int slab, int row, int 
 #undef QEC_OZ_SLICE
 }
 
-// PROB = false: psi <- K_m psi / sqrt(N) (apply pass).  PROB = true: A = sum |K_1 psi_g|^2 and
-// N = sum |psi|^2 over all groups, then the outcome (probability pass; K_1^dagger K_1 is the
-// projector-side operator M of the FP64 pass, so A is the same quantity).
-template <bool PROB>
+// MODE 0 (OZ_APPLY): psi <- K_m psi / sqrt(N).  MODE 1 (OZ_PROB): A = sum |K_1 psi_g|^2 and
+// N = sum |psi|^2 over all groups, then the outcome (K_1^dagger K_1 is the operator M of the FP64
+// pass, so A is the same quantity).  MODE 2 (OZ_PROB_BOUND): the same N exactly, A from the top 3
+// slices only with a rigorous bound on its error; the outcome is decided only where the bound
+// shows the exact pass would decide the same way, else the ctl flag calls the exact pass.
+// f.skip_unless_uncertain (MODE 1): return at once unless that flag is set.
+template <int MODE>
 __global__ void __launch_bounds__(256, 2) k_oz(FusedArgs f) {
+  constexpr bool PROB = MODE != OZ_APPLY;
+  constexpr int NS = MODE == OZ_PROB_BOUND ? 3 : oz::kSlices;       // slices of each operand
+  constexpr int ND = MODE == OZ_PROB_BOUND ? 2 * NS - 1 : oz::kSlices;   // diagonals accumulated
+  if (MODE == OZ_PROB && f.skip_unless_uncertain) {
+    if (*(volatile unsigned int*)&f.ap.ctl->prob_uncertain == 0u) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&f.ap.ctl->prob_fallbacks, 1ull);
+  }
   constexpr int TS = 1 << kOzTileBits;
   extern __shared__ __align__(128) unsigned char osm[];
   const uint32_t lmask = (1u << f.lb) - 1u;
@@ -894,7 +960,11 @@ __global__ void __launch_bounds__(256, 2) k_oz(FusedArgs f) {
     colE[n] = E;
     uint64_t Xb[8];
 #pragma unroll
-    for (int kc = 0; kc < 4; ++kc) put_slices8(B, 32 * 32, n, 8 * kc, b + 8 * kc, E, Xb);
+    for (int kc = 0; kc < 4; ++kc) put_slices8<NS>(B, 32 * 32, n, 8 * kc, b + 8 * kc, E, Xb);
+  }
+  if (MODE == OZ_PROB_BOUND) {   // B slices 3 and 4 = 0: the first MMA then clears diagonals 3 and 4 too
+    uint4* z = reinterpret_cast<uint4*>(B + NS * 32 * 32);
+    for (int i = tid; i < 2 * 32 * 32 / 8; i += 256) z[i] = make_uint4(0u, 0u, 0u, 0u);
   }
   if (tid == 0) {
     s_err = 0;
@@ -955,7 +1025,7 @@ __global__ void __launch_bounds__(256, 2) k_oz(FusedArgs f) {
     cp_async_commit();
   };
   uint32_t phase = 0;
-  double accA = 0.0, accN = 0.0;
+  double accA = 0.0, accN = 0.0, accE = 0.0;   // accE: error bound of accA (MODE 2)
   oz::SqAcc sq;   // probability pass: integer sums of squares, one FP64 conversion per tile and sum
   uint32_t tix = blockIdx.x;
   uint32_t tb = tix < ntile ? tile_base(tix) : 0u;
@@ -980,8 +1050,8 @@ __global__ void __launch_bounds__(256, 2) k_oz(FusedArgs f) {
     E = max(rowE[r], rowE[128 + r]);
     {
       uint64_t X0[8], X1[8];
-      put_slices8(A, kOzSlab, r, 16 * hf, x, E, X0);
-      put_slices8(A, kOzSlab, r, 16 * hf + 8, x + 8, E, X1);
+      put_slices8<NS>(A, kOzSlab, r, 16 * hf, x, E, X0);
+      put_slices8<NS>(A, kOzSlab, r, 16 * hf + 8, x + 8, E, X1);
       if (PROB) {   // N: sum of x^2 with x = X 2^(E - 1078)
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
@@ -1000,12 +1070,15 @@ __global__ void __launch_bounds__(256, 2) k_oz(FusedArgs f) {
       // every diagonal; the rest accumulate.  Descriptors: constant offsets (address field:
       // bytes / 16) from two bases.
       const uint64_t da = umma_desc(smem_u32(A), 128, 512), db = umma_desc(smem_u32(B), 128, 512);
+      // (MODE 2: 3 slices each side, every product, diagonals 0..4; slice 0 of A runs against
+      // B slices 0..4, the last two zero, so that it clears all five diagonals.)
 #pragma unroll
-      for (int p = 0; p < oz::kSlices; ++p)
+      for (int p = 0; p < NS; ++p)
 #pragma unroll
         for (int ks = 0; ks < 2; ++ks)
           umma_f16(tmem + 32u * p, da + ((2u * kOzSlab * p + 256u * ks) >> 4), db + ((256u * ks) >> 4),
-                   idesc_f16(32u * (oz::kSlices - p)), (p > 0 || ks > 0) ? 1u : 0u);
+                   idesc_f16(32u * (MODE == OZ_PROB_BOUND ? (p == 0 ? ND : NS) : oz::kSlices - p)),
+                   (p > 0 || ks > 0) ? 1u : 0u);
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mb) : "memory");
     }
     if (!mbar_wait(mb, phase & 1)) s_err = 1;
@@ -1018,22 +1091,26 @@ __global__ void __launch_bounds__(256, 2) k_oz(FusedArgs f) {
     const bool in_range = E == 0 || (E + cmin >= 1076 && E + cmax <= 2980);
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
-      uint32_t R[oz::kSlices][8];
+      uint32_t R[ND][8];
 #pragma unroll
-      for (int t = 0; t < oz::kSlices; ++t) tmem_ld8_nowait(tmem + tlane + 32u * t + 16u * hf + 8u * c, R[t]);
+      for (int t = 0; t < ND; ++t) tmem_ld8_nowait(tmem + tlane + 32u * t + 16u * hf + 8u * c, R[t]);
       tmem_wait_ld();
 #pragma unroll
-      for (int t = 0; t < oz::kSlices; ++t) reg_fence8(R[t]);
+      for (int t = 0; t < ND; ++t) reg_fence8(R[t]);
 #pragma unroll
       for (int j = 0; j < 8; j += 2) {
         float d0[oz::kSlices], d1[oz::kSlices];
 #pragma unroll
-        for (int t = 0; t < oz::kSlices; ++t) {
+        for (int t = 0; t < ND; ++t) {
           d0[t] = __uint_as_float(R[t][j]);
           d1[t] = __uint_as_float(R[t][j + 1]);
         }
         const int n = 16 * hf + 8 * c + j;
-        if (PROB) {   // A: sum of y^2 with y = Z 2^(E + E_B - 2098)
+        if (MODE == OZ_PROB_BOUND) {   // y^ = Z 2^(E + E_B - 2092), Z = sum_t D_t 2^(8(4-t)) exactly
+          const int64_t z0 = oz::combine5(d0), z1 = oz::combine5(d1);
+          sq.add((uint64_t)(z0 < 0 ? -z0 : z0));
+          sq.add((uint64_t)(z1 < 0 ? -z1 : z1));
+        } else if (PROB) {   // A: sum of y^2 with y = Z 2^(E + E_B - 2098)
           const int64_t z0 = oz::combine7(d0), z1 = oz::combine7(d1);
           sq.add((uint64_t)(z0 < 0 ? -z0 : z0));
           sq.add((uint64_t)(z1 < 0 ? -z1 : z1));
@@ -1044,7 +1121,13 @@ __global__ void __launch_bounds__(256, 2) k_oz(FusedArgs f) {
         }
       }
     }
-    if (PROB) accA += (E && colE[0]) ? sq.take(2 * (E + colE[0] - 2098)) : sq.take(-4000);
+    if (MODE == OZ_PROB_BOUND) {
+      const double ah = (E && colE[0]) ? sq.take(2 * (E + colE[0] - 2092)) : sq.take(-4000);
+      accA += ah;
+      if (E && colE[0]) accE += oz::half_row_bound(ah, E + colE[0]);
+    } else if (PROB) {
+      accA += (E && colE[0]) ? sq.take(2 * (E + colE[0] - 2098)) : sq.take(-4000);
+    }
     tc_sync();         // TMEM read out before the next tile's MMAs overwrite it
     tb = tbn;
   }
@@ -1052,7 +1135,8 @@ __global__ void __launch_bounds__(256, 2) k_oz(FusedArgs f) {
   tc_sync();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem));
   if (s_err && tid == 0) atomicOr(&f.ap.ctl->status, 1u);
-  if (PROB) prob_finish(f.ap, accA, accN, sred, &s_last);
+  if (MODE == OZ_PROB) prob_finish(f.ap, accA, accN, sred, &s_last);
+  if (MODE == OZ_PROB_BOUND) prob_finish_bounded(f.ap, accA, accN, accE, sred, &s_last);
 }
 
 // ---- final Z readout (Sec. III.B): sequential per-qubit sampling -------------------------
@@ -1392,10 +1476,11 @@ bool apply_oz_applies(const PassArgs& ap) {
   return f.nt == kOzTileBits;
 }
 
-static cudaError_t launch_oz(bool prob, const PassArgs& ap, int num_sms, cudaStream_t s) {
+static cudaError_t launch_oz(int mode, bool skip_unless_uncertain, const PassArgs& ap, int num_sms, cudaStream_t s) {
   FusedArgs f;
   f.ap = ap;
   f.pr = ap;
+  f.skip_unless_uncertain = skip_unless_uncertain ? 1 : 0;
   block_tile(ap, ap, 3, kOzTileBits, f);
   if ((ap.w != 2 && ap.w != 4) || f.nt != kOzTileBits) return cudaErrorInvalidValue;
   if (ap.w == 2) {   // spectators: the two lowest tile bits outside the block
@@ -1408,14 +1493,23 @@ static cudaError_t launch_oz(bool prob, const PassArgs& ap, int num_sms, cudaStr
   int64_t g = 2ll * num_sms;   // two CTAs per SM: 103 KiB of shared memory and 256 TMEM columns each
   if (g > (1ll << f.nout)) g = 1ll << f.nout;
   if (g > MAX_PASS_GRID) g = MAX_PASS_GRID;
+  if (mode == OZ_PROB_BOUND && 3 * g > 2 * MAX_PASS_GRID) g = 2 * MAX_PASS_GRID / 3;   // 3 partial sums per CTA
   f.grid = (int)g;
-  if (prob) k_oz<true><<<f.grid, 256, kOzSmem, s>>>(f);
-  else k_oz<false><<<f.grid, 256, kOzSmem, s>>>(f);
+  if (mode == OZ_APPLY) k_oz<OZ_APPLY><<<f.grid, 256, kOzSmem, s>>>(f);
+  else if (mode == OZ_PROB) k_oz<OZ_PROB><<<f.grid, 256, kOzSmem, s>>>(f);
+  else k_oz<OZ_PROB_BOUND><<<f.grid, 256, kOzSmem, s>>>(f);
   return cudaGetLastError();
 }
 
-cudaError_t launch_apply_oz(const PassArgs& ap, int num_sms, cudaStream_t s) { return launch_oz(false, ap, num_sms, s); }
-cudaError_t launch_prob_oz(const PassArgs& ap, int num_sms, cudaStream_t s) { return launch_oz(true, ap, num_sms, s); }
+cudaError_t launch_apply_oz(const PassArgs& ap, int num_sms, cudaStream_t s) {
+  return launch_oz(OZ_APPLY, false, ap, num_sms, s);
+}
+// The probability pass: the bounded 3-slice pass, then the exact pass, which returns at once
+// unless the bounded pass left the outcome undecided.
+cudaError_t launch_prob_oz(const PassArgs& ap, int num_sms, cudaStream_t s) {
+  cudaError_t e = launch_oz(OZ_PROB_BOUND, false, ap, num_sms, s);
+  return e != cudaSuccess ? e : launch_oz(OZ_PROB, true, ap, num_sms, s);
+}
 
 cudaError_t launch_wait_selftest(unsigned int* status, long limit, cudaStream_t s) {
   k_wait_selftest<<<1, 32, 0, s>>>(status, limit);
@@ -1438,10 +1532,13 @@ cudaError_t setup_kernels(int precision, int D) {
   if (is_f64(precision)) {
     cudaError_t e = cudaFuncSetAttribute(k_sample<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess) e = fused_attrs<double>();
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_oz<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kOzSmem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_oz<false>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_oz<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kOzSmem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_oz<true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    auto oz_attrs = [&](const void* fn) {
+      if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kOzSmem);
+      if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    };
+    oz_attrs((const void*)k_oz<OZ_APPLY>);
+    oz_attrs((const void*)k_oz<OZ_PROB>);
+    oz_attrs((const void*)k_oz<OZ_PROB_BOUND>);
     return e;
   }
   cudaError_t e = cudaFuncSetAttribute(k_sample<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);

@@ -17,10 +17,11 @@ struct Ctl {
   unsigned int ticket;          // last-CTA ticket of the reductions (always returned to 0)
   unsigned int n_events;
   unsigned int ev_cap;
-  unsigned int pad;
+  unsigned int prob_uncertain;  // the bounded probability pass left the outcome undecided
   double final_norm;            // sum |psi|^2 of the state the readout sampled
   unsigned int status;          // bit 0: a bounded device wait gave up (results invalid)
-  unsigned int pad2;
+  unsigned int prob_force_exact;        // test hook: the bounded pass never decides
+  unsigned long long prob_fallbacks;    // exact probability passes run after an undecided one
 };
 
 constexpr int KRAUS_STRIDE = 768;
@@ -77,6 +78,7 @@ struct FusedArgs {
                           // complex128 passes: a weight-2 block's two qubits, then two spectators)
   int qp[4];              // probability block's qubits as tile-index bits (ascending; the
                           // tensor-core complex128 passes: qa sorted)
+  int skip_unless_uncertain;   // exact tensor-core probability pass: run only if ctl->prob_uncertain
   int grid;
 };
 

@@ -167,6 +167,30 @@ OZ_HD double assemble7_cvt_inrange(const float* D, int Ea, int Eb) {
   return Z ? u2d(d2u((double)Z) + ((uint64_t)(int64_t)(Ea + Eb - 2098) << 52)) : 0.0;
 }
 
+// The bounded probability pass keeps 3 slices of each operand (the top 24 of the 56 bits) and every
+// product of them: Z = sum_{t<=4} D_t 2^(8(4-t)) exactly (|D_t| < 3 * 32 * 255^2 < 2^23, |Z| < 2^56),
+// and y^ = Z 2^(Ea + Eb - 2092).
+OZ_HD int64_t combine5(const float* D) {
+  return (int64_t)(int32_t)D[0] * (1ll << 32) + (int64_t)(int32_t)D[1] * (1ll << 24) +
+         (int64_t)(int32_t)D[2] * (1ll << 16) + (int64_t)(int32_t)D[3] * (1ll << 8) + (int64_t)(int32_t)D[4];
+}
+
+// Bound on |sum_n y_n^2 - y^_n^2| over 16 outputs of one row, given a = sum y^_n^2 and ee = Ea + Eb.
+// With x = 2^(Ea-1078)(X_hi + rho), b = 2^(Eb-1078)(Y_hi + sigma), X_hi, Y_hi < 2^56 and the dropped
+// parts |rho|, |sigma| < 2^32 + 1 (low 32 bits plus the truncation below the 56-bit integer), each
+// output over 32 terms is off by at most Delta = 2^(ee-2156) * 32 * (2 * 2^56 * 2^33 + 2^66)
+// < 2^(ee-2060); then sum |y^2 - y^^2| <= Delta * (2 * sum |y^| + 16 Delta) and sum |y^| <= 4 sqrt(a).
+// sqrt(a) is bounded above by a power of two with one octave of slack for the rounding of a.
+OZ_HD double half_row_bound(double a, int ee) {
+  const double delta = scale2(1.0, ee - 2060);
+  double root = 0.0;
+  if (a > 0.0) {
+    const int k = (int)((d2u(a) >> 52) & 0x7FF) - 1022 + 1;   // a < 2^(k-1), slack: 2^k
+    root = scale2(1.0, (k + 1) >> 1);                          // 2^ceil(k/2) >= sqrt(a)
+  }
+  return delta * (8.0 * root + 16.0 * delta);
+}
+
 // Exact sums of squares of up to 16 integers below 2^60 without FP64 work per term:
 // v = h 2^30 + l (h, l < 2^30), v^2 = h^2 2^60 + 2 h l 2^30 + l^2, the three partial sums each
 // below 16 * 2^60 = 2^64.  take() converts once (three roundings, relative error below 2^-51).

@@ -73,3 +73,26 @@ def test_emulated_fp64_form_on_d3_uses_fp64_passes():
         for x, y in zip(ra, rb):
             assert (x == y).all()
         assert np.array_equal(a.state(), b.state())
+
+
+def test_bounded_probability_pass_decides_like_the_exact_pass():
+    """c128tc decides most outcomes from a 3-slice probability with a rigorous error bound. Sending
+    every outcome through the exact pass instead changes no outcome and no amplitude bit (N is
+    computed by the same code in both passes), and the exact pass runs only when forced or when
+    the bound leaves the outcome open (rare)."""
+    from paper_2204_11404_gb300 import capi
+    pts = W.D5_CR["points"]
+    for i in (2, 8):
+        with Simulator(5, 3, "cr", "c128tc", **pts[i]) as a:
+            f0 = capi.qec_debug_exact_probability(a.h, 0)
+            ra = a.run(3000 + i, 0, 2)
+            sa = a.state()
+            f1 = capi.qec_debug_exact_probability(a.h, 1)
+            rb = a.run(3000 + i, 0, 2)
+            sb = a.state()
+            f2 = capi.qec_debug_exact_probability(a.h, 0)
+        for x, y in zip(ra, rb):
+            assert (x == y).all()
+        assert np.array_equal(sa, sb)
+        assert f2 - f1 == 2 * 3 * 24          # every noisy-round measurement, forced
+        assert f1 - f0 <= 2                   # unforced: the bound decided (almost) every outcome

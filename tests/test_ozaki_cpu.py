@@ -70,7 +70,7 @@ def test_zero_and_single_term_rows_are_exact(variant):
 def test_bad_variant_rejected():
     a = np.zeros((1, 32))
     with pytest.raises(capi.QecError):
-        capi.qec_debug_ozaki_gemm(a.ctypes.data, np.zeros((32, 32)).ctypes.data, 1, 3, a.ctypes.data)
+        capi.qec_debug_ozaki_gemm(a.ctypes.data, np.zeros((32, 32)).ctypes.data, 1, 4, a.ctypes.data)
 
 
 @pytest.mark.parametrize("seed", [0, 3])
@@ -98,3 +98,27 @@ def test_probability_sums_are_fp64_accurate(seed):
         assert ea <= Fraction(2.0 ** -42) * (Fraction(sa) * Fraction(sb)) ** 2 * 32 + a_ex * Fraction(2.0 ** -50) + tiny, (r, float(ea))
         en = abs(Fraction(out[r, 1]) - n_ex)
         assert en <= Fraction(2.0 ** -50) * n_ex + Fraction(2.0 ** -52) * Fraction(sa) ** 2 + tiny, (r, float(en))
+
+
+@pytest.mark.parametrize("seed", [0, 5, 9])
+def test_bounded_probability_sum_contains_the_exact_value(seed):
+    """Variant 3: A^ from 3 slices of each operand and its bound: |A_exact - A^| <= bound, with
+    the bound below 1e-3 of A for rows of ordinary scale (it is rigorous, so loose: about 1e-4)."""
+    rng = np.random.default_rng(seed)
+    m = 16
+    A = _rows(rng, m)
+    q, _ = np.linalg.qr(rng.standard_normal((16, 16)) + 1j * rng.standard_normal((16, 16)))
+    q[5] = 0.0
+    q[6] *= 1e-9                                   # a small output row beside ordinary ones
+    B = np.zeros((32, 32))
+    B[0::2, 0::2], B[0::2, 1::2] = q.real, -q.imag
+    B[1::2, 0::2], B[1::2, 1::2] = q.imag, q.real
+    out = np.zeros((m, 32))
+    capi.qec_debug_ozaki_gemm(A.ctypes.data, np.ascontiguousarray(B).ctypes.data, m, 3, out.ctypes.data)
+    ex = _exact(A, B)
+    for r in range(m):
+        a_ex = sum((v * v for v in ex[r]), Fraction(0))
+        err = abs(Fraction(out[r, 0]) - a_ex)
+        assert err <= Fraction(out[r, 1]) + Fraction(2.0 ** -1074), (r, float(err), out[r, 1])
+        if float(a_ex) > 1e-200:
+            assert out[r, 1] <= 1e-3 * float(a_ex), (r, out[r, 1], float(a_ex))

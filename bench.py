@@ -316,7 +316,9 @@ def native_arm(args, rank, world, local):
     roof["apply_hbm_gbs"] = bytes_apply / (ms_apply * 1e-3) / 1e9
     roof["prob_fp64_tflops"] = flops_prob / (ms_prob * 1e-3) / 1e12
 
-    launches_per_traj = 1 + 2 * nst * R + 3
+    # instantiate + per block (probability, apply) + readout; the tensor-core complex128 form adds the
+    # exact probability launch after each bounded one (it returns at once unless called for)
+    launches_per_traj = 1 + (3 if args.precision == "c128tc" else 2) * nst * R + 3
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,

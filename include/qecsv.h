@@ -50,8 +50,10 @@ typedef enum { QEC_GATES_CNOT = 0, QEC_GATES_CR = 1 } qec_gateset;
  * products on the FP16 tensor cores: each operand row split into 7 signed
  * 8-bit slices under one exponent, slice products accumulated exactly,
  * recombined in integers and rounded once (Ozaki scheme); sums of squares
- * in exact integers; init and readout in FP64.  Same outcomes and, to
- * within a few FP64 roundings, the same amplitudes as C128. */
+ * in exact integers; each outcome decided from a 3-slice probability with a
+ * rigorous error bound where the bound settles it, else by the exact pass
+ * (qec_debug_exact_probability); init and readout in FP64.  Same outcomes
+ * and, to within a few FP64 roundings, the same amplitudes as C128. */
 typedef enum { QEC_C128 = 0, QEC_C64 = 1, QEC_C64_TC = 2, QEC_C128_TC = 3 } qec_precision;
 
 /* Noise (Sec. III.A).  Probabilities in [0, 1]; angles in radians, |angle| <= 4. */

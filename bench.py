@@ -314,7 +314,10 @@ def native_arm(args, rank, world, local):
     roof["ms_apply"] = ms_apply
     roof["ms_prob"] = ms_prob
     roof["apply_hbm_gbs"] = bytes_apply / (ms_apply * 1e-3) / 1e9
-    roof["prob_fp64_tflops"] = flops_prob / (ms_prob * 1e-3) / 1e12
+    if args.precision == "c128":
+        roof["prob_fp64_tflops"] = flops_prob / (ms_prob * 1e-3) / 1e12
+    elif args.precision == "c128tc":   # the probability pass reads the state once
+        roof["prob_hbm_gbs"] = amps * 16 / (ms_prob * 1e-3) / 1e9
 
     # instantiate + per block (probability, apply) + readout; the tensor-core complex128 form adds the
     # exact probability launch after each bounded one (it returns at once unless called for)

@@ -991,15 +991,25 @@ __global__ void __launch_bounds__(256, 2) k_oz(FusedArgs f) {
   uint32_t offa[8];
 #pragma unroll
   for (int l = 0; l < 8; ++l) offa[l] = gbase + member_off<4>(8 * hf + l, qa);
+  // Tile slot of amplitude e in shared memory: the low 3 bits (the 16-byte bank slot) XOR a fold
+  // of the higher bits, so a warp's 32 group gathers spread over all 8 slots whichever tile bits
+  // the block occupies (a bijection: only the low bits change, and only as a function of the rest).
+  auto slot = [](uint32_t e) { return e ^ (((e >> 3) ^ (e >> 6) ^ (e >> 9)) & 7u); };
+  uint32_t rda[8];
+#pragma unroll
+  for (int l = 0; l < 8; ++l) rda[l] = slot(offa[l]);
   auto t2g = [&](uint32_t e) {   // tile index -> offset within the register (tile bits)
     const uint32_t h = e >> f.lb;
     uint32_t o = 0;
     for (int j = 0; j < f.nt - f.lb; ++j) o |= ((h >> j) & 1u) << f.hbits[j];
     return o | (e & lmask);
   };
-  uint32_t coff[TS / 256];   // this thread's amplitudes of a tile for the copies: e = tid + 256 i
+  uint32_t coff[TS / 256], cdst[TS / 256];   // this thread's copies: amplitude e = tid + 256 i, its slot
 #pragma unroll
-  for (int i = 0; i < TS / 256; ++i) coff[i] = t2g((uint32_t)tid + 256u * i);
+  for (int i = 0; i < TS / 256; ++i) {
+    coff[i] = t2g((uint32_t)tid + 256u * i);
+    cdst[i] = slot((uint32_t)tid + 256u * i);
+  }
   uint32_t goff[8];          // this thread's 8 outputs (apply): written straight to the register
 #pragma unroll
   for (int l = 0; l < 8; ++l) goff[l] = t2g(offa[l]);
@@ -1021,7 +1031,7 @@ __global__ void __launch_bounds__(256, 2) k_oz(FusedArgs f) {
   };
   auto load_tile = [&](uint32_t tb) {
 #pragma unroll
-    for (int i = 0; i < TS / 256; ++i) cp_async16(tile + tid + 256 * i, src + (tb | coff[i]));
+    for (int i = 0; i < TS / 256; ++i) cp_async16(tile + cdst[i], src + (tb | coff[i]));
     cp_async_commit();
   };
   uint32_t phase = 0;
@@ -1037,7 +1047,7 @@ __global__ void __launch_bounds__(256, 2) k_oz(FusedArgs f) {
     int E = 0;
 #pragma unroll
     for (int l = 0; l < 8; ++l) {
-      const double2 v = tile[offa[l]];
+      const double2 v = tile[rda[l]];
       x[2 * l] = v.x;
       x[2 * l + 1] = v.y;
       E = max(E, max(oz::bexp(v.x), oz::bexp(v.y)));

@@ -723,11 +723,16 @@ __global__ void __launch_bounds__(256, 2) k_fused_tc(FusedArgs f) {
     qa[j] = f.qa[j];
     qp[j] = f.qp[j];
   }
+  // Tile slot of float2 e in shared memory: bits 1..3 (the 8-byte bank pair within a 16-byte
+  // chunk's position) XOR a fold of the chunk index's higher bits, so group gathers spread over
+  // the banks whichever tile bits a block occupies; bit 0 is kept, so 16-byte chunks stay whole.
+  // The map is linear over XOR: slot(base + member) = slot(base) ^ slot(member) (disjoint bits).
+  auto slot = [](uint32_t e) { return e ^ ((((e >> 4) ^ (e >> 7) ^ (e >> 10)) & 7u) << 1); };
   uint32_t offa[C], offp[C];
 #pragma unroll
   for (int l = 0; l < C; ++l) {
-    offa[l] = member_off<4>(l, qa);
-    offp[l] = member_off<4>(l, qp);
+    offa[l] = slot(member_off<4>(l, qa));
+    offp[l] = slot(member_off<4>(l, qp));
   }
   // this thread's 16-byte chunks of a tile: chunk e = tid*2 + 512*i, i < 8; register offsets of their
   // high tile bits are the same for every tile
@@ -740,6 +745,11 @@ __global__ void __launch_bounds__(256, 2) k_fused_tc(FusedArgs f) {
     coff[i] = o | (e & lmask);
   }
   const int trow = 128 * (warp >> 2) + 32 * (warp & 3) + lane;
+  const uint32_t sba = slot(local_base<4>((uint32_t)tid, qa)), sbt = slot(local_base<4>((uint32_t)trow, qa));
+  const uint32_t sbp = slot(local_base<4>((uint32_t)tid, qp));
+  uint32_t cd[8];   // slots of this thread's 16-byte chunks
+#pragma unroll
+  for (int i = 0; i < 8; ++i) cd[i] = slot((uint32_t)tid * 2 + 512u * i);
   const uint32_t taddr = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + 32u * (warp >> 2);
   const float2* src = reinterpret_cast<const float2*>(f.ap.src);
   float2* dst = reinterpret_cast<float2*>(f.ap.dst);
@@ -754,7 +764,7 @@ __global__ void __launch_bounds__(256, 2) k_fused_tc(FusedArgs f) {
   auto load_tile = [&](uint32_t tix) {
     const uint32_t tb = tile_base(tix);
 #pragma unroll
-    for (int i = 0; i < 8; ++i) cp_async16(tile + tid * 2 + 512 * i, src + (tb | coff[i]));
+    for (int i = 0; i < 8; ++i) cp_async16(tile + cd[i], src + (tb | coff[i]));
     cp_async_commit();
   };
   if (blockIdx.x < ntile) load_tile(blockIdx.x);
@@ -762,11 +772,8 @@ __global__ void __launch_bounds__(256, 2) k_fused_tc(FusedArgs f) {
     const uint32_t tb = tile_base(tix);
     cp_async_wait<0>();
     __syncthreads();
-    {
-      const uint32_t b = local_base<4>((uint32_t)tid, qa);
 #pragma unroll
-      for (int l = 0; l < C; l += 2) put_a4(Ahi, Alo, tid, 2 * l, tile[b + offa[l]], tile[b + offa[l + 1]]);
-    }
+    for (int l = 0; l < C; l += 2) put_a4(Ahi, Alo, tid, 2 * l, tile[sba ^ offa[l]], tile[sba ^ offa[l + 1]]);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     tc_sync();
     if (tid == 0) issue_gemm(tmem, Ahi, Alo, Bahi, Balo, mb);
@@ -778,17 +785,15 @@ __global__ void __launch_bounds__(256, 2) k_fused_tc(FusedArgs f) {
     {
       float d[32];
       tmem_ld32(taddr, d);
-      const uint32_t b = local_base<4>((uint32_t)trow, qa);
 #pragma unroll
-      for (int r = 0; r < C; ++r) tile[b + offa[r]] = make_float2(d[2 * r], d[2 * r + 1]);
+      for (int r = 0; r < C; ++r) tile[sbt ^ offa[r]] = make_float2(d[2 * r], d[2 * r + 1]);
     }
     tc_sync();
     {
-      const uint32_t b = local_base<4>((uint32_t)tid, qp);
       float sn = 0.f;
 #pragma unroll
       for (int l = 0; l < C; l += 2) {
-        const float2 v0 = tile[b + offp[l]], v1 = tile[b + offp[l + 1]];
+        const float2 v0 = tile[sbp ^ offp[l]], v1 = tile[sbp ^ offp[l + 1]];
         sn = fmaf(v0.x, v0.x, fmaf(v0.y, v0.y, sn));
         sn = fmaf(v1.x, v1.x, fmaf(v1.y, v1.y, sn));
         put_a4(Ahi, Alo, tid, 2 * l, v0, v1);
@@ -802,7 +807,7 @@ __global__ void __launch_bounds__(256, 2) k_fused_tc(FusedArgs f) {
     // start loading the next one into the same buffer
 #pragma unroll
     for (int i = 0; i < 8; ++i)
-      *reinterpret_cast<float4*>(dst + (tb | coff[i])) = *reinterpret_cast<const float4*>(tile + tid * 2 + 512 * i);
+      *reinterpret_cast<float4*>(dst + (tb | coff[i])) = *reinterpret_cast<const float4*>(tile + cd[i]);
     __syncthreads();
     if (tix + gridDim.x < ntile) load_tile(tix + gridDim.x);
     if (!mbar_wait(mb, phase & 1)) s_err = 1;

@@ -107,9 +107,15 @@ OZ_HD void split7(double x, int E, int* d) {
 // sum) and rounded once to FP64 (nearest, ties away from zero).
 // Z = sum_t D_t 2^(8(6-t)) / 2^10 in 64 bits (|Z| < 2^60), the two lowest diagonals truncated
 // separately in 32 bits: floor(D_5 / 4) + floor(D_6 / 1024), within 2 units of the exact quotient.
+// Exact integer of a float holding an integer of magnitude below 2^22: in [2^23, 2^24) after adding
+// 1.5 * 2^23 the float's ulp is 1, so its bit pattern minus that of 1.5 * 2^23 is the integer.
+OZ_HD int32_t small_float_int(float v) { return (int32_t)(f2u(v + 12582912.0f) - 0x4B400000u); }
+
 OZ_HD int64_t combine7(const float* D) {
   int32_t d[kSlices];
-  for (int t = 0; t < kSlices; ++t) d[t] = (int32_t)D[t];
+  d[0] = small_float_int(D[0]);   // |D_0| <= 32 * 255^2 < 2^21
+  d[1] = small_float_int(D[1]);   // |D_1| <= 2 * 32 * 255^2 < 2^22
+  for (int t = 2; t < kSlices; ++t) d[t] = (int32_t)D[t];
   const int32_t tail = (d[5] >> 2) + (d[6] >> 10);   // arithmetic shifts: floor division
   return (int64_t)d[0] * (1ll << 38) + (int64_t)d[1] * (1ll << 30) + (int64_t)d[2] * (1ll << 22) +
          (int64_t)d[3] * (1ll << 14) + (int64_t)d[4] * (1ll << 6) + (int64_t)tail;
@@ -170,8 +176,8 @@ OZ_HD double assemble7_cvt_inrange(const float* D, int Ea, int Eb) {
 // The bounded probability pass keeps 3 slices of each operand (the top 24 of the 56 bits) and every
 // product of them: Z = sum_{t<=4} D_t 2^(8(4-t)) exactly (|D_t| < 3 * 32 * 255^2 < 2^23, |Z| < 2^56),
 // and y^ = Z 2^(Ea + Eb - 2092).
-OZ_HD int64_t combine5(const float* D) {
-  return (int64_t)(int32_t)D[0] * (1ll << 32) + (int64_t)(int32_t)D[1] * (1ll << 24) +
+OZ_HD int64_t combine5(const float* D) {   // D_0, D_1 below 2^22 as in combine7
+  return (int64_t)small_float_int(D[0]) * (1ll << 32) + (int64_t)small_float_int(D[1]) * (1ll << 24) +
          (int64_t)(int32_t)D[2] * (1ll << 16) + (int64_t)(int32_t)D[3] * (1ll << 8) + (int64_t)(int32_t)D[4];
 }
 

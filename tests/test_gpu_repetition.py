@@ -67,3 +67,18 @@ def test_d25_tensor_core_form_agrees_with_fp64_form():
         for x, y in zip(ra, rb):
             assert (x == y).all()
         assert np.abs(a.state() - b.state()).max() < 1e-13
+
+
+@pytest.mark.parametrize("d", [11, 13])
+def test_smallest_tensor_core_registers_agree_with_fp64_form(d):
+    """d = 11: the whole register is one 2^11-amplitude tile (a single CTA runs each pass, and the
+    bounded probability pass reduces one partial); d = 13: four tiles."""
+    pt = dict(W.STRESS)
+    with Simulator(d, 3, "cr", "c128tc", code="repetition", **pt) as a, \
+            Simulator(d, 3, "cr", "c128", code="repetition", **pt) as b:
+        ra, rb = a.run(79, 0, 6), b.run(79, 0, 6)
+        for x, y in zip(ra, rb):
+            assert (x == y).all()
+        assert np.abs(a.state() - b.state()).max() < 1e-13
+    o = _oracle(d, 3, "cr", pt, 79, 5)
+    assert compare_trajectory(ra[0][5], ra[1][5], o, TAU["c128tc"]) == "exact"

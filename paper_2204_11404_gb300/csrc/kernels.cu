@@ -832,17 +832,18 @@ __global__ void __launch_bounds__(256, 2) k_fused_tc(FusedArgs f) {
   prob_finish(f.pr, accA, accN, sred, &s_last);
 }
 
-// ---- complex128 apply pass, FP64-exact on the FP16 tensor cores (Ozaki slices) -----------------
+// ---- complex128 passes, FP64-exact on the FP16 tensor cores (Ozaki slices) ---------------------
 enum OzMode { OZ_APPLY = 0, OZ_PROB = 1, OZ_PROB_BOUND = 2 };
 // A weight-4 block's 16x16 complex matrix (times 1/sqrt(N)) on the 128 groups of a 2048-amplitude
 // tile is a real product y = x . B^T (x: 128 x 32 reals, B: 32 x 32).  A weight-2 block's 4x4
 // matrix K runs as K (x) I on 16-amplitude groups made of its two qubits and two spectator qubits
-// of the tile: the same product with a block-diagonal B.  Each row of x and of B is
-// split into 7 signed 8-bit slices under its own exponent (ozaki.cuh); the 28 slice products with
-// p + q <= 6 run as FP16 MMAs (M = 128, N = 32, K = 16) accumulating each diagonal p + q = t exactly
-// in its own FP32 TMEM accumulator; the epilogue recombines the 7 diagonals in integers and rounds
-// once to FP64.  Two CTAs per SM (103 KiB of shared memory and 256 TMEM columns each) overlap one
-// tile's copies with the other's slicing, MMAs and recombination.
+// of the tile: the same product with a block-diagonal B.  Each row of x and of B is split into 7
+// signed 8-bit slices under its own exponent (ozaki.cuh); the 28 slice products with p + q <= 6 run
+// as 14 FP16 MMAs (M = 128, K = 16, N = 32(7-p) for A slice p against the stacked B slices) that
+// accumulate each diagonal p + q = t exactly in its own FP32 TMEM columns; the epilogue recombines
+// the 7 diagonals in integers and rounds once to FP64.  Two CTAs per SM (103 KiB of shared memory
+// and 256 TMEM columns each) overlap one tile's copies with the other's slicing, MMAs and
+// recombination; the next tile's copy is issued as soon as the current one is sliced.
 // FP16 inputs, FP32 accumulator, K-major A and B, M = 128, N = n
 __host__ __device__ constexpr uint32_t idesc_f16(uint32_t n) { return (1u << 4) | ((n >> 3) << 17) | ((128u >> 4) << 24); }
 constexpr int kOzTileBits = 11;

@@ -495,7 +495,7 @@ def sweep_arm(args, rank, world, local):
     import torch
 
     from paper_2204_11404_gb300.decoder import Decoder
-    from paper_2204_11404_gb300.effective import fit_effective_model
+    from paper_2204_11404_gb300.effective import bootstrap_alpha, fit_effective_model
     from paper_2204_11404_gb300.simulator import Simulator
 
     torch.cuda.set_device(local)
@@ -529,8 +529,10 @@ def sweep_arm(args, rank, world, local):
     if len(cs) > 1:
         try:
             fit = fit_effective_model(rows)
+            sd, (lo, hi) = bootstrap_alpha(rows)
             out["effective_model"] = {"fit_range_p": [1e-3, 3e-3], "A": fit.A, "xi": fit.xi,
                                       "B": {str(c): b for c, b in fit.B.items()}, "alpha": fit.alpha,
+                                      "alpha_spread": sd, "alpha_16_84": [lo, hi],
                                       "paper": {"A": 6.5e5, "xi": 2.92, "alpha": 0.872}}
         except ValueError as e:
             out["effective_model"] = {"error": str(e)}

@@ -46,7 +46,8 @@ def fit_scale(A, xi, p, k, n):
     if not m.any():
         raise ValueError("no point with failures")
     lb = (np.log(k[m] / n[m]) - np.log(A)) / xi - np.log(p[m])
-    return float(np.exp(np.sum(k[m] * lb) / np.sum(k[m])))
+    with np.errstate(over="ignore"):
+        return float(np.exp(np.sum(k[m] * lb) / np.sum(k[m])))
 
 
 def fit_alpha(c, B):
@@ -69,3 +70,26 @@ def fit_effective_model(rows, p_range=(1.0e-3, 3.0e-3)):
         B[c] = fit_scale(A, xi, [r["p"] for r in pts], [r["failures"] for r in pts], [r["trajectories"] for r in pts])
     alpha = fit_alpha(list(B.keys()), list(B.values())) if B else float("nan")
     return EffectiveFit(A, xi, B, alpha)
+
+
+def bootstrap_alpha(rows, n=400, seed=0, p_range=(1.0e-3, 3.0e-3)):
+    """Statistical spread of alpha: the failure counts redrawn as binomial(trajectories, p_L) at the
+    measured rates, the whole fit repeated; returns (half the 16-84 percentile width, (16th, 84th
+    percentiles)).  Percentiles, not a standard deviation: with few failures at the lowest p some
+    resamples make the c = 0 power law nearly flat and B(c) huge.  Resamples where a fit is
+    undefined are skipped."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n):
+        rs = [dict(r, failures=int(rng.binomial(r["trajectories"], r["failures"] / r["trajectories"])))
+              for r in rows]
+        try:
+            a = fit_effective_model(rs, p_range).alpha
+        except (ValueError, np.linalg.LinAlgError):
+            continue
+        if np.isfinite(a):
+            out.append(a)
+    if len(out) < 2:
+        return float("nan"), (float("nan"), float("nan"))
+    lo, hi = float(np.percentile(out, 16)), float(np.percentile(out, 84))
+    return 0.5 * (hi - lo), (lo, hi)

@@ -2,7 +2,8 @@
 import numpy as np
 import pytest
 
-from paper_2204_11404_gb300.effective import fit_alpha, fit_effective_model, fit_power_law, fit_scale
+from paper_2204_11404_gb300.effective import (bootstrap_alpha, fit_alpha, fit_effective_model, fit_power_law,
+                                              fit_scale)
 
 # the paper's fitted values (Sec. III.C): A = 6.5e5, xi = 2.92, alpha = 0.872
 A0, XI0, ALPHA0 = 6.5e5, 2.92, 0.872
@@ -52,3 +53,12 @@ def test_power_law_slope_and_zero_count_points():
     assert fit_alpha([0.5, 1.0], [1.25, 2.0]) == pytest.approx(1.0)
     with pytest.raises(ValueError):
         fit_power_law([1e-3], [5], [100])
+
+
+def test_bootstrap_spread_shrinks_with_statistics():
+    """The spread of alpha from redrawn binomial counts falls like 1/sqrt(trajectories)."""
+    small, _ = bootstrap_alpha(_rows(n=2000), n=200, seed=1)
+    large, (lo, hi) = bootstrap_alpha(_rows(n=200000), n=200, seed=1)
+    assert 0 < large < small
+    assert 5 < small / large < 20                 # sqrt(100) = 10
+    assert lo < ALPHA0 < hi

@@ -659,7 +659,8 @@ qec_status qec_debug_ozaki_gemm(const double* A, const double* B, int32_t m, int
     for (int k = 0; k < 32; ++k) oz::split7(B[n * 32 + k], eb[n], &db[((size_t)n * 32 + k) * oz::kSlices]);
   }
   for (int r = 0; r < m; ++r) {
-    oz::SqAcc sa, sn;   // variants 2, 3: the two halves of a row, as two threads of the pass hold them
+    oz::SqAcc sa, sn;   // variants 2, 3: parts of kPart reals of a row, as the pass's threads hold them
+    oz::SqAccS ss;
     double A2 = 0.0, N2 = 0.0, E3 = 0.0;
     for (int n = 0; n < 32; ++n) {
       if (variant == 3) {   // the bounded pass: 3 slices each, every product, diagonals 0..4
@@ -674,12 +675,11 @@ qec_status qec_debug_ozaki_gemm(const double* A, const double* B, int32_t m, int
           }
           D5[t] = acc;
         }
-        const int64_t z = oz::combine5(D5);
-        sa.add((uint64_t)(z < 0 ? -z : z));
-        if ((n & 15) == 15) {
-          const double ah = (ea[r] && EB) ? sa.take(2 * (ea[r] + EB - 2092)) : sa.take(-4000);
+        ss.add(oz::combine5(D5));
+        if (n % oz::kPart == oz::kPart - 1) {
+          const double ah = (ea[r] && EB) ? ss.take(2 * (ea[r] + EB - 2092)) : ss.take(-4000);
           A2 += ah;
-          if (ea[r] && EB) E3 += oz::half_row_bound(ah, ea[r] + EB);
+          if (ea[r] && EB) E3 += oz::part_bound(ah, ea[r] + EB);
         }
         continue;
       }
@@ -695,7 +695,7 @@ qec_status qec_debug_ozaki_gemm(const double* A, const double* B, int32_t m, int
         const int64_t z = oz::combine7(D);
         sa.add((uint64_t)(z < 0 ? -z : z));
         sn.add(ea[r] ? oz::mag56(A[r * 32 + n], ea[r]) : 0ull);
-        if ((n & 15) == 15) {
+        if (n % oz::kPart == oz::kPart - 1) {
           A2 += (ea[r] && EB) ? sa.take(2 * (ea[r] + EB - 2098)) : sa.take(-4000);
           N2 += sn.take(2 * (ea[r] - 1078));
         }

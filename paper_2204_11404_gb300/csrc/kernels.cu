@@ -952,21 +952,29 @@ __global__ void __launch_bounds__(256, 2) k_oz(FusedArgs f) {
     const double scale = PROB ? 1.0 : 1.0 / sqrt(*f.ap.N);
     const double2* Kg = reinterpret_cast<const double2*>(f.ap.kraus) + (m ? 256 : 0);
     const bool w2 = f.ap.w == 2;
-    double b[32];
-    int E = 0;
-#pragma unroll
-    for (int l = 0; l < 16; ++l) {
+    auto entry = [&](int l, double& b0, double& b1) {   // reals 2l, 2l+1 of row n
       const double2 kv = !w2 ? Kg[r * 16 + l] : ((r >> 2) == (l >> 2) ? Kg[(r & 3) * 16 + (l & 3)] : make_double2(0.0, 0.0));
       const double re = kv.x * scale, im = kv.y * scale;
-      b[2 * l] = (n & 1) ? im : re;
-      b[2 * l + 1] = (n & 1) ? re : -im;
-      E = max(E, max(oz::bexp(b[2 * l]), oz::bexp(b[2 * l + 1])));
+      b0 = (n & 1) ? im : re;
+      b1 = (n & 1) ? re : -im;
+    };
+    int E = 0;
+#pragma unroll 4
+    for (int l = 0; l < 16; ++l) {
+      double b0, b1;
+      entry(l, b0, b1);
+      E = max(E, max(oz::bexp(b0), oz::bexp(b1)));
     }
     if (PROB) E = __reduce_max_sync(0xffffffffu, E);   // one exponent for all of K_1: the outputs share a scale
     colE[n] = E;
-    uint64_t Xb[8];
+#pragma unroll 1
+    for (int kc = 0; kc < 4; ++kc) {   // 8 reals at a time: few registers in this one-off prologue
+      double b[8];
+      uint64_t Xb[8];
 #pragma unroll
-    for (int kc = 0; kc < 4; ++kc) put_slices8<NS>(B, 32 * 32, n, 8 * kc, b + 8 * kc, E, Xb);
+      for (int l = 0; l < 4; ++l) entry(4 * kc + l, b[2 * l], b[2 * l + 1]);
+      put_slices8<NS>(B, 32 * 32, n, 8 * kc, b, E, Xb);
+    }
   }
   if (MODE == OZ_PROB_BOUND) {   // B slices 3 and 4 = 0: the first MMA then clears diagonals 3 and 4 too
     uint4* z = reinterpret_cast<uint4*>(B + NS * 32 * 32);
@@ -1042,7 +1050,8 @@ __global__ void __launch_bounds__(256, 2) k_oz(FusedArgs f) {
   };
   uint32_t phase = 0;
   double accA = 0.0, accN = 0.0, accE = 0.0;   // accE: error bound of accA (MODE 2)
-  oz::SqAcc sq;   // probability pass: integer sums of squares, one FP64 conversion per tile and sum
+  oz::SqAcc sq;    // probability pass: integer sums of squares, one FP64 conversion per tile and sum
+  oz::SqAccS sqs;  // the bounded pass's outputs: signed, squared without taking magnitudes
   uint32_t tix = blockIdx.x;
   uint32_t tb = tix < ntile ? tile_base(tix) : 0u;
   if (tix < ntile) load_tile(tb);
@@ -1123,9 +1132,8 @@ __global__ void __launch_bounds__(256, 2) k_oz(FusedArgs f) {
         }
         const int n = 16 * hf + 8 * c + j;
         if (MODE == OZ_PROB_BOUND) {   // y^ = Z 2^(E + E_B - 2092), Z = sum_t D_t 2^(8(4-t)) exactly
-          const int64_t z0 = oz::combine5(d0), z1 = oz::combine5(d1);
-          sq.add((uint64_t)(z0 < 0 ? -z0 : z0));
-          sq.add((uint64_t)(z1 < 0 ? -z1 : z1));
+          sqs.add(oz::combine5(d0));
+          sqs.add(oz::combine5(d1));
         } else if (PROB) {   // A: sum of y^2 with y = Z 2^(E + E_B - 2098)
           const int64_t z0 = oz::combine7(d0), z1 = oz::combine7(d1);
           sq.add((uint64_t)(z0 < 0 ? -z0 : z0));
@@ -1138,9 +1146,9 @@ __global__ void __launch_bounds__(256, 2) k_oz(FusedArgs f) {
       }
     }
     if (MODE == OZ_PROB_BOUND) {
-      const double ah = (E && colE[0]) ? sq.take(2 * (E + colE[0] - 2092)) : sq.take(-4000);
+      const double ah = (E && colE[0]) ? sqs.take(2 * (E + colE[0] - 2092)) : sqs.take(-4000);
       accA += ah;
-      if (E && colE[0]) accE += oz::half_row_bound(ah, E + colE[0]);
+      if (E && colE[0]) accE += oz::part_bound(ah, E + colE[0]);
     } else if (PROB) {
       accA += (E && colE[0]) ? sq.take(2 * (E + colE[0] - 2098)) : sq.take(-4000);
     }

@@ -11,6 +11,7 @@
 // 2^(Ea+Eb-2044-64) * sum_{t<=6} D_t 2^(8(6-t)) (terms with p+q > 6 are below 2^-56 of the
 // scales and dropped), recombined in integers and rounded once to FP64.
 #pragma once
+#include <math.h>
 #include <stdint.h>
 #include <string.h>
 
@@ -24,6 +25,7 @@ namespace qec {
 namespace oz {
 
 constexpr int kSlices = 7;
+constexpr int kPart = 16;   // reals (inputs) and outputs of one row that one thread of a pass holds
 
 OZ_HD uint64_t d2u(double x) {
 #if defined(__CUDA_ARCH__)
@@ -102,23 +104,33 @@ OZ_HD void split7(double x, int E, int* d) {
 }
 
 // Recombination: y = 2^(Ea + Eb - 2044 - 64) * sum_t D_t 2^(8(6-t)), D_t FP32 values holding exact
-// integers (|D_t| <= (t+1) * 32 * 255^2 < 2^24).  The sum is formed in 64-bit integers with its
-// lowest 10 bits truncated (|sum| < 2^70, so the truncation is below 2^-59 of the largest possible
-// sum) and rounded once to FP64 (nearest, ties away from zero).
-// Z = sum_t D_t 2^(8(6-t)) / 2^10 in 64 bits (|Z| < 2^60), the two lowest diagonals truncated
-// separately in 32 bits: floor(D_5 / 4) + floor(D_6 / 1024), within 2 units of the exact quotient.
+// integers (|D_t| <= (t+1) * 32 * 255^2 < 2^24), formed as Z = sum_t D_t 2^(8(6-t)) / 2^10 in 64-bit
+// integers (|Z| < 2^60) and rounded once to FP64.
 // Exact integer of a float holding an integer of magnitude below 2^22: in [2^23, 2^24) after adding
-// 1.5 * 2^23 the float's ulp is 1, so its bit pattern minus that of 1.5 * 2^23 is the integer.
+// 1.5 * 2^23 the float's ulp is 1, so its bit pattern minus that of 1.5 * 2^23 is the integer (and a
+// float below 2^22 that is not an integer is rounded to the nearest one).
 OZ_HD int32_t small_float_int(float v) { return (int32_t)(f2u(v + 12582912.0f) - 0x4B400000u); }
 
+OZ_HD float fma_f32(float a, float b, float c) {
+#if defined(__CUDA_ARCH__)
+  return __fmaf_rn(a, b, c);
+#else
+  return fmaf(a, b, c);
+#endif
+}
+
+// Z = H 2^30 + M 2^14 + L with three 32-bit pieces and two widening multiply-adds:
+//   H = D_0 2^8 + D_1             (|H| <= 256 * 2080800 + 4161600 < 2^29),
+//   M = D_2 2^8 + D_3             (|M| <= 256 * 6242400 + 8323200 < 2^31),
+//   L = D_4 2^6 + round(D_5 / 4 + D_6 / 1024)   (|L| < 2^30).
+// D_0 and D_1 are below 2^22 and converted by the magic number.  The two lowest diagonals' share
+// D_5 / 4 + D_6 / 1024 (below 2^22) is formed in FP32 with one rounding (error below 1/8) and
+// rounded to an integer: within 1 unit of the exact quotient.
 OZ_HD int64_t combine7(const float* D) {
-  int32_t d[kSlices];
-  d[0] = small_float_int(D[0]);   // |D_0| <= 32 * 255^2 < 2^21
-  d[1] = small_float_int(D[1]);   // |D_1| <= 2 * 32 * 255^2 < 2^22
-  for (int t = 2; t < kSlices; ++t) d[t] = (int32_t)D[t];
-  const int32_t tail = (d[5] >> 2) + (d[6] >> 10);   // arithmetic shifts: floor division
-  return (int64_t)d[0] * (1ll << 38) + (int64_t)d[1] * (1ll << 30) + (int64_t)d[2] * (1ll << 22) +
-         (int64_t)d[3] * (1ll << 14) + (int64_t)d[4] * (1ll << 6) + (int64_t)tail;
+  const int32_t H = small_float_int(D[0]) * 256 + small_float_int(D[1]);
+  const int32_t M = (int32_t)D[2] * 256 + (int32_t)D[3];
+  const int32_t L = (int32_t)D[4] * 64 + small_float_int(fma_f32(D[6], 0x1p-10f, D[5] * 0.25f));
+  return (int64_t)H * (1 << 30) + ((int64_t)M * (1 << 14) + (int64_t)L);
 }
 
 OZ_HD double assemble7(const float* D, int Ea, int Eb) {
@@ -155,7 +167,7 @@ OZ_HD double assemble7(const float* D, int Ea, int Eb) {
 OZ_HD double scale2(double v, int s) {
   const uint64_t u = d2u(v);
   const int be = (int)((u >> 52) & 0x7FF) + s;
-  if (v == 0.0 || be <= 0) return 0.0;
+  if ((u << 1) == 0 || be <= 0) return 0.0;   // zero test on the bits: no FP64 comparison
   if (be >= 2047) return u2d((u & 0x8000000000000000ull) | 0x7FF0000000000000ull);
   return u2d(u + ((uint64_t)(int64_t)s << 52));
 }
@@ -174,32 +186,72 @@ OZ_HD double assemble7_cvt_inrange(const float* D, int Ea, int Eb) {
 }
 
 // The bounded probability pass keeps 3 slices of each operand (the top 24 of the 56 bits) and every
-// product of them: Z = sum_{t<=4} D_t 2^(8(4-t)) exactly (|D_t| < 3 * 32 * 255^2 < 2^23, |Z| < 2^56),
-// and y^ = Z 2^(Ea + Eb - 2092).
-OZ_HD int64_t combine5(const float* D) {   // D_0, D_1 below 2^22 as in combine7
-  return (int64_t)small_float_int(D[0]) * (1ll << 32) + (int64_t)small_float_int(D[1]) * (1ll << 24) +
-         (int64_t)(int32_t)D[2] * (1ll << 16) + (int64_t)(int32_t)D[3] * (1ll << 8) + (int64_t)(int32_t)D[4];
+// product of them: Z = sum_{t<=4} D_t 2^(8(4-t)) exactly, y^ = Z 2^(Ea + Eb - 2092).  Diagonal t holds
+// 1, 2, 3, 2, 1 slice products, so D_0, D_1, D_3 and D_4 are below 2^22 (magic-number conversion)
+// and D_2 below 3 * 2^21: Z = H 2^24 + M 2^8 + D_4 with H = D_0 2^8 + D_1 (< 2^29) and
+// M = D_2 2^8 + D_3 (< 2^31), |Z| < 2^54.
+OZ_HD int64_t combine5(const float* D) {
+  const int32_t H = small_float_int(D[0]) * 256 + small_float_int(D[1]);
+  const int32_t M = (int32_t)D[2] * 256 + small_float_int(D[3]);
+  return (int64_t)H * (1 << 24) + ((int64_t)M * 256 + (int64_t)small_float_int(D[4]));
 }
 
-// Bound on |sum_n y_n^2 - y^_n^2| over 16 outputs of one row, given a = sum y^_n^2 and ee = Ea + Eb.
-// With x = 2^(Ea-1078)(X_hi + rho), b = 2^(Eb-1078)(Y_hi + sigma), X_hi, Y_hi < 2^56 and the dropped
-// parts |rho|, |sigma| < 2^32 + 1 (low 32 bits plus the truncation below the 56-bit integer), each
-// output over 32 terms is off by at most Delta = 2^(ee-2156) * 32 * (2 * 2^56 * 2^33 + 2^66)
-// < 2^(ee-2060); then sum |y^2 - y^^2| <= Delta * (2 * sum |y^| + 16 Delta) and sum |y^| <= 4 sqrt(a).
-// sqrt(a) is bounded above by a power of two with one octave of slack for the rounding of a.
-OZ_HD double half_row_bound(double a, int ee) {
-  const double delta = scale2(1.0, ee - 2060);
-  double root = 0.0;
-  if (a > 0.0) {
-    const int k = (int)((d2u(a) >> 52) & 0x7FF) - 1022 + 1;   // a < 2^(k-1), slack: 2^k
-    root = scale2(1.0, (k + 1) >> 1);                          // 2^ceil(k/2) >= sqrt(a)
+// 2^e1 + 2^e2 rounded up to an FP64 value, built in the exponent and mantissa fields (no FP64
+// arithmetic); at least the smallest normal number, infinity above the range.
+OZ_HD double pow2_sum_up(int e1, int e2) {
+  const int hi = e1 > e2 ? e1 : e2, lo = e1 > e2 ? e2 : e1;
+  int be = hi + 1023;
+  uint64_t mant = 1;                                  // the smaller term below one unit: round up
+  if (hi == lo) {
+    be += 1;
+    mant = 0;
+  } else if (hi - lo <= 52) {
+    mant = 1ull << (52 - (hi - lo));
   }
-  return delta * (8.0 * root + 16.0 * delta);
+  if (be < 1) return u2d(1ull << 52);
+  if (be > 2046) return u2d(0x7FF0000000000000ull);
+  return u2d(((uint64_t)be << 52) | mant);
 }
 
-// Exact sums of squares of up to 16 integers below 2^60 without FP64 work per term:
+// Bound on |sum_n y_n^2 - y^_n^2| over at most kPart outputs of one row, given a = sum y^_n^2 over
+// them and ee = Ea + Eb.  With x = 2^(Ea-1078)(X_hi + rho), b = 2^(Eb-1078)(Y_hi + sigma), X_hi,
+// Y_hi < 2^56 and the dropped parts |rho|, |sigma| < 2^32 + 1 (low 32 bits plus the truncation below
+// the 56-bit integer), each output over 32 terms is off by at most
+// Delta = 2^(ee-2156) * 32 * (2 * 2^56 * 2^33 + 2^66) < 2^(ee-2060); then
+// sum |y^2 - y^^2| <= Delta * (2 * sum |y^| + kPart Delta) and 2 sum |y^| <= 2 sqrt(kPart a) = 8 sqrt(a)
+// (Cauchy-Schwarz).  a < 2^(be-1022) for a's biased exponent be, and a is the correctly rounded
+// value of the exact sum, which is then below 2^(be-1022) too, so sqrt(a) <= 2^ceil((be-1022)/2).
+// Both terms are powers of two; their sum is returned, rounded up.
+OZ_HD double part_bound(double a, int ee) {
+  static_assert(kPart == 16, "the bound's constants are those of 16 outputs");
+  const int d = ee - 2060;                            // Delta = 2^d
+  const uint64_t ua = d2u(a);
+  const int e1 = ua ? d + 3 + (((int)((ua >> 52) & 0x7FF) - 1021) >> 1) : -100000;   // 8 Delta sqrt(a)
+  return pow2_sum_up(e1, 2 * d + 4);                  // + kPart Delta^2
+}
+
+OZ_HD int clz64(uint64_t v) {
+#if defined(__CUDA_ARCH__)
+  return __clzll((long long)v);
+#else
+  return v ? __builtin_clzll(v) : 64;
+#endif
+}
+
+// (hi 2^64 + lo) * 2^s as FP64 for a 128-bit value below 2^126: normalised to 64 significant bits
+// with a sticky bit for the bits below them, so that the one int -> FP64 conversion rounds it
+// correctly (to nearest); 2^s is applied to the exponent field.
+OZ_HD double u128_to_double(uint64_t hi, uint64_t lo, int s) {
+  if (hi == 0) return scale2((double)lo, s);
+  const int lz = clz64(hi);
+  const uint64_t top = lz ? (hi << lz) | (lo >> (64 - lz)) : hi;
+  return scale2((double)(top | ((lo << lz) != 0 ? 1u : 0u)), s + 64 - lz);
+}
+
+// Exact sums of squares of up to kPart integers below 2^60 without FP64 work per term:
 // v = h 2^30 + l (h, l < 2^30), v^2 = h^2 2^60 + 2 h l 2^30 + l^2, the three partial sums each
-// below 16 * 2^60 = 2^64.  take() converts once (three roundings, relative error below 2^-51).
+// below 16 * 2^60 = 2^64.  take() adds them exactly in 128 bits and converts once: one rounding
+// (to nearest), relative error at most 2^-53.
 struct SqAcc {
   uint64_t hh = 0, hl = 0, ll = 0;
   OZ_HD void add(uint64_t v) {
@@ -208,11 +260,41 @@ struct SqAcc {
     hl += h * l;
     ll += l * l;
   }
-  // sum * 2^s as FP64 (scaled exactly), then the accumulators restart
+  // sum * 2^s as FP64, then the accumulators restart
   OZ_HD double take(int s) {
-    const double v = (double)hh * 0x1p60 + ((double)hl * 0x1p31 + (double)ll);
+    uint64_t lo = hh << 60, hi = hh >> 4;
+    const uint64_t m = hl << 31;
+    lo += m;
+    hi += (hl >> 33) + (lo < m ? 1u : 0u);
+    lo += ll;
+    hi += lo < ll ? 1u : 0u;
     hh = hl = ll = 0;
-    return scale2(v, s);
+    return u128_to_double(hi, lo, s);
+  }
+};
+
+// The same for signed integers below 2^56 in magnitude, without taking magnitudes:
+// z = h 2^30 + l with h = floor(z / 2^30) (|h| < 2^26) and 0 <= l < 2^30, so
+// z^2 = h^2 2^60 + 2 h l 2^30 + l^2 with a signed middle sum below 16 * 2^56 in magnitude.
+struct SqAccS {
+  uint64_t hh = 0, ll = 0;
+  int64_t hl = 0;
+  OZ_HD void add(int64_t z) {
+    const int64_t h = z >> 30, l = z & 0x3FFFFFFFll;   // arithmetic shift: floor
+    hh += (uint64_t)(h * h);
+    hl += h * l;
+    ll += (uint64_t)(l * l);
+  }
+  OZ_HD double take(int s) {   // the sum is a sum of squares: its 128-bit value is not negative
+    uint64_t lo = hh << 60, hi = hh >> 4;
+    const uint64_t m = (uint64_t)hl << 31;
+    lo += m;
+    hi += (uint64_t)(hl >> 33) + (lo < m ? 1u : 0u);
+    lo += ll;
+    hi += lo < ll ? 1u : 0u;
+    hh = ll = 0;
+    hl = 0;
+    return u128_to_double(hi, lo, s);
   }
 };
 

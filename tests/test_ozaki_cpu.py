@@ -67,6 +67,34 @@ def test_zero_and_single_term_rows_are_exact(variant):
     assert out[1, 5] == A[1, 5] and np.count_nonzero(out[1]) == 1
 
 
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+def test_largest_digits_recombine_exactly(variant):
+    """Every 8-bit digit at 255 (mantissas of all ones, one exponent per row) drives each diagonal to
+    its largest value, (t + 1) * 32 * 255^2: the 32-bit pieces of the recombination must not overflow.
+    Signs are mixed so that the diagonals reach both extremes."""
+    big = 2.0 - 2.0 ** -52                                  # 53 one-bits
+    sgn = np.where(np.arange(32) % 3 == 0, -1.0, 1.0)
+    A = np.stack([np.full(32, big), -np.full(32, big), big * sgn, big * sgn[::-1]])
+    B = np.stack([np.full(32, big) if n % 2 == 0 else big * sgn for n in range(32)])
+    m = A.shape[0]
+    out = np.zeros((m, 32))
+    capi.qec_debug_ozaki_gemm(A.ctypes.data, np.ascontiguousarray(B).ctypes.data, m, variant, out.ctypes.data)
+    ex = _exact(A, B)
+    if variant in (0, 1):
+        for r in range(m):
+            for n in range(32):
+                e = abs(Fraction(float(out[r, n])) - ex[r, n])
+                assert e <= Fraction(2.0 ** -44) * Fraction(big) ** 2 + abs(ex[r, n]) * Fraction(2.0 ** -53), (r, n)
+    else:
+        for r in range(m):
+            a_ex = sum((v * v for v in ex[r]), Fraction(0))
+            err = abs(Fraction(out[r, 0]) - a_ex)
+            if variant == 2:
+                assert err <= Fraction(2.0 ** -42) * Fraction(big) ** 4 * 32 + a_ex * Fraction(2.0 ** -50), r
+            else:
+                assert err <= Fraction(out[r, 1]), (r, float(err), out[r, 1])
+
+
 def test_bad_variant_rejected():
     a = np.zeros((1, 32))
     with pytest.raises(capi.QecError):

@@ -945,54 +945,9 @@ __global__ void __launch_bounds__(256, 2) k_oz(FusedArgs f) {
   __shared__ int s_err;
   __shared__ double sred[64];
   __shared__ int s_last;
+  __shared__ int s_eb[4];
+  __shared__ uint32_t s_next;   // the tile this CTA takes after the current one
   const int tid = threadIdx.x, warp = tid >> 5;
-  if (tid < 32) {   // B: real embedding of K_m / sqrt(N) (apply) or K_1 (probability), sliced
-    const int n = tid, r = n >> 1;
-    const int m = PROB ? 1 : *f.ap.m;
-    const double scale = PROB ? 1.0 : 1.0 / sqrt(*f.ap.N);
-    const double2* Kg = reinterpret_cast<const double2*>(f.ap.kraus) + (m ? 256 : 0);
-    const bool w2 = f.ap.w == 2;
-    auto entry = [&](int l, double& b0, double& b1) {   // reals 2l, 2l+1 of row n
-      const double2 kv = !w2 ? Kg[r * 16 + l] : ((r >> 2) == (l >> 2) ? Kg[(r & 3) * 16 + (l & 3)] : make_double2(0.0, 0.0));
-      const double re = kv.x * scale, im = kv.y * scale;
-      b0 = (n & 1) ? im : re;
-      b1 = (n & 1) ? re : -im;
-    };
-    int E = 0;
-#pragma unroll 4
-    for (int l = 0; l < 16; ++l) {
-      double b0, b1;
-      entry(l, b0, b1);
-      E = max(E, max(oz::bexp(b0), oz::bexp(b1)));
-    }
-    if (PROB) E = __reduce_max_sync(0xffffffffu, E);   // one exponent for all of K_1: the outputs share a scale
-    colE[n] = E;
-#pragma unroll 1
-    for (int kc = 0; kc < 4; ++kc) {   // 8 reals at a time: few registers in this one-off prologue
-      double b[8];
-      uint64_t Xb[8];
-#pragma unroll
-      for (int l = 0; l < 4; ++l) entry(4 * kc + l, b[2 * l], b[2 * l + 1]);
-      put_slices8<NS>(B, 32 * 32, n, 8 * kc, b, E, Xb);
-    }
-  }
-  if (MODE == OZ_PROB_BOUND) {   // B slices 3 and 4 = 0: the first MMA then clears diagonals 3 and 4 too
-    uint4* z = reinterpret_cast<uint4*>(B + NS * 32 * 32);
-    for (int i = tid; i < 2 * 32 * 32 / 8; i += 256) z[i] = make_uint4(0u, 0u, 0u, 0u);
-  }
-  if (tid == 0) {
-    s_err = 0;
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(smem_u32(&tmem_base)));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-  }
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  tc_sync();
-  const uint32_t tmem = tmem_base;
-  const uint32_t mb = smem_u32(&mbar);
   int qa[4], qs[4];
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
@@ -1024,17 +979,6 @@ __global__ void __launch_bounds__(256, 2) k_oz(FusedArgs f) {
     coff[i] = t2g((uint32_t)tid + 256u * i);
     cdst[i] = slot((uint32_t)tid + 256u * i);
   }
-  uint32_t goff[8];          // this thread's 8 outputs (apply): written straight to the register
-#pragma unroll
-  for (int l = 0; l < 8; ++l) goff[l] = t2g(offa[l]);
-  const uint32_t tlane = (uint32_t)(32 * (warp & 3)) << 16;
-  int cmin = 4095, cmax = 0;   // exponents of this thread's 16 outputs' B rows (nonzero rows for cmin)
-#pragma unroll
-  for (int j = 0; j < 16; ++j) {
-    const int e = colE[16 * hf + j];
-    if (e) cmin = min(cmin, e);
-    cmax = max(cmax, e);
-  }
   const double2* src = reinterpret_cast<const double2*>(f.ap.src);
   double2* dst = reinterpret_cast<double2*>(f.ap.dst);
   const uint32_t ntile = 1u << f.nout;
@@ -1048,16 +992,88 @@ __global__ void __launch_bounds__(256, 2) k_oz(FusedArgs f) {
     for (int i = 0; i < TS / 256; ++i) cp_async16(tile + cdst[i], src + (tb | coff[i]));
     cp_async_commit();
   };
+  // Tiles: CTA b starts with tile b.  Apply: every further tile comes from a device counter, drawn
+  // one tile ahead, so that the CTAs sharing an SM finish together whichever started first.  The
+  // probability passes keep the fixed tiles b, b + grid, ...: their per-CTA sums, and so A and N,
+  // are then the same in every run.  The first copy is issued before the operand setup below,
+  // which it overlaps.
+  constexpr bool DYN = MODE == OZ_APPLY;
+  uint32_t tix = blockIdx.x;
+  uint32_t tb = tix < ntile ? tile_base(tix) : 0u;
+  if (tix < ntile) load_tile(tb);
+  if (tid == 0) s_next = gridDim.x + (DYN ? atomicAdd(&f.ap.ctl->tile_next, 1u) : blockIdx.x);
+  // B: real embedding of K_m / sqrt(N) (apply) or K_1 (probability), sliced; 128 threads, thread =
+  // (row bn of B, reals 8 bkc .. 8 bkc + 7)
+  const int bn = tid >> 2, bkc = tid & 3;
+  double bv[8];
+  int bE = 0;
+  if (tid < 128) {
+    const int br = bn >> 1;
+    const int m = PROB ? 1 : *f.ap.m;
+    const double scale = PROB ? 1.0 : 1.0 / sqrt(*f.ap.N);
+    const double2* Kg = reinterpret_cast<const double2*>(f.ap.kraus) + (m ? 256 : 0);
+    const bool w2 = f.ap.w == 2;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int l = 4 * bkc + j;
+      const double2 kv = !w2 ? Kg[br * 16 + l] : ((br >> 2) == (l >> 2) ? Kg[(br & 3) * 16 + (l & 3)] : make_double2(0.0, 0.0));
+      const double re = kv.x * scale, im = kv.y * scale;
+      bv[2 * j] = (bn & 1) ? im : re;
+      bv[2 * j + 1] = (bn & 1) ? re : -im;
+      bE = max(bE, max(oz::bexp(bv[2 * j]), oz::bexp(bv[2 * j + 1])));
+    }
+    bE = max(bE, __shfl_xor_sync(0xffffffffu, bE, 1));   // the row's 4 threads
+    bE = max(bE, __shfl_xor_sync(0xffffffffu, bE, 2));
+    if (PROB) {   // one exponent for all of K_1: the outputs share a scale
+      const int w = __reduce_max_sync(0xffffffffu, bE);
+      if ((tid & 31) == 0) s_eb[warp] = w;
+    }
+  }
+  if (MODE == OZ_PROB_BOUND) {   // B slices 3 and 4 = 0: the first MMA then clears diagonals 3 and 4 too
+    uint4* z = reinterpret_cast<uint4*>(B + NS * 32 * 32);
+    for (int i = tid; i < 2 * 32 * 32 / 8; i += 256) z[i] = make_uint4(0u, 0u, 0u, 0u);
+  }
+  if (tid == 0) {
+    s_err = 0;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(smem_u32(&tmem_base)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  __syncthreads();
+  if (tid < 128) {
+    const int E = PROB ? max(max(s_eb[0], s_eb[1]), max(s_eb[2], s_eb[3])) : bE;
+    if (bkc == 0) colE[bn] = E;
+    uint64_t Xb[8];
+    put_slices8<NS>(B, 32 * 32, bn, 8 * bkc, bv, E, Xb);
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  tc_sync();
+  const uint32_t tmem = tmem_base;
+  const uint32_t mb = smem_u32(&mbar);
+  uint32_t goff[8];          // this thread's 8 outputs (apply): written straight to the register
+#pragma unroll
+  for (int l = 0; l < 8; ++l) goff[l] = t2g(offa[l]);
+  const uint32_t tlane = (uint32_t)(32 * (warp & 3)) << 16;
+  int cmin = 4095, cmax = 0;   // exponents of this thread's 16 outputs' B rows (nonzero rows for cmin)
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    const int e = colE[16 * hf + j];
+    if (e) cmin = min(cmin, e);
+    cmax = max(cmax, e);
+  }
   uint32_t phase = 0;
   double accA = 0.0, accN = 0.0, accE = 0.0;   // accE: error bound of accA (MODE 2)
   oz::SqAcc sq;    // probability pass: integer sums of squares, one FP64 conversion per tile and sum
   oz::SqAccS sqs;  // the bounded pass's outputs: signed, squared without taking magnitudes
-  uint32_t tix = blockIdx.x;
-  uint32_t tb = tix < ntile ? tile_base(tix) : 0u;
-  if (tix < ntile) load_tile(tb);
-  for (; tix < ntile; tix += gridDim.x) {
+  while (tix < ntile) {
     cp_async_wait<0>();
     __syncthreads();
+    const uint32_t tnext = s_next;
+    uint32_t tfar = ntile;   // the tile after tnext (thread 0 draws it; published at the end)
+    if (tid == 0 && tnext < ntile) tfar = DYN ? gridDim.x + atomicAdd(&f.ap.ctl->tile_next, 1u) : tnext + gridDim.x;
     double x[16];
     int E = 0;
 #pragma unroll
@@ -1069,7 +1085,6 @@ __global__ void __launch_bounds__(256, 2) k_oz(FusedArgs f) {
     }
     rowE[128 * hf + r] = E;
     __syncthreads();   // every thread holds its inputs: the tile buffer takes the next tile's copy
-    const uint32_t tnext = tix + gridDim.x;
     const uint32_t tbn = tnext < ntile ? tile_base(tnext) : 0u;
     if (tnext < ntile) load_tile(tbn);
     E = max(rowE[r], rowE[128 + r]);
@@ -1152,10 +1167,17 @@ __global__ void __launch_bounds__(256, 2) k_oz(FusedArgs f) {
     } else if (PROB) {
       accA += (E && colE[0]) ? sq.take(2 * (E + colE[0] - 2098)) : sq.take(-4000);
     }
+    if (tid == 0) s_next = tfar;   // every thread read s_next before this tile's MMAs
     tc_sync();         // TMEM read out before the next tile's MMAs overwrite it
     tb = tbn;
+    tix = tnext;
   }
   cp_async_wait<0>();  // a copy still in flight after an early exit
+  // The last CTA to finish returns the tile counter to 0: every CTA drew its last tile before.
+  if (DYN && tid == 0 && atomicAdd(&f.ap.ctl->tile_done, 1u) == gridDim.x - 1) {
+    f.ap.ctl->tile_next = 0u;
+    f.ap.ctl->tile_done = 0u;
+  }
   tc_sync();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem));
   if (s_err && tid == 0) atomicOr(&f.ap.ctl->status, 1u);

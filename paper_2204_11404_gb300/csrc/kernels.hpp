@@ -22,6 +22,8 @@ struct Ctl {
   unsigned int status;          // bit 0: a bounded device wait gave up (results invalid)
   unsigned int prob_force_exact;        // test hook: the bounded pass never decides
   unsigned long long prob_fallbacks;    // exact probability passes run after an undecided one
+  unsigned int tile_next;       // tile counter of the tensor-core complex128 apply pass (returned to 0)
+  unsigned int tile_done;       // CTAs of such a pass that have finished (returned to 0)
 };
 
 constexpr int KRAUS_STRIDE = 768;

@@ -964,9 +964,16 @@ __global__ void __launch_bounds__(256, 2) k_oz(FusedArgs f) {
   // of the higher bits, so a warp's 32 group gathers spread over all 8 slots whichever tile bits
   // the block occupies (a bijection: only the low bits change, and only as a function of the rest).
   auto slot = [](uint32_t e) { return e ^ (((e >> 3) ^ (e >> 6) ^ (e >> 9)) & 7u); };
+  // The slicing maps lanes l and l ^ 16 of a warp to the two halves of one row, so that the row's
+  // exponent is one shuffle away: row sr = 16 warp + l % 16, half sh = l / 16.  (The
+  // recombination keeps row r = 32 (warp % 4) + l, the TMEM lane its warp may read.)
+  const int sr = 16 * warp + (tid & 15), sh = (tid >> 4) & 1;
   uint32_t rda[8];
+  {
+    const uint32_t sbase = local_base<4>((uint32_t)sr, qs);
 #pragma unroll
-  for (int l = 0; l < 8; ++l) rda[l] = slot(offa[l]);
+    for (int l = 0; l < 8; ++l) rda[l] = slot(sbase + member_off<4>(8 * sh + l, qa));
+  }
   auto t2g = [&](uint32_t e) {   // tile index -> offset within the register (tile bits)
     const uint32_t h = e >> f.lb;
     uint32_t o = 0;
@@ -1083,15 +1090,12 @@ __global__ void __launch_bounds__(256, 2) k_oz(FusedArgs f) {
       x[2 * l + 1] = v.y;
       E = max(E, max(oz::bexp(v.x), oz::bexp(v.y)));
     }
-    rowE[128 * hf + r] = E;
-    __syncthreads();   // every thread holds its inputs: the tile buffer takes the next tile's copy
-    const uint32_t tbn = tnext < ntile ? tile_base(tnext) : 0u;
-    if (tnext < ntile) load_tile(tbn);
-    E = max(rowE[r], rowE[128 + r]);
+    E = max(E, __shfl_xor_sync(0xffffffffu, E, 16));   // the row's other half
+    if (sh == 0) rowE[sr] = E;   // for the recombination
     {
       uint64_t X0[8], X1[8];
-      put_slices8<NS>(A, kOzSlab, r, 16 * hf, x, E, X0);
-      put_slices8<NS>(A, kOzSlab, r, 16 * hf + 8, x + 8, E, X1);
+      put_slices8<NS>(A, kOzSlab, sr, 16 * sh, x, E, X0);
+      put_slices8<NS>(A, kOzSlab, sr, 16 * sh + 8, x + 8, E, X1);
       if (PROB) {   // N: sum of x^2 with x = X 2^(E - 1078)
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
@@ -1103,6 +1107,9 @@ __global__ void __launch_bounds__(256, 2) k_oz(FusedArgs f) {
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     tc_sync();
+    // every thread has read its inputs: the tile buffer takes the next tile's copy
+    const uint32_t tbn = tnext < ntile ? tile_base(tnext) : 0u;
+    if (tnext < ntile) load_tile(tbn);
     if (tid == 0) {
       // 14 MMAs.  The B slices are contiguous 32-row blocks with one row-group stride, so slices
       // 0..6-p form a single N = 32(7-p) operand; written at TMEM column 32p, its product (p, q)
@@ -1126,6 +1133,7 @@ __global__ void __launch_bounds__(256, 2) k_oz(FusedArgs f) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     __syncthreads();
     if (s_err) break;
+    E = rowE[r];
     // outputs 16hf..16hf+15 of row r: amplitudes 8hf..8hf+7; in range: no output can leave the
     // normal FP64 range, so the recombination skips its range checks
     const bool in_range = E == 0 || (E + cmin >= 1076 && E + cmax <= 2980);

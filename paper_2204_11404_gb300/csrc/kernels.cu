@@ -1176,7 +1176,9 @@ __global__ void __launch_bounds__(256, 2) k_oz(FusedArgs f) {
       accA += (E && colE[0]) ? sq.take(2 * (E + colE[0] - 2098)) : sq.take(-4000);
     }
     if (tid == 0) s_next = tfar;   // every thread read s_next before this tile's MMAs
-    tc_sync();         // TMEM read out before the next tile's MMAs overwrite it
+    // No barrier here: the next tile's MMAs are issued after its slicing barrier (tc_sync, with the
+    // tcgen05 fences), which every thread reaches only after this recombination's TMEM loads have
+    // completed; the loop-top barrier keeps rowE and s_next from being overwritten early.
     tb = tbn;
     tix = tnext;
   }

@@ -1,6 +1,6 @@
 """Tensor-core forms on d=5 trajectories (the tensor-core passes need 4096-amplitude tiles):
 complex64 with weight-4 contractions in 3xTF32, and complex128 with weight-4 applications as
-FP64-exact 8-bit-slice products on the BF16 tensor cores.  Checked against the FP64 oracle and
+FP64-exact 8-bit-slice products on the FP16 tensor cores.  Checked against the FP64 oracle and
 against the CUDA-core forms of the same storage."""
 import numpy as np
 import pytest
@@ -96,3 +96,22 @@ def test_bounded_probability_pass_decides_like_the_exact_pass():
         assert np.array_equal(sa, sb)
         assert f2 - f1 == 2 * 3 * 24          # every noisy-round measurement, forced
         assert f1 - f0 <= 2                   # unforced: the bound decided (almost) every outcome
+
+
+def test_emulated_fp64_form_is_bit_reproducible():
+    """The apply pass draws its tiles from a device counter that its last CTA resets: a rerun of
+    the same trajectory, in the same simulator and in a new one, must give the same bits and the
+    same amplitudes bit for bit (a tile skipped or done twice would change the state)."""
+    pt = W.D5_CR["points"][7]
+    with Simulator(5, 2, "cr", "c128tc", **pt) as a:
+        r1 = a.run(91, 4, 1)
+        s1 = a.state().copy()
+        r2 = a.run(91, 4, 1)
+        s2 = a.state().copy()
+    with Simulator(5, 2, "cr", "c128tc", **pt) as b:
+        r3 = b.run(91, 4, 1)
+        s3 = b.state()
+    for x, y, z in zip(r1, r2, r3):
+        assert (x == y).all() and (x == z).all()
+    assert np.array_equal(s1.view(np.uint64), s2.view(np.uint64))
+    assert np.array_equal(s1.view(np.uint64), s3.view(np.uint64))

@@ -938,7 +938,7 @@ __global__ void __launch_bounds__(256, 2) k_oz(FusedArgs f) {
   double2* tile = reinterpret_cast<double2*>(osm);
   uint16_t* A = reinterpret_cast<uint16_t*>(tile + TS);            // 7 slices x 128 rows x 32
   uint16_t* B = A + oz::kSlices * kOzSlab;                         // 7 slices x 32 rows x 32
-  int* rowE = reinterpret_cast<int*>(B + oz::kSlices * 32 * 32);   // [2][128]: per half row
+  int* rowE = reinterpret_cast<int*>(B + oz::kSlices * 32 * 32);   // [128]: row exponents ([256] reserved)
   int* colE = rowE + 256;
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t tmem_base;
@@ -954,7 +954,8 @@ __global__ void __launch_bounds__(256, 2) k_oz(FusedArgs f) {
     qa[j] = f.qa[j];
     qs[j] = f.qp[j];
   }
-  // thread = (row r, half hf): amplitudes 8hf..8hf+7 of group r, reals 16hf..16hf+15
+  // recombination: thread = (row r, half hf), outputs 16hf..16hf+15 = amplitudes 8hf..8hf+7 of group r
+  // (warp w reads TMEM lanes 32 (w % 4) ..); the slicing maps rows to threads differently (below)
   const int r = tid & 127, hf = tid >> 7;
   const uint32_t gbase = local_base<4>((uint32_t)r, qs);
   uint32_t offa[8];

@@ -331,11 +331,18 @@ def native_arm(args, rank, world, local):
         "e2e": e2e, "gpu_launches": launches_per_traj * args.steps, "roofline": roof,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.code == "surface":
+        from oracle.runner import set_threads
+
         smp = OracleSampler()
         secs_o = smp.run(24)
+        set_threads(1)   # the same oracle on one core: 2 of the round's 24 circuits, scaled to a round
+        secs_1 = smp.run(2) * 12
+        set_threads(smp.threads)
         out["cpu_baseline"] = {"value": 1.0 / secs_o, "unit": UNIT, "cores": smp.threads, "kind": "oracle",
                                "sample": "one d=5 cr noisy round (24 stabilizer circuits with measurement), "
-                                         "p=5e-3 theta_rx=0.05 phi_zz=0.02, on a resident 2^26 FP64 state"}
+                                         "p=5e-3 theta_rx=0.05 phi_zz=0.02, on a resident 2^26 FP64 state",
+                               "value_1_core": 1.0 / secs_1,
+                               "sample_1_core": "2 of the same round's stabilizer circuits on one thread, x 12"}
     for s in sims:
         s.close()
     if rank == 0:

@@ -21,10 +21,17 @@ Logical Z is Z on the first data row (surface code) or on the whole line
 (repetition code, Fig. 2).  A correction chain flips the logical when it
 crosses that support an odd number of times.
 
+Edge weights are 1 by default.  Log-likelihood weights w = log((1 - p) / p) can be
+set from edge probabilities, for instance those estimated from the detection events
+themselves (estimate_edge_probabilities: the two-point correlation of independent
+mechanisms, Spitz et al., Adv. Quantum Technol. 1, 1800012 (2018)); shortest paths are
+then found by Dijkstra instead of breadth-first search.
+
 The matching is exact (dynamic programming over subsets of defects) up to
 MAX_EXACT defects.  Beyond that it falls back to greedy pairing of the closest
 defects, and the count of such trajectories is reported.
 """
+import heapq
 from collections import deque
 from functools import lru_cache
 
@@ -73,34 +80,99 @@ class Decoder:
         self.row = set(range(d))               # logical Z support
         self.fallbacks = 0
         self._graphs = {}
+        self._edges = {}
+        self._w = {}
 
-    def _graph(self, layers):
-        """Space-time graph of `layers` event layers: adjacency (node -> [(node, parity)]), node
-        (e, k) = e * nz + k, boundary = layers * nz."""
-        if layers in self._graphs:
-            return self._graphs[layers]
+    def edges(self, layers):
+        """Edges of the space-time graph of `layers` event layers: list of (u, v, parity, kind), node
+        (e, k) = e * nz + k, boundary node layers * nz, kind "space", "diag", "boundary" or "time"."""
+        if layers in self._edges:
+            return self._edges[layers]
         nz, B = self.nz, layers * self.nz
-        adj = [[] for _ in range(B + 1)]
-
-        def edge(u, v, par):
-            adj[u].append((v, par))
-            adj[v].append((u, par))
-
+        out = []
         for q, ks in enumerate(self.owners):
             par = 1 if q in self.row else 0
             for e in range(layers):
                 if len(ks) == 2:
-                    edge(e * nz + ks[0], e * nz + ks[1], par)
+                    out.append((e * nz + ks[0], e * nz + ks[1], par, "space"))
                     if e + 1 < layers:
                         early, late = sorted(ks, key=lambda k: self.slots[k][q])
-                        edge(e * nz + late, (e + 1) * nz + early, par)
+                        out.append((e * nz + late, (e + 1) * nz + early, par, "diag"))
                 elif len(ks) == 1:
-                    edge(e * nz + ks[0], B, par)
+                    out.append((e * nz + ks[0], B, par, "boundary"))
         for e in range(layers - 1):
             for k in range(nz):
-                edge(e * nz + k, (e + 1) * nz + k, 0)
+                out.append((e * nz + k, (e + 1) * nz + k, 0, "time"))
+        self._edges[layers] = out
+        return out
+
+    def _graph(self, layers):
+        """Adjacency of the space-time graph: node -> [(node, parity, edge index)]."""
+        if layers in self._graphs:
+            return self._graphs[layers]
+        B = layers * self.nz
+        adj = [[] for _ in range(B + 1)]
+        for i, (u, v, par, _) in enumerate(self.edges(layers)):
+            adj[u].append((v, par, i))
+            adj[v].append((u, par, i))
         self._graphs[layers] = (adj, B)
         return adj, B
+
+    def set_edge_probabilities(self, layers, p):
+        """Log-likelihood weights log((1 - p_e) / p_e) for the edges of `layers` layers (in the order
+        of edges(layers)); p is clipped to [1e-12, 0.5 - 1e-12]."""
+        p = np.clip(np.asarray(p, dtype=np.float64), 1e-12, 0.5 - 1e-12)
+        if p.shape != (len(self.edges(layers)),):
+            raise ValueError("one probability per edge")
+        self._w[layers] = np.log((1.0 - p) / p)
+
+    def clear_weights(self):
+        self._w.clear()
+
+    def event_matrix(self, syndromes, data_bits):
+        """0/1 detection events [n][layers * nz] of n trajectories with the same number of rounds."""
+        layers = len(syndromes[0])
+        X = np.zeros((len(syndromes), layers * self.nz), dtype=np.uint8)
+        for t, (s, b) in enumerate(zip(syndromes, data_bits)):
+            for e, k in self.detection_events(s, b):
+                X[t, e * self.nz + k] = 1
+        return X
+
+    def estimate_edge_probabilities(self, events):
+        """Edge probabilities from detection events [n][layers * nz], each edge an independent
+        mechanism that flips its two nodes.  A node pair (i, j) is flipped together with probability
+        p = 1/2 - sqrt(1/4 - (<x_i x_j> - <x_i><x_j>) / (1 - 2<x_i> - 2<x_j> + 4<x_i x_j>)).  A node's
+        boundary edges take what its one-point rate leaves: 1 - 2<x_i> = prod over the node's edges
+        of (1 - 2 p_e).  Parallel edges share their pair's probability equally."""
+        X = np.asarray(events, dtype=np.float64)
+        layers = X.shape[1] // self.nz
+        E = self.edges(layers)
+        m = X.mean(axis=0)
+        groups = {}
+        for i, (u, v, _, kind) in enumerate(E):
+            groups.setdefault((min(u, v), max(u, v)) if kind != "boundary" else (u, -1), []).append(i)
+        p = np.zeros(len(E))
+        rest = np.ones(X.shape[1])   # product of (1 - 2 p_e) over each node's non-boundary edges
+        for (u, v), idx in groups.items():
+            if v < 0:
+                continue
+            xij = float(np.mean(X[:, u] * X[:, v]))
+            den = 1.0 - 2.0 * m[u] - 2.0 * m[v] + 4.0 * xij
+            q = 0.0
+            if den > 0:
+                q = 0.5 - np.sqrt(max(0.0, 0.25 - (xij - m[u] * m[v]) / den))
+            q = min(max(q, 0.0), 0.5 - 1e-12)
+            each = 0.5 * (1.0 - (1.0 - 2.0 * q) ** (1.0 / len(idx)))
+            p[idx] = each
+            rest[u] *= 1.0 - 2.0 * q
+            rest[v] *= 1.0 - 2.0 * q
+        for (u, _), idx in groups.items():
+            if _ >= 0:
+                continue
+            ratio = (1.0 - 2.0 * m[u]) / rest[u] if rest[u] > 0 else 1.0
+            qb = min(max(0.5 * (1.0 - ratio), 0.0), 0.5 - 1e-12)
+            p[idx] = 0.5 * (1.0 - (1.0 - 2.0 * qb) ** (1.0 / len(idx)))
+        return p
 
     def _bfs(self, adj, B, src):
         n = len(adj)
@@ -112,11 +184,29 @@ class Decoder:
             u = dq.popleft()
             if u == B and src != B:
                 continue                       # a chain ends at the boundary
-            for v, pq in adj[u]:
+            for v, pq, _ in adj[u]:
                 if dist[v] < 0:
                     dist[v] = dist[u] + 1
                     par[v] = par[u] ^ pq
                     dq.append(v)
+        return dist, par
+
+    def _dijkstra(self, adj, B, src, w):
+        n = len(adj)
+        dist = [float("inf")] * n
+        par = [0] * n
+        dist[src] = 0.0
+        heap = [(0.0, src)]
+        while heap:
+            du, u = heapq.heappop(heap)
+            if du > dist[u] or (u == B and src != B):
+                continue                       # stale entry, or a chain that ends at the boundary
+            for v, pq, ei in adj[u]:
+                nd = du + float(w[ei])
+                if nd < dist[v]:
+                    dist[v] = nd
+                    par[v] = par[u] ^ pq
+                    heapq.heappush(heap, (nd, v))
         return dist, par
 
     def detection_events(self, syndromes, data_bits):
@@ -133,13 +223,14 @@ class Decoder:
         if n == 0:
             return 0
         adj, B = self._graph(layers)
+        weights = self._w.get(layers)
         nodes = [e * self.nz + k for e, k in defects]
-        w = np.zeros((n, n), dtype=np.int64)
+        w = np.zeros((n, n), dtype=np.float64)
         p = np.zeros((n, n), dtype=np.uint8)
-        wb = np.zeros(n, dtype=np.int64)
+        wb = np.zeros(n, dtype=np.float64)
         pb = np.zeros(n, dtype=np.uint8)
         for i, u in enumerate(nodes):
-            dist, par = self._bfs(adj, B, u)
+            dist, par = self._bfs(adj, B, u) if weights is None else self._dijkstra(adj, B, u, weights)
             for j, v in enumerate(nodes):
                 w[i, j], p[i, j] = dist[v], par[v]
             wb[i], pb[i] = dist[B], par[B]
@@ -154,13 +245,13 @@ class Decoder:
             i = (mask & -mask).bit_length() - 1
             rest = mask & ~(1 << i)
             c, q = best(rest)
-            out = (c + int(wb[i]), q ^ int(pb[i]))
+            out = (c + float(wb[i]), q ^ int(pb[i]))
             m = rest
             while m:
                 j = (m & -m).bit_length() - 1
                 m &= m - 1
                 c2, q2 = best(rest & ~(1 << j))
-                cand = (c2 + int(w[i, j]), q2 ^ int(p[i, j]))
+                cand = (c2 + float(w[i, j]), q2 ^ int(p[i, j]))
                 if cand[0] < out[0]:
                     out = cand
             return out
@@ -182,6 +273,10 @@ class Decoder:
             else:
                 flip ^= int(pb[i])
         return flip
+
+    def correction_parity(self, defects, layers):
+        """Parity of the matched correction across the logical Z support, for defects (layer, k)."""
+        return self._match(list(defects), layers)
 
     def logical_failure(self, syndromes, data_bits, raw_logical):
         """1 if the decoded logical Z differs from the prepared |0_L> (Sec. III.B)."""

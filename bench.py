@@ -501,7 +501,7 @@ def sweep_arm(args, rank, world, local):
     import numpy as np
     import torch
 
-    from paper_2204_11404_gb300.decoder import Decoder
+    from paper_2204_11404_gb300.decoder import Decoder, count_failures
     from paper_2204_11404_gb300.effective import bootstrap_alpha, fit_effective_model
     from paper_2204_11404_gb300.simulator import Simulator
 
@@ -520,16 +520,17 @@ def sweep_arm(args, rank, world, local):
                       overrot_follows=1.0 if args.noise == "follows" else 0.0)
             with Simulator(5, 5, "cr", "c64tc", **nz) as sim:
                 syn, bits, log = sim.run(7000, rank * n, n)
-            f = [dec.logical_failure(a, b, l) for a, b, l in zip(syn, bits, log)]
-            k = int(np.sum(f))
+            # unit weights, and log-likelihood weights estimated from this point's detection events
+            k, kw = count_failures(dec, syn, bits, log)
             if world > 1:
                 import torch.distributed as dist
-                t = torch.tensor([k], dtype=torch.int64, device="cuda")
+                t = torch.tensor([k, kw], dtype=torch.int64, device="cuda")
                 dist.all_reduce(t)
-                k = int(t.item())
+                k, kw = (int(v) for v in t.tolist())
             nt = n * world
             rows.append({"c": c, "p": p, "trajectories": nt, "failures": k, "pL": k / nt,
                          "pL_err": float(np.sqrt(max(k, 1) * (1 - k / nt)) / nt),
+                         "failures_weighted": kw, "pL_weighted": kw / nt,
                          "paper_fit_c0": 6.5e5 * p ** 2.92 if c == 0 else None})
     out = {"metric": "logical error rate p_L(p, c), d=5, 5 rounds, noise=" + args.noise, "unit": "per-point report",
            "data": "synthetic", "points": rows, "decoder_fallbacks": dec.fallbacks}
@@ -543,6 +544,13 @@ def sweep_arm(args, rank, world, local):
                                       "paper": {"A": 6.5e5, "xi": 2.92, "alpha": 0.872}}
         except ValueError as e:
             out["effective_model"] = {"error": str(e)}
+        try:   # the same fit on the log-likelihood-weighted failure counts
+            rows_w = [dict(r, failures=r["failures_weighted"]) for r in rows]
+            fit_w = fit_effective_model(rows_w)
+            out["effective_model_weighted_decoder"] = {"A": fit_w.A, "xi": fit_w.xi, "alpha": fit_w.alpha,
+                                                       "alpha_16_84": list(bootstrap_alpha(rows_w)[1])}
+        except ValueError as e:
+            out["effective_model_weighted_decoder"] = {"error": str(e)}
     if rank == 0:
         print(json.dumps(out))
 

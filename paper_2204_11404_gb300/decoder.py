@@ -286,3 +286,18 @@ class Decoder:
     def logical_error_rate(self, syndromes, data_bits, raw_logical):
         f = [self.logical_failure(s, b, l) for s, b, l in zip(syndromes, data_bits, raw_logical)]
         return float(np.mean(f)) if f else 0.0
+
+
+def count_failures(dec, syndromes, data_bits, raw_logical):
+    """(failures with unit weights, failures with log-likelihood weights) over n trajectories of the
+    same rounds.  The weights come from edge probabilities estimated on these trajectories' own
+    detection events; the decoder's weights are left as they were."""
+    layers = len(syndromes[0])
+    saved = dec._w.pop(layers, None)
+    unit = sum(dec.logical_failure(s, b, l) for s, b, l in zip(syndromes, data_bits, raw_logical))
+    dec.set_edge_probabilities(layers, dec.estimate_edge_probabilities(dec.event_matrix(syndromes, data_bits)))
+    weighted = sum(dec.logical_failure(s, b, l) for s, b, l in zip(syndromes, data_bits, raw_logical))
+    dec._w.pop(layers, None)
+    if saved is not None:
+        dec._w[layers] = saved
+    return int(unit), int(weighted)

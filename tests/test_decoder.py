@@ -194,3 +194,19 @@ def test_log_likelihood_weights_beat_unit_weights_when_measurement_errors_domina
     est_w = failures()
     dec.clear_weights()
     assert true_w < 0.8 * unit and est_w < 0.8 * unit, (unit, true_w, est_w)
+
+
+def test_count_failures_reports_both_weightings_and_restores_the_decoder():
+    """Oracle trajectories at d=3: the unit-weight count equals logical_failure summed, the
+    log-likelihood count is a count over the same trajectories, and no weights stay set."""
+    from paper_2204_11404_gb300.decoder import count_failures
+    dec = Decoder(3)
+    noise = dict(p1=8e-3, p2=8e-3, p_idle=8e-3)
+    trajs = [run_trajectory(3, 3, "cr", "reduced", noise, seed=23, traj=i) for i in range(40)]
+    syn = [t["syndromes"] for t in trajs]
+    bits = [t["data_bits"] for t in trajs]
+    log = [t["raw_logical"] for t in trajs]
+    unit, weighted = count_failures(dec, syn, bits, log)
+    assert unit == sum(dec.logical_failure(s, b, l) for s, b, l in zip(syn, bits, log))
+    assert 0 <= weighted <= len(trajs)
+    assert not dec._w

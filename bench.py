@@ -233,7 +233,11 @@ def native_arm(args, rank, world, local):
     pts = W.D5_CR["points"][: max(1, min(args.points, len(W.D5_CR["points"])))]
     R = W.D5_CR["rounds"]
     dd = 25 if args.code == "repetition" else 5   # 25 data qubits and 24 stabilizers either way
-    sims = [Simulator(dd, R, "cr", args.precision, code=args.code, **pt) for pt in pts]
+    # every run is ordered after and before this stream (through the handle's events), so the CUDA
+    # events of the timed region, recorded on it, bracket all of the simulators' work (torch's
+    # default stream is the legacy stream, handle 0, which the C ABI reads as "no stream")
+    bstream = torch.cuda.Stream()
+    sims = [Simulator(dd, R, "cr", args.precision, stream=bstream.cuda_stream, code=args.code, **pt) for pt in pts]
     seeds = [W.D5_CR["seed_base"] + i for i in range(len(pts))]
     nst = 24
     syn = torch.empty((1, R + 1, nst), dtype=torch.uint8, device="cuda")
@@ -252,17 +256,21 @@ def native_arm(args, rank, world, local):
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    stream = torch.cuda.current_stream()
+    stream = bstream
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    kt = []
+    fb0 = [capi.qec_debug_exact_probability(s.h, -1) for s in sims] if args.precision == "c128tc" else None
     with ClockSampler(local) as clk:
         torch.cuda.synchronize()
         e0.record(stream)
         for i in range(args.steps):
             step(args.warmup + i)
-            kt.append(capi.qec_kernel_times(sims[(args.warmup + i) % len(pts)].h))
         e1.record(stream)
         torch.cuda.synchronize()
+    # the instrumented block's device times, from event-record nodes inside each simulator's
+    # trajectory graph (its most recent trajectory), read after the timed region
+    used = sorted({(args.warmup + i) % len(pts) for i in range(args.steps)})
+    kt = [capi.qec_kernel_times(sims[j].h) for j in used]
+    fallbacks = (sum(capi.qec_debug_exact_probability(s.h, -1) for s in sims) - sum(fb0)) if fb0 else None
     if world > 1:
         dist.barrier()
     secs = e0.elapsed_time(e1) / 1e3
@@ -273,8 +281,10 @@ def native_arm(args, rank, world, local):
     rounds = world * args.steps * R
     value = rounds / secs
 
-    # e2e through the host-output call (inputs: seed + trajectory index; outputs copied to host)
-    n_e2e = min(args.steps, len(pts))
+    # e2e through the host-output call (inputs: seed + trajectory index; outputs copied to host),
+    # over as many trajectories as the timed steps
+    n_e2e = args.steps
+    torch.cuda.synchronize()
     h0 = time.perf_counter()
     for i in range(n_e2e):
         j = i % len(pts)
@@ -288,7 +298,8 @@ def native_arm(args, rank, world, local):
            "h2d_bytes_per_step": 32, "d2h_bytes_per_step": (R + 1) * nst + 25 + 1}
 
     # roofline of the dominant kernel: the pass that applies a weight-4 block (psi <- K_m psi / sqrt(N));
-    # in the complex64 form it also accumulates the next block's probability (fused, one read + write)
+    # in the complex64 and tensor-core complex128 forms it also computes the next block's probability
+    # (fused: one read + one write of the register per stabilizer)
     ms_prob = float(np.mean([k[0] for k in kt]))
     ms_apply = float(np.mean([k[1] for k in kt]))
     amps = 1 << 25
@@ -307,7 +318,8 @@ def native_arm(args, rank, world, local):
     roof["kernel"] = {"c128": "k_apply<double,4> (weight-4 block, 2^25 amplitudes)",
                       "c64": "k_fused<float,4,4> (apply weight-4 block + next block's probability, 2^25 amplitudes)",
                       "c64tc": "k_fused_tc (tcgen05 3xTF32: apply weight-4 block + next probability, 2^25 amplitudes)",
-                      "c128tc": "k_oz<OZ_APPLY> (apply pass on tcgen05: FP64-exact 8-bit-slice products, weight-4 block, 2^25 amplitudes)",
+                      "c128tc": "k_ozf (tcgen05: apply weight-4 block as FP64-exact 8-bit-slice products + next block's "
+                                "bounded probability on the same tiles, 2^25 amplitudes)",
                       }[args.precision]
     if args.code == "repetition":
         roof["kernel"] = roof["kernel"].replace("weight-4 block", "weight-2 block Z_k Z_(k+1)")
@@ -316,12 +328,16 @@ def native_arm(args, rank, world, local):
     roof["apply_hbm_gbs"] = bytes_apply / (ms_apply * 1e-3) / 1e9
     if args.precision == "c128":
         roof["prob_fp64_tflops"] = flops_prob / (ms_prob * 1e-3) / 1e12
-    elif args.precision == "c128tc":   # the probability pass reads the state once
-        roof["prob_hbm_gbs"] = amps * 16 / (ms_prob * 1e-3) / 1e9
+    roof["timed_blocks"] = len(kt)
 
-    # instantiate + per block (probability, apply) + readout; the tensor-core complex128 form adds the
-    # exact probability launch after each bounded one (it returns at once unless called for)
-    launches_per_traj = 1 + (3 if args.precision == "c128tc" else 2) * nst * R + 3
+    # launches per trajectory: instantiate; the first block's probability pass (the tensor-core
+    # complex128 form: bounded + exact launch); per later block one fused pass (the tensor-core
+    # complex128 form: + the exact-probability launch, which returns at once unless the bound left
+    # the outcome open) or, in the FP64 CUDA-core form, a probability and an apply pass; the last
+    # block's apply; the readout (3)
+    S = nst * R
+    launches_per_traj = {"c128": 1 + 2 * S + 3, "c128tc": 1 + 2 + 2 * (S - 1) + 1 + 3,
+                         "c64": 1 + 1 + (S - 1) + 1 + 3, "c64tc": 1 + 1 + (S - 1) + 1 + 3}[args.precision]
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,
@@ -330,6 +346,8 @@ def native_arm(args, rank, world, local):
         "data": "synthetic", "config": workload_config(args, world), "clocks": clk.summary(),
         "e2e": e2e, "gpu_launches": launches_per_traj * args.steps, "roofline": roof,
     }
+    if fallbacks is not None:   # measurements the bound left open (exact pass run), of S per trajectory
+        out["exact_probability_passes"] = {"count": fallbacks, "measurements": S * args.steps}
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.code == "surface":
         from oracle.runner import set_threads
 

@@ -189,8 +189,13 @@ qec_status qec_selftest_wait(qec_sim* sim, uint32_t polls);
  * parameters, the trajectory range and DEVICE output buffers with the shapes
  * of qec_run_trajectories (all three required when n > 0); results are
  * identical to qec_run_trajectories for the same parameters, seed and
- * trajectory indices.  Work is enqueued asynchronously on cuda_stream (NULL =
- * the legacy default stream); no sim handle is involved.
+ * trajectory indices: it launches the same kernels with the same grids in the
+ * same order (for complex64, each block's apply pass fused with the next
+ * block's probability pass), so every reduction adds in the same order.  Work
+ * is enqueued asynchronously on cuda_stream (NULL = the legacy default
+ * stream); no sim handle is involved.  At the sizes it accepts none of its
+ * kernels waits on a barrier or flag, so it has no bounded-wait timeout to
+ * report.
  * All device working memory (program, state vectors, Kraus blocks, reduction
  * and readout scratch) is one static 2 MiB device array inside the library,
  * which every GPU that loads the library holds until the process exits.  It
@@ -242,6 +247,23 @@ qec_status qec_batch_run(qec_batch* b, uint64_t seed, uint32_t n, const uint64_t
 qec_status qec_batch_autotune(qec_batch* b, uint64_t seed, uint32_t n, const uint64_t* traj, const int32_t* kind,
                               const qec_noise* noise, int32_t* chosen_warps, float* best_ms);
 
+/*
+ * Test hook: choose one trajectory of the next qec_batch_run (item = its index i in that call's
+ * arrays, 0 <= i < n; -1 = none) whose data-register state after its last noisy round is
+ * recorded on the device, so that its amplitudes can be compared with another simulation of
+ * the same trajectory (Sec. II.B: the reduced and the unreduced register hold the same data
+ * state).  QEC_EINVAL on a null handle or item < -1.
+ */
+qec_status qec_batch_snapshot(qec_batch* b, int64_t item);
+
+/*
+ * Copy the state recorded by the last qec_batch_run that had a snapshot item: the 2^9
+ * amplitudes of the nine data qubits (every ancilla is |0> after the round), normalised, as
+ * complex128 (re, im) pairs whatever the trajectory's precision.  bytes must be >= 16 * 512.
+ * QEC_EINVAL if no such run has completed, or the item was not below that run's n.
+ */
+qec_status qec_batch_get_state(qec_batch* b, void* host_buf, size_t bytes);
+
 /* Device time (ms, CUDA events around the persistent launch) of the last qec_batch_run. */
 qec_status qec_batch_last_ms(const qec_batch* b, float* ms);
 qec_status qec_batch_destroy(qec_batch* b);
@@ -282,7 +304,10 @@ qec_status qec_debug_blocks(const qec_params* params, uint64_t seed, uint64_t tr
  * sum_k A[r][k]^2 (each half-row's squares summed in integers, converted once), the rest
  * untouched; 3: the bounded probability pass: out[r][0] = sum_n y^_n^2 from the top 3
  * slices of each operand, out[r][1] = its error bound (|sum_n (A[r] . B[n])^2 - out[r][0]|
- * <= out[r][1]).  Returns QEC_EINVAL for any other variant.  The paper has no counterpart
+ * <= out[r][1]); 4: the fused tensor-core pass's probability, A taken as one tile (one exponent for
+ * all of A and one for all of B), 24-bit truncations, 3 slices each, diagonals 0..2:
+ * out[r][0] = estimate of sum_n (A[r] . B[n])^2, out[r][1] its error bound, out[r][2] = estimate
+ * of sum_k A[r][k]^2, out[r][3] its error bound.  Returns QEC_EINVAL for any other variant.  The paper has no counterpart
  * (an arithmetic form of the gate application of Sec. III).  Returns QEC_EINVAL on null
  * pointers or m <= 0.
  */

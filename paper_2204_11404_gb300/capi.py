@@ -57,6 +57,8 @@ SIGNATURES = {
                          ctypes.c_int),
     "qec_batch_run": ([_P, ctypes.c_uint64, ctypes.c_uint32, _P, _P, _P, _P, _P, _P], ctypes.c_int),
     "qec_batch_autotune": ([_P, ctypes.c_uint64, ctypes.c_uint32, _P, _P, _P, _P, _P], ctypes.c_int),
+    "qec_batch_snapshot": ([_P, ctypes.c_int64], ctypes.c_int),
+    "qec_batch_get_state": ([_P, _P, ctypes.c_size_t], ctypes.c_int),
     "qec_batch_last_ms": ([_P, _P], ctypes.c_int),
     "qec_batch_destroy": ([_P], ctypes.c_int),
     "qec_last_error": ([], ctypes.c_char_p),
@@ -169,6 +171,14 @@ def qec_batch_autotune(b, seed, n, traj_ptr, kind_ptr, noise_ptr):
     check(lib().qec_batch_autotune(b, seed, n, traj_ptr, kind_ptr, noise_ptr, ctypes.cast(ctypes.pointer(w), _P),
                                    ctypes.cast(ctypes.pointer(ms), _P)))
     return int(w.value), float(ms.value)
+
+
+def qec_batch_snapshot(b, item):
+    return check(lib().qec_batch_snapshot(b, item))
+
+
+def qec_batch_get_state(b, host_ptr, nbytes):
+    return check(lib().qec_batch_get_state(b, host_ptr, nbytes))
 
 
 def qec_batch_last_ms(b):

@@ -44,6 +44,7 @@ struct BatchCtl {
   unsigned int counter;       // their work queue head (zeroed before every run)
   uint32_t n_u;               // unreduced-register (17-qubit) trajectories in this run
   unsigned int counter_u;     // their work queue head
+  uint32_t snap_item;         // item whose final data-register state goes to snap (~0u = none)
 };
 
 struct BatchArgs {
@@ -70,6 +71,7 @@ struct BatchArgs {
   uint8_t* syn;               // [n][rounds+1][8]
   uint8_t* bits;              // [n][9]
   uint8_t* logical;           // [n]
+  double2* snap;              // [512] data-register state of ctl->snap_item after its last round
   int init_mode;              // 1: compute the init state of precision init_prec into init_out
   int init_prec;
   void* init_out;
@@ -330,6 +332,8 @@ __device__ void run_warp(const BatchArgs& a, unsigned char* wsm, uint32_t item) 
     for (int i = lane; i < kNAmp; i += 32) out[i] = psi[i];
     return;
   }
+  if (item == a.ctl->snap_item)
+    for (int i = lane; i < kNAmp; i += 32) a.snap[i] = make_double2((double)psi[i].x, (double)psi[i].y);
   // final Z readout: qubit j gets [u_j < P(q_j = 1 | earlier outcomes)]
   uint8_t* bits = a.bits + (size_t)item * kND;
   uint32_t prefix = 0;
@@ -569,6 +573,8 @@ __device__ void run_cta_u(const BatchArgs& a, unsigned char* sm, uint32_t item) 
     for (int i = tid; i < kUAmp; i += nt) out[i] = slab[i];
     return;
   }
+  if (item == a.ctl->snap_item)   // slab entries 0..511: the data qubits with every ancilla |0>
+    for (int i = tid; i < kNAmp; i += nt) a.snap[i] = make_double2((double)slab[i].x, (double)slab[i].y);
   // final Z readout of the data qubits (the ancillas are all |0>: slab entries 0..511)
   uint8_t* bits = a.bits + (size_t)item * kND;
   uint32_t prefix = 0;
@@ -658,6 +664,9 @@ struct qec_batch {
   int warps_per_cta = 8;
   int ctas_per_sm = 1;
   float last_ms = 0.f;
+  double2* d_snap = nullptr;
+  int64_t snap_item = -1;   // for the next run
+  bool snap_valid = false;  // a completed run recorded a snapshot
 };
 
 namespace {
@@ -687,7 +696,7 @@ void batch_free(qec_batch* b) {
   void* ptrs[] = {b->d_ops, b->d_blocks, b->d_iops, b->d_iblocks, b->d_mats, b->d_psi0[0], b->d_psi0[1],
                   b->d_noise, b->d_kind, b->d_traj, b->d_ctl, b->d_syn, b->d_bits, b->d_log,
                   b->d_uops, b->d_uitems, b->d_iuops, b->d_iuitems, b->d_psi0_u[0], b->d_psi0_u[1],
-                  b->d_idx, b->d_idx_u};
+                  b->d_idx, b->d_idx_u, b->d_snap};
   for (void* p : ptrs) if (p) cudaFree(p);
   if (b->fork) cudaEventDestroy(b->fork);
   if (b->join) cudaEventDestroy(b->join);
@@ -725,6 +734,7 @@ BatchArgs batch_args(const qec_batch* b) {
   a.syn = b->d_syn;
   a.bits = b->d_bits;
   a.logical = b->d_log;
+  a.snap = b->d_snap;
   a.init_mode = 0;
   a.init_prec = 0;
   a.init_out = nullptr;
@@ -822,7 +832,7 @@ qec_status qec_batch_create(int32_t d, int32_t rounds, int32_t gates, uint32_t m
                      (void**)&b->d_traj, (void**)&b->d_ctl, (void**)&b->d_syn, (void**)&b->d_bits,
                      (void**)&b->d_log, (void**)&b->d_uops, (void**)&b->d_uitems, (void**)&b->d_iuops,
                      (void**)&b->d_iuitems, &b->d_psi0_u[0], &b->d_psi0_u[1], (void**)&b->d_idx,
-                     (void**)&b->d_idx_u};
+                     (void**)&b->d_idx_u, (void**)&b->d_snap};
   const size_t sizes[] = {sizeof(ProgOp) * (b->prog.ops.size() + 1), sizeof(BlockInfo) * kNStab,
                           sizeof(ProgOp) * (b->iprog.ops.size() + 1), sizeof(BlockInfo) * kNStab,
                           sizeof(b->prog.mats), (size_t)kNAmp * 16, (size_t)kNAmp * 8,
@@ -831,7 +841,7 @@ qec_status qec_batch_create(int32_t d, int32_t rounds, int32_t gates, uint32_t m
                           sizeof(ProgOp) * (b->uprog.ops.size() + 1), sizeof(UItem) * (b->uprog.items.size() + 1),
                           sizeof(ProgOp) * (b->iuprog.ops.size() + 1), sizeof(UItem) * (b->iuprog.items.size() + 1),
                           (size_t)kUAmp * 16, (size_t)kUAmp * 8, sizeof(uint32_t) * max_traj,
-                          sizeof(uint32_t) * max_traj};
+                          sizeof(uint32_t) * max_traj, sizeof(double2) * kNAmp};
   for (size_t i = 0; i < sizeof(sizes) / sizeof(sizes[0]); ++i) {
     e = cudaMalloc(allocs[i], sizes[i]);
     if (e != cudaSuccess) return bail(bfail(QEC_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e)));
@@ -923,6 +933,9 @@ qec_status qec_batch_run(qec_batch* b, uint64_t seed, uint32_t n, const uint64_t
   b->h_ctl->counter = 0;
   b->h_ctl->n_u = (uint32_t)b->h_idx_u.size();
   b->h_ctl->counter_u = 0;
+  const bool snap = b->snap_item >= 0 && b->snap_item < (int64_t)n;
+  b->h_ctl->snap_item = snap ? (uint32_t)b->snap_item : ~0u;
+  b->snap_valid = false;
   QEC_BCUDA(cudaMemcpyAsync(b->d_ctl, b->h_ctl, sizeof(BatchCtl), cudaMemcpyHostToDevice, b->work));
   QEC_BCUDA(cudaEventRecord(b->t0, b->work));
   QEC_BCUDA(cudaGraphLaunch(b->gexec, b->work));
@@ -937,6 +950,7 @@ qec_status qec_batch_run(qec_batch* b, uint64_t seed, uint32_t n, const uint64_t
   }
   QEC_BCUDA(cudaStreamSynchronize(b->work));
   QEC_BCUDA(cudaEventElapsedTime(&b->last_ms, b->t0, b->t1));
+  b->snap_valid = snap;
   return QEC_OK;
 }
 
@@ -964,6 +978,25 @@ qec_status qec_batch_autotune(qec_batch* b, uint64_t seed, uint32_t n, const uin
   if (st) return st;
   *chosen_warps = best;
   *best_ms = best_t;
+  return QEC_OK;
+}
+
+qec_status qec_batch_snapshot(qec_batch* b, int64_t item) {
+  if (!b || item < -1) return bfail(QEC_EINVAL, "null handle or item < -1");
+  b->snap_item = item;
+  return QEC_OK;
+}
+
+qec_status qec_batch_get_state(qec_batch* b, void* host_buf, size_t bytes) {
+  if (!b || !host_buf) return bfail(QEC_EINVAL, "null argument");
+  if (bytes < sizeof(double2) * kNAmp) return bfail(QEC_EINVAL, "host buffer too small");
+  if (!b->snap_valid) return bfail(QEC_EINVAL, "no completed run recorded a snapshot");
+  double* out = static_cast<double*>(host_buf);
+  QEC_BCUDA(cudaMemcpy(out, b->d_snap, sizeof(double2) * kNAmp, cudaMemcpyDeviceToHost));
+  double nrm = 0.0;   // the reduced register keeps the norm P(m) of the last outcome; report unit norm
+  for (int i = 0; i < 2 * kNAmp; ++i) nrm += out[i] * out[i];
+  const double sc = nrm > 0.0 ? 1.0 / std::sqrt(nrm) : 1.0;
+  for (int i = 0; i < 2 * kNAmp; ++i) out[i] *= sc;
   return QEC_OK;
 }
 

@@ -53,7 +53,7 @@ struct qec_sim {
   cudaStream_t work = nullptr;          // owned; all kernels and the graph run here
   cudaStream_t user = nullptr;          // caller's stream (ordering only)
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
-  cudaEvent_t kev[3] = {nullptr, nullptr, nullptr};   // around the instrumented block's two passes
+  cudaEvent_t kev[3] = {nullptr, nullptr, nullptr};   // event-record nodes around the instrumented block
   int timed_block = -1;
   Program init_prog, prog;
   int D = 0, nstab = 0, R = 0, S = 0;
@@ -81,11 +81,9 @@ struct qec_sim {
   uint8_t* d_log = nullptr;
   int32_t* d_events = nullptr;
   uint32_t ev_cap = 0;
-  // The trajectory runs as graph[0] (instantiate + blocks before the timed block), the timed
-  // block's two passes launched directly between timing events, then graph[1] (the rest).
-  // Without a timed block (no noisy round) graph[0] holds everything.
-  cudaGraph_t graph[2] = {nullptr, nullptr};
-  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+  // One trajectory is one graph; event-record nodes bracket the instrumented block's passes.
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
   bool ran = false;
   int blk_cap = 0;      // blocks the Kraus/measurement buffers hold
   int syn_cap = 0;      // bytes per trajectory the syndrome buffer holds
@@ -191,13 +189,19 @@ PassArgs traj_pass(const qec_sim* s, int b) {
   return pass_args(s, s->prog, b, src, s->psi, false, s->d_syn, rnd * s->nstab + k);
 }
 
-// The complex64 form fuses block b's apply pass with block b+1's probability pass (one HBM
-// read + write per stabilizer); complex128 keeps them separate (both passes are FP64-ALU
-// bound, so fusing saves nothing there).
-bool fused_mode(const qec_sim* s) { return !is_f64(s->p.precision); }
+// Block b's apply pass is fused with block b+1's probability pass (one HBM read + write per
+// stabilizer) in the complex64 forms (k_fused, k_fused_tc) and in the tensor-core complex128 form
+// (k_ozf) wherever both blocks fit one tile; the FP64 CUDA-core form keeps them separate (both of its
+// passes are bound by the FP64 pipe, so one pass saves no time there).
+bool fused_step(const qec_sim* s, int b) {
+  if (b < 0 || b + 1 >= s->S) return false;
+  if (!is_f64(s->p.precision)) return true;
+  if (s->p.precision != QEC_C128_TC) return false;
+  return fused_oz_applies(traj_pass(s, b), traj_pass(s, b + 1));
+}
 
-// One probability / apply pass of a block outside the fused complex64 path: on the tensor cores
-// for QEC_C128_TC weight-4 blocks, else the CUDA-core pass of the precision.
+// One probability / apply pass of a block outside the fused steps: on the tensor cores for
+// QEC_C128_TC blocks whose tile fits, else the CUDA-core pass of the precision.
 cudaError_t prob_pass(qec_sim* s, const PassArgs& a) {
   if (s->p.precision == QEC_C128_TC && apply_oz_applies(a)) return launch_prob_oz(a, s->num_sms, s->work);
   return launch_prob(s->p.precision, a, pass_grid_for(s->p.precision, true, s->D, a.w, s->num_sms), s->work);
@@ -208,32 +212,9 @@ cudaError_t apply_pass(qec_sim* s, const PassArgs& a) {
   return launch_apply(s->p.precision, a, pass_grid_for(s->p.precision, false, s->D, a.w, s->num_sms), s->work);
 }
 
-qec_status enqueue_prob(qec_sim* s, int b) {
-  QEC_CUDA(prob_pass(s, traj_pass(s, b)));
+qec_status record(qec_sim* s, int i) {
+  QEC_CUDA(cudaEventRecordWithFlags(s->kev[i], s->work, cudaEventRecordExternal));
   return QEC_OK;
-}
-
-// The pass(es) that apply block b: apply(b) + prob(b+1) fused, or apply(b) then prob(b+1).
-qec_status enqueue_apply(qec_sim* s, int b) {
-  PassArgs a = traj_pass(s, b);
-  const bool last = b + 1 >= s->S;
-  if (fused_mode(s) && !last) {
-    PassArgs n = traj_pass(s, b + 1);
-    n.src = s->psi;
-    QEC_CUDA(launch_fused(s->p.precision, a, n, s->num_sms, s->work));
-    return QEC_OK;
-  }
-  QEC_CUDA(apply_pass(s, a));
-  return (fused_mode(s) || last) ? QEC_OK : enqueue_prob(s, b + 1);
-}
-
-// Blocks [b0, b1): block b0's probability pass is enqueued only when b0 == 0 (later blocks
-// get theirs from the previous block's apply step).
-qec_status enqueue_blocks(qec_sim* s, int b0, int b1) {
-  qec_status st = QEC_OK;
-  if (b0 == 0 && b1 > 0) st = enqueue_prob(s, 0);
-  for (int b = b0; b < b1 && st == QEC_OK; ++b) st = enqueue_apply(s, b);
-  return st;
 }
 
 qec_status enqueue_readout(qec_sim* s) {
@@ -256,41 +237,44 @@ qec_status enqueue_readout(qec_sim* s) {
   return QEC_OK;
 }
 
-// Part 0: instantiate + blocks [0, timed); part 1: blocks (timed, S) + readout.
-// Part 0: instantiate, then blocks [0, b*) except b*'s probability pass; part 1: everything after
-// block b*'s apply step, then the readout.  Without a timed block part 0 is the whole trajectory.
-qec_status enqueue_part(qec_sim* s, int part) {
+// The whole trajectory: instantiate, then per block b its probability pass (unless block b-1's
+// fused pass computed it) and its apply pass (fused with block b+1's probability pass where
+// fused_step), then the readout.  The instrumented block's passes are bracketed by event-record
+// nodes: kev[0]..kev[1] its separate probability pass (empty when fused into the previous block's
+// pass), kev[1]..kev[2] its apply pass or fused pass (without the exact-probability launch that
+// follows a tensor-core fused pass).
+qec_status enqueue_trajectory(qec_sim* s) {
   const int tb = s->timed_block;
   qec_status st = QEC_OK;
-  if (part == 0) {
-    if (s->S > 0) QEC_CUDA(launch_instantiate(s->p.precision, inst_args(s, 1, 1, s->S, true), s->work));
-    if (tb < 0) {
-      st = enqueue_blocks(s, 0, s->S);
-      if (st == QEC_OK) st = enqueue_readout(s);
-      return st;
-    }
-    if (s->S > 0) st = enqueue_prob(s, 0);
-    for (int b = 0; b < tb && st == QEC_OK; ++b) {
-      // in the separate-pass form, stop before block b*'s probability pass (timed directly)
-      PassArgs a = traj_pass(s, b);
-      if (fused_mode(s)) {
-        st = enqueue_apply(s, b);
-      } else {
-        QEC_CUDA(apply_pass(s, a));
-        if (b + 1 < tb) st = enqueue_prob(s, b + 1);
+  if (s->S > 0) QEC_CUDA(launch_instantiate(s->p.precision, inst_args(s, 1, 1, s->S, true), s->work));
+  for (int b = 0; b < s->S && st == QEC_OK; ++b) {
+    const bool timed = b == tb, fused = fused_step(s, b);
+    if (timed && (st = record(s, 0))) return st;
+    if (b == 0 || !fused_step(s, b - 1)) QEC_CUDA(prob_pass(s, traj_pass(s, b)));
+    if (timed && (st = record(s, 1))) return st;
+    const PassArgs a = traj_pass(s, b);
+    if (fused) {
+      PassArgs n = traj_pass(s, b + 1);
+      n.src = s->psi;
+      if (s->p.precision == QEC_C128_TC) {
+        QEC_CUDA(launch_fused_oz(a, n, s->num_sms, s->work));
+        if (timed && (st = record(s, 2))) return st;
+        QEC_CUDA(launch_prob_oz_check(n, s->num_sms, s->work));
+        continue;
       }
+      QEC_CUDA(launch_fused(s->p.precision, a, n, s->num_sms, s->work));
+    } else {
+      QEC_CUDA(apply_pass(s, a));
     }
-  } else {
-    if (!fused_mode(s) && tb + 1 < s->S) st = enqueue_prob(s, tb + 1);
-    for (int b = tb + 1; b < s->S && st == QEC_OK; ++b) st = enqueue_apply(s, b);
-    if (st == QEC_OK) st = enqueue_readout(s);
+    if (timed) st = record(s, 2);
   }
+  if (st == QEC_OK) st = enqueue_readout(s);
   return st;
 }
 
-qec_status capture(qec_sim* s, int part) {
+qec_status capture(qec_sim* s) {
   QEC_CUDA(cudaStreamBeginCapture(s->work, cudaStreamCaptureModeThreadLocal));
-  qec_status st = enqueue_part(s, part);
+  qec_status st = enqueue_trajectory(s);
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamEndCapture(s->work, &g);
   if (st != QEC_OK) {
@@ -298,48 +282,26 @@ qec_status capture(qec_sim* s, int part) {
     return st;
   }
   if (e != cudaSuccess) return fail(QEC_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
-  s->graph[part] = g;
-  QEC_CUDA(cudaGraphInstantiate(&s->gexec[part], g, 0));
+  s->graph = g;
+  QEC_CUDA(cudaGraphInstantiate(&s->gexec, g, 0));
   return QEC_OK;
 }
 
 qec_status ensure_graph(qec_sim* s) {
-  if (s->gexec[0]) return QEC_OK;
-  qec_status st = capture(s, 0);
-  if (st == QEC_OK && s->timed_block >= 0) st = capture(s, 1);
-  return st;
+  if (s->gexec) return QEC_OK;
+  return capture(s);
 }
 
-// Timed block b*: its apply step (fused apply + next probability in the complex64 form) runs
-// between kev[1] and kev[2]; in the complex128 form kev[0]..kev[1] brackets nothing and the
-// probability pass of b* is timed from the end of graph part 0 instead (see enqueue_part).
 qec_status launch_trajectory(qec_sim* s) {
-  QEC_CUDA(cudaGraphLaunch(s->gexec[0], s->work));
-  if (s->timed_block < 0) return QEC_OK;
-  const int b = s->timed_block;
-  PassArgs a = traj_pass(s, b);
-  QEC_CUDA(cudaEventRecord(s->kev[0], s->work));
-  if (!fused_mode(s)) QEC_CUDA(prob_pass(s, a));
-  QEC_CUDA(cudaEventRecord(s->kev[1], s->work));
-  if (fused_mode(s)) {
-    PassArgs n = traj_pass(s, b + 1);
-    n.src = s->psi;
-    QEC_CUDA(launch_fused(s->p.precision, a, n, s->num_sms, s->work));
-  } else {
-    QEC_CUDA(apply_pass(s, a));
-  }
-  QEC_CUDA(cudaEventRecord(s->kev[2], s->work));
-  QEC_CUDA(cudaGraphLaunch(s->gexec[1], s->work));
+  QEC_CUDA(cudaGraphLaunch(s->gexec, s->work));
   return QEC_OK;
 }
 
 void drop_graph(qec_sim* s) {
-  for (int i = 0; i < 2; ++i) {
-    if (s->gexec[i]) cudaGraphExecDestroy(s->gexec[i]);
-    if (s->graph[i]) cudaGraphDestroy(s->graph[i]);
-    s->gexec[i] = nullptr;
-    s->graph[i] = nullptr;
-  }
+  if (s->gexec) cudaGraphExecDestroy(s->gexec);
+  if (s->graph) cudaGraphDestroy(s->graph);
+  s->gexec = nullptr;
+  s->graph = nullptr;
 }
 
 void free_all(qec_sim* s) {
@@ -640,8 +602,64 @@ qec_status qec_debug_program(const qec_params* params, int32_t* ops, uint32_t ca
   return QEC_OK;
 }
 
+// Variant 4: the fused pass's probability arithmetic on the CPU, A as one tile (one exponent for all
+// of A, one for all of B), as the fused kernel's threads hold it: 16 inputs and 16 outputs each.
+static void ozaki_fused_prob(const double* A, const double* B, int m, double* out) {
+  int Et = 0, EP = 0;
+  for (int i = 0; i < m * 32; ++i) Et = std::max(Et, oz::bexp(A[i]));
+  for (int i = 0; i < 32 * 32; ++i) EP = std::max(EP, oz::bexp(B[i]));
+  Et = std::max(Et, 24);
+  std::vector<int> da((size_t)m * 32 * 3), db(32 * 32 * 3);
+  std::vector<uint32_t> a24((size_t)m * 32);
+  for (int i = 0; i < m * 32; ++i) {
+    const uint32_t a = oz::top24(oz::d2u(A[i]), Et);
+    a24[i] = a;
+    const int neg = (int)(oz::d2u(A[i]) >> 63);
+    for (int p = 0; p < 3; ++p) da[(size_t)i * 3 + p] = (neg ? -1 : 1) * (int)((a >> (16 - 8 * p)) & 0xFF);
+  }
+  for (int i = 0; i < 32 * 32; ++i) {   // B: the top 3 bytes of its 56-bit magnitude under EP
+    const uint64_t X = EP ? oz::mag56(B[i], EP) : 0ull;
+    const int neg = (int)(oz::d2u(B[i]) >> 63);
+    for (int p = 0; p < 3; ++p) db[(size_t)i * 3 + p] = (neg ? -1 : 1) * (int)((X >> (48 - 8 * p)) & 0xFF);
+  }
+  for (int r = 0; r < m; ++r) {
+    double sa = 0.0, ea = 0.0, sn = 0.0, en = 0.0;
+    for (int h = 0; h < 2; ++h) {   // a thread's 16 outputs n = 16h..16h+15 and 16 inputs k = 16h..16h+15
+      uint64_t aacc = 0, nacc = 0;
+      for (int n = 16 * h; n < 16 * h + 16; ++n) {
+        float D[3];
+        for (int t = 0; t < 3; ++t) {
+          float acc = 0.f;   // exact: integers below 2^23
+          for (int p = 0; p <= t; ++p)
+            for (int k = 0; k < 32; ++k)
+              acc += (float)(da[((size_t)r * 32 + k) * 3 + p] * db[((size_t)n * 32 + k) * 3 + (t - p)]);
+          D[t] = acc;
+        }
+        const int64_t z = oz::combine3(D);
+        aacc += (uint64_t)(z * z);
+        const uint64_t a = a24[(size_t)r * 32 + n];
+        nacc += a * a;
+      }
+      const double nth = oz::scale2((double)nacc, 2 * (Et - 1046));
+      const double ath = EP ? oz::scale2((double)aacc, 2 * (Et + EP - 2068)) : 0.0;
+      sn += nth;
+      sa += ath;
+      en += oz::part_bound(nth, Et + 1015);
+      ea += EP ? oz::part_bound(ath, Et + EP) : 0.0;
+    }
+    out[r * 32] = sa;
+    out[r * 32 + 1] = ea;
+    out[r * 32 + 2] = sn;
+    out[r * 32 + 3] = en;
+  }
+}
+
 qec_status qec_debug_ozaki_gemm(const double* A, const double* B, int32_t m, int32_t variant, double* out) {
-  if (!A || !B || !out || m <= 0 || variant < 0 || variant > 3) return fail(QEC_EINVAL, "bad argument");
+  if (!A || !B || !out || m <= 0 || variant < 0 || variant > 4) return fail(QEC_EINVAL, "bad argument");
+  if (variant == 4) {
+    ozaki_fused_prob(A, B, m, out);
+    return QEC_OK;
+  }
   std::vector<int> ea(m), eb(32);
   std::vector<int> da((size_t)m * 32 * oz::kSlices), db(32 * 32 * oz::kSlices);
   for (int r = 0; r < m; ++r) {

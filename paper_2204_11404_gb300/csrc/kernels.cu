@@ -227,7 +227,7 @@ __device__ void prob_finish(const PassArgs& a, double accA, double accN, double*
     const double p1 = sA / sN;
     const int m = a.forced >= 0 ? a.forced : (*a.u < p1 ? 1 : 0);
     *a.A = sA;
-    *a.N = sN;
+    if (a.store_n) *a.N = sN;
     *a.m = m;
     if (a.syn) {
       const unsigned long long t = a.ctl->traj - a.ctl->first;
@@ -243,7 +243,7 @@ __device__ void prob_finish(const PassArgs& a, double accA, double accN, double*
 // the same way; it then stores A^, N (bit-identical to the exact pass's N), m and the syndrome bit.
 // Otherwise (or with ctl->prob_force_exact) it sets ctl->prob_uncertain and stores nothing.
 __device__ void prob_finish_bounded(const PassArgs& a, double accA, double accN, double accE, double* sred,
-                                    int* s_last) {
+                                    int* s_last, bool n_always = false) {
   double dummy = 0.0;
   block_sum2(accA, accN, sred);
   __syncthreads();
@@ -277,9 +277,10 @@ __device__ void prob_finish_bounded(const PassArgs& a, double accA, double accN,
       m = u < sA / sN ? 1 : 0;
     }
     a.ctl->prob_uncertain = decided ? 0u : 1u;
+    if (n_always) *a.N = sN;   // the fused pass's norm estimate renormalises whichever pass decides
     if (decided) {
       *a.A = sA;
-      *a.N = sN;
+      if (!n_always) *a.N = sN;
       *a.m = m;
       if (a.syn) {
         const unsigned long long t = a.ctl->traj - a.ctl->first;
@@ -893,17 +894,16 @@ __device__ __forceinline__ uint32_t digit_pair(uint64_t Xa, uint64_t Xb, uint32_
   return r;
 }
 
-// Writes the first NS FP16 slices of 8 consecutive reals x[0..7] (row `row`, k0 % 8 == 0) under
-// exponent E; X[0..7] receives their 56-bit magnitudes.
+// Writes the first NS FP16 slices of 8 consecutive reals (row `row`, k0 % 8 == 0) given their
+// magnitudes X[0..7] (digit P = byte 6 - P of the 56-bit value) and the high words of the reals
+// (for their signs).
 template <int NS = oz::kSlices>
-__device__ __forceinline__ void put_slices8(uint16_t* S, int slab, int row, int k0, const double* x, int E,
-                                            uint64_t (&X)[8]) {
+__device__ __forceinline__ void put_digits8(uint16_t* S, int slab, int row, int k0, const uint64_t (&X)[8],
+                                            const uint32_t (&hw)[8]) {
   uint32_t sg[4], nsg[4];
 #pragma unroll
-  for (int j = 0; j < 8; ++j) X[j] = E ? oz::mag56(x[j], E) : 0ull;
-#pragma unroll
   for (int i = 0; i < 4; ++i) {
-    const uint32_t sb = (uint32_t)(oz::d2u(x[2 * i]) >> 63) << 15 | (uint32_t)(oz::d2u(x[2 * i + 1]) >> 63) << 31;
+    const uint32_t sb = ((hw[2 * i] >> 16) & 0x8000u) | (hw[2 * i + 1] & 0x80000000u);
     sg[i] = 0x3C003C00u | sb;
     nsg[i] = 0xE400E400u ^ sb;
   }
@@ -915,6 +915,20 @@ __device__ __forceinline__ void put_slices8(uint16_t* S, int slab, int row, int 
                  digit_pair<P>(X[4], X[5], sg[2], nsg[2]), digit_pair<P>(X[6], X[7], sg[3], nsg[3]));
   QEC_OZ_SLICE(0) QEC_OZ_SLICE(1) QEC_OZ_SLICE(2) QEC_OZ_SLICE(3) QEC_OZ_SLICE(4) QEC_OZ_SLICE(5) QEC_OZ_SLICE(6)
 #undef QEC_OZ_SLICE
+}
+
+// Writes the first NS FP16 slices of 8 consecutive reals x[0..7] (row `row`, k0 % 8 == 0) under
+// exponent E; X[0..7] receives their 56-bit magnitudes.
+template <int NS = oz::kSlices>
+__device__ __forceinline__ void put_slices8(uint16_t* S, int slab, int row, int k0, const double* x, int E,
+                                            uint64_t (&X)[8]) {
+  uint32_t hw[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    X[j] = E ? oz::mag56(x[j], E) : 0ull;
+    hw[j] = (uint32_t)(oz::d2u(x[j]) >> 32);
+  }
+  put_digits8<NS>(S, slab, row, k0, X, hw);
 }
 
 // MODE 0 (OZ_APPLY): psi <- K_m psi / sqrt(N).  MODE 1 (OZ_PROB): A = sum |K_1 psi_g|^2 and
@@ -1194,6 +1208,321 @@ __global__ void __launch_bounds__(256, 2) k_oz(FusedArgs f) {
   if (s_err && tid == 0) atomicOr(&f.ap.ctl->status, 1u);
   if (MODE == OZ_PROB) prob_finish(f.ap, accA, accN, sred, &s_last);
   if (MODE == OZ_PROB_BOUND) prob_finish_bounded(f.ap, accA, accN, accE, sred, &s_last);
+}
+
+// ---- fused complex128 pass on the tensor cores: apply block s, then block s+1's probability ----------
+// The tile holds both blocks' qubits (at most 8) and the lowest register bits: 2^11 amplitudes.  Per
+// tile, on 256 threads, two CTAs per SM:
+//  1. Apply block s exactly as k_oz<OZ_APPLY> does (7 slices under each group's exponent, 14 MMAs,
+//     integer recombination, one rounding to FP64).  The results go to the register and, on chip,
+//     into the A-operand slices 3..6 (free once the MMAs have read them), so the tile buffer takes
+//     the next tile's copy as soon as this tile's digits are written.
+//  2. Probability of block s+1 on the updated tile (Sec. II.B: the ancilla is |0> again, so the
+//     next measurement is a quadratic form of this state).  Every real is cut to its top 24 bits
+//     under the tile's largest exponent (3 slices); 6 MMAs against the 3 slices of K_1 (one
+//     exponent) accumulate the diagonals 0..2; A^ = sum of the squared outputs and N^ = sum of the
+//     squared 24-bit inputs, each summed exactly in 64-bit integers per thread, each with a rigorous
+//     bound on its error (oz::part_bound with the per-output error 2^(Et + EP - 2060) and the
+//     per-input error 2^(Et - 1046)).  The last CTA decides the outcome where |u N^ - A^| exceeds
+//     twice the summed bound plus 1e-10 (A^ + N^), where the exact pass must decide the same way;
+//     otherwise it flags the exact pass.  N^ (within 2^-22 of the norm) renormalises block s+1's
+//     apply whichever pass decides: it scales the whole state, which no outcome depends on (every
+//     probability is a ratio of two sums over one state) and which the readout removes.
+// Tiles are fixed per CTA (b, b + grid, ...), so every per-thread sum, and so A^, N^ and the
+// outcome, are the same in every run.
+constexpr int kOzfOut = 3 * kOzSlab;   // outputs: A slices 3..6 (4 x 8 KiB = 2048 complex128)
+constexpr int kOzfSmem = 16 * (1 << kOzTileBits) + 2 * oz::kSlices * kOzSlab + 2 * oz::kSlices * 32 * 32 +
+                         2 * 3 * 32 * 32 + 4 * 128 + 4 * 32;
+
+__global__ void __launch_bounds__(256, 2) k_ozf(FusedArgs f) {
+  constexpr int TS = 1 << kOzTileBits;
+  extern __shared__ __align__(128) unsigned char osm[];
+  const uint32_t lmask = (1u << f.lb) - 1u;
+  double2* tile = reinterpret_cast<double2*>(osm);
+  uint16_t* A = reinterpret_cast<uint16_t*>(tile + TS);            // 7 slices x 128 rows x 32
+  double2* outb = reinterpret_cast<double2*>(A + kOzfOut);         // updated tile (slots as the tile)
+  uint16_t* BA = A + oz::kSlices * kOzSlab;                        // K_m / sqrt(N) of block s, 7 slices
+  uint16_t* BP = BA + oz::kSlices * 32 * 32;                       // K_1 of block s+1, 3 slices
+  int* rowE = reinterpret_cast<int*>(BP + 3 * 32 * 32);            // [128]
+  int* colE = rowE + 128;                                          // [32]
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_base;
+  __shared__ int s_err;
+  __shared__ double sred[64];
+  __shared__ int s_last;
+  __shared__ int s_eb[4];
+  __shared__ uint32_t s_emax[8];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  int qa[4], qas[4], qp[4], qps[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    qa[j] = f.qa[j];
+    qas[j] = f.qa_s[j];
+    qp[j] = f.qp[j];
+    qps[j] = f.qp_s[j];
+  }
+  // Tile slot of amplitude e (as in k_oz): linear over XOR, so slot(base | member) = slot(base) ^
+  // slot(member) for disjoint bits, and the 8 addresses of a half row are one base and 3 generators.
+  auto slot = [](uint32_t e) { return e ^ (((e >> 3) ^ (e >> 6) ^ (e >> 9)) & 7u); };
+  auto t2g = [&](uint32_t e) {   // tile index -> offset within the register (also linear over XOR)
+    const uint32_t h = e >> f.lb;
+    uint32_t o = 0;
+    for (int j = 0; j < f.nt - f.lb; ++j) o |= ((h >> j) & 1u) << f.hbits[j];
+    return o | (e & lmask);
+  };
+  // recombination: thread = (b-group r = its TMEM lane, half hf: amplitudes 8hf..8hf+7)
+  const int r = tid & 127, hf = tid >> 7;
+  // slicing: row sr, half sh; lanes l and l ^ 16 hold the two halves of a row
+  const int sr = 16 * warp + (tid & 15), sh = (tid >> 4) & 1;
+  uint32_t sa[3], spb[3], ga[3];   // generators: member bits 0..2 of block s (tile slot, register
+                                   // offset) and of block s+1 (tile slot)
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    sa[j] = slot(1u << qa[j]);
+    spb[j] = slot(1u << qp[j]);
+    ga[j] = t2g(1u << qa[j]);
+  }
+  const uint32_t rda0 = slot(local_base<4>((uint32_t)sr, qas)) ^ (sh ? slot(1u << qa[3]) : 0u);
+  const uint32_t rdp0 = slot(local_base<4>((uint32_t)sr, qps)) ^ (sh ? slot(1u << qp[3]) : 0u);
+  const uint32_t gb = local_base<4>((uint32_t)r, qas) | (hf ? (1u << qa[3]) : 0u);
+  const uint32_t sd0 = slot(gb), go0 = t2g(gb);
+  auto gen = [](uint32_t b0, const uint32_t (&g)[3], int l) {
+    return b0 ^ ((l & 1) ? g[0] : 0u) ^ ((l & 2) ? g[1] : 0u) ^ ((l & 4) ? g[2] : 0u);
+  };
+  uint32_t coff[TS / 256], cdst[TS / 256];   // this thread's copies: amplitude e = tid + 256 i, its slot
+#pragma unroll
+  for (int i = 0; i < TS / 256; ++i) {
+    coff[i] = t2g((uint32_t)tid + 256u * i);
+    cdst[i] = slot((uint32_t)tid + 256u * i);
+  }
+  const double2* src = reinterpret_cast<const double2*>(f.ap.src);
+  double2* dst = reinterpret_cast<double2*>(f.ap.dst);
+  const uint32_t ntile = 1u << f.nout;
+  auto tile_base = [&](uint32_t tix) {
+    uint32_t tb = 0;
+    for (int j = 0; j < f.nout; ++j) tb |= ((tix >> j) & 1u) << f.obits[j];
+    return tb;
+  };
+  auto load_tile = [&](uint32_t tb) {
+#pragma unroll
+    for (int i = 0; i < TS / 256; ++i) cp_async16(tile + cdst[i], src + (tb | coff[i]));
+    cp_async_commit();
+  };
+  uint32_t tix = blockIdx.x;
+  uint32_t tb = tix < ntile ? tile_base(tix) : 0u;
+  if (tix < ntile) load_tile(tb);
+  // B operands, overlapping the first copy: threads 0..127 the real embedding of K_m / sqrt(N) of
+  // block s (7 slices, each row under its own exponent), threads 128..255 that of K_1 of block s+1
+  // (3 slices, one exponent for all of it).  Thread = (row bn, reals 8 bkc .. 8 bkc + 7).
+  const bool isP = tid >= 128;
+  const int bn = (tid & 127) >> 2, bkc = tid & 3;
+  double bv[8];
+  int bE = 0;
+  {
+    const int br = bn >> 1;
+    const int m = isP ? 1 : *f.ap.m;
+    const double scale = isP ? 1.0 : 1.0 / sqrt(*f.ap.N);
+    const double2* Kg = reinterpret_cast<const double2*>(isP ? f.pr.kraus : f.ap.kraus) + (m ? 256 : 0);
+    const bool w2 = (isP ? f.pr.w : f.ap.w) == 2;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int l = 4 * bkc + j;
+      const double2 kv = !w2 ? Kg[br * 16 + l] : ((br >> 2) == (l >> 2) ? Kg[(br & 3) * 16 + (l & 3)] : make_double2(0.0, 0.0));
+      const double re = kv.x * scale, im = kv.y * scale;
+      bv[2 * j] = (bn & 1) ? im : re;
+      bv[2 * j + 1] = (bn & 1) ? re : -im;
+      bE = max(bE, max(oz::bexp(bv[2 * j]), oz::bexp(bv[2 * j + 1])));
+    }
+    bE = max(bE, __shfl_xor_sync(0xffffffffu, bE, 1));
+    bE = max(bE, __shfl_xor_sync(0xffffffffu, bE, 2));
+    if (isP) {
+      const int w = __reduce_max_sync(0xffffffffu, bE);
+      if (lane == 0) s_eb[warp - 4] = w;
+    }
+  }
+  if (tid == 0) {
+    s_err = 0;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(smem_u32(&tmem_base)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  __syncthreads();
+  const int EP = max(max(s_eb[0], s_eb[1]), max(s_eb[2], s_eb[3]));
+  {
+    uint64_t Xb[8];
+    if (!isP) {
+      if (bkc == 0) colE[bn] = bE;
+      put_slices8<oz::kSlices>(BA, 32 * 32, bn, 8 * bkc, bv, bE, Xb);
+    } else {
+      put_slices8<3>(BP, 32 * 32, bn, 8 * bkc, bv, EP, Xb);
+    }
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  tc_sync();
+  const uint32_t tmem = tmem_base;
+  const uint32_t mb = smem_u32(&mbar);
+  const uint32_t tlane = (uint32_t)(32 * (warp & 3)) << 16;
+  int cmin = 4095, cmax = 0;   // exponents of this thread's 16 outputs' B rows (nonzero rows for cmin)
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    const int e = colE[16 * hf + j];
+    if (e) cmin = min(cmin, e);
+    cmax = max(cmax, e);
+  }
+  uint32_t phase = 0;
+  double accA = 0.0, accN = 0.0, accE = 0.0;
+  while (tix < ntile) {
+    cp_async_wait<0>();
+    __syncthreads();
+    const uint32_t tnext = tix + gridDim.x;
+    // ---- 1. apply block s: digits of this thread's half row under the row's exponent
+    {
+      double x[16];
+      int E = 0;
+#pragma unroll
+      for (int l = 0; l < 8; ++l) {
+        const double2 v = tile[gen(rda0, sa, l)];
+        x[2 * l] = v.x;
+        x[2 * l + 1] = v.y;
+        E = max(E, max(oz::bexp(v.x), oz::bexp(v.y)));
+      }
+      E = max(E, __shfl_xor_sync(0xffffffffu, E, 16));
+      if (sh == 0) rowE[sr] = E;
+      uint64_t X0[8], X1[8];
+      put_slices8(A, kOzSlab, sr, 16 * sh, x, E, X0);
+      put_slices8(A, kOzSlab, sr, 16 * sh + 8, x + 8, E, X1);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    tc_sync();
+    // every thread has read its inputs: the tile buffer takes the next tile's copy
+    const uint32_t tbn = tnext < ntile ? tile_base(tnext) : 0u;
+    if (tnext < ntile) load_tile(tbn);
+    if (tid == 0) {   // the 14 MMAs of k_oz<OZ_APPLY>
+      const uint64_t da = umma_desc(smem_u32(A), 128, 512), db = umma_desc(smem_u32(BA), 128, 512);
+#pragma unroll
+      for (int p = 0; p < oz::kSlices; ++p)
+#pragma unroll
+        for (int ks = 0; ks < 2; ++ks)
+          umma_f16(tmem + 32u * p, da + ((2u * kOzSlab * p + 256u * ks) >> 4), db + ((256u * ks) >> 4),
+                   idesc_f16(32u * (oz::kSlices - p)), (p > 0 || ks > 0) ? 1u : 0u);
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mb) : "memory");
+    }
+    if (!mbar_wait(mb, phase & 1)) s_err = 1;
+    ++phase;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (s_err) break;
+    {
+      const int E = rowE[r];
+      const bool in_range = E == 0 || (E + cmin >= 1076 && E + cmax <= 2980);
+      uint32_t emax = 0;
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        uint32_t R[oz::kSlices][8];
+#pragma unroll
+        for (int t = 0; t < oz::kSlices; ++t) tmem_ld8_nowait(tmem + tlane + 32u * t + 16u * hf + 8u * c, R[t]);
+        tmem_wait_ld();
+#pragma unroll
+        for (int t = 0; t < oz::kSlices; ++t) reg_fence8(R[t]);
+#pragma unroll
+        for (int j = 0; j < 8; j += 2) {
+          float d0[oz::kSlices], d1[oz::kSlices];
+#pragma unroll
+          for (int t = 0; t < oz::kSlices; ++t) {
+            d0[t] = __uint_as_float(R[t][j]);
+            d1[t] = __uint_as_float(R[t][j + 1]);
+          }
+          const int n = 16 * hf + 8 * c + j, l = 4 * c + j / 2;
+          const double y0 = in_range ? oz::assemble7_cvt_inrange(d0, E, colE[n]) : oz::assemble7_cvt(d0, E, colE[n]);
+          const double y1 = in_range ? oz::assemble7_cvt_inrange(d1, E, colE[n + 1]) : oz::assemble7_cvt(d1, E, colE[n + 1]);
+          const double2 yv = make_double2(y0, y1);
+          dst[tb | gen(go0, ga, l)] = yv;
+          outb[gen(sd0, sa, l)] = yv;
+          emax = max(emax, max((uint32_t)(oz::d2u(y0) >> 32) & 0x7FF00000u, (uint32_t)(oz::d2u(y1) >> 32) & 0x7FF00000u));
+        }
+      }
+      emax = __reduce_max_sync(0xffffffffu, emax);
+      if (lane == 0) s_emax[warp] = emax;
+    }
+    __syncthreads();   // the updated tile and its exponent are in shared memory
+    // ---- 2. probability of block s+1: 24-bit digits under the tile's largest exponent
+    uint32_t em = s_emax[0];
+#pragma unroll
+    for (int w = 1; w < 8; ++w) em = max(em, s_emax[w]);
+    const int Et = max((int)(em >> 20), 24);   // >= 24: zero and subnormal reals give 0 digits
+    uint64_t nacc = 0;                         // sum of a^2 over this thread's 16 reals (< 2^52)
+#pragma unroll
+    for (int hh = 0; hh < 2; ++hh) {
+      uint64_t X[8];
+      uint32_t hw[8];
+#pragma unroll
+      for (int l = 0; l < 4; ++l) {
+        const double2 v = outb[gen(rdp0, spb, 4 * hh + l)];
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          const uint64_t u = oz::d2u(c ? v.y : v.x);
+          const uint32_t a = oz::top24(u, Et);   // < 2^24
+          X[2 * l + c] = (uint64_t)a << 32;
+          hw[2 * l + c] = (uint32_t)(u >> 32);
+          nacc += (uint64_t)a * a;
+        }
+      }
+      put_digits8<3>(A, kOzSlab, sr, 16 * sh + 8 * hh, X, hw);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    tc_sync();
+    if (tid == 0) {   // 6 MMAs: A slice p at TMEM column 32p against the stacked K_1 slices 0..2-p
+      const uint64_t da = umma_desc(smem_u32(A), 128, 512), db = umma_desc(smem_u32(BP), 128, 512);
+#pragma unroll
+      for (int p = 0; p < 3; ++p)
+#pragma unroll
+        for (int ks = 0; ks < 2; ++ks)
+          umma_f16(tmem + 32u * p, da + ((2u * kOzSlab * p + 256u * ks) >> 4), db + ((256u * ks) >> 4),
+                   idesc_f16(32u * (3 - p)), (p > 0 || ks > 0) ? 1u : 0u);
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mb) : "memory");
+    }
+    if (!mbar_wait(mb, phase & 1)) s_err = 1;
+    ++phase;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (s_err) break;
+    uint64_t aacc = 0;   // sum of Zt^2 over this thread's 16 outputs of K_1 (< 2^62)
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      uint32_t R[3][8];
+#pragma unroll
+      for (int t = 0; t < 3; ++t) tmem_ld8_nowait(tmem + tlane + 32u * t + 16u * hf + 8u * c, R[t]);
+      tmem_wait_ld();
+#pragma unroll
+      for (int t = 0; t < 3; ++t) reg_fence8(R[t]);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const float D[3] = {__uint_as_float(R[0][j]), __uint_as_float(R[1][j]), __uint_as_float(R[2][j])};
+        const int64_t z = oz::combine3(D);
+        aacc += (uint64_t)(z * z);
+      }
+    }
+    // this tile's per-thread sums in FP64: N^ = nacc 2^(2(Et - 1046)), A^ = aacc 2^(2(Et + EP - 2068)),
+    // with their bounds (16 inputs each off by less than 2^(Et - 1046); 16 outputs each off by less
+    // than 2^(Et + EP - 2060))
+    const double nth = oz::scale2((double)nacc, 2 * (Et - 1046));
+    const double ath = EP ? oz::scale2((double)aacc, 2 * (Et + EP - 2068)) : 0.0;
+    accN += nth;
+    accA += ath;
+    accE += oz::part_bound(nth, Et + 1015) + (EP ? oz::part_bound(ath, Et + EP) : 0.0);
+    // no barrier here: the next tile's MMAs are issued after its slicing barrier (tc_sync), which
+    // every thread reaches after these TMEM loads; the loop-top barrier protects rowE and s_emax
+    tb = tbn;
+    tix = tnext;
+  }
+  cp_async_wait<0>();   // a copy still in flight after an early exit
+  tc_sync();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem));
+  if (s_err && tid == 0) atomicOr(&f.pr.ctl->status, 1u);
+  prob_finish_bounded(f.pr, accA, accN, accE, sred, &s_last, true);
 }
 
 // ---- final Z readout (Sec. III.B): sequential per-qubit sampling -------------------------
@@ -1568,6 +1897,48 @@ cudaError_t launch_prob_oz(const PassArgs& ap, int num_sms, cudaStream_t s) {
   return e != cudaSuccess ? e : launch_oz(OZ_PROB, true, ap, num_sms, s);
 }
 
+bool fused_oz_applies(const PassArgs& ap, const PassArgs& pr) {
+  if ((ap.w != 2 && ap.w != 4) || (pr.w != 2 && pr.w != 4)) return false;
+  FusedArgs f;
+  block_tile(ap, pr, 3, kOzTileBits, f);
+  return f.nt == kOzTileBits;
+}
+
+// A weight-2 block's spectators: the two lowest tile bits outside it; q[0..3] then holds its two
+// qubits and the spectators, qs the same bits sorted.
+static void oz_block_bits(int w, int* q, int* qs, int nt) {
+  if (w == 2) {
+    int k = 2;
+    for (int b = 0; b < nt && k < 4; ++b)
+      if (b != q[0] && b != q[1]) q[k++] = b;
+  }
+  for (int j = 0; j < 4; ++j) qs[j] = q[j];
+  std::sort(qs, qs + 4);
+}
+
+cudaError_t launch_fused_oz(const PassArgs& ap, const PassArgs& pr, int num_sms, cudaStream_t s) {
+  FusedArgs f;
+  f.ap = ap;
+  f.pr = pr;
+  f.skip_unless_uncertain = 0;
+  block_tile(ap, pr, 3, kOzTileBits, f);
+  if ((ap.w != 2 && ap.w != 4) || (pr.w != 2 && pr.w != 4) || f.nt != kOzTileBits) return cudaErrorInvalidValue;
+  oz_block_bits(ap.w, f.qa, f.qa_s, f.nt);
+  oz_block_bits(pr.w, f.qp, f.qp_s, f.nt);
+  int64_t g = 2ll * num_sms;   // two CTAs per SM: 109 KiB of shared memory and 256 TMEM columns each
+  if (g > (1ll << f.nout)) g = 1ll << f.nout;
+  if (3 * g > 2 * MAX_PASS_GRID) g = 2 * MAX_PASS_GRID / 3;   // 3 partial sums per CTA
+  f.grid = (int)g;
+  k_ozf<<<f.grid, 256, kOzfSmem, s>>>(f);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prob_oz_check(const PassArgs& pr, int num_sms, cudaStream_t s) {
+  PassArgs a = pr;
+  a.store_n = 0;   // the fused pass's norm estimate stays
+  return launch_oz(OZ_PROB, true, a, num_sms, s);
+}
+
 cudaError_t launch_wait_selftest(unsigned int* status, long limit, cudaStream_t s) {
   k_wait_selftest<<<1, 32, 0, s>>>(status, limit);
   return cudaGetLastError();
@@ -1596,6 +1967,8 @@ cudaError_t setup_kernels(int precision, int D) {
     oz_attrs((const void*)k_oz<OZ_APPLY>);
     oz_attrs((const void*)k_oz<OZ_PROB>);
     oz_attrs((const void*)k_oz<OZ_PROB_BOUND>);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute((const void*)k_ozf, cudaFuncAttributeMaxDynamicSharedMemorySize, kOzfSmem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute((const void*)k_ozf, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     return e;
   }
   cudaError_t e = cudaFuncSetAttribute(k_sample<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);

@@ -64,6 +64,8 @@ struct PassArgs {
   int syn_stride;         // bytes per trajectory
   int syn_idx;            // round * nstab + stab
   int offset;             // syndrome = raw ^ offset
+  int store_n = 1;        // 0: the pass leaves *N as it is (the exact pass after a fused tensor-core
+                          // complex128 pass, whose norm estimate renormalises the state)
 };
 
 // Fused pass: apply block s (ap) and accumulate the probability of block s+1 (pr) on tiles
@@ -80,6 +82,8 @@ struct FusedArgs {
                           // complex128 passes: a weight-2 block's two qubits, then two spectators)
   int qp[4];              // probability block's qubits as tile-index bits (ascending; the
                           // tensor-core complex128 passes: qa sorted)
+  int qa_s[4], qp_s[4];   // fused tensor-core complex128 pass: qa and qp (each with its own
+                          // spectators) sorted ascending, for the group base addresses
   int skip_unless_uncertain;   // exact tensor-core probability pass: run only if ctl->prob_uncertain
   int grid;
 };
@@ -113,6 +117,13 @@ cudaError_t launch_wait_selftest(unsigned int* status, long limit, cudaStream_t 
 bool apply_oz_applies(const PassArgs& ap);
 cudaError_t launch_apply_oz(const PassArgs& ap, int num_sms, cudaStream_t s);
 cudaError_t launch_prob_oz(const PassArgs& ap, int num_sms, cudaStream_t s);   // once per process/device, before any capture
+// Fused tensor-core complex128 pass: apply block `ap`, then block `pr`'s bounded probability on the
+// same tiles, then the exact probability launch that runs only if the bound left the outcome open.
+// Both blocks' qubits must fit one 2^11-amplitude tile (fused_oz_applies).
+bool fused_oz_applies(const PassArgs& ap, const PassArgs& pr);
+cudaError_t launch_fused_oz(const PassArgs& ap, const PassArgs& pr, int num_sms, cudaStream_t s);
+// The exact probability launch of block pr after a fused pass (returns at once unless needed).
+cudaError_t launch_prob_oz_check(const PassArgs& pr, int num_sms, cudaStream_t s);
 int pass_grid(int D, int w, int num_sms);
 // One wave of resident CTAs for the probability (prob = true) or apply pass kernel.
 int pass_grid_for(int precision, bool prob, int D, int w, int num_sms);

@@ -55,11 +55,8 @@ struct Carve {
   }
 };
 
-}  // namespace
-
-extern "C" qec_status qec_run_trajectories_noalloc(const qec_params* params, uint64_t seed, uint64_t first_traj,
-                                                   uint32_t n, uint8_t* d_syndromes, uint8_t* d_data_bits,
-                                                   uint8_t* d_raw_logical, void* cuda_stream) {
+qec_status run_noalloc(const qec_params* params, uint64_t seed, uint64_t first_traj, uint32_t n,
+                       uint8_t* d_syndromes, uint8_t* d_data_bits, uint8_t* d_raw_logical, void* cuda_stream) {
   if (!params) return nfail(QEC_EINVAL, "null params");
   std::string err;
   if (!validate_params(*params, err)) return nfail(QEC_EINVAL, err);
@@ -109,7 +106,8 @@ extern "C" qec_status qec_run_trajectories_noalloc(const qec_params* params, uin
   const size_t o_kraus = c.take((size_t)nblk * KRAUS_STRIDE * amp);
   const size_t o_u = c.take(sizeof(double) * nblk), o_A = c.take(sizeof(double) * nblk);
   const size_t o_N = c.take(sizeof(double) * nblk), o_m = c.take(sizeof(int) * nblk);
-  const size_t o_part = c.take(sizeof(double) * 2 * pgrid), o_ctl = c.take(sizeof(Ctl));
+  const size_t o_part = c.take(sizeof(double) * 2 * (pgrid > MAX_PASS_GRID ? pgrid : MAX_PASS_GRID));
+  const size_t o_ctl = c.take(sizeof(Ctl));
   const size_t o_hp = c.take(sizeof(double) * ((size_t)hgrid << k1)), o_h = c.take(sizeof(double) << k1);
   if (c.off > kNoAllocBytes) return nfail(QEC_EINVAL, "request does not fit the 2 MiB static scratch");
 
@@ -179,24 +177,40 @@ extern "C" qec_status qec_run_trajectories_noalloc(const qec_params* params, uin
     return a;
   };
 
+  // The same launches, grids and kernel sequence as qec_create / qec_run_trajectories, so that the
+  // reductions add in the same order and the results are identical: probability then apply per
+  // block for complex128; for complex64 each block's apply pass fused with the next block's
+  // probability pass.  (At d <= 3 the tensor-core passes do not apply: their tiles are larger than
+  // the register.)
+  auto prob = [&](const PassArgs& a) { return launch_prob(prec, a, pass_grid_for(prec, true, D, a.w, sms), st); };
+  auto apply = [&](const PassArgs& a) { return launch_apply(prec, a, pass_grid_for(prec, false, D, a.w, sms), st); };
+  const bool fused = !is_f64(prec);
   // Noise-free init round with outcomes forced to the zero syndrome (Sec. III.B), in psi0.
   e = launch_set_basis0(prec, psi0, D, st);
   if (e == cudaSuccess) e = launch_instantiate(prec, inst(0, 0, nstab, false), st);
   for (int k = 0; k < nstab && e == cudaSuccess; ++k) {
     PassArgs a = pass(init_prog, k, psi0, true, nullptr, 0);
     a.dst = psi0;
-    const int g = pass_grid(D, a.w, sms);
-    e = launch_prob(prec, a, g, st);
-    if (e == cudaSuccess) e = launch_apply(prec, a, g, st);
+    e = prob(a);
+    if (e == cudaSuccess) e = apply(a);
   }
+  auto traj_pass = [&](int b) {
+    const int rnd = 1 + b / nstab, k = b % nstab;
+    return pass(prog, b, b == 0 ? psi0 : psi, false, d_syndromes, rnd * nstab + k);
+  };
   for (uint32_t t = 0; t < n && e == cudaSuccess; ++t) {
     if (S > 0) e = launch_instantiate(prec, inst(1, 1, S, true), st);
+    if (S > 0 && e == cudaSuccess) e = prob(traj_pass(0));
     for (int b = 0; b < S && e == cudaSuccess; ++b) {
-      const int rnd = 1 + b / nstab, k = b % nstab;
-      PassArgs a = pass(prog, b, b == 0 ? psi0 : psi, false, d_syndromes, rnd * nstab + k);
-      const int g = pass_grid(D, a.w, sms);
-      e = launch_prob(prec, a, g, st);
-      if (e == cudaSuccess) e = launch_apply(prec, a, g, st);
+      const PassArgs a = traj_pass(b);
+      if (fused && b + 1 < S) {
+        PassArgs nx = traj_pass(b + 1);
+        nx.src = psi;
+        e = launch_fused(prec, a, nx, sms, st);
+        continue;
+      }
+      e = apply(a);
+      if (e == cudaSuccess && !fused && b + 1 < S) e = prob(traj_pass(b + 1));
     }
     if (e != cudaSuccess) break;
     ReadArgs r;
@@ -218,4 +232,16 @@ extern "C" qec_status qec_run_trajectories_noalloc(const qec_params* params, uin
   }
   if (e != cudaSuccess) return nfail(QEC_ECUDA, std::string("launch: ") + cudaGetErrorString(e));
   return QEC_OK;
+}
+
+}  // namespace
+
+extern "C" qec_status qec_run_trajectories_noalloc(const qec_params* params, uint64_t seed, uint64_t first_traj,
+                                                   uint32_t n, uint8_t* d_syndromes, uint8_t* d_data_bits,
+                                                   uint8_t* d_raw_logical, void* cuda_stream) {
+  try {
+    return run_noalloc(params, seed, first_traj, n, d_syndromes, d_data_bits, d_raw_logical, cuda_stream);
+  } catch (...) {   // a host allocation of the circuit program failed: nothing crosses the C ABI
+    return nfail(QEC_ENOMEM, "exception in qec_run_trajectories_noalloc");
+  }
 }

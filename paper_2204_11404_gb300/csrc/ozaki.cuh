@@ -196,6 +196,32 @@ OZ_HD int64_t combine5(const float* D) {
   return (int64_t)H * (1 << 24) + ((int64_t)M * 256 + (int64_t)small_float_int(D[4]));
 }
 
+// The fused pass's probability inputs: the top 24 bits of |x|'s significand (implicit bit included)
+// aligned to the tile's largest biased exponent Et (>= 24, so that zero and subnormal x give 0):
+// |x| = 2^(Et - 1046) (a + rho) with a < 2^24 and 0 <= rho < 1.  Its 3 digits are its bytes 2, 1, 0.
+OZ_HD uint32_t top24(uint64_t u, int Et) {
+  const uint32_t hi = (uint32_t)(u >> 32), lo = (uint32_t)u;
+  const int ex = (int)((hi >> 20) & 0x7FFu);
+  const uint32_t mh = (hi & 0xFFFFFu) | 0x100000u;
+#if defined(__CUDA_ARCH__)
+  const uint32_t m24 = __funnelshift_l(lo, mh, 3);
+#else
+  const uint32_t m24 = (mh << 3) | (lo >> 29);
+#endif
+  const int k = Et - ex;
+  return m24 >> (k < 31 ? k : 31);
+}
+
+// The fused pass's probability recombination keeps 3 slices of each operand (24-bit integers a and
+// b) and only the diagonals t <= 2: Zt = round((D_0 2^32 + D_1 2^24 + D_2 2^16) / 2^24)
+// = D_0 2^8 + D_1 + round(D_2 / 2^8).  D_0 < 2^21 and D_1 < 2^22 convert exactly by the magic number,
+// D_2 / 2^8 (< 2^15, exact in FP32) is rounded to nearest; |Zt| < 2^29.  Against the exact product a b
+// / 2^24 it is off by the dropped diagonals 3 and 4 (below 32 * 255^2 * 513 < 2^30 units of 2^-24) and
+// the rounding (1/2).
+OZ_HD int32_t combine3(const float* D) {
+  return small_float_int(D[0]) * 256 + small_float_int(D[1]) + small_float_int(D[2] * 0x1p-8f);
+}
+
 // 2^e1 + 2^e2 rounded up to an FP64 value, built in the exponent and mantissa fields (no FP64
 // arithmetic); at least the smallest normal number, infinity above the range.
 OZ_HD double pow2_sum_up(int e1, int e2) {

@@ -114,6 +114,18 @@ class BatchSimulator:
         n, t, k, nz = self._inputs(traj, kind, noise)
         return capi.qec_batch_autotune(self.h, seed, n, t.ctypes.data, k.ctypes.data, ctypes.addressof(nz))
 
+    def snapshot(self, item):
+        """Record the final data-register state of trajectory `item` (index into the next run's
+        arrays; -1 = none) during the next run."""
+        capi.qec_batch_snapshot(self.h, int(item))
+
+    def state(self):
+        """The normalised 2^9-amplitude data-register state recorded by the last run with a
+        snapshot item (complex128)."""
+        out = np.zeros(1 << 9, dtype=np.complex128)
+        capi.qec_batch_get_state(self.h, out.ctypes.data, out.nbytes)
+        return out
+
     def last_ms(self):
         return capi.qec_batch_last_ms(self.h)
 

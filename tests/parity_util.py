@@ -33,3 +33,25 @@ def compare_trajectory(gpu_syn, gpu_bits, o, tau):
             assert abs(u - p1) < tau, "mismatch at %s: u=%.17g P(1)=%.17g" % (key, u, p1)
             return "ambiguous"
     raise AssertionError("outputs differ but no measurement differs")
+
+
+def min_margin(o):
+    """Smallest |u - P(1)| over every measurement of an oracle trajectory (ancillas and readout).
+    A trajectory whose margin is at least TAU[form] has no draw that another summation order may
+    legitimately decide differently, so its outcomes and amplitudes must match outright."""
+    m = [abs(u - p1) for (rnd, _, u, p1, _) in o["anc_records"] if rnd > 0]   # round 0: outcomes forced
+    m += [abs(u - p1) for (_, u, p1, _) in o["readout_records"]]
+    return min(m) if m else float("inf")
+
+
+def unambiguous(oracle_fn, candidates, tau, count=1):
+    """The first `count` trajectory indices among `candidates` whose oracle run (oracle_fn(traj),
+    computed with want_state=True) has no near-threshold draw; returns [(traj, oracle result)]."""
+    out = []
+    for t in candidates:
+        o = oracle_fn(t)
+        if min_margin(o) >= tau:
+            out.append((t, o))
+            if len(out) == count:
+                return out
+    raise AssertionError("no trajectory without a near-threshold draw among %r" % (list(candidates),))

@@ -6,7 +6,7 @@ import pytest
 
 import workloads as W
 from oracle import run_trajectory
-from parity_util import TAU, compare_trajectory
+from parity_util import AMP_TOL, TAU, compare_trajectory, unambiguous
 
 pytestmark = pytest.mark.gpu
 
@@ -101,3 +101,32 @@ def test_batched_sign_follows_variant_matches_oracle():
             assert kind == "exact", (i, kinds[i])
         amb += kind == "ambiguous"
     assert amb <= 2
+
+
+@pytest.mark.parametrize("gates", ["cr", "cnot"])
+def test_batched_amplitudes_match_oracle(gates):
+    """The state of one trajectory of each kind (10 and 17 qubits x complex128 and complex64),
+    recorded inside a mixed batch, against the oracle's state of the same trajectory: within
+    1e-12 (complex128) and 2e-5 (complex64) max-abs.  The unreduced register's data state (every
+    ancilla |0> after the round) is compared with the oracle's unreduced run."""
+    n = 48
+    kinds = ["c128", "c64", "c128u", "c64u"] * (n // 4)
+    noise = [dict(W.STRESS) if i % 2 else dict(p1=0.01, p2=0.01, p_idle=0.01, theta_rx=0.08, phi_zz=0.03)
+             for i in range(n)]
+    traj = [700 + i for i in range(n)]
+    with BatchSimulator(3, gates, max_traj=64) as b:
+        for k, kind in enumerate(("c128", "c64", "c128u", "c64u")):
+            layout = "unreduced" if kind.endswith("u") else "reduced"
+            prec = kind.rstrip("u")
+            cand = [i for i in range(n) if kinds[i] == kind]
+            [(item, o)] = unambiguous(
+                lambda i: run_trajectory(3, 3, gates, layout, noise[i], seed=95, traj=traj[i], want_state=True),
+                cand, TAU[prec])
+            b.snapshot(item)
+            syn, bits, log = b.run(95, traj, kinds, noise)
+            assert compare_trajectory(syn[item], bits[item], o, TAU[prec]) == "exact"
+            ref = o["state"][: 1 << 9]
+            assert np.abs(o["state"][1 << 9:]).max() < 1e-15     # every ancilla |0> after the round
+            err = np.abs(b.state() - ref).max()
+            assert err < AMP_TOL[prec], (kind, err)
+        b.snapshot(-1)

@@ -7,7 +7,7 @@ import pytest
 
 import workloads as W
 from oracle import run_trajectory
-from parity_util import AMP_TOL, TAU, compare_trajectory
+from parity_util import AMP_TOL, TAU, compare_trajectory, min_margin
 
 pytestmark = pytest.mark.gpu
 
@@ -21,12 +21,14 @@ from paper_2204_11404_gb300.simulator import Simulator  # noqa: E402
 def test_tensor_core_form_matches_oracle_two_rounds():
     pt = dict(W.STRESS)
     o = run_trajectory(5, 2, "cr", "reduced", pt, seed=42, traj=3, want_state=True)
+    # no draw of this trajectory lies within 1e-4 of its probability (margin 0.031), so the
+    # complex64 form must match its outcomes exactly and its amplitudes within 2e-5
+    assert min_margin(o) >= TAU["c64tc"]
     with Simulator(5, 2, "cr", "c64tc", **pt) as sim:
         syn, bits, log = sim.run(42, 3, 1)
-        kind = compare_trajectory(syn[0], bits[0], o, TAU["c64tc"])
-        if kind == "exact":
-            err = np.abs(sim.state() - o["state"][: 1 << 25]).max()
-            assert err < AMP_TOL["c64tc"], err
+        assert compare_trajectory(syn[0], bits[0], o, TAU["c64tc"]) == "exact"
+        err = np.abs(sim.state() - o["state"][: 1 << 25]).max()
+        assert err < AMP_TOL["c64tc"], err
 
 
 def test_tensor_core_form_agrees_with_cuda_core_form():
@@ -76,10 +78,11 @@ def test_emulated_fp64_form_on_d3_uses_fp64_passes():
 
 
 def test_bounded_probability_pass_decides_like_the_exact_pass():
-    """c128tc decides most outcomes from a 3-slice probability with a rigorous error bound. Sending
-    every outcome through the exact pass instead changes no outcome and no amplitude bit (N is
-    computed by the same code in both passes), and the exact pass runs only when forced or when
-    the bound leaves the outcome open (rare)."""
+    """c128tc decides most outcomes from a 24-bit probability with a rigorous error bound (in the
+    pass fused with the previous block's apply, and in the first block's own bounded pass).
+    Sending every outcome through the exact pass instead changes no outcome and no amplitude bit
+    (the exact pass decides the outcome but leaves the norm that renormalises the next apply), and
+    the exact pass runs only when forced or when the bound leaves the outcome open (rare)."""
     from paper_2204_11404_gb300 import capi
     pts = W.D5_CR["points"]
     for i in (2, 8):
@@ -115,3 +118,34 @@ def test_emulated_fp64_form_is_bit_reproducible():
         assert (x == y).all() and (x == z).all()
     assert np.array_equal(s1.view(np.uint64), s2.view(np.uint64))
     assert np.array_equal(s1.view(np.uint64), s3.view(np.uint64))
+
+
+def test_fused_pass_matches_separate_passes_and_oracle_on_stress_noise():
+    """The fused tensor-core pass (block s's apply and block s+1's probability on the same tiles)
+    against the FP64 oracle on the stress noise at d=5, where every noise channel and coherent term
+    is on: outcomes identical, amplitudes within 1e-12; and against the FP64 CUDA-core form on the
+    same trajectories: identical outcomes, states within 1e-13."""
+    pt = dict(W.STRESS)
+    o = run_trajectory(5, 2, "cr", "reduced", pt, seed=42, traj=3, want_state=True)
+    with Simulator(5, 2, "cr", "c128tc", **pt) as a, Simulator(5, 2, "cr", "c128", **pt) as b:
+        ra = a.run(42, 3, 1)
+        assert compare_trajectory(ra[0][0], ra[1][0], o, TAU["c128tc"]) == "exact"
+        assert np.abs(a.state() - o["state"][: 1 << 25]).max() < AMP_TOL["c128tc"]
+        ra = a.run(42, 10, 3)
+        rb = b.run(42, 10, 3)
+        for x, y in zip(ra, rb):
+            assert (x == y).all()
+        assert np.abs(a.state() - b.state()).max() < 1e-13
+
+
+def test_fused_pass_on_repetition_code():
+    """Weight-2 blocks in the fused pass (K (x) I over spectator qubits of the union tile): the
+    d=25 repetition code against the FP64 CUDA-core form."""
+    pt = dict(p1=0.01, p2=0.01, p_idle=0.01, theta_rx=0.05, phi_zz=0.02)
+    with Simulator(25, 2, "cr", "c128tc", code="repetition", **pt) as a, \
+            Simulator(25, 2, "cr", "c128", code="repetition", **pt) as b:
+        ra = a.run(8, 0, 2)
+        rb = b.run(8, 0, 2)
+        for x, y in zip(ra, rb):
+            assert (x == y).all()
+        assert np.abs(a.state() - b.state()).max() < 1e-13

@@ -67,7 +67,7 @@ def test_zero_and_single_term_rows_are_exact(variant):
     assert out[1, 5] == A[1, 5] and np.count_nonzero(out[1]) == 1
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4])
 def test_largest_digits_recombine_exactly(variant):
     """Every 8-bit digit at 255 (mantissas of all ones, one exponent per row) drives each diagonal to
     its largest value, (t + 1) * 32 * 255^2: the 32-bit pieces of the recombination must not overflow.
@@ -93,12 +93,15 @@ def test_largest_digits_recombine_exactly(variant):
                 assert err <= Fraction(2.0 ** -42) * Fraction(big) ** 4 * 32 + a_ex * Fraction(2.0 ** -50), r
             else:
                 assert err <= Fraction(out[r, 1]), (r, float(err), out[r, 1])
+            if variant == 4:
+                n_ex = sum((Fraction(float(v)) ** 2 for v in A[r]), Fraction(0))
+                assert abs(Fraction(out[r, 2]) - n_ex) <= Fraction(out[r, 3]), r
 
 
 def test_bad_variant_rejected():
     a = np.zeros((1, 32))
     with pytest.raises(capi.QecError):
-        capi.qec_debug_ozaki_gemm(a.ctypes.data, np.zeros((32, 32)).ctypes.data, 1, 4, a.ctypes.data)
+        capi.qec_debug_ozaki_gemm(a.ctypes.data, np.zeros((32, 32)).ctypes.data, 1, 5, a.ctypes.data)
 
 
 @pytest.mark.parametrize("seed", [0, 3])
@@ -150,3 +153,55 @@ def test_bounded_probability_sum_contains_the_exact_value(seed):
         assert err <= Fraction(out[r, 1]) + Fraction(2.0 ** -1074), (r, float(err), out[r, 1])
         if float(a_ex) > 1e-200:
             assert out[r, 1] <= 1e-3 * float(a_ex), (r, out[r, 1], float(a_ex))
+
+
+def _unitary_embedding(rng, zero_row=None, small_row=None):
+    q, _ = np.linalg.qr(rng.standard_normal((16, 16)) + 1j * rng.standard_normal((16, 16)))
+    if zero_row is not None:
+        q[zero_row] = 0.0
+    if small_row is not None:
+        q[small_row] *= 1e-9
+    B = np.zeros((32, 32))
+    B[0::2, 0::2], B[0::2, 1::2] = q.real, -q.imag
+    B[1::2, 0::2], B[1::2, 1::2] = q.imag, q.real
+    return np.ascontiguousarray(B)
+
+
+@pytest.mark.parametrize("seed", [0, 4, 8])
+def test_fused_probability_bounds_contain_the_exact_values(seed):
+    """Variant 4, the fused pass's probability: the whole A is one tile under one exponent, each real
+    cut to 24 bits, 3 slices, diagonals 0..2.  Per row, |sum_n (A[r] . B[n])^2 - A^| and
+    |sum_k A[r][k]^2 - N^| must lie within the returned bounds, whatever the row's scale (zero rows,
+    rows far below the tile's largest value, subnormals)."""
+    rng = np.random.default_rng(seed)
+    m = 16
+    A = _rows(rng, m)
+    B = _unitary_embedding(rng, zero_row=5, small_row=6)
+    out = np.zeros((m, 32))
+    capi.qec_debug_ozaki_gemm(A.ctypes.data, B.ctypes.data, m, 4, out.ctypes.data)
+    ex = _exact(A, B)
+    tiny = Fraction(2.0 ** -1074)
+    for r in range(m):
+        a_ex = sum((v * v for v in ex[r]), Fraction(0))
+        n_ex = sum((Fraction(float(v)) ** 2 for v in A[r]), Fraction(0))
+        assert abs(Fraction(out[r, 0]) - a_ex) <= Fraction(out[r, 1]) + tiny, (r, out[r, 0], float(a_ex), out[r, 1])
+        assert abs(Fraction(out[r, 2]) - n_ex) <= Fraction(out[r, 3]) + tiny, (r, out[r, 2], float(n_ex), out[r, 3])
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_fused_probability_bound_is_tight_on_an_ordinary_tile(seed):
+    """On a tile whose amplitudes share one scale (the code state's equal magnitudes with noise
+    spread), the summed bounds stay below 2e-4 of A + N (measured: 6e-5; the per-output bound takes
+    all 32 terms at their largest magnitudes), so the outcome is left to the exact pass only for
+    draws within about 1e-4 of their probability."""
+    rng = np.random.default_rng(seed)
+    m = 128
+    A = rng.standard_normal((m, 32)) / 64
+    A[rng.random((m, 32)) < 0.5] *= 1e-3
+    B = _unitary_embedding(rng)
+    out = np.zeros((m, 32))
+    capi.qec_debug_ozaki_gemm(A.ctypes.data, B.ctypes.data, m, 4, out.ctypes.data)
+    a_sum, n_sum = out[:, 0].sum(), out[:, 2].sum()
+    assert abs(a_sum - float(((A @ B.T) ** 2).sum())) <= out[:, 1].sum()
+    assert abs(n_sum - float((A ** 2).sum())) <= out[:, 3].sum()
+    assert out[:, 1].sum() + out[:, 3].sum() < 2e-4 * (a_sum + n_sum)

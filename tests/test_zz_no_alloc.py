@@ -3,9 +3,13 @@
 qec_run_trajectories_noalloc serves callers that cannot call cudaMalloc (a
 framework that owns all device memory through its own pool, a latency-critical
 path that cannot take cudaMalloc's implicit synchronisation, a plug-in handed
-only a stream and output buffers).  Its outputs are integers, so they must
-equal qec_run_trajectories' bit for bit; two calls in a row check that the
-shared static scratch carries nothing over from the previous call.  This file
+only a stream and output buffers).  It launches the same kernels, with the
+same grids and in the same order, as qec_run_trajectories (for complex64 the
+apply pass fused with the next block's probability pass), so its outputs,
+which are integers, must equal qec_run_trajectories' bit for bit in every
+precision, on the stress noise where many draws fall near their thresholds.
+Calls in a row with different settings check that the shared static scratch
+carries nothing over from the previous call.  This file
 is collected last so a failure here cannot hide failures elsewhere.
 """
 import numpy as np
@@ -35,9 +39,12 @@ def noalloc_run(params, seed, first, n):
     return syn.cpu().numpy(), bits.cpu().numpy(), log.cpu().numpy()
 
 
-CASES = [  # two calls in a row with different settings, then a repeat of the first
+CASES = [  # calls in a row with different settings, then a repeat of the first
     dict(d=3, rounds=3, gates="cr", precision="c128", seed=11, first=0, n=64),
     dict(d=3, rounds=16, gates="cnot", precision="c64", seed=12, first=500, n=24),
+    dict(d=3, rounds=3, gates="cr", precision="c64", seed=13, first=0, n=64),
+    dict(d=3, rounds=5, gates="cr", precision="c64tc", seed=14, first=90, n=48),
+    dict(d=3, rounds=4, gates="cnot", precision="c128tc", seed=15, first=7, n=32),
     dict(d=3, rounds=3, gates="cr", precision="c128", seed=11, first=0, n=64),
 ]
 

@@ -623,7 +623,7 @@ static void ozaki_fused_prob(const double* A, const double* B, int m, double* ou
     for (int p = 0; p < 3; ++p) db[(size_t)i * 3 + p] = (neg ? -1 : 1) * (int)((X >> (48 - 8 * p)) & 0xFF);
   }
   for (int r = 0; r < m; ++r) {
-    double sa = 0.0, ea = 0.0, sn = 0.0, en = 0.0;
+    oz::FusedSums sums;   // the row's two threads' sums, as the kernel's threads accumulate them
     for (int h = 0; h < 2; ++h) {   // a thread's 16 outputs n = 16h..16h+15 and 16 inputs k = 16h..16h+15
       uint64_t aacc = 0, nacc = 0;
       for (int n = 16 * h; n < 16 * h + 16; ++n) {
@@ -640,13 +640,10 @@ static void ozaki_fused_prob(const double* A, const double* B, int m, double* ou
         const uint64_t a = a24[(size_t)r * 32 + n];
         nacc += a * a;
       }
-      const double nth = oz::scale2((double)nacc, 2 * (Et - 1046));
-      const double ath = EP ? oz::scale2((double)aacc, 2 * (Et + EP - 2068)) : 0.0;
-      sn += nth;
-      sa += ath;
-      en += oz::part_bound(nth, Et + 1015);
-      ea += EP ? oz::part_bound(ath, Et + EP) : 0.0;
+      sums.add_tile(nacc, aacc, Et, EP);
     }
+    double sn, en, sa, ea;
+    sums.finish(sn, en, sa, ea);
     out[r * 32] = sa;
     out[r * 32 + 1] = ea;
     out[r * 32 + 2] = sn;
@@ -673,7 +670,7 @@ qec_status qec_debug_ozaki_gemm(const double* A, const double* B, int32_t m, int
   for (int n = 0; n < 32; ++n) {
     int E = 0;
     for (int k = 0; k < 32; ++k) E = std::max(E, oz::bexp(B[n * 32 + k]));
-    eb[n] = variant >= 2 ? EB : E;
+    eb[n] = (variant == 2 || variant == 3) ? EB : E;
     for (int k = 0; k < 32; ++k) oz::split7(B[n * 32 + k], eb[n], &db[((size_t)n * 32 + k) * oz::kSlices]);
   }
   for (int r = 0; r < m; ++r) {

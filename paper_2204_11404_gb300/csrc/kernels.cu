@@ -1214,9 +1214,10 @@ __global__ void __launch_bounds__(256, 2) k_oz(FusedArgs f) {
 // The tile holds both blocks' qubits (at most 8) and the lowest register bits: 2^11 amplitudes.  Per
 // tile, on 256 threads, two CTAs per SM:
 //  1. Apply block s exactly as k_oz<OZ_APPLY> does (7 slices under each group's exponent, 14 MMAs,
-//     integer recombination, one rounding to FP64).  The results go to the register and, on chip,
-//     into the A-operand slices 3..6 (free once the MMAs have read them), so the tile buffer takes
-//     the next tile's copy as soon as this tile's digits are written.
+//     integer recombination, one rounding to FP64).  The results go, on chip, into the A-operand
+//     slices 3..6 (free once the MMAs have read them), so that the tile buffer takes the next tile's
+//     copy as soon as this tile's digits are written; from there they are stored to the register
+//     in whole 128-byte runs.
 //  2. Probability of block s+1 on the updated tile (Sec. II.B: the ancilla is |0> again, so the
 //     next measurement is a quadratic form of this state).  Every real is cut to its top 24 bits
 //     under the tile's largest exponent (3 slices); 6 MMAs against the 3 slices of K_1 (one
@@ -1274,27 +1275,28 @@ __global__ void __launch_bounds__(256, 2) k_ozf(FusedArgs f) {
   const int r = tid & 127, hf = tid >> 7;
   // slicing: row sr, half sh; lanes l and l ^ 16 hold the two halves of a row
   const int sr = 16 * warp + (tid & 15), sh = (tid >> 4) & 1;
-  uint32_t sa[3], spb[3], ga[3];   // generators: member bits 0..2 of block s (tile slot, register
-                                   // offset) and of block s+1 (tile slot)
+  uint32_t sa[3], spb[3];   // generators: member bits 0..2 of block s and of block s+1 (tile slots)
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
     sa[j] = slot(1u << qa[j]);
     spb[j] = slot(1u << qp[j]);
-    ga[j] = t2g(1u << qa[j]);
   }
   const uint32_t rda0 = slot(local_base<4>((uint32_t)sr, qas)) ^ (sh ? slot(1u << qa[3]) : 0u);
   const uint32_t rdp0 = slot(local_base<4>((uint32_t)sr, qps)) ^ (sh ? slot(1u << qp[3]) : 0u);
   const uint32_t gb = local_base<4>((uint32_t)r, qas) | (hf ? (1u << qa[3]) : 0u);
-  const uint32_t sd0 = slot(gb), go0 = t2g(gb);
+  const uint32_t sd0 = slot(gb);
   auto gen = [](uint32_t b0, const uint32_t (&g)[3], int l) {
     return b0 ^ ((l & 1) ? g[0] : 0u) ^ ((l & 2) ? g[1] : 0u) ^ ((l & 4) ? g[2] : 0u);
   };
-  uint32_t coff[TS / 256], cdst[TS / 256];   // this thread's copies: amplitude e = tid + 256 i, its slot
+  // This thread's copies in and out: amplitudes e = tid + 256 i, i < 8, whose low bits run along the
+  // register, so that each quarter warp moves one whole 128-byte run.  Both maps are linear over XOR
+  // and tid, 256 i have disjoint bits: a base and 3 generators (slot(256 i) is a constant).
+  const uint32_t cb = t2g((uint32_t)tid), cs = slot((uint32_t)tid);
+  uint32_t cg[3];
 #pragma unroll
-  for (int i = 0; i < TS / 256; ++i) {
-    coff[i] = t2g((uint32_t)tid + 256u * i);
-    cdst[i] = slot((uint32_t)tid + 256u * i);
-  }
+  for (int j = 0; j < 3; ++j) cg[j] = t2g(256u << j);
+  auto coff = [&](int i) { return cb ^ ((i & 1) ? cg[0] : 0u) ^ ((i & 2) ? cg[1] : 0u) ^ ((i & 4) ? cg[2] : 0u); };
+  auto cdst = [&](int i) { return cs ^ slot(256u * (uint32_t)i); };
   const double2* src = reinterpret_cast<const double2*>(f.ap.src);
   double2* dst = reinterpret_cast<double2*>(f.ap.dst);
   const uint32_t ntile = 1u << f.nout;
@@ -1305,7 +1307,7 @@ __global__ void __launch_bounds__(256, 2) k_ozf(FusedArgs f) {
   };
   auto load_tile = [&](uint32_t tb) {
 #pragma unroll
-    for (int i = 0; i < TS / 256; ++i) cp_async16(tile + cdst[i], src + (tb | coff[i]));
+    for (int i = 0; i < TS / 256; ++i) cp_async16(tile + cdst(i), src + (tb | coff(i)));
     cp_async_commit();
   };
   uint32_t tix = blockIdx.x;
@@ -1373,7 +1375,7 @@ __global__ void __launch_bounds__(256, 2) k_ozf(FusedArgs f) {
     cmax = max(cmax, e);
   }
   uint32_t phase = 0;
-  double accA = 0.0, accN = 0.0, accE = 0.0;
+  oz::FusedSums sums;
   while (tix < ntile) {
     cp_async_wait<0>();
     __syncthreads();
@@ -1439,7 +1441,6 @@ __global__ void __launch_bounds__(256, 2) k_ozf(FusedArgs f) {
           const double y0 = in_range ? oz::assemble7_cvt_inrange(d0, E, colE[n]) : oz::assemble7_cvt(d0, E, colE[n]);
           const double y1 = in_range ? oz::assemble7_cvt_inrange(d1, E, colE[n + 1]) : oz::assemble7_cvt(d1, E, colE[n + 1]);
           const double2 yv = make_double2(y0, y1);
-          dst[tb | gen(go0, ga, l)] = yv;
           outb[gen(sd0, sa, l)] = yv;
           emax = max(emax, max((uint32_t)(oz::d2u(y0) >> 32) & 0x7FF00000u, (uint32_t)(oz::d2u(y1) >> 32) & 0x7FF00000u));
         }
@@ -1448,6 +1449,11 @@ __global__ void __launch_bounds__(256, 2) k_ozf(FusedArgs f) {
       if (lane == 0) s_emax[warp] = emax;
     }
     __syncthreads();   // the updated tile and its exponent are in shared memory
+    // the updated tile to the register, with the copy-in mapping (whole 128-byte runs per quarter
+    // warp whatever qubits the block acts on; stores straight from the recombination threads
+    // scatter when the block holds low register bits)
+#pragma unroll
+    for (int i = 0; i < TS / 256; ++i) dst[tb | coff(i)] = outb[cdst(i)];
     // ---- 2. probability of block s+1: 24-bit digits under the tile's largest exponent
     uint32_t em = s_emax[0];
 #pragma unroll
@@ -1505,14 +1511,8 @@ __global__ void __launch_bounds__(256, 2) k_ozf(FusedArgs f) {
         aacc += (uint64_t)(z * z);
       }
     }
-    // this tile's per-thread sums in FP64: N^ = nacc 2^(2(Et - 1046)), A^ = aacc 2^(2(Et + EP - 2068)),
-    // with their bounds (16 inputs each off by less than 2^(Et - 1046); 16 outputs each off by less
-    // than 2^(Et + EP - 2060))
-    const double nth = oz::scale2((double)nacc, 2 * (Et - 1046));
-    const double ath = EP ? oz::scale2((double)aacc, 2 * (Et + EP - 2068)) : 0.0;
-    accN += nth;
-    accA += ath;
-    accE += oz::part_bound(nth, Et + 1015) + (EP ? oz::part_bound(ath, Et + EP) : 0.0);
+    // this tile's per-thread sums and their truncation bounds, as FP32 intervals (no FP64 work)
+    sums.add_tile(nacc, aacc, Et, EP);
     // no barrier here: the next tile's MMAs are issued after its slicing barrier (tc_sync), which
     // every thread reaches after these TMEM loads; the loop-top barrier protects rowE and s_emax
     tb = tbn;
@@ -1522,7 +1522,9 @@ __global__ void __launch_bounds__(256, 2) k_ozf(FusedArgs f) {
   tc_sync();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem));
   if (s_err && tid == 0) atomicOr(&f.pr.ctl->status, 1u);
-  prob_finish_bounded(f.pr, accA, accN, accE, sred, &s_last, true);
+  double accN, rN, accA, rA;
+  sums.finish(accN, rN, accA, rA);
+  prob_finish_bounded(f.pr, accA, accN, rN + rA, sred, &s_last, true);
 }
 
 // ---- final Z readout (Sec. III.B): sequential per-qubit sampling -------------------------

@@ -222,6 +222,72 @@ OZ_HD int32_t combine3(const float* D) {
   return small_float_int(D[0]) * 256 + small_float_int(D[1]) + small_float_int(D[2] * 0x1p-8f);
 }
 
+// ---- FP32 with directed rounding (the device's IEEE intrinsics; on the host an emulation through
+// FP64 that the CPU tests use: FP32 products are exact in FP64, sums are checked against the FP64
+// result) -------------------------------------------------------------------------------------------
+#if defined(__CUDA_ARCH__)
+OZ_HD float f_add_rd(float a, float b) { return __fadd_rd(a, b); }
+OZ_HD float f_add_ru(float a, float b) { return __fadd_ru(a, b); }
+OZ_HD float f_mul_rd(float a, float b) { return __fmul_rd(a, b); }
+OZ_HD float f_mul_ru(float a, float b) { return __fmul_ru(a, b); }
+OZ_HD float f_fma_rd(float a, float b, float c) { return __fmaf_rd(a, b, c); }
+OZ_HD float f_fma_ru(float a, float b, float c) { return __fmaf_ru(a, b, c); }
+OZ_HD float f_sqrt_ru(float a) { return __fsqrt_ru(a); }
+OZ_HD float u2f_rd(uint32_t v) { return __uint2float_rd(v); }
+OZ_HD float u2f_ru(uint32_t v) { return __uint2float_ru(v); }
+#else
+inline float f_down(double r) { float f = (float)r; return (double)f > r ? nextafterf(f, -INFINITY) : f; }
+inline float f_up(double r) { float f = (float)r; return (double)f < r ? nextafterf(f, INFINITY) : f; }
+inline float f_add_rd(float a, float b) { return f_down((double)a + (double)b); }
+inline float f_add_ru(float a, float b) { return f_up((double)a + (double)b); }
+inline float f_mul_rd(float a, float b) { return f_down((double)a * (double)b); }
+inline float f_mul_ru(float a, float b) { return f_up((double)a * (double)b); }
+inline float f_fma_rd(float a, float b, float c) { return f_down((double)a * (double)b + (double)c); }
+inline float f_fma_ru(float a, float b, float c) { return f_up((double)a * (double)b + (double)c); }
+inline float f_sqrt_ru(float a) { float f = sqrtf(a); return (double)f * (double)f < (double)a ? nextafterf(f, INFINITY) : f; }
+inline float u2f_rd(uint32_t v) { return f_down((double)v); }
+inline float u2f_ru(uint32_t v) { return f_up((double)v); }
+#endif
+
+// Per-thread sums of the fused pass's probability phase over its tiles, in units of 2^-64, as FP32
+// intervals with directed rounding (no FP64 work per tile).  Per tile the thread adds
+//   N_t = nacc 2^(2 Et - 2092)   (nacc = sum of its 16 inputs' squared 24-bit integers, < 2^52),
+//   A_t = aacc 2^(2 (Et + EP) - 4136)   (aacc = sum of its 16 outputs' squared Zt, < 2^62),
+// and their truncation bounds 8 d sqrt(N_t) + 16 d^2 with d = 2^(Et - 1045) (inputs off by less than
+// 2^(Et - 1046) each) and 8 D sqrt(A_t) + 16 D^2 with D = 2^(Et + EP - 2060) (outputs), which in the
+// same units are 16 s_N (sqrt(nacc) + 4) and 2^11 s_A (sqrt(aacc) + 512) with s_N = 2^(2 Et - 2028),
+// s_A = 2^(2 (Et + EP) - 4072).  Scales below the FP32 normal range (tiles whose squares are below
+// about 2^-138) count as 0 in the lower sums and as 2^-126 in the upper ones.
+struct FusedSums {
+  float nlo = 0.f, nhi = 0.f, alo = 0.f, ahi = 0.f, en = 0.f, ea = 0.f;
+  OZ_HD void add_tile(uint64_t nacc, uint64_t aacc, int Et, int EP) {
+    const int kN = 2 * Et - 2028, kA = 2 * (Et + EP) - 4072;
+    const float sN = kN >= -126 ? u2f(uint32_t(kN + 127) << 23) : 0.f;
+    const float sNh = kN >= -126 ? sN : 0x1p-126f;
+    const float sA = EP && kA >= -126 ? u2f(uint32_t(kA + 127) << 23) : 0.f;
+    const float sAh = EP ? (kA >= -126 ? sA : 0x1p-126f) : 0.f;
+    const float two32 = 4294967296.f;
+    const uint32_t nh = (uint32_t)(nacc >> 32), nl = (uint32_t)nacc;   // nh < 2^20: exact in FP32
+    const float n_lo = f_fma_rd((float)nh, two32, u2f_rd(nl)), n_hi = f_fma_ru((float)nh, two32, u2f_ru(nl));
+    const uint32_t ah = (uint32_t)(aacc >> 32), al = (uint32_t)aacc;
+    const float a_lo = f_fma_rd(u2f_rd(ah), two32, u2f_rd(al)), a_hi = f_fma_ru(u2f_ru(ah), two32, u2f_ru(al));
+    nlo = f_add_rd(nlo, f_mul_rd(n_lo, sN));
+    nhi = f_add_ru(nhi, f_mul_ru(n_hi, sNh));
+    alo = f_add_rd(alo, f_mul_rd(a_lo, sA));
+    ahi = f_add_ru(ahi, f_mul_ru(a_hi, sAh));
+    en = f_add_ru(en, f_mul_ru(f_add_ru(f_sqrt_ru(n_hi), 4.f), f_mul_ru(16.f, sNh)));
+    ea = f_add_ru(ea, f_mul_ru(f_add_ru(f_sqrt_ru(a_hi), 512.f), f_mul_ru(2048.f, sAh)));
+  }
+  // Midpoints and radii in real units: N in [n - rn, n + rn], A in [a - ra, a + ra].
+  OZ_HD void finish(double& n, double& rn, double& a, double& ra) const {
+    const double u = 0x1p-64;
+    n = 0.5 * ((double)nlo + (double)nhi) * u;
+    a = 0.5 * ((double)alo + (double)ahi) * u;
+    rn = (0.5 * ((double)nhi - (double)nlo) + (double)en) * u;
+    ra = (0.5 * ((double)ahi - (double)alo) + (double)ea) * u;
+  }
+};
+
 // 2^e1 + 2^e2 rounded up to an FP64 value, built in the exponent and mantissa fields (no FP64
 // arithmetic); at least the smallest normal number, infinity above the range.
 OZ_HD double pow2_sum_up(int e1, int e2) {

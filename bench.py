@@ -48,9 +48,12 @@ def parse():
     ap.add_argument("--workload", default="d5", choices=["d5", "batched", "serve", "precision", "sweep"],
                     help="d5: the d=5 26-qubit trajectories (default); batched: 8192 d=3 trajectories per "
                          "launch; serve: Poisson trace of mixed jobs through the continuous-batching server")
-    ap.add_argument("--requests", type=int, default=64, help="serve: requests in the trace")
+    ap.add_argument("--requests", type=int, default=32, help="serve: requests in the trace")
     ap.add_argument("--rate", type=float, default=50.0, help="serve: mean arrival rate (requests/s)")
-    ap.add_argument("--max-traj", type=int, default=8, help="serve: trajectories per request drawn from 1..max")
+    ap.add_argument("--max-traj", type=int, default=64, help="serve: trajectories per request drawn from 1..max")
+    ap.add_argument("--sustainable-requests", type=int, default=20,
+                    help="serve: requests in the second trace, at 0.7 of the capacity the first one measured")
+    ap.add_argument("--no-serve", action="store_true", help="d5: skip the serving trace added to the line")
     ap.add_argument("--mem-gib", type=float, default=32.0, help="serve: device memory budget for state vectors")
     ap.add_argument("--noise", default="full", choices=["full", "idle", "twirl", "follows"],
                     help="sweep: full = p on every step (Eqs. 1-2); idle = p on waiting qubits only; "
@@ -363,6 +366,10 @@ def native_arm(args, rank, world, local):
                                "sample_1_core": "2 of the same round's stabilizer circuits on one thread, x 12"}
     for s in sims:
         s.close()
+    if not args.no_serve and args.code == "surface":   # serve p50/p99 (the metric's third part)
+        rep = serve_measure(args, rank, world, local)
+        rep.pop("out_bytes", None)
+        out["serve"] = rep
     if rank == 0:
         print(json.dumps(out))
     if world > 1:
@@ -380,7 +387,8 @@ def batched_arm(args, rank, world, local):
     traj, kinds, noise, rounds, seed = W.batched_mix(n=8192)
     traj = [t + rank * 8192 for t in traj]
     with BatchSimulator(rounds, "cr", max_traj=8192) as b:
-        warps, _ = b.autotune(seed, traj[:1024], kinds[:1024], noise[:1024])
+        b.autotune(seed, traj[:1024], kinds[:1024], noise[:1024])
+        warps, fusion_k, u_threads = b.config()
         for _ in range(args.warmup):
             b.run(seed, traj, kinds, noise)
         dev_ms = []
@@ -401,7 +409,10 @@ def batched_arm(args, rank, world, local):
         "config": {"workload": "8192 d=3 trajectories per step in equal quarters: reduced 10-qubit and "
                                "unreduced 17-qubit registers x complex128/complex64; 3 rounds, cr gates, "
                                "p~U[1e-4,1e-2], theta_rx~U[0,0.1]",
-                   "autotuned_warps_per_cta": warps, "rounds_per_s": world * n * rounds * args.steps / dev},
+                   "autotuned": {"reduced_warps_per_cta": warps, "unreduced_fusion_width": fusion_k,
+                                 "unreduced_threads_per_cta": u_threads,
+                                 "sample": "the first 1024 trajectories, each engine on its own register's"},
+                   "rounds_per_s": world * n * rounds * args.steps / dev},
         "clocks": clk.summary(),
         "e2e": {"value": world * n * args.steps / wall, "unit": "trajectories/s",
                 "h2d_bytes_per_step": n * (8 + 4 + 72) + 16, "d2h_bytes_per_step": n * ((rounds + 1) * 8 + 9 + 1)},
@@ -411,9 +422,10 @@ def batched_arm(args, rank, world, local):
         print(json.dumps(out))
 
 
-def serve_arm(args, rank, world, local):
-    """A Poisson trace of mixed jobs (d in {3,5}, rounds 1..10, complex64/complex128, per-job noise)
-    through the continuous-batching server; latency percentiles beside throughput."""
+def serve_measure(args, rank, world, local):
+    """A Poisson trace of mixed jobs (the serving configuration: d in {3, 5}, rounds U{1..10},
+    trajectories U{1..max_traj}, complex64 or complex128, per-job noise) through the continuous-batching
+    server, then a second trace at 0.7 of the capacity the first one measured.  Returns the report."""
     import torch
 
     from paper_2204_11404_gb300.serve import Job, Server, latency_summary
@@ -434,14 +446,20 @@ def serve_arm(args, rank, world, local):
     traj = sum(j.n_traj for j in jobs)
     tr_rounds = sum(j.n_traj * j.rounds for j in jobs)
     span = max(j.arrival for j in jobs)
-    lat = latency_summary(jobs)
     out_bytes = sum(j.n_traj * ((j.rounds + 1) * (j.d * j.d - 1) + j.d * j.d + 1) for j in jobs)
-    # second trace at a sustainable rate: utilisation about 0.7 of the capacity the first one measured
     offered = tr_rounds / span if span > 0 else None
-    sustainable = None
-    if offered:
+    rep = {"trace": "Poisson arrivals, d in {3,5}, rounds U{1..10}, trajectories U{1..%d}, c64/c128 "
+                    "(d=5 c128 on the tensor-core complex128 engine), p~U[1e-4,1e-2], theta_rx~U[0,0.1]"
+                    % args.max_traj,
+           "requests": len(jobs), "rate_per_s": args.rate, "trajectories": traj,
+           "trajectories_per_s": world * traj / makespan, "makespan_s": makespan,
+           "latency_ms": latency_summary(jobs),
+           "offered_trajectory_rounds_per_s": offered, "achieved_trajectory_rounds_per_s": tr_rounds / makespan,
+           "mem_budget_gib": args.mem_gib, "clocks": clk.summary(), "out_bytes": out_bytes}
+    # second trace at a sustainable rate: utilisation about 0.7 of the capacity the first one measured
+    if offered and args.sustainable_requests > 0:
         rate2 = 0.7 * args.rate * (tr_rounds / makespan) / offered
-        jobs2 = [Job(**j) for j in W.serving_trace(n_req=args.requests, rate=rate2, seed=6000 + rank,
+        jobs2 = [Job(**j) for j in W.serving_trace(n_req=args.sustainable_requests, rate=rate2, seed=6000 + rank,
                                                     max_traj=args.max_traj)]
         srv = Server(int(args.mem_gib * 2**30))
         try:
@@ -451,33 +469,67 @@ def serve_arm(args, rank, world, local):
         finally:
             srv.close()
         tr2 = sum(j.n_traj * j.rounds for j in jobs2)
-        sustainable = {"rate_per_s": rate2, "utilisation_target": 0.7, "requests": len(jobs2),
-                       "offered_trajectory_rounds_per_s": tr2 / max(j.arrival for j in jobs2),
-                       "achieved_trajectory_rounds_per_s": tr2 / span2, "latency_ms": latency_summary(jobs2)}
+        rep["sustainable_trace"] = {"rate_per_s": rate2, "utilisation_target": 0.7, "requests": len(jobs2),
+                                    "offered_trajectory_rounds_per_s": tr2 / max(j.arrival for j in jobs2),
+                                    "achieved_trajectory_rounds_per_s": tr2 / span2,
+                                    "latency_ms": latency_summary(jobs2)}
+    return rep
+
+
+def serve_arm(args, rank, world, local):
+    rep = serve_measure(args, rank, world, local)
     out = {
         "metric": "serving: trajectories/s with p50/p99 job latency (continuous batching)",
-        "value": world * traj / makespan, "unit": "trajectories/s", "n_gpus": world, "steps": len(jobs),
-        "warmup": len(warm), "ms_per_step": 1e3 * makespan / len(jobs), "higher_is_better": True,
+        "value": rep["trajectories_per_s"], "unit": "trajectories/s", "n_gpus": world, "steps": rep["requests"],
+        "warmup": 4, "ms_per_step": 1e3 * rep["makespan_s"] / rep["requests"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
-        "config": {"workload": "Poisson trace: d in {3,5}, rounds U{1..10}, trajectories U{1..%d}, c64/c128, "
-                               "p~U[1e-4,1e-2], theta_rx~U[0,0.1]" % args.max_traj,
-                   "requests": len(jobs), "rate_per_s": args.rate, "mem_budget_gib": args.mem_gib,
-                   "offered_trajectory_rounds_per_s": offered,
-                   "achieved_trajectory_rounds_per_s": tr_rounds / makespan,
-                   "complex128_engine_d5": "tensor-core complex128 (c128tc)"},
-        "latency_ms": lat, "clocks": clk.summary(),
-        "e2e": {"value": world * traj / makespan, "unit": "trajectories/s",
-                "h2d_bytes_per_step": 32, "d2h_bytes_per_step": out_bytes / len(jobs)},
-        "sustainable_trace": sustainable,
+        "config": {"workload": rep["trace"], "requests": rep["requests"], "rate_per_s": args.rate,
+                   "mem_budget_gib": args.mem_gib,
+                   "offered_trajectory_rounds_per_s": rep["offered_trajectory_rounds_per_s"],
+                   "achieved_trajectory_rounds_per_s": rep["achieved_trajectory_rounds_per_s"]},
+        "latency_ms": rep["latency_ms"], "clocks": rep["clocks"],
+        "e2e": {"value": rep["trajectories_per_s"], "unit": "trajectories/s",
+                "h2d_bytes_per_step": 32, "d2h_bytes_per_step": rep["out_bytes"] / rep["requests"]},
+        "sustainable_trace": rep.get("sustainable_trace"),
     }
     if rank == 0:
         print(json.dumps(out))
 
 
+def _oracle_state_file(point_index, rounds, path):
+    """Worker (spawned process): trajectory 0 of a d=5 noise point on the FP64 oracle; saves the
+    state after the last round and the smallest |u - P(1)| of the trajectory; returns the path."""
+    import numpy as np
+
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from oracle import run_trajectory
+    from parity_util import min_margin
+
+    pt = W.D5_CR["points"][point_index]
+    o = run_trajectory(5, rounds, "cr", "reduced", pt, seed=W.D5_CR["seed_base"] + point_index, traj=0,
+                       want_state=True)
+    np.save(path, o["state"][: 1 << 25])
+    return path, min_margin(o), o["syndromes"].tolist(), o["data_bits"].tolist()
+
+
 def precision_arm(args, rank, world, local):
-    """Per noise point of the d=5 workload: the same trajectories in complex128 (which matches the FP64
-    oracle bit for bit and to 1e-12), complex64 and complex64/tensor-core; reports syndrome agreement,
-    max amplitude deviation of the last trajectory's state, and decoded logical error rates."""
+    """Error of every form against the FP64 oracle, per noise point of the d=5 workload: trajectory 0
+    of each point on the oracle (a spawned worker on the host cores, overlapping the GPU work) against
+    the same trajectory in complex128, complex128 on the tensor cores, complex64 and complex64 on the
+    tensor cores (max |psi - psi_oracle| after the last round, and whether the outcomes match); then
+    --steps trajectories per point in the three fast forms: how many have outcomes identical to the
+    tensor-core complex128 form (itself bit-identical to the oracle), and the decoded logical error
+    rates."""
+    import multiprocessing
+    import tempfile
+
+    ctx = multiprocessing.get_context("spawn")   # started before the first GPU call
+    pool = ctx.Pool(1)
+    tmp = tempfile.mkdtemp(prefix="qec_prec_")
+    R = W.D5_CR["rounds"]
+    npts = max(1, min(args.points, len(W.D5_CR["points"])))
+    futs = [pool.apply_async(_oracle_state_file, (i, R, os.path.join(tmp, "o%d.npy" % i))) for i in range(npts)]
+    pool.close()
     import numpy as np
     import torch
 
@@ -488,25 +540,43 @@ def precision_arm(args, rank, world, local):
     n = max(1, args.steps)
     dec = Decoder(5)
     rows = []
-    for i, pt in enumerate(W.D5_CR["points"]):
+    t0 = time.perf_counter()
+    for i in range(npts):
+        pt = W.D5_CR["points"][i]
         seed = W.D5_CR["seed_base"] + i
+        row = {"p": pt["p1"], "theta_rx": pt["theta_rx"], "phi_zz": pt["phi_zz"]}
+        # (1) the same trajectories in the fast forms, outcomes against the tensor-core complex128 form
         res = {}
-        for prec in ("c128", "c128tc", "c64", "c64tc"):
-            with Simulator(5, W.D5_CR["rounds"], "cr", prec, **pt) as sim:
-                syn, bits, log = sim.run(seed, 0, n)
-                res[prec] = (syn, bits, log, sim.state())
-        ref = res["c128"]
-        row = {"p": pt["p1"], "theta_rx": pt["theta_rx"], "trajectories": n,
-               "pL_c128": dec.logical_error_rate(*ref[:3])}
         for prec in ("c128tc", "c64", "c64tc"):
-            s, b, l, st = res[prec]
-            same = [bool((s[t] == ref[0][t]).all() and (b[t] == ref[1][t]).all()) for t in range(n)]
-            row[prec] = {"identical_trajectories": int(sum(same)), "pL": dec.logical_error_rate(s, b, l),
-                         "amp_maxabs_dev_last_traj": float(np.abs(st - ref[3]).max()) if same[-1] else None}
+            with Simulator(5, R, "cr", prec, **pt) as sim:
+                res[prec] = sim.run(seed, 0, n)
+        ref = res["c128tc"]
+        row["trajectories"] = n
+        row["pL"] = {prec: dec.logical_error_rate(*res[prec]) for prec in res}
+        row["identical_outcomes_to_c128tc"] = {
+            prec: int(sum(bool((res[prec][0][t] == ref[0][t]).all() and (res[prec][1][t] == ref[1][t]).all())
+                          for t in range(n))) for prec in ("c64", "c64tc")}
+        # (2) trajectory 0 of every form against the oracle
+        path, margin, o_syn, o_bits = futs[i].get()
+        psi_o = np.load(path)
+        os.remove(path)
+        row["oracle_min_margin"] = margin
+        row["amp_maxabs_vs_oracle"] = {}
+        row["outcomes_equal_oracle"] = {}
+        for prec in ("c128", "c128tc", "c64", "c64tc"):
+            with Simulator(5, R, "cr", prec, **pt) as sim:
+                syn, bits, _ = sim.run(seed, 0, 1)
+                same = bool((syn[0] == np.array(o_syn)).all() and (bits[0] == np.array(o_bits)).all())
+                row["outcomes_equal_oracle"][prec] = same
+                row["amp_maxabs_vs_oracle"][prec] = float(np.abs(sim.state() - psi_o).max()) if same else None
+        del psi_o
         rows.append(row)
+        print("point %d done after %.0f s" % (i, time.perf_counter() - t0), file=sys.stderr, flush=True)
+    pool.join()
     if rank == 0:
-        print(json.dumps({"metric": "precision forms vs complex128 per noise point (d=5, 5 rounds)",
+        print(json.dumps({"metric": "error of each form against the FP64 oracle per noise point (d=5, %d rounds)" % R,
                           "unit": "per-point report", "data": "synthetic", "points": rows,
+                          "bars": {"c128": 1e-12, "c128tc": 1e-12, "c64": 2e-5, "c64tc": 2e-5},
                           "decoder_fallbacks": dec.fallbacks}))
 
 

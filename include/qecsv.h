@@ -240,12 +240,26 @@ qec_status qec_batch_run(qec_batch* b, uint64_t seed, uint32_t n, const uint64_t
                          const qec_noise* noise, uint8_t* syndromes, uint8_t* data_bits, uint8_t* raw_logical);
 
 /*
- * Autotuner: times qec_batch_run on the given sample for each candidate CTA
- * shape (warps per CTA; one resident wave per SM) and keeps the fastest.
- * *chosen_warps and *best_ms report the choice and its device time.
+ * Autotuner: times qec_batch_run on the given sample and keeps the fastest
+ * configuration of each engine, each timed on the sample's trajectories of its
+ * register: the reduced-register engine's CTA shape (warps per CTA, one
+ * resident wave per SM), then the unreduced engine's fusion width k (2..6 slab
+ * bits per pass: consecutive gate units on disjoint bits, which commute, are
+ * applied in one pass over the 2^13-amplitude slab) and threads per CTA (128,
+ * 256).  *chosen_warps gets the reduced engine's warps per CTA, *best_ms the
+ * device time of the whole sample with the chosen configuration;
+ * qec_batch_config reports all three choices.
  */
 qec_status qec_batch_autotune(qec_batch* b, uint64_t seed, uint32_t n, const uint64_t* traj, const int32_t* kind,
                               const qec_noise* noise, int32_t* chosen_warps, float* best_ms);
+
+/* The current configuration: reduced engine warps per CTA, unreduced engine fusion width and
+ * threads per CTA. */
+qec_status qec_batch_config(const qec_batch* b, int32_t* warps_per_cta, int32_t* fusion_width, int32_t* u_threads);
+
+/* Sets the configuration by hand (QEC_EINVAL outside warps 2..10 that fit, fusion width 2..6,
+ * threads 128/256; QEC_EUNSUPPORTED when a shape does not fit an SM).  Results do not depend on it. */
+qec_status qec_batch_set_config(qec_batch* b, int32_t warps_per_cta, int32_t fusion_width, int32_t u_threads);
 
 /*
  * Test hook: choose one trajectory of the next qec_batch_run (item = its index i in that call's

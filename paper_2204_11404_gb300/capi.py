@@ -57,6 +57,8 @@ SIGNATURES = {
                          ctypes.c_int),
     "qec_batch_run": ([_P, ctypes.c_uint64, ctypes.c_uint32, _P, _P, _P, _P, _P, _P], ctypes.c_int),
     "qec_batch_autotune": ([_P, ctypes.c_uint64, ctypes.c_uint32, _P, _P, _P, _P, _P], ctypes.c_int),
+    "qec_batch_config": ([_P, _P, _P, _P], ctypes.c_int),
+    "qec_batch_set_config": ([_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
     "qec_batch_snapshot": ([_P, ctypes.c_int64], ctypes.c_int),
     "qec_batch_get_state": ([_P, _P, ctypes.c_size_t], ctypes.c_int),
     "qec_batch_last_ms": ([_P, _P], ctypes.c_int),
@@ -171,6 +173,17 @@ def qec_batch_autotune(b, seed, n, traj_ptr, kind_ptr, noise_ptr):
     check(lib().qec_batch_autotune(b, seed, n, traj_ptr, kind_ptr, noise_ptr, ctypes.cast(ctypes.pointer(w), _P),
                                    ctypes.cast(ctypes.pointer(ms), _P)))
     return int(w.value), float(ms.value)
+
+
+def qec_batch_config(b):
+    """(reduced-engine warps per CTA, unreduced-engine fusion width, unreduced-engine threads per CTA)."""
+    v = [ctypes.c_int32(0) for _ in range(3)]
+    check(lib().qec_batch_config(b, *[ctypes.cast(ctypes.pointer(x), _P) for x in v]))
+    return tuple(int(x.value) for x in v)
+
+
+def qec_batch_set_config(b, warps_per_cta, fusion_width, u_threads):
+    return check(lib().qec_batch_set_config(b, warps_per_cta, fusion_width, u_threads))
 
 
 def qec_batch_snapshot(b, item):

@@ -33,6 +33,7 @@ constexpr int kND = kD * kD;             // 9 data qubits
 constexpr int kNAmp = 1 << kND;          // 512 amplitudes
 constexpr int kNStab = kND - 1;          // 8 stabilizers
 constexpr int kWarpSmem = 32 * 16 * 16 + kNAmp * 16 + M_COUNT * 16 * 16 + 64;   // U, psi, mats, misc (c128)
+constexpr int kUMaxFusionDecl = 6;       // widest pass of the unreduced engine (slab bits)
 
 template <typename T> struct C2;
 template <> struct C2<double> { using t = double2; };
@@ -45,6 +46,24 @@ struct BatchCtl {
   uint32_t n_u;               // unreduced-register (17-qubit) trajectories in this run
   unsigned int counter_u;     // their work queue head
   uint32_t snap_item;         // item whose final data-register state goes to snap (~0u = none)
+};
+
+// One pass of the unreduced engine over the slab: kind 0 applies the units punits[u0, u1) (disjoint
+// slab bits, together `nbits` bits listed in bits[]); kind 1 measures the ancilla of items[item].
+struct UPass {
+  int32_t kind;
+  int32_t item;
+  int32_t u0, u1;
+  int32_t nbits;
+  int32_t bits[kUMaxFusionDecl];
+};
+
+// A unit inside a pass: items[item] on slab bits qa (, qb), and the pass's other bits.
+struct UPassUnit {
+  int32_t item;
+  int32_t nq, qa, qb;
+  int32_t nother;
+  int32_t other[kUMaxFusionDecl];
 };
 
 struct BatchArgs {
@@ -64,6 +83,12 @@ struct BatchArgs {
   const UItem* iuitems;
   int n_iuitems;
   const void* psi0_u[2];      // unreduced init slab per precision
+  const UPass* upasses;       // its passes for one round (fusion width of the batch)
+  int n_upasses;
+  const UPassUnit* upunits;
+  const UPass* iupasses;      // the init round's passes
+  int n_iupasses;
+  const UPassUnit* iupunits;
   const uint64_t* traj;       // [n]
   BatchCtl* ctl;
   int rounds;
@@ -384,9 +409,18 @@ __global__ void k_batch(BatchArgs a) {
 }
 
 // ---- unreduced register: one CTA per 17-qubit trajectory --------------------------------
+// Each round's gate units (a gate with its coherent terms and sampled Paulis on 1 or 2 slab bits)
+// are fused into their matrices at the start of the round, one thread per unit: the noise draws
+// depend only on (seed, trajectory, round, step, site), not on the state.  The slab is then
+// updated in passes: a pass holds consecutive units on disjoint slab bits (which commute), at most
+// `fusion width` bits in all, and each thread applies every unit of the pass to whole groups of
+// amplitudes (all combinations of the pass's bits) that it alone touches, so a pass needs one
+// barrier however many units it holds.  Measurements are passes of their own.
 constexpr int kUBits = kND + kNStab / 2;      // 13 slab bits: 9 data + the active part's 4 ancillas
 constexpr int kUAmp = 1 << kUBits;            // 8192 amplitudes
-constexpr int kUSmem = kUAmp * 16 + M_COUNT * 16 * 16 + 16 * 16 + 64 * 8 + 16;   // slab, mats, F, reduction, flag
+constexpr int kUMaxItems = 192;               // items of one round (units and measurements)
+// slab, mats, unit matrices (FP64) and flags, reduction, flag
+constexpr int kUSmem = kUAmp * 16 + M_COUNT * 16 * 16 + kUMaxItems * 16 * 16 + kUMaxItems * 4 + 64 * 8 + 16;
 
 template <typename T>
 __device__ void block_sum2_u(double& x, double& y, double* sh) {
@@ -402,6 +436,103 @@ __device__ void block_sum2_u(double& x, double& y, double* sh) {
   __syncthreads();
 }
 
+// Left-multiplies the DIM x DIM unit matrix M (row stride 4) by a one-qubit gate g on local bit BIT.
+template <int DIM, int BIT, typename T2>
+__device__ __forceinline__ void left1(double2 (&M)[16], const T2* g) {
+  const double2 g00 = make_double2((double)g[0].x, (double)g[0].y), g01 = make_double2((double)g[1].x, (double)g[1].y);
+  const double2 g10 = make_double2((double)g[4].x, (double)g[4].y), g11 = make_double2((double)g[5].x, (double)g[5].y);
+#pragma unroll
+  for (int r0 = 0; r0 < DIM; ++r0) {
+    if (r0 & (1 << BIT)) continue;
+    const int r1 = r0 | (1 << BIT);
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) {
+      const double2 x = M[r0 * 4 + c], y = M[r1 * 4 + c];
+      M[r0 * 4 + c] = make_double2(g00.x * x.x - g00.y * x.y + g01.x * y.x - g01.y * y.y,
+                                   g00.x * x.y + g00.y * x.x + g01.x * y.y + g01.y * y.x);
+      M[r1 * 4 + c] = make_double2(g10.x * x.x - g10.y * x.y + g11.x * y.x - g11.y * y.y,
+                                   g10.x * x.y + g10.y * x.x + g11.x * y.y + g11.y * y.x);
+    }
+  }
+}
+
+// Left-multiplies the 4x4 unit matrix M by a two-qubit gate g (local index 2 bit(qa) + bit(qb)).
+template <typename T2>
+__device__ __forceinline__ void left2(double2 (&M)[16], const T2* g) {
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    double2 v[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] = M[k * 4 + c];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      double re = 0.0, im = 0.0;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const double gx = (double)g[r * 4 + k].x, gy = (double)g[r * 4 + k].y;
+        re += gx * v[k].x - gy * v[k].y;
+        im += gx * v[k].y + gy * v[k].x;
+      }
+      M[r * 4 + c] = make_double2(re, im);
+    }
+  }
+}
+
+// The fused matrix of one unit: the product, in op order, of its gate, coherent terms and the
+// Paulis its noise sites draw (DIM 2 or 4; local index 2 bit(qa) + bit(qb), qa the only bit of a
+// one-qubit unit), built in place by left multiplications.  Returns 0 when no op of the unit acts
+// (every draw came up empty and no gate): the unit is then the identity.
+template <int DIM, typename T2>
+__device__ int fuse_unit(const UItem& u, const ProgOp* ops, const T2 (*mats)[16], const double* prob,
+                         uint64_t seed, uint64_t traj, int rnd, double2* F) {
+  double2 M[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) M[i] = make_double2((i / 4 == i % 4) ? 1.0 : 0.0, 0.0);
+  int any = 0;
+  auto one = [&](int id, bool on_qa) {   // one-qubit matrix id on qa (local bit 1) or qb (bit 0)
+    if (id == M_I) return;
+    if (DIM == 2) left1<DIM, 0>(M, mats[id]);
+    else if (on_qa) left1<DIM, 1>(M, mats[id]);
+    else left1<DIM, 0>(M, mats[id]);
+  };
+  for (int oi = u.op_begin; oi < u.op_end; ++oi) {
+    const ProgOp op = ops[oi];
+    int code = 0;
+    if (op.kind == OP_N1 || op.kind == OP_N2) {
+      code = noise_code(op, prob[op.pidx], seed, traj, (uint64_t)rnd);
+      if (!code) continue;
+    }
+    if ((op.kind == OP_T1 || op.kind == OP_T2) && !twirl_fires(op, prob[op.pidx], seed, traj, (uint64_t)rnd))
+      continue;
+    any = 1;
+    if (DIM == 4 && (op.kind == OP_U2 || op.kind == OP_T2)) {
+      left2(M, mats[op.mat]);
+    } else if (op.kind == OP_N2) {   // Pauli code >> 2 on op.q0, code & 3 on op.q1
+      one(code >> 2, op.q0 == u.qa);
+      one(code & 3, op.q1 == u.qa);
+    } else {
+      one((op.kind == OP_U1 || op.kind == OP_T1) ? op.mat : code, op.q0 == u.qa);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 16; ++i) F[i] = M[i];
+  return any;
+}
+
+// Offset of pass-local combination s over the `n` slab bits in b[] (bit j of s -> slab bit b[j]).
+__device__ __forceinline__ int deposit_bits(int s, const int* b, int n) {
+  int o = 0;
+  for (int j = 0; j < n; ++j) o |= ((s >> j) & 1) << b[j];
+  return o;
+}
+
+// Slab index of group g of a pass: g's bits spread over the slab bits outside the pass
+// (insert a zero at each pass bit, ascending).
+__device__ __forceinline__ int group_base_u(int g, const int* bits, int nbits) {
+  for (int j = 0; j < nbits; ++j) g = ((g >> bits[j]) << (bits[j] + 1)) | (g & ((1 << bits[j]) - 1));
+  return g;
+}
+
 // One trajectory (or the noise-free init round) of the unreduced register on one CTA.
 template <typename T>
 __device__ void run_cta_u(const BatchArgs& a, unsigned char* sm, uint32_t item) {
@@ -409,9 +540,9 @@ __device__ void run_cta_u(const BatchArgs& a, unsigned char* sm, uint32_t item) 
   const int tid = threadIdx.x, nt = blockDim.x;
   T2* slab = reinterpret_cast<T2*>(sm);
   T2 (*mats)[16] = reinterpret_cast<T2 (*)[16]>(slab + kUAmp);
-  double2* F = reinterpret_cast<double2*>(mats + M_COUNT);         // fused unit matrix (FP64, 16 entries)
-  double* sh = reinterpret_cast<double*>(F + 16);                  // 64 doubles
-  int* sflag = reinterpret_cast<int*>(sh + 64);
+  double2* Ft = reinterpret_cast<double2*>(sm + kUAmp * 16 + M_COUNT * 16 * 16);   // [kUMaxItems][16]
+  int* Fon = reinterpret_cast<int*>(Ft + kUMaxItems * 16);                           // [kUMaxItems]
+  double* sh = reinterpret_cast<double*>(Fon + kUMaxItems);                          // 64 doubles
   const bool init = a.init_mode != 0;
   const qec_noise nz = init ? qec_noise{} : a.noise[item];
   const uint64_t traj = init ? 0ull : a.traj[item];
@@ -419,6 +550,9 @@ __device__ void run_cta_u(const BatchArgs& a, unsigned char* sm, uint32_t item) 
   const ProgOp* ops = init ? a.iuops : a.uops;
   const UItem* items = init ? a.iuitems : a.uitems;
   const int nitems = init ? a.n_iuitems : a.n_uitems;
+  const UPass* passes = init ? a.iupasses : a.upasses;
+  const int npass = init ? a.n_iupasses : a.n_upasses;
+  const UPassUnit* punits = init ? a.iupunits : a.upunits;
   double prob[PR_COUNT];
   traj_probs(nz, prob);
   for (int i = tid; i < M_COUNT * 16; i += nt) {
@@ -439,108 +573,19 @@ __device__ void run_cta_u(const BatchArgs& a, unsigned char* sm, uint32_t item) 
     for (int k = tid; k < kNStab; k += nt) syn[k] = 0;
   const int r_first = init ? 0 : 1, r_last = init ? 0 : a.rounds;
   for (int rnd = r_first; rnd <= r_last; ++rnd) {
-    for (int it = 0; it < nitems; ++it) {
+    // every unit of the round, one thread each
+    for (int it = tid; it < nitems; it += nt) {
       const UItem u = items[it];
-      if (u.kind == 0) {
-        // thread 0 fuses the unit: F = (Pauli) (coherent) (gate), applied in op order
-        if (tid == 0) {
-          const int dim = u.nq == 1 ? 2 : 4;
-          double2 M[16];
-          for (int i = 0; i < 16; ++i) M[i] = make_double2((i / 4 == i % 4) ? 1.0 : 0.0, 0.0);
-          int any = 0;
-          for (int oi = u.op_begin; oi < u.op_end; ++oi) {
-            const ProgOp op = ops[oi];
-            int code = 0;
-            if (op.kind == OP_N1 || op.kind == OP_N2) {
-              code = noise_code(op, prob[op.pidx], seed, traj, (uint64_t)rnd);
-              if (!code) continue;
-            }
-            if ((op.kind == OP_T1 || op.kind == OP_T2) && !twirl_fires(op, prob[op.pidx], seed, traj, (uint64_t)rnd))
-              continue;
-            // left-multiply M by this op's matrix G (dim x dim, embedded in the unit's local qubits)
-            double2 G[16];
-            for (int i = 0; i < 16; ++i) G[i] = make_double2(0.0, 0.0);
-            auto from_tab = [&](int id, int r, int c) {
-              return make_double2((double)mats[id][r * 4 + c].x, (double)mats[id][r * 4 + c].y);
-            };
-            if (dim == 2) {
-              const int id = (op.kind == OP_U1 || op.kind == OP_T1) ? op.mat : code;
-              for (int r = 0; r < 2; ++r)
-                for (int c = 0; c < 2; ++c) G[r * 4 + c] = from_tab(id, r, c);
-            } else if (op.kind == OP_U2 || op.kind == OP_T2) {
-              for (int r = 0; r < 4; ++r)
-                for (int c = 0; c < 4; ++c) G[r * 4 + c] = from_tab(op.mat, r, c);
-            } else {
-              // one-qubit op or Pauli pair on a 2-qubit unit: local index 2*bit(qa) + bit(qb)
-              int ida = 0, idb = 0;
-              if (op.kind == OP_N2) { ida = code >> 2; idb = code & 3; }
-              else {
-                const int id = op.kind == OP_U1 ? op.mat : code;
-                if (op.q0 == u.qa) ida = id; else idb = id;
-              }
-              if (op.kind == OP_N2 && op.q0 != u.qa) { const int t = ida; ida = idb; idb = t; }
-              for (int ra = 0; ra < 2; ++ra)
-                for (int rb = 0; rb < 2; ++rb)
-                  for (int ca = 0; ca < 2; ++ca)
-                    for (int cb = 0; cb < 2; ++cb) {
-                      const double2 x = from_tab(ida, ra, ca), y = from_tab(idb, rb, cb);
-                      G[(2 * ra + rb) * 4 + 2 * ca + cb] = make_double2(x.x * y.x - x.y * y.y, x.x * y.y + x.y * y.x);
-                    }
-            }
-            double2 R[16];
-            for (int r = 0; r < dim; ++r)
-              for (int c = 0; c < dim; ++c) {
-                double re = 0.0, im = 0.0;
-                for (int k = 0; k < dim; ++k) {
-                  const double2 g = G[r * 4 + k], m = M[k * 4 + c];
-                  re += g.x * m.x - g.y * m.y;
-                  im += g.x * m.y + g.y * m.x;
-                }
-                R[r * 4 + c] = make_double2(re, im);
-              }
-            for (int r = 0; r < dim; ++r)
-              for (int c = 0; c < dim; ++c) M[r * 4 + c] = R[r * 4 + c];
-            any = 1;
-          }
-          for (int i = 0; i < 16; ++i) F[i] = M[i];
-          *sflag = any;
-        }
-        __syncthreads();
-        if (*sflag) {
-          T2 f[16];
-          for (int i = 0; i < 16; ++i) f[i] = mk<T2>(F[i].x, F[i].y);
-          if (u.nq == 1) {
-            const int b = u.qa;
-            for (int pr = tid; pr < kUAmp / 2; pr += nt) {
-              const int i0 = (int)ins0(pr, b), i1 = i0 | (1 << b);
-              const T2 x = slab[i0], y = slab[i1];
-              T2 o0 = mk<T2>(0, 0), o1 = mk<T2>(0, 0);
-              o0 = cmul_add<T>(o0, f[0], x); o0 = cmul_add<T>(o0, f[1], y);
-              o1 = cmul_add<T>(o1, f[4], x); o1 = cmul_add<T>(o1, f[5], y);
-              slab[i0] = o0;
-              slab[i1] = o1;
-            }
-          } else {
-            const int qa = u.qa, qb = u.qb, lo = qa < qb ? qa : qb, hi = qa < qb ? qb : qa;
-            for (int qd = tid; qd < kUAmp / 4; qd += nt) {
-              const int base = (int)ins0(ins0(qd, lo), hi);
-              int idx[4];
-              T2 x[4];
-              for (int l = 0; l < 4; ++l) {
-                idx[l] = base | ((l >> 1) << qa) | ((l & 1) << qb);
-                x[l] = slab[idx[l]];
-              }
-              for (int r = 0; r < 4; ++r) {
-                T2 acc = mk<T2>(0, 0);
-                for (int k = 0; k < 4; ++k) acc = cmul_add<T>(acc, f[r * 4 + k], x[k]);
-                slab[idx[r]] = acc;
-              }
-            }
-          }
-        }
-        __syncthreads();
-      } else {
+      Fon[it] = u.kind != 0 ? 0
+                : u.nq == 1 ? fuse_unit<2, T2>(u, ops, mats, prob, seed, traj, rnd, Ft + 16 * it)
+                            : fuse_unit<4, T2>(u, ops, mats, prob, seed, traj, rnd, Ft + 16 * it);
+    }
+    __syncthreads();
+    for (int pi = 0; pi < npass; ++pi) {
+      const UPass P = passes[pi];
+      if (P.kind == 1) {
         // measurement of the ancilla at slab bit u.qa: Born rule, collapse, renormalise, reset
+        const UItem u = items[P.item];
         const int b = u.qa;
         double s0 = 0.0, s1 = 0.0;
         for (int pr = tid; pr < kUAmp / 2; pr += nt) {
@@ -565,7 +610,57 @@ __device__ void run_cta_u(const BatchArgs& a, unsigned char* sm, uint32_t item) 
         }
         __syncthreads();
         if (syn && tid == 0) syn[rnd * kNStab + u.stab] = (uint8_t)(m ^ u.offset);
+        continue;
       }
+      // apply: thread-local groups over the pass's bits, every unit of the pass in turn
+      const int G = kUAmp >> P.nbits;
+      for (int pu = P.u0; pu < P.u1; ++pu) {
+        const UPassUnit U = punits[pu];
+        if (!Fon[U.item]) continue;
+        const double2* Fg = Ft + 16 * U.item;
+        const int nsub = 1 << U.nother;
+        if (U.nq == 1) {
+          const T2 f0 = mk<T2>(Fg[0].x, Fg[0].y), f1 = mk<T2>(Fg[1].x, Fg[1].y);
+          const T2 f4 = mk<T2>(Fg[4].x, Fg[4].y), f5 = mk<T2>(Fg[5].x, Fg[5].y);
+          for (int g = tid; g < G; g += nt) {
+            const int base = group_base_u(g, P.bits, P.nbits);
+            for (int sub = 0; sub < nsub; ++sub) {
+              const int i0 = base | deposit_bits(sub, U.other, U.nother), i1 = i0 | (1 << U.qa);
+              const T2 x = slab[i0], y = slab[i1];
+              T2 o0 = mk<T2>(0, 0), o1 = mk<T2>(0, 0);
+              o0 = cmul_add<T>(o0, f0, x); o0 = cmul_add<T>(o0, f1, y);
+              o1 = cmul_add<T>(o1, f4, x); o1 = cmul_add<T>(o1, f5, y);
+              slab[i0] = o0;
+              slab[i1] = o1;
+            }
+          }
+        } else {
+          T2 f[16];
+#pragma unroll
+          for (int i = 0; i < 16; ++i) f[i] = mk<T2>(Fg[i].x, Fg[i].y);
+          for (int g = tid; g < G; g += nt) {
+            const int base = group_base_u(g, P.bits, P.nbits);
+            for (int sub = 0; sub < nsub; ++sub) {
+              const int b0 = base | deposit_bits(sub, U.other, U.nother);
+              int idx[4];
+              T2 x[4];
+#pragma unroll
+              for (int l = 0; l < 4; ++l) {
+                idx[l] = b0 | ((l >> 1) << U.qa) | ((l & 1) << U.qb);
+                x[l] = slab[idx[l]];
+              }
+#pragma unroll
+              for (int r = 0; r < 4; ++r) {
+                T2 acc = mk<T2>(0, 0);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) acc = cmul_add<T>(acc, f[r * 4 + k], x[k]);
+                slab[idx[r]] = acc;
+              }
+            }
+          }
+        }
+      }
+      __syncthreads();
     }
   }
   if (init) {
@@ -667,6 +762,11 @@ struct qec_batch {
   double2* d_snap = nullptr;
   int64_t snap_item = -1;   // for the next run
   bool snap_valid = false;  // a completed run recorded a snapshot
+  int fusion_k = 4;         // unreduced engine: widest pass (slab bits)
+  int u_threads = 256;      // unreduced engine: threads per CTA
+  UPass* d_upasses[2] = {nullptr, nullptr};        // [0] noisy round, [1] init round
+  UPassUnit* d_upunits[2] = {nullptr, nullptr};
+  int n_upasses[2] = {0, 0};
 };
 
 namespace {
@@ -696,7 +796,8 @@ void batch_free(qec_batch* b) {
   void* ptrs[] = {b->d_ops, b->d_blocks, b->d_iops, b->d_iblocks, b->d_mats, b->d_psi0[0], b->d_psi0[1],
                   b->d_noise, b->d_kind, b->d_traj, b->d_ctl, b->d_syn, b->d_bits, b->d_log,
                   b->d_uops, b->d_uitems, b->d_iuops, b->d_iuitems, b->d_psi0_u[0], b->d_psi0_u[1],
-                  b->d_idx, b->d_idx_u, b->d_snap};
+                  b->d_idx, b->d_idx_u, b->d_snap, b->d_upasses[0], b->d_upasses[1], b->d_upunits[0],
+                  b->d_upunits[1]};
   for (void* p : ptrs) if (p) cudaFree(p);
   if (b->fork) cudaEventDestroy(b->fork);
   if (b->join) cudaEventDestroy(b->join);
@@ -735,6 +836,12 @@ BatchArgs batch_args(const qec_batch* b) {
   a.bits = b->d_bits;
   a.logical = b->d_log;
   a.snap = b->d_snap;
+  a.upasses = b->d_upasses[0];
+  a.n_upasses = b->n_upasses[0];
+  a.upunits = b->d_upunits[0];
+  a.iupasses = b->d_upasses[1];
+  a.n_iupasses = b->n_upasses[1];
+  a.iupunits = b->d_upunits[1];
   a.init_mode = 0;
   a.init_prec = 0;
   a.init_out = nullptr;
@@ -757,7 +864,7 @@ qec_status ensure_batch_graph(qec_batch* b) {
     le = cudaGetLastError();
   }
   if (le == cudaSuccess) {
-    k_batch_u<<<b->num_sms * b->u_ctas_per_sm, 256, kUSmem, b->side>>>(a);
+    k_batch_u<<<b->num_sms * b->u_ctas_per_sm, b->u_threads, kUSmem, b->side>>>(a);
     le = cudaGetLastError();
   }
   if (le == cudaSuccess) le = cudaEventRecord(b->join, b->side);
@@ -770,6 +877,87 @@ qec_status ensure_batch_graph(qec_batch* b) {
   }
   b->graph = g;
   QEC_BCUDA(cudaGraphInstantiate(&b->gexec, g, 0));
+  return QEC_OK;
+}
+
+// Passes of one round of the unreduced engine for fusion width k: consecutive units whose slab bits
+// are disjoint from those already in the pass (they commute with them) join it while the pass has at
+// most k bits; a unit on a bit already in the pass, or a measurement, closes it.
+void build_passes(const UProgram& U, int k, std::vector<UPass>& passes, std::vector<UPassUnit>& punits) {
+  passes.clear();
+  punits.clear();
+  UPass cur{};
+  uint32_t mask = 0;
+  auto close = [&]() {
+    if (cur.u1 == cur.u0) return;
+    cur.nbits = 0;
+    for (int q = 0; q < 32; ++q)
+      if (mask & (1u << q)) cur.bits[cur.nbits++] = q;
+    for (int i = cur.u0; i < cur.u1; ++i) {
+      UPassUnit& pu = punits[i];
+      const uint32_t um = (1u << pu.qa) | (pu.nq == 2 ? (1u << pu.qb) : 0u);
+      pu.nother = 0;
+      for (int j = 0; j < cur.nbits; ++j)
+        if (!(um & (1u << cur.bits[j]))) pu.other[pu.nother++] = cur.bits[j];
+    }
+    passes.push_back(cur);
+  };
+  auto open = [&]() {
+    cur = UPass{};
+    cur.kind = 0;
+    cur.u0 = cur.u1 = (int32_t)punits.size();
+    mask = 0;
+  };
+  open();
+  for (int it = 0; it < (int)U.items.size(); ++it) {
+    const UItem& u = U.items[it];
+    if (u.kind == 1) {
+      close();
+      UPass m{};
+      m.kind = 1;
+      m.item = it;
+      passes.push_back(m);
+      open();
+      continue;
+    }
+    const uint32_t um = (1u << u.qa) | (u.nq == 2 ? (1u << u.qb) : 0u);
+    if ((mask & um) || __builtin_popcount(mask | um) > k) {
+      close();
+      open();
+    }
+    UPassUnit pu{};
+    pu.item = it;
+    pu.nq = u.nq;
+    pu.qa = u.qa;
+    pu.qb = u.nq == 2 ? u.qb : 0;
+    punits.push_back(pu);
+    cur.u1 = (int32_t)punits.size();
+    mask |= um;
+  }
+  close();
+}
+
+// Fusion width (2..6 slab bits per pass) and threads per CTA (128..512) of the unreduced engine.
+qec_status set_fusion(qec_batch* b, int k, int threads) {
+  if (k < 2 || k > kUMaxFusionDecl || (threads != 128 && threads != 256 && threads != 512))
+    return bfail(QEC_EINVAL, "fusion width must be in [2, 6] and threads 128, 256 or 512");
+  const UProgram* progs[2] = {&b->uprog, &b->iuprog};
+  for (int w = 0; w < 2; ++w) {
+    std::vector<UPass> passes;
+    std::vector<UPassUnit> punits;
+    build_passes(*progs[w], k, passes, punits);
+    QEC_BCUDA(cudaMemcpy(b->d_upasses[w], passes.data(), sizeof(UPass) * passes.size(), cudaMemcpyHostToDevice));
+    if (!punits.empty())
+      QEC_BCUDA(cudaMemcpy(b->d_upunits[w], punits.data(), sizeof(UPassUnit) * punits.size(), cudaMemcpyHostToDevice));
+    b->n_upasses[w] = (int)passes.size();
+  }
+  int occ = 0;
+  QEC_BCUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch_u, threads, kUSmem));
+  if (occ < 1) return bfail(QEC_EUNSUPPORTED, "unreduced batched kernel does not fit an SM with this shape");
+  drop_batch_graph(b);
+  b->fusion_k = k;
+  b->u_threads = threads;
+  b->u_ctas_per_sm = occ;
   return QEC_OK;
 }
 
@@ -814,6 +1002,8 @@ qec_status qec_batch_create(int32_t d, int32_t rounds, int32_t gates, uint32_t m
   if (!build_program(p, true, b->prog, err, true) || !build_program(p, false, b->iprog, err) ||
       !build_unreduced_program(p, true, b->uprog, err, true) || !build_unreduced_program(p, false, b->iuprog, err))
     return bail(bfail(QEC_EINVAL, err));
+  if (b->uprog.items.size() > (size_t)kUMaxItems || b->iuprog.items.size() > (size_t)kUMaxItems)
+    return bail(bfail(QEC_EUNSUPPORTED, "unreduced round has more items than the engine's unit table"));
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, dev);
@@ -832,7 +1022,8 @@ qec_status qec_batch_create(int32_t d, int32_t rounds, int32_t gates, uint32_t m
                      (void**)&b->d_traj, (void**)&b->d_ctl, (void**)&b->d_syn, (void**)&b->d_bits,
                      (void**)&b->d_log, (void**)&b->d_uops, (void**)&b->d_uitems, (void**)&b->d_iuops,
                      (void**)&b->d_iuitems, &b->d_psi0_u[0], &b->d_psi0_u[1], (void**)&b->d_idx,
-                     (void**)&b->d_idx_u, (void**)&b->d_snap};
+                     (void**)&b->d_idx_u, (void**)&b->d_snap, (void**)&b->d_upasses[0], (void**)&b->d_upasses[1],
+                     (void**)&b->d_upunits[0], (void**)&b->d_upunits[1]};
   const size_t sizes[] = {sizeof(ProgOp) * (b->prog.ops.size() + 1), sizeof(BlockInfo) * kNStab,
                           sizeof(ProgOp) * (b->iprog.ops.size() + 1), sizeof(BlockInfo) * kNStab,
                           sizeof(b->prog.mats), (size_t)kNAmp * 16, (size_t)kNAmp * 8,
@@ -841,7 +1032,10 @@ qec_status qec_batch_create(int32_t d, int32_t rounds, int32_t gates, uint32_t m
                           sizeof(ProgOp) * (b->uprog.ops.size() + 1), sizeof(UItem) * (b->uprog.items.size() + 1),
                           sizeof(ProgOp) * (b->iuprog.ops.size() + 1), sizeof(UItem) * (b->iuprog.items.size() + 1),
                           (size_t)kUAmp * 16, (size_t)kUAmp * 8, sizeof(uint32_t) * max_traj,
-                          sizeof(uint32_t) * max_traj, sizeof(double2) * kNAmp};
+                          sizeof(uint32_t) * max_traj, sizeof(double2) * kNAmp,
+                          sizeof(UPass) * (b->uprog.items.size() + 1), sizeof(UPass) * (b->iuprog.items.size() + 1),
+                          sizeof(UPassUnit) * (b->uprog.items.size() + 1),
+                          sizeof(UPassUnit) * (b->iuprog.items.size() + 1)};
   for (size_t i = 0; i < sizeof(sizes) / sizeof(sizes[0]); ++i) {
     e = cudaMalloc(allocs[i], sizes[i]);
     if (e != cudaSuccess) return bail(bfail(QEC_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e)));
@@ -869,9 +1063,8 @@ qec_status qec_batch_create(int32_t d, int32_t rounds, int32_t gates, uint32_t m
   qec_status st = set_shape(b, 8);
   if (st) return bail(st);
   e = cudaFuncSetAttribute(k_batch_u, cudaFuncAttributeMaxDynamicSharedMemorySize, kUSmem);
-  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b->u_ctas_per_sm, k_batch_u, 256, kUSmem);
-  if (e != cudaSuccess || b->u_ctas_per_sm < 1)
-    return bail(bfail(QEC_ECUDA, "unreduced batched kernel does not fit an SM"));
+  if (e != cudaSuccess) return bail(bfail(QEC_ECUDA, "unreduced batched kernel does not fit an SM"));
+  if ((st = set_fusion(b, 4, 256))) return bail(st);
   for (int prec = 0; prec < 2; ++prec) {   // the noise-free init round, once per precision
     BatchArgs a = batch_args(b);
     a.init_mode = 1;
@@ -956,18 +1149,37 @@ qec_status qec_batch_run(qec_batch* b, uint64_t seed, uint32_t n, const uint64_t
 
 qec_status qec_batch_autotune(qec_batch* b, uint64_t seed, uint32_t n, const uint64_t* traj, const int32_t* kind,
                               const qec_noise* noise, int32_t* chosen_warps, float* best_ms) {
-  if (!b || !chosen_warps || !best_ms) return bfail(QEC_EINVAL, "null argument");
+  if (!b || !chosen_warps || !best_ms || !traj || !kind || !noise) return bfail(QEC_EINVAL, "null argument");
+  // the sample split by register: each engine is tuned on its own trajectories
+  std::vector<uint64_t> tr[2];
+  std::vector<int32_t> kd[2];
+  std::vector<qec_noise> nz[2];
+  for (uint32_t i = 0; i < n; ++i) {
+    const int u = (kind[i] & 2) ? 1 : 0;
+    tr[u].push_back(traj[i]);
+    kd[u].push_back(kind[i]);
+    nz[u].push_back(noise[i]);
+  }
+  auto time_run = [&](int u, float& t) -> qec_status {
+    t = 1e30f;
+    if (tr[u].empty()) return QEC_OK;
+    for (int rep = 0; rep < 2; ++rep) {   // first run warms up
+      qec_status st = qec_batch_run(b, seed, (uint32_t)tr[u].size(), tr[u].data(), kd[u].data(), nz[u].data(),
+                                    nullptr, nullptr, nullptr);
+      if (st) return st;
+      if (rep) t = b->last_ms;
+    }
+    return QEC_OK;
+  };
+  // reduced register: warps per CTA
   const int cand[] = {2, 4, 6, 8, 10};
   int best = -1;
   float best_t = 0.f;
   for (int w : cand) {
     if (set_shape(b, w) != QEC_OK) continue;
-    float t = 1e30f;
-    for (int rep = 0; rep < 2; ++rep) {   // first run warms up
-      qec_status st = qec_batch_run(b, seed, n, traj, kind, noise, nullptr, nullptr, nullptr);
-      if (st) return st;
-      if (rep) t = b->last_ms;
-    }
+    float t;
+    qec_status st = time_run(0, t);
+    if (st) return st;
     if (best < 0 || t < best_t) {
       best = w;
       best_t = t;
@@ -976,9 +1188,45 @@ qec_status qec_batch_autotune(qec_batch* b, uint64_t seed, uint32_t n, const uin
   if (best < 0) return bfail(QEC_EUNSUPPORTED, "no batched kernel shape fits");
   qec_status st = set_shape(b, best);
   if (st) return st;
+  // unreduced register: fusion width (slab bits per pass) x threads per CTA
+  int bk = -1, bthr = 256;
+  float bu = 0.f;
+  for (int k = 2; k <= kUMaxFusionDecl; ++k)
+    for (int thr : {128, 256}) {
+      if (set_fusion(b, k, thr) != QEC_OK) continue;
+      float t;
+      if ((st = time_run(1, t))) return st;
+      if (bk < 0 || t < bu) {
+        bk = k;
+        bthr = thr;
+        bu = t;
+      }
+    }
+  if (bk < 0) return bfail(QEC_EUNSUPPORTED, "no unreduced engine shape fits");
+  if ((st = set_fusion(b, bk, bthr))) return st;
+  float t_all = 0.f;   // the whole sample with the chosen configuration
+  for (int rep = 0; rep < 2; ++rep) {
+    if ((st = qec_batch_run(b, seed, n, traj, kind, noise, nullptr, nullptr, nullptr))) return st;
+    t_all = b->last_ms;
+  }
   *chosen_warps = best;
-  *best_ms = best_t;
+  *best_ms = t_all;
   return QEC_OK;
+}
+
+qec_status qec_batch_config(const qec_batch* b, int32_t* warps_per_cta, int32_t* fusion_width, int32_t* u_threads) {
+  if (!b || !warps_per_cta || !fusion_width || !u_threads) return bfail(QEC_EINVAL, "null argument");
+  *warps_per_cta = b->warps_per_cta;
+  *fusion_width = b->fusion_k;
+  *u_threads = b->u_threads;
+  return QEC_OK;
+}
+
+qec_status qec_batch_set_config(qec_batch* b, int32_t warps_per_cta, int32_t fusion_width, int32_t u_threads) {
+  if (!b) return bfail(QEC_EINVAL, "null handle");
+  qec_status st = set_shape(b, warps_per_cta);
+  if (st) return st;
+  return set_fusion(b, fusion_width, u_threads);
 }
 
 qec_status qec_batch_snapshot(qec_batch* b, int64_t item) {

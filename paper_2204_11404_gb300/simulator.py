@@ -114,6 +114,13 @@ class BatchSimulator:
         n, t, k, nz = self._inputs(traj, kind, noise)
         return capi.qec_batch_autotune(self.h, seed, n, t.ctypes.data, k.ctypes.data, ctypes.addressof(nz))
 
+    def config(self):
+        """(warps per CTA of the reduced engine, fusion width and threads per CTA of the unreduced one)."""
+        return capi.qec_batch_config(self.h)
+
+    def set_config(self, warps_per_cta, fusion_width, u_threads):
+        capi.qec_batch_set_config(self.h, warps_per_cta, fusion_width, u_threads)
+
     def snapshot(self, item):
         """Record the final data-register state of trajectory `item` (index into the next run's
         arrays; -1 = none) during the next run."""

@@ -130,3 +130,34 @@ def test_batched_amplitudes_match_oracle(gates):
             err = np.abs(b.state() - ref).max()
             assert err < AMP_TOL[prec], (kind, err)
         b.snapshot(-1)
+
+
+def test_unreduced_engine_fusion_widths_are_bit_identical_and_autotuned():
+    """The 17-qubit engine applies consecutive gate units on disjoint slab bits in one pass of up to
+    k bits; inside a pass every amplitude still sees the units in program order, so every fusion
+    width and CTA size gives the same outcomes and the same state bits.  The autotuner then picks a
+    configuration among them and reports it."""
+    n = 24
+    traj = [900 + i for i in range(n)]
+    kinds = ["c128u", "c64u"] * (n // 2)
+    noise = [dict(W.STRESS) if i % 3 else dict(W.STRESS, twirl=1, theta_rx=0.4, phi_zz=0.2) for i in range(n)]
+    ref = None
+    with BatchSimulator(3, "cr", max_traj=128) as b:
+        for k in (2, 3, 4, 5, 6):
+            for thr in (128, 256):
+                b.set_config(8, k, thr)
+                assert b.config() == (8, k, thr)
+                b.snapshot(5)
+                out = b.run(97, traj, kinds, noise)
+                st = b.state()
+                if ref is None:
+                    ref = (out, st)
+                    continue
+                for x, y in zip(out, ref[0]):
+                    assert (x == y).all(), (k, thr)
+                assert np.array_equal(st.view(np.uint64), ref[1].view(np.uint64)), (k, thr)
+        w, ms = b.autotune(97, traj * 4, kinds * 4, noise * 4)
+        warps, k, thr = b.config()
+        assert w == warps and 2 <= k <= 6 and thr in (128, 256) and ms > 0
+    o = run_trajectory(3, 3, "cr", "unreduced", noise[5], seed=97, traj=traj[5], want_state=True)
+    assert compare_trajectory(ref[0][0][5], ref[0][1][5], o, TAU["c64"]) in ("exact", "ambiguous")

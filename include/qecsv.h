@@ -201,10 +201,10 @@ qec_status qec_selftest_wait(qec_sim* sim, uint32_t polls);
  * which every GPU that loads the library holds until the process exits.  It
  * fits d = 3 with at most 16 noisy rounds; larger requests return QEC_EINVAL.
  * The first call on a device looks up that array's device address (once per
- * device, with the device current); make that first call before any stream
- * capture.  Every call reuses the same array and resets what must start from
- * zero, so calls that overlap on the GPU (different streams, or concurrent host
- * threads) race and corrupt each other: serialise them.
+ * device, with the device current).  Every call reuses the same array and
+ * resets what must start from zero, so calls that overlap on the GPU
+ * (different streams, or concurrent host threads) race and corrupt each
+ * other: serialise them.
  */
 qec_status qec_run_trajectories_noalloc(const qec_params* params, uint64_t seed, uint64_t first_traj, uint32_t n,
                                         uint8_t* d_syndromes, uint8_t* d_data_bits, uint8_t* d_raw_logical,

@@ -202,6 +202,15 @@ __device__ __forceinline__ uint32_t member_off(int l, const int (&q)[4]) {
   return o;
 }
 
+// Register offset of tile tix in a tiled pass: bit j of tix goes to register bit obits[j], j < nout
+// (nout <= 25 < 32).  Lane j deposits bit j (obit = obits[lane], loaded once per thread) and the warp
+// ORs the lanes' bits: one step per thread instead of a loop over nout bits.  Every lane of the warp
+// must call it with the same tix.
+__device__ __forceinline__ uint32_t tile_base_warp(uint32_t tix, int nout, int obit) {
+  const int lane = threadIdx.x & 31;
+  return __reduce_or_sync(0xffffffffu, lane < nout ? ((tix >> lane) & 1u) << obit : 0u);
+}
+
 // End of a probability pass: block sums of (A, N) into per-CTA partials; the last CTA to finish
 // (ticket) sums the partials in a fixed order, draws the outcome m (u < A/N, or the forced value),
 // stores A, N, m and the syndrome bit, and resets the ticket.  Deterministic for a fixed grid.
@@ -454,11 +463,8 @@ __global__ void __launch_bounds__(256) k_fused(FusedArgs f) {
   const T2* src = reinterpret_cast<const T2*>(f.ap.src);
   T2* dst = reinterpret_cast<T2*>(f.ap.dst);
   const uint32_t ntile = 1u << f.nout;
-  auto tile_base = [&](uint32_t tix) {
-    uint32_t tb = 0;
-    for (int j = 0; j < f.nout; ++j) tb |= ((tix >> j) & 1u) << f.obits[j];
-    return tb;
-  };
+  const int obit = (threadIdx.x & 31) < (unsigned)f.nout ? f.obits[threadIdx.x & 31] : 0;
+  auto tile_base = [&](uint32_t tix) { return tile_base_warp(tix, f.nout, obit); };
   auto issue = [&](uint32_t tix, T2* buf) {
     const uint32_t tb = tile_base(tix);
     for (uint32_t e = threadIdx.x * CH; e < tsz; e += blockDim.x * CH)
@@ -757,11 +763,8 @@ __global__ void __launch_bounds__(256, 2) k_fused_tc(FusedArgs f) {
   const uint32_t ntile = 1u << f.nout;
   double accA = 0.0, accN = 0.0;
   uint32_t phase = 0;
-  auto tile_base = [&](uint32_t tix) {
-    uint32_t tb = 0;
-    for (int j = 0; j < f.nout; ++j) tb |= ((tix >> j) & 1u) << f.obits[j];
-    return tb;
-  };
+  const int obit = (threadIdx.x & 31) < (unsigned)f.nout ? f.obits[threadIdx.x & 31] : 0;
+  auto tile_base = [&](uint32_t tix) { return tile_base_warp(tix, f.nout, obit); };
   auto load_tile = [&](uint32_t tix) {
     const uint32_t tb = tile_base(tix);
 #pragma unroll
@@ -1004,11 +1007,8 @@ __global__ void __launch_bounds__(256, 2) k_oz(FusedArgs f) {
   const double2* src = reinterpret_cast<const double2*>(f.ap.src);
   double2* dst = reinterpret_cast<double2*>(f.ap.dst);
   const uint32_t ntile = 1u << f.nout;
-  auto tile_base = [&](uint32_t tix) {
-    uint32_t tb = 0;
-    for (int j = 0; j < f.nout; ++j) tb |= ((tix >> j) & 1u) << f.obits[j];
-    return tb;
-  };
+  const int obit = (threadIdx.x & 31) < (unsigned)f.nout ? f.obits[threadIdx.x & 31] : 0;
+  auto tile_base = [&](uint32_t tix) { return tile_base_warp(tix, f.nout, obit); };
   auto load_tile = [&](uint32_t tb) {
 #pragma unroll
     for (int i = 0; i < TS / 256; ++i) cp_async16(tile + cdst[i], src + (tb | coff[i]));
@@ -1300,11 +1300,8 @@ __global__ void __launch_bounds__(256, 2) k_ozf(FusedArgs f) {
   const double2* src = reinterpret_cast<const double2*>(f.ap.src);
   double2* dst = reinterpret_cast<double2*>(f.ap.dst);
   const uint32_t ntile = 1u << f.nout;
-  auto tile_base = [&](uint32_t tix) {
-    uint32_t tb = 0;
-    for (int j = 0; j < f.nout; ++j) tb |= ((tix >> j) & 1u) << f.obits[j];
-    return tb;
-  };
+  const int obit = (threadIdx.x & 31) < (unsigned)f.nout ? f.obits[threadIdx.x & 31] : 0;
+  auto tile_base = [&](uint32_t tix) { return tile_base_warp(tix, f.nout, obit); };
   auto load_tile = [&](uint32_t tb) {
 #pragma unroll
     for (int i = 0; i < TS / 256; ++i) cp_async16(tile + cdst(i), src + (tb | coff(i)));

@@ -64,6 +64,25 @@ def test_d3_stress_matches_oracle(gates, prec):
             assert ev == sorted(o["events"])
 
 
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+def test_d3_certain_noise_matches_oracle(prec):
+    """Degenerate noise rates: p = 1 at every site (a Pauli at every step of every qubit) beside
+    p = 0 for the idle steps, with the coherent terms on.  The occurrence test compares a 53-bit
+    uniform with p, so p = 1 always fires and p = 0 never does; draws, syndromes, bits and the state
+    must still match the oracle."""
+    nz = dict(p1=1.0, p2=1.0, p_idle=0.0, theta_rx=0.1, phi_zz=0.05)
+    with Simulator(3, 2, "cr", prec, **nz) as sim:
+        kinds = check_batch(sim, 3, 2, "cr", nz, 37, 0, 24, prec)
+        assert kinds.count("ambiguous") <= (0 if prec == "c128" else 2)
+        sim.record_events(4096)
+        [(traj, o)] = unambiguous(lambda t: oracle_traj(3, 2, "cr", nz, 37, t, want_state=True), range(24, 60), TAU[prec])
+        syn, bits, log = sim.run(37, traj, 1)
+        assert compare_trajectory(syn[0], bits[0], o, TAU[prec]) == "exact"
+        assert np.abs(sim.state() - o["state"][: 1 << 9]).max() < AMP_TOL[prec]
+        ev = sorted(tuple(int(x) for x in e[1:]) for e in sim.events())
+        assert ev == sorted(o["events"]) and len(ev) > 0
+
 def test_offsets_chunking_and_device_outputs():
     nz = W.STRESS
     n = 1100   # more than one internal batch

@@ -683,11 +683,61 @@ __device__ __forceinline__ void tc_sync() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
-// Shared memory: one 32 KiB tile, 3xTF32 A operands (2 x 32 KiB), four 4 KiB B operands,
-// 113 KiB in all, so two CTAs share an SM and one's tensor-core phases overlap the other's
-// memory phases.  Tile addresses are computed from the bit lists (no offset table).
-constexpr int kTcSmem = 8 * 4096 + 2 * 4 * 256 * 32 + 4 * 4 * 32 * 32;
+// TF32 MMA M = 128, N = 32, D = F32, with A in tensor memory (row m in lane m, its K = 8 elements
+// in 8 consecutive 32-bit columns from a_tmem) and B K-major in shared memory.
+__device__ __forceinline__ void umma_tf32_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t bd, uint32_t acc) {
+  asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+               " tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n"
+               ::"r"(d_tmem), "r"(a_tmem), "l"(bd), "r"(kIdescTf32), "r"(acc));
+}
 
+// Stores v[0..7] into 8 consecutive columns of this thread's lane (warp quarter rule as tcgen05.ld).
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const float (&v)[8]) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};"
+               ::"r"(taddr), "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+                 "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+                 "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7]))
+               : "memory");
+}
+
+// The probability GEMM of a regrouped tile whose 3xTF32 A operands are in tensor memory: M-half h
+// has A_hi at columns ca + 64h .. + 31 and A_lo at ca + 64h + 32 .. + 63; D at column dc + 32h.
+// 2 M-halves x 4 K-steps x 3 split terms, in the order of issue_gemm; commit arrives on mbar.
+__device__ __forceinline__ void issue_gemm_ts(uint32_t tmem, uint32_t dc, uint32_t ca, const float* Bhi,
+                                              const float* Blo, uint32_t mbar) {
+  const uint64_t bh = umma_desc(smem_u32(Bhi), 128, 1024), bl = umma_desc(smem_u32(Blo), 128, 1024);
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const uint32_t d = tmem + dc + 32u * h;
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      const uint32_t ah = tmem + ca + 64u * h + 8u * s, ko = (256u * s) >> 4;
+      umma_tf32_ts(d, ah, bh + ko, s > 0);
+      umma_tf32_ts(d, ah, bl + ko, 1);
+      umma_tf32_ts(d, ah + 32u, bh + ko, 1);
+    }
+  }
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
+}
+
+// Shared memory: the input tile (32 KiB), the first GEMM's 3xTF32 A operands (2 x 32 KiB; the
+// updated tile takes their place once that GEMM has read them) and four 4 KiB B operands: 112 KiB,
+// so two CTAs share an SM.  Tensor memory, 256 columns per CTA (two CTAs fill an SM's 512): D of
+// the apply GEMM (columns 0..63), D of the probability GEMM (64..127) and that GEMM's A operands,
+// the regrouped updated tile in TF32 hi and lo (128..255).  Tile addresses are computed from the
+// bit lists (no offset table).
+constexpr int kTcSmem = 8 * 4096 + 2 * 4 * 256 * 32 + 4 * 4 * 32 * 32;
+constexpr uint32_t kTcColD2 = 64, kTcColA2 = 128;
+
+// Per 4096-amplitude tile (256 groups of 16 amplitudes, one per thread):
+//  1. gather each group of block s from the input tile as a row of K = 32 reals, split hi + lo in
+//     TF32 into the A operands; the input buffer then takes the next tile's copy at once;
+//  2. the apply GEMM (24 MMAs into TMEM); under it, the previous tile's probability sums;
+//  3. its outputs, the updated tile, go where the A operands were;
+//  4. regroup the updated tile by block s+1 (sum |psi|^2 for N), split it into tensor memory as the
+//     probability GEMM's A, and store the updated tile to the register;
+//  5. the probability GEMM (A from tensor memory), left running under the next tile's gather.
+// Per-thread sums are taken in tile order, as one thread's tiles are fixed (b, b + grid, ...).
 __global__ void __launch_bounds__(256, 2) k_fused_tc(FusedArgs f) {
   constexpr int C = 16;
   extern __shared__ __align__(128) unsigned char tsm[];
@@ -695,11 +745,12 @@ __global__ void __launch_bounds__(256, 2) k_fused_tc(FusedArgs f) {
   float2* tile = reinterpret_cast<float2*>(tsm);
   float* Ahi = reinterpret_cast<float*>(tile + tsz);
   float* Alo = Ahi + 256 * 32;
+  float2* outt = reinterpret_cast<float2*>(Ahi);                  // the updated tile (tile slots)
   float* Bahi = Alo + 256 * 32;
   float* Balo = Bahi + 32 * 32;
   float* Bphi = Balo + 32 * 32;
   float* Bplo = Bphi + 32 * 32;
-  __shared__ __align__(8) uint64_t mbar;
+  __shared__ __align__(8) uint64_t mbar[2];
   __shared__ uint32_t tmem_base;
   __shared__ int s_err;
   __shared__ double sred[64];
@@ -712,18 +763,19 @@ __global__ void __launch_bounds__(256, 2) k_fused_tc(FusedArgs f) {
     build_b(reinterpret_cast<const float2*>(f.pr.kraus) + 256, 1.0, Bphi, Bplo);
     if (tid == 0) {
       s_err = 0;
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[1])));
       asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
-      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(smem_u32(&tmem_base)));
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(smem_u32(&tmem_base)));
       asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
   }
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   tc_sync();
   const uint32_t tmem = tmem_base;
-  const uint32_t mb = smem_u32(&mbar);
+  const uint32_t mb1 = smem_u32(&mbar[0]), mb2 = smem_u32(&mbar[1]);
   int qa[4], qp[4];
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
@@ -751,18 +803,22 @@ __global__ void __launch_bounds__(256, 2) k_fused_tc(FusedArgs f) {
     for (int j = 0; j < f.nt - f.lb; ++j) o |= ((h >> j) & 1u) << f.hbits[j];
     coff[i] = o | (e & lmask);
   }
-  const int trow = 128 * (warp >> 2) + 32 * (warp & 3) + lane;
-  const uint32_t sba = slot(local_base<4>((uint32_t)tid, qa)), sbt = slot(local_base<4>((uint32_t)trow, qa));
-  const uint32_t sbp = slot(local_base<4>((uint32_t)tid, qp));
+  // Thread tid owns row tid of both GEMMs: M-half tid / 128, TMEM lane tid % 128, which is in its
+  // warp's lane quarter (32 (warp % 4) ..).
+  const uint32_t sba = slot(local_base<4>((uint32_t)tid, qa)), sbp = slot(local_base<4>((uint32_t)tid, qp));
   uint32_t cd[8];   // slots of this thread's 16-byte chunks
 #pragma unroll
   for (int i = 0; i < 8; ++i) cd[i] = slot((uint32_t)tid * 2 + 512u * i);
-  const uint32_t taddr = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + 32u * (warp >> 2);
+  const uint32_t tq = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
+  const uint32_t taddr = tq + 32u * (warp >> 2);                      // D of the apply GEMM, this row
+  const uint32_t taddr2 = tq + kTcColD2 + 32u * (warp >> 2);          // D of the probability GEMM
+  const uint32_t tA2 = tq + kTcColA2 + 64u * (warp >> 2);             // this row of its A (hi; lo at +32)
   const float2* src = reinterpret_cast<const float2*>(f.ap.src);
   float2* dst = reinterpret_cast<float2*>(f.ap.dst);
   const uint32_t ntile = 1u << f.nout;
   double accA = 0.0, accN = 0.0;
-  uint32_t phase = 0;
+  uint32_t ph1 = 0, ph2 = 0;
+  bool pending = false;   // a probability GEMM whose sums are not taken yet
   const int obit = (threadIdx.x & 31) < (unsigned)f.nout ? f.obits[threadIdx.x & 31] : 0;
   auto tile_base = [&](uint32_t tix) { return tile_base_warp(tix, f.nout, obit); };
   auto load_tile = [&](uint32_t tix) {
@@ -771,18 +827,34 @@ __global__ void __launch_bounds__(256, 2) k_fused_tc(FusedArgs f) {
     for (int i = 0; i < 8; ++i) cp_async16(tile + cd[i], src + (tb | coff[i]));
     cp_async_commit();
   };
+  // sum of |y|^2 over this row's outputs of the probability GEMM (every thread waits on its barrier)
+  auto take_sums = [&]() {
+    if (!mbar_wait(mb2, ph2 & 1)) s_err = 1;
+    ++ph2;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    float d[32];
+    tmem_ld32(taddr2, d);
+    float sa = 0.f;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) sa = fmaf(d[j], d[j], sa);
+    accA += (double)sa;
+  };
   if (blockIdx.x < ntile) load_tile(blockIdx.x);
   for (uint32_t tix = blockIdx.x; tix < ntile; tix += gridDim.x) {
     const uint32_t tb = tile_base(tix);
     cp_async_wait<0>();
-    __syncthreads();
+    __syncthreads();   // the input tile is in; the previous tile's readers of the updated tile are done
 #pragma unroll
     for (int l = 0; l < C; l += 2) put_a4(Ahi, Alo, tid, 2 * l, tile[sba ^ offa[l]], tile[sba ^ offa[l + 1]]);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     tc_sync();
-    if (tid == 0) issue_gemm(tmem, Ahi, Alo, Bahi, Balo, mb);
-    if (!mbar_wait(mb, phase & 1)) s_err = 1;
-    ++phase;
+    // every thread has read the input tile: it takes the next tile's copy
+    if (tix + gridDim.x < ntile) load_tile(tix + gridDim.x);
+    if (tid == 0) issue_gemm(tmem, Ahi, Alo, Bahi, Balo, mb1);
+    if (pending) take_sums();   // the previous tile's probability GEMM, under this tile's apply GEMM
+    pending = false;
+    if (!mbar_wait(mb1, ph1 & 1)) s_err = 1;
+    ++ph1;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     __syncthreads();
     if (s_err) break;
@@ -790,48 +862,42 @@ __global__ void __launch_bounds__(256, 2) k_fused_tc(FusedArgs f) {
       float d[32];
       tmem_ld32(taddr, d);
 #pragma unroll
-      for (int r = 0; r < C; ++r) tile[sbt ^ offa[r]] = make_float2(d[2 * r], d[2 * r + 1]);
+      for (int r = 0; r < C; ++r) outt[sba ^ offa[r]] = make_float2(d[2 * r], d[2 * r + 1]);
     }
-    tc_sync();
+    __syncthreads();
     {
+      // regroup by block s+1 into the probability GEMM's A (tensor memory), 4 members at a time
       float sn = 0.f;
 #pragma unroll
-      for (int l = 0; l < C; l += 2) {
-        const float2 v0 = tile[sbp ^ offp[l]], v1 = tile[sbp ^ offp[l + 1]];
-        sn = fmaf(v0.x, v0.x, fmaf(v0.y, v0.y, sn));
-        sn = fmaf(v1.x, v1.x, fmaf(v1.y, v1.y, sn));
-        put_a4(Ahi, Alo, tid, 2 * l, v0, v1);
+      for (int l = 0; l < C; l += 4) {
+        float hv[8], lv[8];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float2 v = outt[sbp ^ offp[l + q]];
+          sn = fmaf(v.x, v.x, fmaf(v.y, v.y, sn));
+          hv[2 * q] = tf32_rna(v.x);
+          lv[2 * q] = tf32_rna(v.x - hv[2 * q]);
+          hv[2 * q + 1] = tf32_rna(v.y);
+          lv[2 * q + 1] = tf32_rna(v.y - hv[2 * q + 1]);
+        }
+        tmem_st8(tA2 + 2u * l, hv);
+        tmem_st8(tA2 + 32u + 2u * l, lv);
       }
       accN += (double)sn;
     }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    tc_sync();
-    if (tid == 0) issue_gemm(tmem, Ahi, Alo, Bphi, Bplo, mb);
-    // while the tensor cores work on the probability GEMM: write the updated tile out and
-    // start loading the next one into the same buffer
+    // the updated tile to the register
 #pragma unroll
     for (int i = 0; i < 8; ++i)
-      *reinterpret_cast<float4*>(dst + (tb | coff[i])) = *reinterpret_cast<const float4*>(tile + cd[i]);
-    __syncthreads();
-    if (tix + gridDim.x < ntile) load_tile(tix + gridDim.x);
-    if (!mbar_wait(mb, phase & 1)) s_err = 1;
-    ++phase;
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    __syncthreads();
-    if (s_err) break;
-    {
-      float d[32];
-      tmem_ld32(taddr, d);
-      float sa = 0.f;
-#pragma unroll
-      for (int j = 0; j < 32; ++j) sa = fmaf(d[j], d[j], sa);
-      accA += (double)sa;
-    }
+      *reinterpret_cast<float4*>(dst + (tb | coff[i])) = *reinterpret_cast<const float4*>(outt + cd[i]);
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
     tc_sync();
+    if (tid == 0) issue_gemm_ts(tmem, kTcColD2, kTcColA2, Bphi, Bplo, mb2);
+    pending = true;
   }
+  if (pending && !s_err) take_sums();
   cp_async_wait<0>();
   tc_sync();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tmem));
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem));
   if (s_err && tid == 0) atomicOr(&f.pr.ctl->status, 1u);
   prob_finish(f.pr, accA, accN, sred, &s_last);
 }

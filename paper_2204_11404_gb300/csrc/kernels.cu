@@ -635,11 +635,13 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
 }
 
-// Writes the 3xTF32-split real embedding of a 16x16 complex matrix (times scale) as B operands.
-__device__ void build_b(const float2* Kg, double scale, float* Bhi, float* Blo) {
+// Writes the 3xTF32-split real embedding of a 16x16 complex matrix (times scale) as B operands.  A
+// weight-2 block (w2) has its 4x4 matrix K in rows and columns 0..3; it is embedded as K (x) I on
+// groups whose index bits 0..1 are its qubits and bits 2..3 two spectator qubits.
+__device__ void build_b(const float2* Kg, double scale, float* Bhi, float* Blo, bool w2) {
   for (int idx = threadIdx.x; idx < 32 * 32; idx += blockDim.x) {
     const int n = idx >> 5, k = idx & 31, r = n >> 1, c = k >> 1;
-    const float2 kv = Kg[r * 16 + c];
+    const float2 kv = !w2 ? Kg[r * 16 + c] : ((r >> 2) == (c >> 2) ? Kg[(r & 3) * 16 + (c & 3)] : make_float2(0.f, 0.f));
     const double re = (double)kv.x * scale, im = (double)kv.y * scale;
     const float v = (float)((n & 1) ? ((k & 1) ? re : im) : ((k & 1) ? -im : re));
     const float hi = tf32_rna(v);
@@ -759,8 +761,8 @@ __global__ void __launch_bounds__(256, 2) k_fused_tc(FusedArgs f) {
   {
     const int m = *f.ap.m;
     const double scale = 1.0 / sqrt(*f.ap.N);
-    build_b(reinterpret_cast<const float2*>(f.ap.kraus) + (m ? 256 : 0), scale, Bahi, Balo);
-    build_b(reinterpret_cast<const float2*>(f.pr.kraus) + 256, 1.0, Bphi, Bplo);
+    build_b(reinterpret_cast<const float2*>(f.ap.kraus) + (m ? 256 : 0), scale, Bahi, Balo, f.ap.w == 2);
+    build_b(reinterpret_cast<const float2*>(f.pr.kraus) + 256, 1.0, Bphi, Bplo, f.pr.w == 2);
     if (tid == 0) {
       s_err = 0;
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])));
@@ -776,11 +778,13 @@ __global__ void __launch_bounds__(256, 2) k_fused_tc(FusedArgs f) {
   tc_sync();
   const uint32_t tmem = tmem_base;
   const uint32_t mb1 = smem_u32(&mbar[0]), mb2 = smem_u32(&mbar[1]);
-  int qa[4], qp[4];
+  int qa[4], qp[4], qas[4], qps[4];   // member bits (a weight-2 block's qubits, then spectators) and sorted
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
     qa[j] = f.qa[j];
     qp[j] = f.qp[j];
+    qas[j] = f.qa_s[j];
+    qps[j] = f.qp_s[j];
   }
   // Tile slot of float2 e in shared memory: bits 1..3 (the 8-byte bank pair within a 16-byte
   // chunk's position) XOR a fold of the chunk index's higher bits, so group gathers spread over
@@ -805,7 +809,7 @@ __global__ void __launch_bounds__(256, 2) k_fused_tc(FusedArgs f) {
   }
   // Thread tid owns row tid of both GEMMs: M-half tid / 128, TMEM lane tid % 128, which is in its
   // warp's lane quarter (32 (warp % 4) ..).
-  const uint32_t sba = slot(local_base<4>((uint32_t)tid, qa)), sbp = slot(local_base<4>((uint32_t)tid, qp));
+  const uint32_t sba = slot(local_base<4>((uint32_t)tid, qas)), sbp = slot(local_base<4>((uint32_t)tid, qps));
   uint32_t cd[8];   // slots of this thread's 16-byte chunks
 #pragma unroll
   for (int i = 0; i < 8; ++i) cd[i] = slot((uint32_t)tid * 2 + 512u * i);
@@ -1835,6 +1839,8 @@ static cudaError_t fused_attrs() {
   return cudaSuccess;
 }
 
+static void oz_block_bits(int w, int* q, int* qs, int nt);
+
 cudaError_t launch_fused(int precision, const PassArgs& ap, const PassArgs& pr, int num_sms, cudaStream_t s) {
   if ((ap.w != 2 && ap.w != 4) || (pr.w != 2 && pr.w != 4)) return cudaErrorInvalidValue;
   const size_t amp = is_f64(precision) ? 16 : 8;
@@ -1869,7 +1875,11 @@ cudaError_t launch_fused(int precision, const PassArgs& ap, const PassArgs& pr, 
     f.qa[j] = j < ap.w ? tile_pos(ap.q[j], lb, f.hbits, nh) : 0;
     f.qp[j] = j < pr.w ? tile_pos(pr.q[j], lb, f.hbits, nh) : 0;
   }
-  if (precision == QEC_C64_TC && ap.w == 4 && pr.w == 4 && f.nt == 12) {
+  // the tensor-core pass for pairs with a weight-4 block (a weight-2 block of the pair as K (x) I over
+  // two spectator bits); two weight-2 blocks are faster on the CUDA cores
+  if (precision == QEC_C64_TC && (ap.w == 4 || pr.w == 4) && f.nt == 12) {
+    oz_block_bits(ap.w, f.qa, f.qa_s, f.nt);
+    oz_block_bits(pr.w, f.qp, f.qp_s, f.nt);
     const size_t tsmem = kTcSmem;
     // sized for two resident CTAs per SM (113 KiB each; the occupancy query under-reports this
     // shape), capped by the tile count

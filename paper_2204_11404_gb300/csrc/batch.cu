@@ -58,12 +58,24 @@ struct UPass {
   int32_t bits[kUMaxFusionDecl];
 };
 
-// A unit inside a pass: items[item] on slab bits qa (, qb), and the pass's other bits.
+// A unit inside a pass: items[item] on slab bits qa (, qb), and the pass's other bits.  A two-qubit
+// unit also carries the one-qubit units folded into its matrix: entries abs0 .. abs0 + nabs - 1 of
+// the program's UAbs list.
 struct UPassUnit {
   int32_t item;
   int32_t nq, qa, qb;
   int32_t nother;
   int32_t other[kUMaxFusionDecl];
+  int32_t abs0, nabs;
+};
+
+// A one-qubit unit folded into a two-qubit unit's matrix: item1's matrix on the unit's local bit
+// (mode bit 1: 1 = qa, 0 = qb), multiplied from the left (mode bit 0 = 1: it follows the unit) or
+// from the right (it precedes).  A unit's entries list the right factors latest first, then the
+// left factors in program order.
+struct UAbs {
+  int32_t item1;
+  int32_t mode;
 };
 
 struct BatchArgs {
@@ -89,6 +101,9 @@ struct BatchArgs {
   const UPass* iupasses;      // the init round's passes
   int n_iupasses;
   const UPassUnit* iupunits;
+  int n_upunits, n_iupunits;
+  const UAbs* uabs;           // one-qubit units folded into two-qubit units (noisy round, init round)
+  const UAbs* iuabs;
   const uint64_t* traj;       // [n]
   BatchCtl* ctl;
   int rounds;
@@ -478,6 +493,27 @@ __device__ __forceinline__ void left2(double2 (&M)[16], const T2* g) {
   }
 }
 
+// Right-multiplies the DIM x DIM unit matrix M (row stride 4) by a one-qubit gate g on local bit BIT:
+// M <- M (g on BIT), the gate applied before M.
+template <int DIM, int BIT, typename T2>
+__device__ __forceinline__ void right1(double2 (&M)[16], const T2* g) {
+  const double2 g00 = make_double2((double)g[0].x, (double)g[0].y), g01 = make_double2((double)g[1].x, (double)g[1].y);
+  const double2 g10 = make_double2((double)g[4].x, (double)g[4].y), g11 = make_double2((double)g[5].x, (double)g[5].y);
+#pragma unroll
+  for (int r = 0; r < DIM; ++r) {
+#pragma unroll
+    for (int c0 = 0; c0 < DIM; ++c0) {
+      if (c0 & (1 << BIT)) continue;
+      const int c1 = c0 | (1 << BIT);
+      const double2 x = M[r * 4 + c0], y = M[r * 4 + c1];
+      M[r * 4 + c0] = make_double2(x.x * g00.x - x.y * g00.y + y.x * g10.x - y.y * g10.y,
+                                   x.x * g00.y + x.y * g00.x + y.x * g10.y + y.y * g10.x);
+      M[r * 4 + c1] = make_double2(x.x * g01.x - x.y * g01.y + y.x * g11.x - y.y * g11.y,
+                                   x.x * g01.y + x.y * g01.x + y.x * g11.y + y.y * g11.x);
+    }
+  }
+}
+
 // The fused matrix of one unit: the product, in op order, of its gate, coherent terms and the
 // Paulis its noise sites draw (DIM 2 or 4; local index 2 bit(qa) + bit(qb), qa the only bit of a
 // one-qubit unit), built in place by left multiplications.  Returns 0 when no op of the unit acts
@@ -553,6 +589,8 @@ __device__ void run_cta_u(const BatchArgs& a, unsigned char* sm, uint32_t item) 
   const UPass* passes = init ? a.iupasses : a.upasses;
   const int npass = init ? a.n_iupasses : a.n_upasses;
   const UPassUnit* punits = init ? a.iupunits : a.upunits;
+  const int npunits = init ? a.n_iupunits : a.n_upunits;
+  const UAbs* uabs = init ? a.iuabs : a.uabs;
   double prob[PR_COUNT];
   traj_probs(nz, prob);
   for (int i = tid; i < M_COUNT * 16; i += nt) {
@@ -579,6 +617,31 @@ __device__ void run_cta_u(const BatchArgs& a, unsigned char* sm, uint32_t item) 
       Fon[it] = u.kind != 0 ? 0
                 : u.nq == 1 ? fuse_unit<2, T2>(u, ops, mats, prob, seed, traj, rnd, Ft + 16 * it)
                             : fuse_unit<4, T2>(u, ops, mats, prob, seed, traj, rnd, Ft + 16 * it);
+    }
+    __syncthreads();
+    // the one-qubit units next to a two-qubit unit on the same qubit, folded into its matrix (one
+    // thread per two-qubit unit; each one-qubit unit belongs to at most one); the passes skip them
+    for (int pu = tid; pu < npunits; pu += nt) {
+      const UPassUnit U = punits[pu];
+      if (U.nabs == 0) continue;
+      double2 M[16];
+      double2* F = Ft + 16 * U.item;
+#pragma unroll
+      for (int i = 0; i < 16; ++i) M[i] = F[i];
+      for (int e = U.abs0; e < U.abs0 + U.nabs; ++e) {
+        const UAbs A = uabs[e];
+        if (!Fon[A.item1]) continue;   // the identity
+        const double2* g = Ft + 16 * A.item1;
+        if (A.mode & 1) {
+          if (A.mode & 2) left1<4, 1>(M, g);
+          else left1<4, 0>(M, g);
+        } else {
+          if (A.mode & 2) right1<4, 1>(M, g);
+          else right1<4, 0>(M, g);
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < 16; ++i) F[i] = M[i];
     }
     __syncthreads();
     for (int pi = 0; pi < npass; ++pi) {
@@ -767,6 +830,8 @@ struct qec_batch {
   UPass* d_upasses[2] = {nullptr, nullptr};        // [0] noisy round, [1] init round
   UPassUnit* d_upunits[2] = {nullptr, nullptr};
   int n_upasses[2] = {0, 0};
+  int n_upunits[2] = {0, 0};
+  UAbs* d_uabs[2] = {nullptr, nullptr};           // one-qubit units folded into two-qubit units
 };
 
 namespace {
@@ -797,7 +862,7 @@ void batch_free(qec_batch* b) {
                   b->d_noise, b->d_kind, b->d_traj, b->d_ctl, b->d_syn, b->d_bits, b->d_log,
                   b->d_uops, b->d_uitems, b->d_iuops, b->d_iuitems, b->d_psi0_u[0], b->d_psi0_u[1],
                   b->d_idx, b->d_idx_u, b->d_snap, b->d_upasses[0], b->d_upasses[1], b->d_upunits[0],
-                  b->d_upunits[1]};
+                  b->d_upunits[1], b->d_uabs[0], b->d_uabs[1]};
   for (void* p : ptrs) if (p) cudaFree(p);
   if (b->fork) cudaEventDestroy(b->fork);
   if (b->join) cudaEventDestroy(b->join);
@@ -842,6 +907,10 @@ BatchArgs batch_args(const qec_batch* b) {
   a.iupasses = b->d_upasses[1];
   a.n_iupasses = b->n_upasses[1];
   a.iupunits = b->d_upunits[1];
+  a.n_upunits = b->n_upunits[0];
+  a.n_iupunits = b->n_upunits[1];
+  a.uabs = b->d_uabs[0];
+  a.iuabs = b->d_uabs[1];
   a.init_mode = 0;
   a.init_prec = 0;
   a.init_out = nullptr;
@@ -883,9 +952,58 @@ qec_status ensure_batch_graph(qec_batch* b) {
 // Passes of one round of the unreduced engine for fusion width k: consecutive units whose slab bits
 // are disjoint from those already in the pass (they commute with them) join it while the pass has at
 // most k bits; a unit on a bit already in the pass, or a measurement, closes it.
-void build_passes(const UProgram& U, int k, std::vector<UPass>& passes, std::vector<UPassUnit>& punits) {
+// One-qubit units folded into two-qubit units: on each slab bit, a run of consecutive one-qubit units
+// (nothing else on that bit between them) directly before a two-qubit unit on the bit goes into that
+// unit's matrix from the right; a run directly after one (and before nothing of its own) from the
+// left.  Moving the run next to the unit is exact: the run acts on its bit alone, and nothing else
+// acts on that bit in between.  absorbed[it] marks the folded units; pre/post list them per
+// two-qubit unit in program order.
+void plan_absorb(const UProgram& U, std::vector<char>& absorbed, std::vector<std::vector<UAbs>>& pre,
+                 std::vector<std::vector<UAbs>>& post) {
+  const int n = (int)U.items.size();
+  absorbed.assign(n, 0);
+  pre.assign(n, {});
+  post.assign(n, {});
+  auto is1 = [&](int it) { return U.items[it].kind == 0 && U.items[it].nq == 1; };
+  auto is2 = [&](int it) { return U.items[it].kind == 0 && U.items[it].nq == 2; };
+  for (int b = 0; b < U.nbits; ++b) {
+    std::vector<int> seq;   // items acting on bit b, in order
+    for (int it = 0; it < n; ++it) {
+      const UItem& u = U.items[it];
+      if (u.qa == b || (u.kind == 0 && u.nq == 2 && u.qb == b)) seq.push_back(it);
+    }
+    for (size_t i = 0; i < seq.size();) {
+      if (!is1(seq[i])) { ++i; continue; }
+      size_t j = i;
+      while (j < seq.size() && is1(seq[j])) ++j;
+      int target = -1;
+      bool after = false;
+      if (j < seq.size() && is2(seq[j])) {
+        target = seq[j];
+      } else if (i > 0 && is2(seq[i - 1])) {
+        target = seq[i - 1];
+        after = true;
+      }
+      if (target >= 0) {
+        const int bit = U.items[target].qa == b ? 2 : 0;
+        for (size_t r = i; r < j; ++r) {
+          absorbed[seq[r]] = 1;
+          (after ? post : pre)[target].push_back({seq[r], bit | (after ? 1 : 0)});
+        }
+      }
+      i = j;
+    }
+  }
+}
+
+void build_passes(const UProgram& U, int k, std::vector<UPass>& passes, std::vector<UPassUnit>& punits,
+                  std::vector<UAbs>& uabs) {
   passes.clear();
   punits.clear();
+  uabs.clear();
+  std::vector<char> absorbed;
+  std::vector<std::vector<UAbs>> pre, post;
+  plan_absorb(U, absorbed, pre, post);
   UPass cur{};
   uint32_t mask = 0;
   auto close = [&]() {
@@ -920,6 +1038,7 @@ void build_passes(const UProgram& U, int k, std::vector<UPass>& passes, std::vec
       open();
       continue;
     }
+    if (absorbed[it]) continue;
     const uint32_t um = (1u << u.qa) | (u.nq == 2 ? (1u << u.qb) : 0u);
     if ((mask & um) || __builtin_popcount(mask | um) > k) {
       close();
@@ -930,6 +1049,10 @@ void build_passes(const UProgram& U, int k, std::vector<UPass>& passes, std::vec
     pu.nq = u.nq;
     pu.qa = u.qa;
     pu.qb = u.nq == 2 ? u.qb : 0;
+    pu.abs0 = (int32_t)uabs.size();
+    for (auto r = pre[it].rbegin(); r != pre[it].rend(); ++r) uabs.push_back(*r);   // right factors, latest first
+    for (const UAbs& x : post[it]) uabs.push_back(x);                              // left factors, in order
+    pu.nabs = (int32_t)uabs.size() - pu.abs0;
     punits.push_back(pu);
     cur.u1 = (int32_t)punits.size();
     mask |= um;
@@ -945,11 +1068,15 @@ qec_status set_fusion(qec_batch* b, int k, int threads) {
   for (int w = 0; w < 2; ++w) {
     std::vector<UPass> passes;
     std::vector<UPassUnit> punits;
-    build_passes(*progs[w], k, passes, punits);
+    std::vector<UAbs> uabs;
+    build_passes(*progs[w], k, passes, punits, uabs);
     QEC_BCUDA(cudaMemcpy(b->d_upasses[w], passes.data(), sizeof(UPass) * passes.size(), cudaMemcpyHostToDevice));
     if (!punits.empty())
       QEC_BCUDA(cudaMemcpy(b->d_upunits[w], punits.data(), sizeof(UPassUnit) * punits.size(), cudaMemcpyHostToDevice));
+    if (!uabs.empty())
+      QEC_BCUDA(cudaMemcpy(b->d_uabs[w], uabs.data(), sizeof(UAbs) * uabs.size(), cudaMemcpyHostToDevice));
     b->n_upasses[w] = (int)passes.size();
+    b->n_upunits[w] = (int)punits.size();
   }
   int occ = 0;
   QEC_BCUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch_u, threads, kUSmem));
@@ -1023,7 +1150,8 @@ qec_status qec_batch_create(int32_t d, int32_t rounds, int32_t gates, uint32_t m
                      (void**)&b->d_log, (void**)&b->d_uops, (void**)&b->d_uitems, (void**)&b->d_iuops,
                      (void**)&b->d_iuitems, &b->d_psi0_u[0], &b->d_psi0_u[1], (void**)&b->d_idx,
                      (void**)&b->d_idx_u, (void**)&b->d_snap, (void**)&b->d_upasses[0], (void**)&b->d_upasses[1],
-                     (void**)&b->d_upunits[0], (void**)&b->d_upunits[1]};
+                     (void**)&b->d_upunits[0], (void**)&b->d_upunits[1], (void**)&b->d_uabs[0],
+                     (void**)&b->d_uabs[1]};
   const size_t sizes[] = {sizeof(ProgOp) * (b->prog.ops.size() + 1), sizeof(BlockInfo) * kNStab,
                           sizeof(ProgOp) * (b->iprog.ops.size() + 1), sizeof(BlockInfo) * kNStab,
                           sizeof(b->prog.mats), (size_t)kNAmp * 16, (size_t)kNAmp * 8,
@@ -1035,7 +1163,8 @@ qec_status qec_batch_create(int32_t d, int32_t rounds, int32_t gates, uint32_t m
                           sizeof(uint32_t) * max_traj, sizeof(double2) * kNAmp,
                           sizeof(UPass) * (b->uprog.items.size() + 1), sizeof(UPass) * (b->iuprog.items.size() + 1),
                           sizeof(UPassUnit) * (b->uprog.items.size() + 1),
-                          sizeof(UPassUnit) * (b->iuprog.items.size() + 1)};
+                          sizeof(UPassUnit) * (b->iuprog.items.size() + 1),
+                          sizeof(UAbs) * (b->uprog.items.size() + 1), sizeof(UAbs) * (b->iuprog.items.size() + 1)};
   for (size_t i = 0; i < sizeof(sizes) / sizeof(sizes[0]); ++i) {
     e = cudaMalloc(allocs[i], sizes[i]);
     if (e != cudaSuccess) return bail(bfail(QEC_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e)));

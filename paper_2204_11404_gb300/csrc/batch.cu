@@ -435,7 +435,9 @@ constexpr int kUBits = kND + kNStab / 2;      // 13 slab bits: 9 data + the acti
 constexpr int kUAmp = 1 << kUBits;            // 8192 amplitudes
 constexpr int kUMaxItems = 192;               // items of one round (units and measurements)
 // slab, mats, unit matrices (FP64) and flags, reduction, flag
-constexpr int kUSmem = kUAmp * 16 + M_COUNT * 16 * 16 + kUMaxItems * 16 * 16 + kUMaxItems * 4 + 64 * 8 + 16;
+constexpr int kUChunks = 256;                 // complex64 measurement: chunks of the 4096 amplitude pairs
+constexpr int kUSmem = kUAmp * 16 + M_COUNT * 16 * 16 + kUMaxItems * 16 * 16 + kUMaxItems * 4 + 64 * 8 +
+                       2 * kUChunks * 8 + 16;
 
 template <typename T>
 __device__ void block_sum2_u(double& x, double& y, double* sh) {
@@ -579,6 +581,7 @@ __device__ void run_cta_u(const BatchArgs& a, unsigned char* sm, uint32_t item) 
   double2* Ft = reinterpret_cast<double2*>(sm + kUAmp * 16 + M_COUNT * 16 * 16);   // [kUMaxItems][16]
   int* Fon = reinterpret_cast<int*>(Ft + kUMaxItems * 16);                           // [kUMaxItems]
   double* sh = reinterpret_cast<double*>(Fon + kUMaxItems);                          // 64 doubles
+  double* csum = sh + 64;                                                            // [2][kUChunks]
   const bool init = a.init_mode != 0;
   const qec_noise nz = init ? qec_noise{} : a.noise[item];
   const uint64_t traj = init ? 0ull : a.traj[item];
@@ -651,12 +654,48 @@ __device__ void run_cta_u(const BatchArgs& a, unsigned char* sm, uint32_t item) 
         const UItem u = items[P.item];
         const int b = u.qa;
         double s0 = 0.0, s1 = 0.0;
-        for (int pr = tid; pr < kUAmp / 2; pr += nt) {
-          const int i0 = (int)ins0(pr, b), i1 = i0 | (1 << b);
-          s0 += (double)slab[i0].x * slab[i0].x + (double)slab[i0].y * slab[i0].y;
-          s1 += (double)slab[i1].x * slab[i1].x + (double)slab[i1].y * slab[i1].y;
+        if constexpr (sizeof(T) == 4) {
+          // complex64: the squares summed in FP32 over fixed chunks (chunk c: pairs c, c + 256, ..., 16 of
+          // them), the chunk sums in FP64 in a fixed order by one warp, so that the sums, like the rest of
+          // the run, do not depend on the CTA size
+          for (int c = tid; c < kUChunks; c += nt) {
+            float f0 = 0.f, f1 = 0.f;
+            for (int pr = c; pr < kUAmp / 2; pr += kUChunks) {
+              const int i0 = (int)ins0(pr, b), i1 = i0 | (1 << b);
+              f0 = fmaf(slab[i0].x, slab[i0].x, fmaf(slab[i0].y, slab[i0].y, f0));
+              f1 = fmaf(slab[i1].x, slab[i1].x, fmaf(slab[i1].y, slab[i1].y, f1));
+            }
+            csum[c] = (double)f0;
+            csum[kUChunks + c] = (double)f1;
+          }
+          __syncthreads();
+          if (tid < 32) {
+            double a0 = 0.0, a1 = 0.0;
+            for (int c = tid; c < kUChunks; c += 32) {
+              a0 += csum[c];
+              a1 += csum[kUChunks + c];
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+              a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+              a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+            }
+            if (tid == 0) {
+              csum[0] = a0;
+              csum[1] = a1;
+            }
+          }
+          __syncthreads();
+          s0 = csum[0];
+          s1 = csum[1];
+        } else {
+          for (int pr = tid; pr < kUAmp / 2; pr += nt) {
+            const int i0 = (int)ins0(pr, b), i1 = i0 | (1 << b);
+            s0 += (double)slab[i0].x * slab[i0].x + (double)slab[i0].y * slab[i0].y;
+            s1 += (double)slab[i1].x * slab[i1].x + (double)slab[i1].y * slab[i1].y;
+          }
+          block_sum2_u<T>(s0, s1, sh);
         }
-        block_sum2_u<T>(s0, s1, sh);
         int m;
         if (init) {
           m = u.offset;
@@ -664,11 +703,15 @@ __device__ void run_cta_u(const BatchArgs& a, unsigned char* sm, uint32_t item) 
           const double uu = uniform53(draw(seed, traj, (uint64_t)rnd, 0u, (uint32_t)(kND + u.stab), TAG_MEASURE).v[0]);
           m = uu < s1 / (s0 + s1) ? 1 : 0;
         }
-        const double sc = 1.0 / sqrt(m ? s1 : s0);
+        const double sc = 1.0 / sqrt(m ? s1 : s0);   // the renormalisation factor in FP64
+        const T scT = (T)sc;                            // applied in the state's precision
         for (int pr = tid; pr < kUAmp / 2; pr += nt) {
           const int i0 = (int)ins0(pr, b), i1 = i0 | (1 << b);
           const T2 kept = m ? slab[i1] : slab[i0];
-          slab[i0] = mk<T2>((double)kept.x * sc, (double)kept.y * sc);
+          T2 v;
+          v.x = kept.x * scT;
+          v.y = kept.y * scT;
+          slab[i0] = v;
           slab[i1] = mk<T2>(0, 0);
         }
         __syncthreads();

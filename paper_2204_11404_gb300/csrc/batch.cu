@@ -623,10 +623,13 @@ __device__ void run_cta_u(const BatchArgs& a, unsigned char* sm, uint32_t item) 
     }
     __syncthreads();
     // the one-qubit units next to a two-qubit unit on the same qubit, folded into its matrix (one
-    // thread per two-qubit unit; each one-qubit unit belongs to at most one); the passes skip them
+    // thread per two-qubit unit; each one-qubit unit belongs to at most one); the passes skip them.
+    // Then the unit's shape, from exact zeros: Fon = 2 when the matrix is block-diagonal in its first
+    // qubit (local bit 1: the two-qubit gates act on the second qubit conditioned on the first), 3
+    // when block-antidiagonal (an X or Y drawn on the first qubit), else 1 (dense).
     for (int pu = tid; pu < npunits; pu += nt) {
       const UPassUnit U = punits[pu];
-      if (U.nabs == 0) continue;
+      if (U.nq != 2) continue;
       double2 M[16];
       double2* F = Ft + 16 * U.item;
 #pragma unroll
@@ -645,6 +648,14 @@ __device__ void run_cta_u(const BatchArgs& a, unsigned char* sm, uint32_t item) 
       }
 #pragma unroll
       for (int i = 0; i < 16; ++i) F[i] = M[i];
+      bool bd = true, ad = true;
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const bool z = M[i].x == 0.0 && M[i].y == 0.0;
+        if (((i >> 3) & 1) != ((i >> 1) & 1)) bd = bd && z;   // row bit 1 != column bit 1
+        else ad = ad && z;
+      }
+      if (Fon[U.item]) Fon[U.item] = bd ? 2 : ad ? 3 : 1;
     }
     __syncthreads();
     for (int pi = 0; pi < npass; ++pi) {
@@ -744,6 +755,40 @@ __device__ void run_cta_u(const BatchArgs& a, unsigned char* sm, uint32_t item) 
           T2 f[16];
 #pragma unroll
           for (int i = 0; i < 16; ++i) f[i] = mk<T2>(Fg[i].x, Fg[i].y);
+          const int shape = Fon[U.item];
+          if (shape != 1) {
+            // block-(anti)diagonal in the first qubit: rows 0, 1 from one column pair, rows 2, 3 from the
+            // other (the nonzero terms of the dense sum, in the same order); selects keep every index
+            // a constant
+            const bool bd = shape == 2;
+            T2 h[8];   // row r, term j: f[r][c(r) + j]
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+              for (int j = 0; j < 2; ++j) h[2 * r + j] = ((r < 2) == bd) ? f[r * 4 + j] : f[r * 4 + 2 + j];
+            for (int g = tid; g < G; g += nt) {
+              const int base = group_base_u(g, P.bits, P.nbits);
+              for (int sub = 0; sub < nsub; ++sub) {
+                const int b0 = base | deposit_bits(sub, U.other, U.nother);
+                int idx[4];
+                T2 x[4];
+#pragma unroll
+                for (int l = 0; l < 4; ++l) {
+                  idx[l] = b0 | ((l >> 1) << U.qa) | ((l & 1) << U.qb);
+                  x[l] = slab[idx[l]];
+                }
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                  const bool low = (r < 2) == bd;   // this row reads columns 0, 1
+                  T2 acc = mk<T2>(0, 0);
+                  acc = cmul_add<T>(acc, h[2 * r], low ? x[0] : x[2]);
+                  acc = cmul_add<T>(acc, h[2 * r + 1], low ? x[1] : x[3]);
+                  slab[idx[r]] = acc;
+                }
+              }
+            }
+            continue;
+          }
           for (int g = tid; g < G; g += nt) {
             const int base = group_base_u(g, P.bits, P.nbits);
             for (int sub = 0; sub < nsub; ++sub) {
@@ -997,8 +1042,8 @@ qec_status ensure_batch_graph(qec_batch* b) {
 // most k bits; a unit on a bit already in the pass, or a measurement, closes it.
 // One-qubit units folded into two-qubit units: on each slab bit, a run of consecutive one-qubit units
 // (nothing else on that bit between them) directly before a two-qubit unit on the bit goes into that
-// unit's matrix from the right; a run directly after one (and before nothing of its own) from the
-// left.  Moving the run next to the unit is exact: the run acts on its bit alone, and nothing else
+// unit's matrix from the right, a run directly after one from the left (between two, into the one
+// whose second qubit is the bit).  Moving the run next to the unit is exact: the run acts on its bit alone, and nothing else
 // acts on that bit in between.  absorbed[it] marks the folded units; pre/post list them per
 // two-qubit unit in program order.
 void plan_absorb(const UProgram& U, std::vector<char>& absorbed, std::vector<std::vector<UAbs>>& pre,
@@ -1021,9 +1066,12 @@ void plan_absorb(const UProgram& U, std::vector<char>& absorbed, std::vector<std
       while (j < seq.size() && is1(seq[j])) ++j;
       int target = -1;
       bool after = false;
-      if (j < seq.size() && is2(seq[j])) {
+      const bool next2 = j < seq.size() && is2(seq[j]), prev2 = i > 0 && is2(seq[i - 1]);
+      // between two two-qubit units, the one in which b is the second qubit (the gate's target) takes
+      // the run: a one-qubit matrix there keeps that unit block-diagonal in its first qubit
+      if (next2 && (!prev2 || U.items[seq[j]].qb == b || U.items[seq[i - 1]].qb != b)) {
         target = seq[j];
-      } else if (i > 0 && is2(seq[i - 1])) {
+      } else if (prev2) {
         target = seq[i - 1];
         after = true;
       }

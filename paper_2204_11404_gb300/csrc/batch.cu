@@ -658,6 +658,20 @@ __device__ void run_cta_u(const BatchArgs& a, unsigned char* sm, uint32_t item) 
       if (Fon[U.item]) Fon[U.item] = bd ? 2 : ad ? 3 : 1;
     }
     __syncthreads();
+    if constexpr (sizeof(T) == 4) {
+      // complex64: each unit's matrix converted once, in place (the first half of its slot), instead of
+      // by every thread of every pass
+      for (int it = tid; it < nitems; it += nt) {
+        if (!Fon[it]) continue;
+        double2 v[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] = Ft[16 * it + i];
+        T2* o = reinterpret_cast<T2*>(Ft + 16 * it);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) o[i] = mk<T2>(v[i].x, v[i].y);
+      }
+      __syncthreads();
+    }
     for (int pi = 0; pi < npass; ++pi) {
       const UPass P = passes[pi];
       if (P.kind == 1) {
@@ -734,11 +748,10 @@ __device__ void run_cta_u(const BatchArgs& a, unsigned char* sm, uint32_t item) 
       for (int pu = P.u0; pu < P.u1; ++pu) {
         const UPassUnit U = punits[pu];
         if (!Fon[U.item]) continue;
-        const double2* Fg = Ft + 16 * U.item;
+        const T2* Fg = reinterpret_cast<const T2*>(Ft + 16 * U.item);   // the unit's matrix in the state's precision
         const int nsub = 1 << U.nother;
         if (U.nq == 1) {
-          const T2 f0 = mk<T2>(Fg[0].x, Fg[0].y), f1 = mk<T2>(Fg[1].x, Fg[1].y);
-          const T2 f4 = mk<T2>(Fg[4].x, Fg[4].y), f5 = mk<T2>(Fg[5].x, Fg[5].y);
+          const T2 f0 = Fg[0], f1 = Fg[1], f4 = Fg[4], f5 = Fg[5];
           for (int g = tid; g < G; g += nt) {
             const int base = group_base_u(g, P.bits, P.nbits);
             for (int sub = 0; sub < nsub; ++sub) {
@@ -754,7 +767,7 @@ __device__ void run_cta_u(const BatchArgs& a, unsigned char* sm, uint32_t item) 
         } else {
           T2 f[16];
 #pragma unroll
-          for (int i = 0; i < 16; ++i) f[i] = mk<T2>(Fg[i].x, Fg[i].y);
+          for (int i = 0; i < 16; ++i) f[i] = Fg[i];
           const int shape = Fon[U.item];
           if (shape != 1) {
             // block-(anti)diagonal in the first qubit: rows 0, 1 from one column pair, rows 2, 3 from the

@@ -32,7 +32,7 @@ constexpr int kD = 3;                    // register of the batched form: d = 3
 constexpr int kND = kD * kD;             // 9 data qubits
 constexpr int kNAmp = 1 << kND;          // 512 amplitudes
 constexpr int kNStab = kND - 1;          // 8 stabilizers
-constexpr int kWarpSmem = 32 * 16 * 16 + kNAmp * 16 + M_COUNT * 16 * 16 + 64;   // U, psi, mats, misc (c128)
+constexpr int kWarpSmem = 32 * 16 * 16 + kNAmp * 16 + M_COUNT * 16 * 16 + 16 * 16 + 64;   // U, psi, mats, pending factor, misc (c128)
 constexpr int kUMaxFusionDecl = 6;       // widest pass of the unreduced engine (slab bits)
 
 template <typename T> struct C2;
@@ -295,6 +295,96 @@ __device__ int measure_block(typename C2<T>::t* psi, const typename C2<T>::t* U,
   return m;
 }
 
+// A block's compile folds consecutive ops on the same qubits into one pending factor before it
+// touches the 32 x 16 block matrix U: a 2x2 on one qubit (pb < 0; entries 0, 1, 4, 5 of P) or a 4x4
+// on a qubit pair (local index 2 bit(pa) + bit(pb)).  An op on other qubits first applies the
+// pending factor to U.  The product is the same operator as the ops applied one at a time.
+template <typename T>
+struct PendingOp {
+  using T2 = typename C2<T>::t;
+  T2* P;        // [16], the warp's pending factor
+  int pa = -1, pb = -1;
+  int lane;
+  static __device__ __forceinline__ int sw(int i) { return ((i & 1) << 1) | (i >> 1); }
+  // P <- G P for a 4x4 G (qubit order of G swapped against P's when swap)
+  __device__ void lmul2(const T2* g, bool swap) {
+    T2 acc = mk<T2>(0, 0);
+    if (lane < 16) {
+      const int r = lane >> 2, c = lane & 3;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) acc = cmul_add<T>(acc, g[4 * (swap ? sw(r) : r) + (swap ? sw(k) : k)], P[4 * k + c]);
+    }
+    __syncwarp();
+    if (lane < 16) P[lane] = acc;
+    __syncwarp();
+  }
+  // P <- (g on local bit) P for a 2x2 g (entries 0, 1, 4, 5), P a 4x4 (dim 4) or a 2x2 (dim 2)
+  __device__ void lmul1(const T2* g, int bit, int dim) {
+    T2 acc = mk<T2>(0, 0);
+    const int r = lane >> 2, c = lane & 3;
+    const bool on = dim == 4 ? lane < 16 : (r < 2 && c < 2);
+    if (on) {
+      const int rb = (r >> bit) & 1, r0 = r & ~(1 << bit), r1 = r | (1 << bit);
+      acc = cmul_add<T>(acc, g[4 * rb], P[4 * r0 + c]);
+      acc = cmul_add<T>(acc, g[4 * rb + 1], P[4 * r1 + c]);
+    }
+    __syncwarp();
+    if (on) P[lane] = acc;
+    __syncwarp();
+  }
+  __device__ void flush(T2* U, int w) {
+    if (pa < 0) return;
+    if (pb < 0) apply1_w<T>(U, w, pa, P, lane);
+    else apply2_w<T>(U, w, pa, pb, P, lane);
+    pa = pb = -1;
+  }
+  __device__ void start(const T2* g, int x, int y) {   // P <- g (a 4x4 on (x, y), or a 2x2 on x when y < 0)
+    if (lane < 16) P[lane] = g[lane];
+    __syncwarp();
+    pa = x;
+    pb = y;
+  }
+  __device__ void one(T2* U, int w, int x, const T2* g) {
+    if (pa == x && pb < 0) {
+      lmul1(g, 0, 2);
+    } else if (pb >= 0 && (x == pa || x == pb)) {
+      lmul1(g, x == pa ? 1 : 0, 4);
+    } else {
+      flush(U, w);
+      start(g, x, -1);
+    }
+  }
+  __device__ void two(T2* U, int w, int x, int y, const T2* g) {
+    if (pb >= 0 && ((x == pa && y == pb) || (x == pb && y == pa))) {
+      lmul2(g, x != pa);
+      return;
+    }
+    if (pb < 0 && pa >= 0 && (x == pa || y == pa)) {
+      // the pending one-qubit factor becomes a 4x4 on (x, y): Q on its bit, the identity on the other
+      const int bit = x == pa ? 1 : 0;
+      T2 q00 = P[0], q01 = P[1], q10 = P[4], q11 = P[5];
+      __syncwarp();
+      if (lane < 16) {
+        const int r = lane >> 2, c = lane & 3;
+        const int ob = 1 - bit;
+        T2 v = mk<T2>(0, 0);
+        if (((r >> ob) & 1) == ((c >> ob) & 1)) {
+          const int rb = (r >> bit) & 1, cb = (c >> bit) & 1;
+          v = rb ? (cb ? q11 : q10) : (cb ? q01 : q00);
+        }
+        P[lane] = v;
+      }
+      __syncwarp();
+      pa = x;
+      pb = y;
+      lmul2(g, false);
+      return;
+    }
+    flush(U, w);
+    start(g, x, y);
+  }
+};
+
 // One trajectory (or, in init mode, the noise-free init round) on one warp.
 template <typename T>
 __device__ void run_warp(const BatchArgs& a, unsigned char* wsm, uint32_t item) {
@@ -303,6 +393,9 @@ __device__ void run_warp(const BatchArgs& a, unsigned char* wsm, uint32_t item) 
   T2* U = reinterpret_cast<T2*>(wsm);
   T2* psi = U + 32 * 16;
   T2 (*mats)[16] = reinterpret_cast<T2 (*)[16]>(psi + kNAmp);
+  PendingOp<T> pend;
+  pend.P = reinterpret_cast<T2*>(mats + M_COUNT);
+  pend.lane = lane;
   const bool init = a.init_mode != 0;
   const qec_noise nz = init ? qec_noise{} : a.noise[item];
   const uint64_t traj = init ? 0ull : a.traj[item];
@@ -340,8 +433,8 @@ __device__ void run_warp(const BatchArgs& a, unsigned char* wsm, uint32_t item) 
           if (lane == 0) fire = twirl_fires(op, prob[op.pidx], a.ctl->seed, traj, (uint64_t)rnd) ? 1 : 0;
           fire = __shfl_sync(0xffffffffu, fire, 0);
           if (!fire) continue;
-          if (op.kind == OP_T1) apply1_w<T>(U, w, op.q0, mats[op.mat], lane);
-          else apply2_w<T>(U, w, op.q0, op.q1, mats[op.mat], lane);
+          if (op.kind == OP_T1) pend.one(U, w, op.q0, mats[op.mat]);
+          else pend.two(U, w, op.q0, op.q1, mats[op.mat]);
           continue;
         }
         if (op.kind == OP_N1 || op.kind == OP_N2) {
@@ -350,17 +443,18 @@ __device__ void run_warp(const BatchArgs& a, unsigned char* wsm, uint32_t item) 
           code = __shfl_sync(0xffffffffu, code, 0);
           if (!code) continue;
           if (op.kind == OP_N1) {
-            apply1_w<T>(U, w, op.q0, mats[code], lane);
+            pend.one(U, w, op.q0, mats[code]);
           } else {
-            if (code >> 2) apply1_w<T>(U, w, op.q0, mats[code >> 2], lane);
-            if (code & 3) apply1_w<T>(U, w, op.q1, mats[code & 3], lane);
+            if (code >> 2) pend.one(U, w, op.q0, mats[code >> 2]);
+            if (code & 3) pend.one(U, w, op.q1, mats[code & 3]);
           }
         } else if (op.kind == OP_U1) {
-          apply1_w<T>(U, w, op.q0, mats[op.mat], lane);
+          pend.one(U, w, op.q0, mats[op.mat]);
         } else {
-          apply2_w<T>(U, w, op.q0, op.q1, mats[op.mat], lane);
+          pend.two(U, w, op.q0, op.q1, mats[op.mat]);
         }
       }
+      pend.flush(U, w);
       int m;
       if (w == 4) m = measure_block<T, 4>(psi, U, bi, init, a.ctl->seed, traj, rnd, k, lane);
       else m = measure_block<T, 2>(psi, U, bi, init, a.ctl->seed, traj, rnd, k, lane);
@@ -1345,7 +1439,12 @@ qec_status qec_batch_run(qec_batch* b, uint64_t seed, uint32_t n, const uint64_t
   QEC_BCUDA(cudaMemcpyAsync(b->d_noise, noise, sizeof(qec_noise) * n, cudaMemcpyHostToDevice, b->work));
   b->h_idx.clear();
   b->h_idx_u.clear();
-  for (uint32_t i = 0; i < n; ++i) ((kind[i] & 2) ? b->h_idx_u : b->h_idx).push_back(i);
+  // each engine's items complex128 first, then complex64: the warps (CTAs) then run one precision's
+  // code at a time instead of interleaving both instantiations, and the longer items start first.
+  // Every trajectory's result is independent of the order.
+  for (int prec = 0; prec < 2; ++prec)
+    for (uint32_t i = 0; i < n; ++i)
+      if ((kind[i] & 1) == prec) ((kind[i] & 2) ? b->h_idx_u : b->h_idx).push_back(i);
   if (!b->h_idx.empty())
     QEC_BCUDA(cudaMemcpyAsync(b->d_idx, b->h_idx.data(), sizeof(uint32_t) * b->h_idx.size(), cudaMemcpyHostToDevice, b->work));
   if (!b->h_idx_u.empty())

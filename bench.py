@@ -449,7 +449,7 @@ def serve_measure(args, rank, world, local):
     out_bytes = sum(j.n_traj * ((j.rounds + 1) * (j.d * j.d - 1) + j.d * j.d + 1) for j in jobs)
     offered = tr_rounds / span if span > 0 else None
     rep = {"trace": "Poisson arrivals, d in {3,5}, rounds U{1..10}, trajectories U{1..%d}, c64/c128 "
-                    "(d=5 c128 on the tensor-core complex128 engine), p~U[1e-4,1e-2], theta_rx~U[0,0.1]"
+                    "(d=5 on the tensor-core engines), p~U[1e-4,1e-2], theta_rx~U[0,0.1]"
                     % args.max_traj,
            "requests": len(jobs), "rate_per_s": args.rate, "trajectories": traj,
            "trajectories_per_s": world * traj / makespan, "makespan_s": makespan,

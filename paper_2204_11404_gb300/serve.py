@@ -75,10 +75,13 @@ class Slot:
 
 class Server:
     """fp64_on_tensor_cores: complex128 jobs with d >= 5 run on the tensor-core complex128 engine
-    ("c128tc": the same outcomes, amplitudes within a few FP64 roundings, about 5x faster); False
-    keeps them on the FP64 CUDA-core engine."""
+    ("c128tc": the same outcomes, amplitudes within a few FP64 roundings, about 10x faster); False
+    keeps them on the FP64 CUDA-core engine.  fp32_on_tensor_cores: complex64 jobs with d >= 5 run on
+    the tensor-core complex64 engine ("c64tc": 3xTF32 products with FP32 accumulation, within the
+    complex64 tolerance of the oracle, about 1.2x faster); False keeps them on the FP32 CUDA cores."""
 
-    def __init__(self, mem_budget_bytes, device=0, max_heavy=2, heavy_d=5, fp64_on_tensor_cores=True):
+    def __init__(self, mem_budget_bytes, device=0, max_heavy=2, heavy_d=5, fp64_on_tensor_cores=True,
+                 fp32_on_tensor_cores=True):
         import torch
 
         self.torch = torch
@@ -87,6 +90,7 @@ class Server:
         self.max_heavy = int(max_heavy)
         self.heavy_d = int(heavy_d)
         self.fp64_on_tensor_cores = bool(fp64_on_tensor_cores)
+        self.fp32_on_tensor_cores = bool(fp32_on_tensor_cores)
         lo, hi = torch.cuda.Stream.priority_range() if hasattr(torch.cuda.Stream, "priority_range") else (0, -1)
         self.prio_light = min(lo, hi)      # numerically lower = higher priority
         self.prio_heavy = max(lo, hi)
@@ -104,6 +108,8 @@ class Server:
         """The simulator precision that serves a job's requested precision."""
         if job.precision == "c128" and job.d >= 5 and self.fp64_on_tensor_cores:
             return "c128tc"
+        if job.precision == "c64" and job.d >= 5 and self.fp32_on_tensor_cores:
+            return "c64tc"
         return job.precision
 
     def _acquire(self, job):

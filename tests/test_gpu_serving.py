@@ -26,10 +26,14 @@ def test_continuous_batching_results_equal_solo_runs():
     jobs = [Job(**j) for j in trace]
     budget = 2 * state_bytes(5, "c64") + state_bytes(5, "c128") // 2 + 64 * 2**20   # forces waiting
     srv = Server(budget)
-    # complex128 at d=5 is served by the tensor-core complex128 engine; the solo runs below use the
-    # FP64 CUDA-core engine, so the equality checks cover the two engines against each other
+    # complex128 at d=5 is served by the tensor-core complex128 engine; its solo runs below use the
+    # FP64 CUDA-core engine, so the equality checks cover the two FP64-accurate engines against each
+    # other.  complex64 at d=5 is served by the tensor-core complex64 engine, and its solo runs use the
+    # same engine (the two complex64 engines agree only within FP32 roundings).
     assert [srv.engine(j) for j in jobs if j.d == 5 and j.precision == "c128"] == \
         ["c128tc"] * sum(j.d == 5 and j.precision == "c128" for j in jobs)
+    assert [srv.engine(j) for j in jobs if j.d == 5 and j.precision == "c64"] == \
+        ["c64tc"] * sum(j.d == 5 and j.precision == "c64" for j in jobs)
     try:
         srv.run(jobs)
     finally:
@@ -39,7 +43,8 @@ def test_continuous_batching_results_equal_solo_runs():
     dones = [t for (t, ev, _) in srv.log if ev == "done"]
     assert admits and dones and min(dones) < max(admits)   # later jobs admitted while others ran
     for j in jobs:
-        with Simulator(j.d, j.rounds, j.gates, j.precision, **j.noise) as sim:
+        solo = srv.engine(j) if j.precision == "c64" else j.precision
+        with Simulator(j.d, j.rounds, j.gates, solo, **j.noise) as sim:
             syn, bits, log = sim.run(j.seed, j.first_traj, j.n_traj)
         assert (syn == j.syndromes).all() and (bits == j.data_bits).all() and (log == j.raw_logical).all()
         if j.d == 3:

@@ -43,8 +43,11 @@ typedef enum { QEC_GATES_CNOT = 0, QEC_GATES_CR = 1 } qec_gateset;
 
 /* Amplitude storage / arithmetic.  C128: complex128 state, FP64 arithmetic.
  * C64: complex64 state, FP32 gate arithmetic, FP64 probability reductions.
- * C64_TC: complex64 state; weight-4 block contractions on the tensor cores
- * (3xTF32 split, FP32 accumulation), FP64 probability reductions.
+ * C64_TC: complex64 state; the fused apply + next-probability pass of every
+ * pair of blocks with a weight-4 block on the tensor cores (3xTF32 split,
+ * FP32 accumulation; a weight-2 block of the pair as K (x) I over two
+ * spectator qubits; tiles of 2^12 amplitudes, so d >= 5), pairs of weight-2
+ * blocks on the CUDA cores; FP64 probability reductions.
  * C128_TC: complex128 state; the apply and probability passes of every
  * stabilizer block (tiles of 2^11 amplitudes, so d >= 5) as emulated FP64
  * products on the FP16 tensor cores: each operand row split into 7 signed

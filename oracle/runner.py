@@ -1,4 +1,4 @@
-"""ctypes driver for the C state-vector core; runs one trajectory end to end.
+"""ctypes wrapper of the C state-vector core; runs one trajectory end to end.
 
 Test infrastructure only (see ``oracle/__init__.py``).
 """

@@ -55,6 +55,12 @@ def parse():
                     help="serve: requests in the second trace, at 0.7 of the capacity the first one measured")
     ap.add_argument("--no-serve", action="store_true", help="d5: skip the serving trace added to the line")
     ap.add_argument("--mem-gib", type=float, default=32.0, help="serve: device memory budget for state vectors")
+    ap.add_argument("--kinds", default="c128,c64,c128u,c64u",
+                    help="batched: the kinds kept from the 8192-trajectory mix (comma-separated; a subset runs "
+                         "fewer trajectories)")
+    ap.add_argument("--config", default=None,
+                    help="batched: W,K,T = reduced-engine warps per CTA, unreduced fusion width, unreduced threads "
+                         "per CTA, instead of the autotuner's choice")
     ap.add_argument("--noise", default="full", choices=["full", "idle", "twirl", "follows"],
                     help="sweep: full = p on every step (Eqs. 1-2); idle = p on waiting qubits only; "
                          "twirl = full with the coherent terms replaced by their Pauli twirl")
@@ -386,8 +392,14 @@ def batched_arm(args, rank, world, local):
     torch.cuda.set_device(local)
     traj, kinds, noise, rounds, seed = W.batched_mix(n=8192)
     traj = [t + rank * 8192 for t in traj]
+    keep = set(args.kinds.split(","))
+    sel = [i for i in range(len(traj)) if kinds[i] in keep]
+    traj, kinds, noise = [traj[i] for i in sel], [kinds[i] for i in sel], [noise[i] for i in sel]
     with BatchSimulator(rounds, "cr", max_traj=8192) as b:
-        b.autotune(seed, traj[:1024], kinds[:1024], noise[:1024])
+        if args.config:
+            b.set_config(*(int(x) for x in args.config.split(",")))
+        else:
+            b.autotune(seed, traj[:1024], kinds[:1024], noise[:1024])
         warps, fusion_k, u_threads = b.config()
         for _ in range(args.warmup):
             b.run(seed, traj, kinds, noise)
@@ -409,9 +421,12 @@ def batched_arm(args, rank, world, local):
         "config": {"workload": "8192 d=3 trajectories per step in equal quarters: reduced 10-qubit and "
                                "unreduced 17-qubit registers x complex128/complex64; 3 rounds, cr gates, "
                                "p~U[1e-4,1e-2], theta_rx~U[0,0.1]",
-                   "autotuned": {"reduced_warps_per_cta": warps, "unreduced_fusion_width": fusion_k,
-                                 "unreduced_threads_per_cta": u_threads,
-                                 "sample": "the first 1024 trajectories, each engine on its own register's"},
+                   ("configured" if args.config else "autotuned"): {
+                       "reduced_warps_per_cta": warps, "unreduced_fusion_width": fusion_k,
+                       "unreduced_threads_per_cta": u_threads,
+                       "sample": "--config" if args.config else
+                                 "the first 1024 trajectories, each engine on its own register's"},
+                   "kinds": args.kinds,
                    "rounds_per_s": world * n * rounds * args.steps / dev},
         "clocks": clk.summary(),
         "e2e": {"value": world * n * args.steps / wall, "unit": "trajectories/s",

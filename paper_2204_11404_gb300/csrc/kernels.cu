@@ -510,6 +510,7 @@ __global__ void __launch_bounds__(256) k_fused(FusedArgs f) {
       }
     }
     __syncthreads();
+    T tA = 0, tN = 0;   // this thread's sums over its groups of the tile (complex64: added in FP64 once per tile)
     for (uint32_t g = threadIdx.x; g < (tsz >> W2); g += blockDim.x) {
       const uint32_t b = local_base<W2>(g, qp);
       T2 v[C2];
@@ -549,8 +550,17 @@ __global__ void __launch_bounds__(256) k_fused(FusedArgs f) {
         diag = fma_t(lds_v2(&sM[i * C2 + i]).x, nv, diag);
         sn += nv;
       }
-      accA += (double)(2 * cross + diag);
-      accN += (double)sn;
+      if constexpr (sizeof(T) == 4) {
+        tA += 2 * cross + diag;
+        tN += sn;
+      } else {
+        accA += (double)(2 * cross + diag);
+        accN += (double)sn;
+      }
+    }
+    if constexpr (sizeof(T) == 4) {
+      accA += (double)tA;
+      accN += (double)tN;
     }
     const uint32_t tb = tile_base(tix);
     for (uint32_t e = threadIdx.x * CH; e < tsz; e += blockDim.x * CH)

@@ -323,6 +323,20 @@ def native_arm(args, rank, world, local):
         roof = {"bound": "hbm", "achieved": bytes_apply / (ms_apply * 1e-3) / 1e9, "peak": peaks["hbm_gbs"],
                 "unit": "GB/s"}
     roof["frac"] = roof["achieved"] / roof["peak"]
+    # the fused pass of a pair of two weight-2 blocks (a quarter of the stabilizer pairs at d = 5),
+    # instrumented on three more trajectories after the timed region
+    if args.code == "surface" and args.precision != "c128":
+        blk = capi.qec_select_timed_block(sims[0].h, 2, 2)
+        ms22 = []
+        for t in range(3):
+            sims[0].run_device(seeds[0], 20_000 + t, 1, syn.data_ptr(), bits.data_ptr(), log.data_ptr())
+            ms22.append(capi.qec_kernel_times(sims[0].h)[1])
+        ms22 = float(np.median(ms22))
+        roof["weight2_pair"] = {
+            "kernel": {"c64": "k_fused<float,2,2>", "c64tc": "k_fused<float,2,2> (CUDA cores)",
+                       "c128tc": "k_ozf (both blocks as K (x) I)"}[args.precision],
+            "block": blk, "ms": ms22, "achieved": bytes_apply / (ms22 * 1e-3) / 1e9,
+            "frac": bytes_apply / (ms22 * 1e-3) / 1e9 / roof["peak"], "unit": "GB/s"}
     roof["traffic"] = traffic_record(args.precision)
     roof["kernel"] = {"c128": "k_apply<double,4> (weight-4 block, 2^25 amplitudes)",
                       "c64": "k_fused<float,4,4> (apply weight-4 block + next block's probability, 2^25 amplitudes)",

@@ -174,6 +174,17 @@ qec_status qec_get_events(qec_sim* sim, int32_t* host_events, uint32_t max_event
 qec_status qec_kernel_times(qec_sim* sim, float* ms, int32_t* block);
 
 /*
+ * Measurement hook: instrument, from the next trajectory on, the first block
+ * of the middle noisy round whose weight is w_apply and whose successor's
+ * weight is w_next (2 or 4; with the fused passes, ms[1] of qec_kernel_times
+ * is then the pass that applies that block and computes its successor's
+ * probability).  *block gets its index.  QEC_EINVAL if the sim has no noisy
+ * round or no such pair of blocks.  The trajectory graph is rebuilt at the
+ * next run; results do not change.
+ */
+qec_status qec_select_timed_block(qec_sim* sim, int32_t w_apply, int32_t w_next, int32_t* block);
+
+/*
  * Self-test of failure detection: runs, on the sim's stream, the bounded
  * mbarrier wait used by the tensor-core pass on a barrier that nothing ever
  * arrives on, giving up after `polls` polls (1..1e7).  Returns QEC_ETIMEOUT

@@ -49,6 +49,7 @@ SIGNATURES = {
     "qec_record_events": ([_P, ctypes.c_uint32], ctypes.c_int),
     "qec_get_events": ([_P, _P, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32)], ctypes.c_int),
     "qec_kernel_times": ([_P, _P, _P], ctypes.c_int),
+    "qec_select_timed_block": ([_P, ctypes.c_int32, ctypes.c_int32, _P], ctypes.c_int),
     "qec_selftest_wait": ([_P, ctypes.c_uint32], ctypes.c_int),
     "qec_run_trajectories_noalloc": ([ctypes.POINTER(qec_params), ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32,
                                       _P, _P, _P, _P], ctypes.c_int),
@@ -149,6 +150,14 @@ def qec_kernel_times(sim):
     blk = ctypes.c_int32(0)
     check(lib().qec_kernel_times(sim, ctypes.cast(ms, _P), ctypes.cast(ctypes.pointer(blk), _P)))
     return float(ms[0]), float(ms[1]), int(blk.value)
+
+
+def qec_select_timed_block(sim, w_apply, w_next):
+    """Instrument the first block of the middle noisy round with weight w_apply followed by one of
+    weight w_next; returns its index."""
+    blk = ctypes.c_int32(0)
+    check(lib().qec_select_timed_block(sim, w_apply, w_next, ctypes.cast(ctypes.pointer(blk), _P)))
+    return int(blk.value)
 
 
 def qec_run_trajectories_noalloc(params, seed, first_traj, n, d_syn_ptr, d_bits_ptr, d_log_ptr, cuda_stream=None):

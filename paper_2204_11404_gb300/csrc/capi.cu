@@ -567,6 +567,23 @@ qec_status qec_kernel_times(qec_sim* s, float* ms, int32_t* block) {
   return QEC_OK;
 }
 
+qec_status qec_select_timed_block(qec_sim* s, int32_t w_apply, int32_t w_next, int32_t* block) {
+  if (!s || !block) return fail(QEC_EINVAL, "null argument");
+  if (s->R <= 0) return fail(QEC_EINVAL, "the sim has no noisy round");
+  const int rnd = (s->R + 1) / 2;
+  for (int k = 0; k < s->nstab; ++k) {
+    const int b = (rnd - 1) * s->nstab + k;
+    if (b + 1 >= s->S) break;
+    if (s->prog.blocks[k].w == w_apply && s->prog.blocks[(k + 1) % s->nstab].w == w_next) {
+      drop_graph(s);   // the next trajectory records the events around block b
+      s->timed_block = b;
+      *block = b;
+      return QEC_OK;
+    }
+  }
+  return fail(QEC_EINVAL, "no block of the middle noisy round with those weights");
+}
+
 qec_status qec_destroy(qec_sim* s) {
   if (!s) return QEC_OK;
   if (s->work) cudaStreamSynchronize(s->work);

@@ -72,6 +72,34 @@ def test_maximum_rounds_d3_matches_oracle():
         assert compare_trajectory(syn[i], bits[i], o, 1e-9) == "exact"
 
 
+
+@pytest.mark.parametrize("prec", ["c64", "c128"])
+def test_select_timed_block_instruments_the_chosen_pair(prec):
+    """The measurement hook moves the instrumented block to the first block of the middle noisy round
+    with the requested weights (the d = 3 code has weight-2 and weight-4 stabilizers); outcomes do not
+    change, and weights no block has are rejected."""
+    with Simulator(3, 3, "cr", prec, **W.STRESS) as ref:
+        expect = ref.run(8, 0, 2)
+    with Simulator(3, 3, "cr", prec, **W.STRESS) as sim:
+        sim.run(8, 5, 1)
+        _, _, b4 = capi.qec_kernel_times(sim.h)
+        for wa, wn in ((2, 2), (2, 4), (4, 2)):
+            try:
+                blk = capi.qec_select_timed_block(sim.h, wa, wn)
+            except capi.QecError as e:
+                assert e.status == capi.QEC_EINVAL
+                continue
+            assert 8 <= blk < 16                      # the middle noisy round of three (8 blocks per round)
+            got = sim.run(8, 0, 2)
+            for x, y in zip(got, expect):
+                assert (x == y).all()
+            ms_p, ms_a, b = capi.qec_kernel_times(sim.h)
+            assert b == blk and ms_a > 0 and ms_p >= 0
+        with pytest.raises(capi.QecError) as e:
+            capi.qec_select_timed_block(sim.h, 3, 3)
+        assert e.value.status == capi.QEC_EINVAL
+    assert 8 <= b4 < 16
+
 def test_batch_rejects_bad_inputs():
     from paper_2204_11404_gb300.simulator import BatchSimulator
     with pytest.raises(capi.QecError):

@@ -310,6 +310,21 @@ qec_status qec_debug_program(const qec_params* params, int32_t* ops, uint32_t ca
                              int32_t* block_info, uint32_t block_cap, uint32_t* n_blocks);
 
 /*
+ * Host-only test hook (no GPU needed): the batched form's plan for one round
+ * of the unreduced 17-qubit register (d = 3, gate set `gates`, every noise
+ * site present), at fusion width k.  items: int32 quadruples (kind 0 = unit /
+ * 1 = measurement, qubits 1 or 2, slab bit qa, slab bit qb or -1) in
+ * execution order, *n_items of them.  pass_units: the unit items the passes
+ * apply, in order (*n_pass_units).  absorbs: int32 triples (one-qubit item,
+ * two-qubit item it is folded into, mode: bit 0 = from the left (after),
+ * bit 1 = on the unit's first qubit), *n_absorbs of them.  All arrays hold up
+ * to `cap` entries; QEC_EINVAL if that is too small.
+ */
+qec_status qec_debug_unreduced_plan(int32_t gates, int32_t k, int32_t* items, uint32_t cap, uint32_t* n_items,
+                                    int32_t* pass_units, uint32_t* n_pass_units, int32_t* absorbs,
+                                    uint32_t* n_absorbs);
+
+/*
  * Host-only test hook (no GPU needed): runs the same block-instantiation code
  * the device runs, on the CPU, for trajectory `traj` of round `round` (0 = the
  * forced init round).  For each of the d^2-1 blocks writes K0 and K1 (16x16

@@ -50,6 +50,8 @@ SIGNATURES = {
     "qec_get_events": ([_P, _P, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32)], ctypes.c_int),
     "qec_kernel_times": ([_P, _P, _P], ctypes.c_int),
     "qec_select_timed_block": ([_P, ctypes.c_int32, ctypes.c_int32, _P], ctypes.c_int),
+    "qec_debug_unreduced_plan": ([ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_uint32, _P, _P, _P, _P, _P],
+                                 ctypes.c_int),
     "qec_selftest_wait": ([_P, ctypes.c_uint32], ctypes.c_int),
     "qec_run_trajectories_noalloc": ([ctypes.POINTER(qec_params), ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32,
                                       _P, _P, _P, _P], ctypes.c_int),
@@ -231,6 +233,19 @@ def qec_debug_program(params, ops_ptr, cap, block_ptr, block_cap):
     check(lib().qec_debug_program(ctypes.byref(params), ops_ptr, cap, ctypes.byref(n_ops), block_ptr, block_cap,
                                   ctypes.byref(n_blk)))
     return int(n_ops.value), int(n_blk.value)
+
+
+def qec_debug_unreduced_plan(gates, k, cap=512):
+    """(items [n][4], pass unit items [m], absorptions [a][3]) of the batched form's unreduced round plan."""
+    import numpy as np
+
+    items = np.zeros((cap, 4), np.int32)
+    pu = np.zeros(cap, np.int32)
+    ab = np.zeros((cap, 3), np.int32)
+    ni, npu, na = ctypes.c_uint32(0), ctypes.c_uint32(0), ctypes.c_uint32(0)
+    check(lib().qec_debug_unreduced_plan(gates, k, items.ctypes.data, cap, ctypes.byref(ni), pu.ctypes.data,
+                                         ctypes.byref(npu), ab.ctypes.data, ctypes.byref(na)))
+    return items[: ni.value].copy(), pu[: npu.value].copy(), ab[: na.value].copy()
 
 
 def qec_debug_blocks(params, seed, traj, rnd, kraus_ptr, u_ptr):

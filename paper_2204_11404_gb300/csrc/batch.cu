@@ -1301,6 +1301,54 @@ qec_status set_shape(qec_batch* b, int warps) {
 
 extern "C" {
 
+qec_status qec_debug_unreduced_plan(int32_t gates, int32_t k, int32_t* items, uint32_t cap, uint32_t* n_items,
+                                    int32_t* pass_units, uint32_t* n_pass_units, int32_t* absorbs, uint32_t* n_absorbs) {
+  if (!items || !n_items || !pass_units || !n_pass_units || !absorbs || !n_absorbs)
+    return bfail(QEC_EINVAL, "null argument");
+  if (k < 2 || k > kUMaxFusionDecl) return bfail(QEC_EINVAL, "fusion width must be in [2, 6]");
+  try {
+    qec_params p{};
+    p.d = kD;
+    p.rounds = 1;
+    p.layout = QEC_LAYOUT_REDUCED;   // the parameters qec_batch_create builds both programs from
+    p.gates = gates;
+    p.precision = QEC_C128;
+    p.noise = qec_noise{1, 1, 1, 1, 1, 1, 1, 1, 1, 0};   // every site and coherent op present
+    std::string err;
+    UProgram U;
+    if (!build_unreduced_program(p, true, U, err, true)) return bfail(QEC_EINVAL, err);
+    std::vector<UPass> passes;
+    std::vector<UPassUnit> punits;
+    std::vector<UAbs> uabs;
+    build_passes(U, k, passes, punits, uabs);
+    *n_items = (uint32_t)U.items.size();
+    if (U.items.size() > cap || punits.size() > cap || uabs.size() > cap)
+      return bfail(QEC_EINVAL, "capacity too small");
+    for (size_t i = 0; i < U.items.size(); ++i) {
+      const UItem& u = U.items[i];
+      items[4 * i] = u.kind;
+      items[4 * i + 1] = u.nq;
+      items[4 * i + 2] = u.qa;
+      items[4 * i + 3] = u.kind == 0 && u.nq == 2 ? u.qb : -1;
+    }
+    uint32_t na = 0;
+    for (size_t i = 0; i < punits.size(); ++i) {
+      pass_units[i] = punits[i].item;
+      for (int e = punits[i].abs0; e < punits[i].abs0 + punits[i].nabs; ++e) {
+        absorbs[3 * na] = uabs[e].item1;
+        absorbs[3 * na + 1] = punits[i].item;
+        absorbs[3 * na + 2] = uabs[e].mode;
+        ++na;
+      }
+    }
+    *n_pass_units = (uint32_t)punits.size();
+    *n_absorbs = na;
+    return QEC_OK;
+  } catch (...) {
+    return bfail(QEC_ENOMEM, "host allocation failed");
+  }
+}
+
 qec_status qec_batch_create(int32_t d, int32_t rounds, int32_t gates, uint32_t max_traj, void* cuda_stream,
                             qec_batch** out) {
   if (!out) return bfail(QEC_EINVAL, "null output handle");

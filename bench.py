@@ -55,6 +55,8 @@ def parse():
                     help="serve: requests in the second trace, at 0.7 of the capacity the first one measured")
     ap.add_argument("--no-serve", action="store_true", help="d5: skip the serving trace added to the line")
     ap.add_argument("--mem-gib", type=float, default=32.0, help="serve: device memory budget for state vectors")
+    ap.add_argument("--policy", default="sjf", choices=["fifo", "sjf"],
+                    help="serve: admission order of waiting jobs (shortest aged estimated work first, or arrival order)")
     ap.add_argument("--kinds", default="c128,c64,c128u,c64u",
                     help="batched: the kinds kept from the 8192-trajectory mix (comma-separated; a subset runs "
                          "fewer trajectories)")
@@ -463,7 +465,7 @@ def serve_measure(args, rank, world, local):
     warm = [Job(**j) for j in W.serving_trace(n_req=4, rate=1e6, seed=1, max_traj=1)]
     trace = W.serving_trace(n_req=args.requests, rate=args.rate, seed=5000 + rank, max_traj=args.max_traj)
     jobs = [Job(**j) for j in trace]
-    srv = Server(int(args.mem_gib * 2**30))
+    srv = Server(int(args.mem_gib * 2**30), policy=args.policy)
     try:
         srv.run(warm)
         with ClockSampler(local) as clk:
@@ -484,13 +486,13 @@ def serve_measure(args, rank, world, local):
            "trajectories_per_s": world * traj / makespan, "makespan_s": makespan,
            "latency_ms": latency_summary(jobs),
            "offered_trajectory_rounds_per_s": offered, "achieved_trajectory_rounds_per_s": tr_rounds / makespan,
-           "mem_budget_gib": args.mem_gib, "clocks": clk.summary(), "out_bytes": out_bytes}
+           "mem_budget_gib": args.mem_gib, "policy": args.policy, "clocks": clk.summary(), "out_bytes": out_bytes}
     # second trace at a sustainable rate: utilisation about 0.7 of the capacity the first one measured
     if offered and args.sustainable_requests > 0:
         rate2 = 0.7 * args.rate * (tr_rounds / makespan) / offered
         jobs2 = [Job(**j) for j in W.serving_trace(n_req=args.sustainable_requests, rate=rate2, seed=6000 + rank,
                                                     max_traj=args.max_traj)]
-        srv = Server(int(args.mem_gib * 2**30))
+        srv = Server(int(args.mem_gib * 2**30), policy=args.policy)
         try:
             t1 = time.perf_counter()
             srv.run(jobs2)
@@ -513,7 +515,7 @@ def serve_arm(args, rank, world, local):
         "warmup": 4, "ms_per_step": 1e3 * rep["makespan_s"] / rep["requests"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
         "config": {"workload": rep["trace"], "requests": rep["requests"], "rate_per_s": args.rate,
-                   "mem_budget_gib": args.mem_gib,
+                   "mem_budget_gib": args.mem_gib, "policy": args.policy,
                    "offered_trajectory_rounds_per_s": rep["offered_trajectory_rounds_per_s"],
                    "achieved_trajectory_rounds_per_s": rep["achieved_trajectory_rounds_per_s"]},
         "latency_ms": rep["latency_ms"], "clocks": rep["clocks"],

@@ -17,7 +17,8 @@ from paper_2204_11404_gb300.serve import Job, Server, latency_summary, state_byt
 from paper_2204_11404_gb300.simulator import Simulator  # noqa: E402
 
 
-def test_continuous_batching_results_equal_solo_runs():
+@pytest.mark.parametrize("policy", ["fifo", "sjf"])
+def test_continuous_batching_results_equal_solo_runs(policy):
     trace = W.serving_trace(n_req=14, rate=200.0, seed=11, max_traj=3, precisions=("c64", "c64", "c128"))
     for j in trace:                          # keep d=5 complex128 jobs short
         if j["d"] == 5 and j["precision"] == "c128":
@@ -25,7 +26,7 @@ def test_continuous_batching_results_equal_solo_runs():
             j["n_traj"] = 1
     jobs = [Job(**j) for j in trace]
     budget = 2 * state_bytes(5, "c64") + state_bytes(5, "c128") // 2 + 64 * 2**20   # forces waiting
-    srv = Server(budget)
+    srv = Server(budget, policy=policy)
     # complex128 at d=5 is served by the tensor-core complex128 engine; its solo runs below use the
     # FP64 CUDA-core engine, so the equality checks cover the two FP64-accurate engines against each
     # other.  complex64 at d=5 is served by the tensor-core complex64 engine, and its solo runs use the

@@ -270,6 +270,7 @@ def native_arm(args, rank, world, local):
     stream = bstream
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     fb0 = [capi.qec_debug_exact_probability(s.h, -1) for s in sims] if args.precision == "c128tc" else None
+    sm0 = [capi.qec_debug_speculation(s.h, -1) for s in sims] if args.precision == "c128tc" else None
     with ClockSampler(local) as clk:
         torch.cuda.synchronize()
         e0.record(stream)
@@ -282,6 +283,7 @@ def native_arm(args, rank, world, local):
     used = sorted({(args.warmup + i) % len(pts) for i in range(args.steps)})
     kt = [capi.qec_kernel_times(sims[j].h) for j in used]
     fallbacks = (sum(capi.qec_debug_exact_probability(s.h, -1) for s in sims) - sum(fb0)) if fb0 else None
+    misses = (sum(capi.qec_debug_speculation(s.h, -1) for s in sims) - sum(sm0)) if sm0 else None
     if world > 1:
         dist.barrier()
     secs = e0.elapsed_time(e1) / 1e3
@@ -309,8 +311,9 @@ def native_arm(args, rank, world, local):
            "h2d_bytes_per_step": 32, "d2h_bytes_per_step": (R + 1) * nst + 25 + 1}
 
     # roofline of the dominant kernel: the pass that applies a weight-4 block (psi <- K_m psi / sqrt(N));
-    # in the complex64 and tensor-core complex128 forms it also computes the next block's probability
-    # (fused: one read + one write of the register per stabilizer)
+    # in the complex64 forms it also computes the next block's probability (fused: one read + one
+    # write of the register per stabilizer); in the tensor-core complex128 form it applies the guessed
+    # outcome's operator and sums |in|^2 and |out|^2 for the decision (one read + one write)
     ms_prob = float(np.mean([k[0] for k in kt]))
     ms_apply = float(np.mean([k[1] for k in kt]))
     amps = 1 << 25
@@ -336,15 +339,16 @@ def native_arm(args, rank, world, local):
         ms22 = float(np.median(ms22))
         roof["weight2_pair"] = {
             "kernel": {"c64": "k_fused<float,2,2>", "c64tc": "k_fused<float,2,2> (CUDA cores)",
-                       "c128tc": "k_ozf (both blocks as K (x) I)"}[args.precision],
+                       "c128tc": "k_ozs<false> (weight-2 block as K (x) I)"}[args.precision],
             "block": blk, "ms": ms22, "achieved": bytes_apply / (ms22 * 1e-3) / 1e9,
             "frac": bytes_apply / (ms22 * 1e-3) / 1e9 / roof["peak"], "unit": "GB/s"}
     roof["traffic"] = traffic_record(args.precision)
     roof["kernel"] = {"c128": "k_apply<double,4> (weight-4 block, 2^25 amplitudes)",
                       "c64": "k_fused<float,4,4> (apply weight-4 block + next block's probability, 2^25 amplitudes)",
                       "c64tc": "k_fused_tc (tcgen05 3xTF32: apply weight-4 block + next probability, 2^25 amplitudes)",
-                      "c128tc": "k_ozf (tcgen05: apply weight-4 block as FP64-exact 8-bit-slice products + next block's "
-                                "bounded probability on the same tiles, 2^25 amplitudes)",
+                      "c128tc": "k_ozs<false> (tcgen05: speculative apply of a weight-4 block, the outcome guessed "
+                                "from the previous round, as FP64-exact 8-bit-slice products + bounded |in|^2 and "
+                                "|out|^2 sums on the same tiles, 2^25 amplitudes)",
                       }[args.precision]
     if args.code == "repetition":
         roof["kernel"] = roof["kernel"].replace("weight-4 block", "weight-2 block Z_k Z_(k+1)")
@@ -355,13 +359,13 @@ def native_arm(args, rank, world, local):
         roof["prob_fp64_tflops"] = flops_prob / (ms_prob * 1e-3) / 1e12
     roof["timed_blocks"] = len(kt)
 
-    # launches per trajectory: instantiate; the first block's probability pass (the tensor-core
-    # complex128 form: bounded + exact launch); per later block one fused pass (the tensor-core
-    # complex128 form: + the exact-probability launch, which returns at once unless the bound left
-    # the outcome open) or, in the FP64 CUDA-core form, a probability and an apply pass; the last
-    # block's apply; the readout (3)
+    # launches per trajectory: instantiate; the complex64 forms: the first block's probability pass,
+    # per later block one fused pass, the last block's apply; the FP64 CUDA-core form: a probability
+    # and an apply pass per block; the tensor-core complex128 form: per block the speculative pass,
+    # the exact-probability launch and the corrective launch (these two return at once unless the
+    # bound left the outcome open / the guess was wrong); the readout (3)
     S = nst * R
-    launches_per_traj = {"c128": 1 + 2 * S + 3, "c128tc": 1 + 2 + 2 * (S - 1) + 1 + 3,
+    launches_per_traj = {"c128": 1 + 2 * S + 3, "c128tc": 1 + 3 * S + 3,
                          "c64": 1 + 1 + (S - 1) + 1 + 3, "c64tc": 1 + 1 + (S - 1) + 1 + 3}[args.precision]
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -373,6 +377,8 @@ def native_arm(args, rank, world, local):
     }
     if fallbacks is not None:   # measurements the bound left open (exact pass run), of S per trajectory
         out["exact_probability_passes"] = {"count": fallbacks, "measurements": S * args.steps}
+    if misses is not None:      # outcomes that differed from the guess (corrective apply run)
+        out["speculation"] = {"corrective_applies": misses, "measurements": S * args.steps}
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.code == "surface":
         from oracle.runner import set_threads
 

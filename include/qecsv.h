@@ -48,15 +48,19 @@ typedef enum { QEC_GATES_CNOT = 0, QEC_GATES_CR = 1 } qec_gateset;
  * FP32 accumulation; a weight-2 block of the pair as K (x) I over two
  * spectator qubits; tiles of 2^12 amplitudes, so d >= 5), pairs of weight-2
  * blocks on the CUDA cores; FP64 probability reductions.
- * C128_TC: complex128 state; the apply and probability passes of every
- * stabilizer block (tiles of 2^11 amplitudes, so d >= 5) as emulated FP64
- * products on the FP16 tensor cores: each operand row split into 7 signed
- * 8-bit slices under one exponent, slice products accumulated exactly,
- * recombined in integers and rounded once (Ozaki scheme); sums of squares
- * in exact integers; each outcome decided from a 3-slice probability with a
- * rigorous error bound where the bound settles it, else by the exact pass
- * (qec_debug_exact_probability); init and readout in FP64.  Same outcomes
- * and, to within a few FP64 roundings, the same amplitudes as C128. */
+ * C128_TC: complex128 state; the apply of every stabilizer block (tiles of
+ * 2^11 amplitudes, so registers of at least 11 qubits: d >= 4) as emulated
+ * FP64 products on the FP16 tensor cores: each operand row split into 7
+ * signed 8-bit slices under one exponent, slice products accumulated exactly,
+ * recombined in integers and rounded once (Ozaki scheme).  One speculative
+ * pass per block (qec_debug_speculation): it applies the Kraus operator of the
+ * outcome the same stabilizer gave one round earlier (the init round's for the
+ * first noisy round) into a second working state, and on the same tiles sums
+ * |input|^2 and |output|^2 as 24-bit truncations with rigorous error bounds;
+ * the outcome is decided from them where the bounds settle it, else by the
+ * exact pass on the untouched input (qec_debug_exact_probability), and a wrong
+ * guess is re-applied from that input.  Init and readout in FP64.  Same
+ * outcomes and, to within a few FP64 roundings, the same amplitudes as C128. */
 typedef enum { QEC_C128 = 0, QEC_C64 = 1, QEC_C64_TC = 2, QEC_C128_TC = 3 } qec_precision;
 
 /* Noise (Sec. III.A).  Probabilities in [0, 1]; angles in radians, |angle| <= 4. */
@@ -167,7 +171,10 @@ qec_status qec_get_events(qec_sim* sim, int32_t* host_events, uint32_t max_event
  * Measurement hook: device time in milliseconds of the probability pass
  * (ms[0]) and of the collapse/apply pass (ms[1]) of one weight-4 stabilizer
  * block of the middle noisy round, in the most recent trajectory (CUDA events
- * recorded inside the trajectory's graph).  *block gets that block's index
+ * recorded inside the trajectory's graph).  With the fused passes ms[0] is
+ * empty for a block whose probability the previous pass computed; with the
+ * speculative passes (QEC_C128_TC) ms[0] is empty and ms[1] is the block's
+ * speculative pass, without the exact and corrective launches after it.  *block gets that block's index
  * (round-major, d^2-1 per round).  QEC_EINVAL if no trajectory ran yet or the
  * sim has no noisy round.
  */
@@ -358,15 +365,29 @@ qec_status qec_debug_ozaki_gemm(const double* A, const double* B, int32_t m, int
 
 /*
  * Test hook for QEC_C128_TC (the paper has no counterpart: an evaluation order of Sec. II.B's
- * measurement probability).  Its probability pass first computes A = |K_1 psi|^2 from the top
- * 3 of the 7 slices of each operand together with a rigorous bound on the error, and N exactly;
- * it decides the outcome on the device when |u N - A| exceeds twice the bound plus
- * 1e-10 (A + N), where the exact pass must decide the same way, and otherwise runs the exact
- * pass.  force = 1: every outcome goes through the exact pass; 0: the default; -1: unchanged.
+ * measurement probability).  Each outcome is first decided from estimates with a rigorous
+ * error bound: A = |K_1 psi|^2 and N = |psi|^2 from the speculative pass's sums (see
+ * qec_debug_speculation), or A from the top 3 of the 7 slices of each operand in the fused pass;
+ * the device decides when |u N - A| exceeds twice the bound plus 1e-10 (A + N), where the exact
+ * pass must decide the same way, and otherwise runs the exact pass.  force = 1: every outcome goes through the exact pass; 0: the default; -1: unchanged.
  * *fallbacks (may be NULL) receives the number of exact passes run on this handle so far.
  * Waits for the handle's queued work.  QEC_EINVAL on a null handle or force outside -1..1.
  */
 qec_status qec_debug_exact_probability(qec_sim* sim, int32_t force, uint64_t* fallbacks);
+
+/*
+ * Test hook for QEC_C128_TC (the paper has no counterpart: an evaluation order of Sec. II.B's
+ * measurement and collapse).  enable = 1: the speculative passes (the default wherever every
+ * block's tile fits the register); 0: per block pair, the pass fused with the next block's
+ * 3-slice bounded probability; -1: unchanged.  Both give the same outcomes (except within the
+ * exact pass's own rounding of a threshold) and states within a few FP64 roundings.  *misses (may
+ * be NULL) receives the number of corrective applies run on this handle so far (outcomes that
+ * differed from the guess).  Waits for the handle's queued work; switching rebuilds the
+ * trajectory graph and requires a new run before qec_get_state.  QEC_EINVAL on a null handle or
+ * enable outside -1..1; QEC_EUNSUPPORTED for enable = 1 where the speculative pass does not
+ * apply (another precision, or a register below 11 qubits).
+ */
+qec_status qec_debug_speculation(qec_sim* sim, int32_t enable, uint64_t* misses);
 
 #ifdef __cplusplus
 }

@@ -73,6 +73,7 @@ SIGNATURES = {
                          ctypes.c_int),
     "qec_debug_ozaki_gemm": ([_P, _P, ctypes.c_int32, ctypes.c_int32, _P], ctypes.c_int),
     "qec_debug_exact_probability": ([_P, ctypes.c_int32, _P], ctypes.c_int),
+    "qec_debug_speculation": ([_P, ctypes.c_int32, _P], ctypes.c_int),
 }
 
 
@@ -256,6 +257,13 @@ def qec_debug_exact_probability(sim, force):
     """Set the exact-probability mode (1, 0, or -1 = unchanged); returns the exact passes run so far."""
     c = ctypes.c_uint64(0)
     check(lib().qec_debug_exact_probability(sim, force, ctypes.byref(c)))
+    return int(c.value)
+
+
+def qec_debug_speculation(sim, enable):
+    """Set the speculative-pass mode (1, 0, or -1 = unchanged); returns the corrective applies run so far."""
+    c = ctypes.c_uint64(0)
+    check(lib().qec_debug_speculation(sim, enable, ctypes.byref(c)))
     return int(c.value)
 
 

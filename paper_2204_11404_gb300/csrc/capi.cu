@@ -60,6 +60,8 @@ struct qec_sim {
   size_t amp = 16;
   void* psi = nullptr;
   void* psi0 = nullptr;
+  void* psi2 = nullptr;                        // second working state of the speculative passes
+  bool spec = false;                           // QEC_C128_TC with every block on the speculative pass
   ProgOp* d_ops[2] = {nullptr, nullptr};       // [0] init, [1] noisy
   BlockInfo* d_blocks[2] = {nullptr, nullptr};
   double* d_mats[2] = {nullptr, nullptr};
@@ -189,6 +191,37 @@ PassArgs traj_pass(const qec_sim* s, int b) {
   return pass_args(s, s->prog, b, src, s->psi, false, s->d_syn, rnd * s->nstab + k);
 }
 
+// Speculative passes (QEC_C128_TC where every block's tile fits the register): block b reads the
+// state block b-1 wrote (block 0 the init state) and writes the other working buffer, so that a
+// wrong guess is corrected from its untouched input.
+void* spec_out(const qec_sim* s, int b) { return (b & 1) ? s->psi2 : s->psi; }
+
+PassArgs spec_pass(const qec_sim* s, int b) {
+  PassArgs a = traj_pass(s, b);
+  a.src = b == 0 ? s->psi0 : spec_out(s, b - 1);
+  a.dst = spec_out(s, b);
+  a.spec_prev = b >= s->nstab ? a.syn_idx - s->nstab : -1;
+  return a;
+}
+
+bool spec_applies(const qec_sim* s) {
+  if (s->p.precision != QEC_C128_TC) return false;
+  for (int k = 0; k < s->nstab; ++k) {
+    PassArgs a;
+    a.D = s->D;
+    a.w = s->prog.blocks[k].w;
+    for (int j = 0; j < 4; ++j) a.q[j] = s->prog.blocks[k].q[j] < 0 ? 0 : s->prog.blocks[k].q[j];
+    if (!apply_oz_applies(a)) return false;
+  }
+  return true;
+}
+
+// The state the last block wrote (the init state when there are no noisy rounds).
+const void* final_state(const qec_sim* s) {
+  if (s->S == 0) return s->psi0;
+  return s->spec ? spec_out(s, s->S - 1) : s->psi;
+}
+
 // Block b's apply pass is fused with block b+1's probability pass (one HBM read + write per
 // stabilizer) in the complex64 forms (k_fused, k_fused_tc) and in the tensor-core complex128 form
 // (k_ozf) wherever both blocks fit one tile; the FP64 CUDA-core form keeps them separate (both of its
@@ -219,7 +252,7 @@ qec_status record(qec_sim* s, int i) {
 
 qec_status enqueue_readout(qec_sim* s) {
   ReadArgs r;
-  r.src = s->S > 0 ? s->psi : s->psi0;
+  r.src = final_state(s);
   r.D = s->D;
   r.k1 = hist_k1(s->D);
   r.d = s->p.d;
@@ -239,14 +272,27 @@ qec_status enqueue_readout(qec_sim* s) {
 
 // The whole trajectory: instantiate, then per block b its probability pass (unless block b-1's
 // fused pass computed it) and its apply pass (fused with block b+1's probability pass where
-// fused_step), then the readout.  The instrumented block's passes are bracketed by event-record
-// nodes: kev[0]..kev[1] its separate probability pass (empty when fused into the previous block's
-// pass), kev[1]..kev[2] its apply pass or fused pass (without the exact-probability launch that
-// follows a tensor-core fused pass).
+// fused_step), or with the speculative passes its speculative pass and that pass's completion;
+// then the readout.  The instrumented block's passes are bracketed by event-record nodes:
+// kev[0]..kev[1] its separate probability pass (empty when fused into the previous block's pass, and
+// with the speculative passes), kev[1]..kev[2] its apply, fused or speculative pass (without the
+// exact-probability and corrective launches that follow the tensor-core passes).
 qec_status enqueue_trajectory(qec_sim* s) {
   const int tb = s->timed_block;
   qec_status st = QEC_OK;
   if (s->S > 0) QEC_CUDA(launch_instantiate(s->p.precision, inst_args(s, 1, 1, s->S, true), s->work));
+  if (s->spec) {   // per block: the speculative pass (kev[1]..kev[2]), then its completion
+    for (int b = 0; b < s->S && st == QEC_OK; ++b) {
+      const bool timed = b == tb;
+      const PassArgs a = spec_pass(s, b);
+      double* n_next = b + 1 < s->S ? s->d_N + b + 1 : nullptr;
+      if (timed && ((st = record(s, 0)) || (st = record(s, 1)))) return st;
+      QEC_CUDA(launch_spec_oz(a, n_next, b == 0, s->num_sms, s->work));
+      if (timed && (st = record(s, 2))) return st;
+      QEC_CUDA(launch_spec_oz_fix(a, n_next, b == 0, s->num_sms, s->work));
+    }
+    return st == QEC_OK ? enqueue_readout(s) : st;
+  }
   for (int b = 0; b < s->S && st == QEC_OK; ++b) {
     const bool timed = b == tb, fused = fused_step(s, b);
     if (timed && (st = record(s, 0))) return st;
@@ -306,7 +352,7 @@ void drop_graph(qec_sim* s) {
 
 void free_all(qec_sim* s) {
   drop_graph(s);
-  void* ptrs[] = {s->psi, s->psi0, s->d_kraus, s->d_u, s->d_A, s->d_N, s->d_m, s->d_partials, s->d_ctl,
+  void* ptrs[] = {s->psi, s->psi0, s->psi2, s->d_kraus, s->d_u, s->d_A, s->d_N, s->d_m, s->d_partials, s->d_ctl,
                   s->d_hist_part, s->d_hist, s->d_syn, s->d_bits, s->d_log, s->d_events,
                   s->d_ops[0], s->d_ops[1], s->d_blocks[0], s->d_blocks[1], s->d_mats[0], s->d_mats[1]};
   for (void* p : ptrs) if (p) cudaFree(p);
@@ -354,6 +400,8 @@ qec_status create_impl(const qec_params* params, void* stream, qec_sim** out) {
   const size_t state_bytes = ((size_t)1 << s->D) * s->amp;
   const int nblk = s->nstab * kMaxRounds;   // room for any round count (qec_reconfigure)
   const int k1 = hist_k1(s->D);
+  s->spec = spec_applies(s);
+  if (s->spec && (st = dmalloc(&s->psi2, state_bytes))) return bail(st);
   if ((st = dmalloc(&s->psi, state_bytes)) || (st = dmalloc(&s->psi0, state_bytes)) ||
       (st = dmalloc(&s->d_kraus, (size_t)nblk * KRAUS_STRIDE * s->amp)) ||
       (st = dmalloc(&s->d_u, sizeof(double) * nblk)) || (st = dmalloc(&s->d_A, sizeof(double) * nblk)) ||
@@ -469,7 +517,7 @@ qec_status qec_get_state(qec_sim* s, void* host_buf, size_t bytes) {
   QEC_CUDA(cudaStreamSynchronize(s->work));
   Ctl c;
   QEC_CUDA(cudaMemcpy(&c, s->d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
-  const void* src = s->S > 0 ? s->psi : s->psi0;
+  const void* src = final_state(s);
   double* out = static_cast<double*>(host_buf);
   const double scale = 1.0 / std::sqrt(c.final_norm);
   if (is_f64(s->p.precision)) {
@@ -770,6 +818,26 @@ qec_status qec_debug_exact_probability(qec_sim* sim, int32_t force, uint64_t* fa
     QEC_CUDA(cudaMemcpy(&c, reinterpret_cast<char*>(sim->d_ctl) + offsetof(Ctl, prob_fallbacks), sizeof(c),
                         cudaMemcpyDeviceToHost));
     *fallbacks = c;
+  }
+  return QEC_OK;
+}
+
+qec_status qec_debug_speculation(qec_sim* sim, int32_t enable, uint64_t* misses) {
+  if (!sim || enable < -1 || enable > 1) return fail(QEC_EINVAL, "bad argument");
+  QEC_CUDA(cudaStreamSynchronize(sim->work));
+  if (enable >= 0) {
+    if (enable == 1 && !sim->psi2) return fail(QEC_EUNSUPPORTED, "no speculative pass for this simulator");
+    if ((enable == 1) != sim->spec) {
+      drop_graph(sim);
+      sim->spec = enable == 1;
+      sim->ran = false;   // the last trajectory's state may sit in the other buffer
+    }
+  }
+  if (misses) {
+    unsigned long long c = 0;
+    QEC_CUDA(cudaMemcpy(&c, reinterpret_cast<char*>(sim->d_ctl) + offsetof(Ctl, spec_misses), sizeof(c),
+                        cudaMemcpyDeviceToHost));
+    *misses = c;
   }
   return QEC_OK;
 }

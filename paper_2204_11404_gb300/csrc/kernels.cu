@@ -767,7 +767,7 @@ __global__ void __launch_bounds__(256, 2) k_fused_tc(FusedArgs f) {
   __shared__ int s_err;
   __shared__ double sred[64];
   __shared__ int s_last;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tid = threadIdx.x, warp = tid >> 5;
   {
     const int m = *f.ap.m;
     const double scale = 1.0 / sqrt(*f.ap.N);
@@ -1604,6 +1604,318 @@ __global__ void __launch_bounds__(256, 2) k_ozf(FusedArgs f) {
   prob_finish_bounded(f.pr, accA, accN, rN + rA, sred, &s_last, true);
 }
 
+// ---- speculative complex128 pass on the tensor cores ------------------------------------------------
+// Block b's outcome is drawn from the state that block b's own apply reads, so a pass that applies it
+// and decides it together must apply before it knows it.  The outcome usually repeats the same
+// stabilizer's outcome one round earlier (it changes only at a detection event, Sec. II.B), so the
+// pass applies K_g / sqrt(N) for that guess g at once, from the input register into the other buffer,
+// and sums on the same tiles, per thread, as FP32 intervals with directed rounding (oz::SqSum24):
+//   Nin^ = sum |psi|^2 from each input real's top 24 bits under its group's exponent,
+//   Y^   = sum |y|^2 of the FP64 outputs y = K_g psi / sqrt(N), top 24 bits under the tile's largest.
+// With N' = Nin^ / N: P(g) = Y^ / N', and P(1) N' = Y^ for g = 1, N' - Y^ for g = 0
+// (K_0^dagger K_0 + K_1^dagger K_1 = I).  The last CTA decides the outcome where |u N' - P(1) N'|
+// exceeds twice the summed bounds plus 1e-10 (N' + Y^), where the exact pass must decide the same
+// way; otherwise the exact pass runs on the input, which the pass left untouched.  If the outcome is
+// not g, the corrective launch (FIX) applies K_m from the same input over the speculative output.
+// Either way |output|^2 of the apply that stands is stored for the next block's scale (the state's
+// scale is free: every probability is a ratio of two sums over one state, and the readout removes
+// it).  Tiles are fixed per CTA (b, b + grid, ...), so the sums and outcomes repeat in every run.
+constexpr int kOzsSmem = 16 * (1 << kOzTileBits) + 2 * oz::kSlices * kOzSlab + 2 * oz::kSlices * 32 * 32 +
+                         4 * 128 + 4 * 32;
+
+// The guessed raw outcome of block a: the forced one, else the same stabilizer's raw outcome one round
+// earlier (the init round's, forced to offset, for the first noisy round).
+__device__ __forceinline__ int spec_guess(const PassArgs& a) {
+  if (a.forced >= 0) return a.forced;
+  if (a.spec_prev < 0 || !a.syn) return a.offset;
+  const unsigned long long t = a.ctl->traj - a.ctl->first;
+  return (int)(a.syn[t * (unsigned long long)a.syn_stride + a.spec_prev] & 1u) ^ a.offset;
+}
+
+// End of a speculative (FIX = false) or corrective (FIX = true) pass: block sums of (Nin^, its bound)
+// and (Y^, its bound) into 4 partials per CTA; the last CTA sums them in a fixed order, stores Y^ for
+// the next block, and (speculative pass) decides the outcome as above.
+template <bool FIX>
+__device__ void spec_finish(const FusedArgs& f, int g, double nI, double rI, double nO, double rO, double* sred,
+                            int* s_last) {
+  const PassArgs& a = f.ap;
+  block_sum2(nI, rI, sred);
+  block_sum2(nO, rO, sred);
+  if (threadIdx.x == 0) {
+    double* p = a.partials + 4 * blockIdx.x;
+    p[0] = nI;
+    p[1] = rI;
+    p[2] = nO;
+    p[3] = rO;
+    __threadfence();
+    const unsigned int t = atomicAdd(&a.ctl->ticket, 1u);
+    *s_last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!*s_last) return;
+  __threadfence();
+  double sI = 0.0, sRI = 0.0, sO = 0.0, sRO = 0.0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
+    sI += __ldcg(&a.partials[4 * i]);
+    sRI += __ldcg(&a.partials[4 * i + 1]);
+    sO += __ldcg(&a.partials[4 * i + 2]);
+    sRO += __ldcg(&a.partials[4 * i + 3]);
+  }
+  block_sum2(sI, sRI, sred);
+  block_sum2(sO, sRO, sred);
+  if (threadIdx.x == 0) {
+    if (f.n_next) *f.n_next = sO;
+    if (FIX) {
+      atomicAdd(&a.ctl->spec_misses, 1ull);
+    } else {
+      const double inv = f.spec_unit ? 1.0 : 1.0 / *a.N;   // the inputs' scale squared
+      const double Np = sI * inv, rNp = sRI * inv;
+      const double A1 = g ? sO : Np - sO;                  // P(1) N'
+      bool decided = true;
+      int m = a.forced;
+      if (m < 0) {
+        const double u = *a.u;
+        decided = !a.ctl->prob_force_exact && fabs(u * Np - A1) > 2.0 * (rNp + sRO) + 1e-10 * (Np + sO);
+        m = u * Np < A1 ? 1 : 0;
+      }
+      a.ctl->prob_uncertain = decided ? 0u : 1u;
+      if (decided) {
+        *a.A = A1;
+        *a.m = m;
+        if (a.syn) {
+          const unsigned long long t = a.ctl->traj - a.ctl->first;
+          a.syn[t * (unsigned long long)a.syn_stride + a.syn_idx] = (uint8_t)(m ^ a.offset);
+        }
+      }
+    }
+    a.ctl->ticket = 0u;
+  }
+}
+
+template <bool FIX>
+__global__ void __launch_bounds__(256, 2) k_ozs(FusedArgs f) {
+  const int g = spec_guess(f.ap);
+  const int m = FIX ? *f.ap.m : g;   // the corrective pass applies the decided outcome ...
+  if (FIX && m == g) return;         // ... only where the guess was wrong
+  constexpr int TS = 1 << kOzTileBits;
+  extern __shared__ __align__(128) unsigned char osm[];
+  const uint32_t lmask = (1u << f.lb) - 1u;
+  double2* tile = reinterpret_cast<double2*>(osm);
+  uint16_t* A = reinterpret_cast<uint16_t*>(tile + TS);            // 7 slices x 128 rows x 32
+  double2* outb = reinterpret_cast<double2*>(A + kOzfOut);         // updated tile (slots as the tile)
+  uint16_t* BA = A + oz::kSlices * kOzSlab;                        // K_m / sqrt(N), 7 slices
+  int* rowE = reinterpret_cast<int*>(BA + oz::kSlices * 32 * 32);  // [128]
+  int* colE = rowE + 128;                                          // [32]
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_base;
+  __shared__ int s_err;
+  __shared__ double sred[64];
+  __shared__ int s_last;
+  __shared__ uint32_t s_emax[8];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  int qa[4], qas[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    qa[j] = f.qa[j];
+    qas[j] = f.qa_s[j];
+  }
+  // tile slots, tile-to-register map and thread roles as in k_ozf
+  auto slot = [](uint32_t e) { return e ^ (((e >> 3) ^ (e >> 6) ^ (e >> 9)) & 7u); };
+  auto t2g = [&](uint32_t e) {
+    const uint32_t h = e >> f.lb;
+    uint32_t o = 0;
+    for (int j = 0; j < f.nt - f.lb; ++j) o |= ((h >> j) & 1u) << f.hbits[j];
+    return o | (e & lmask);
+  };
+  const int r = tid & 127, hf = tid >> 7;                     // recombination: group r, half hf
+  const int sr = 16 * warp + (tid & 15), sh = (tid >> 4) & 1;   // slicing: row sr, half sh
+  uint32_t sa[3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) sa[j] = slot(1u << qa[j]);
+  const uint32_t rda0 = slot(local_base<4>((uint32_t)sr, qas)) ^ (sh ? slot(1u << qa[3]) : 0u);
+  const uint32_t gb = local_base<4>((uint32_t)r, qas) | (hf ? (1u << qa[3]) : 0u);
+  const uint32_t sd0 = slot(gb);
+  auto gen = [](uint32_t b0, const uint32_t (&gg)[3], int l) {
+    return b0 ^ ((l & 1) ? gg[0] : 0u) ^ ((l & 2) ? gg[1] : 0u) ^ ((l & 4) ? gg[2] : 0u);
+  };
+  const uint32_t cb = t2g((uint32_t)tid), cs = slot((uint32_t)tid);
+  uint32_t cg[3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) cg[j] = t2g(256u << j);
+  auto coff = [&](int i) { return cb ^ ((i & 1) ? cg[0] : 0u) ^ ((i & 2) ? cg[1] : 0u) ^ ((i & 4) ? cg[2] : 0u); };
+  auto cdst = [&](int i) { return cs ^ slot(256u * (uint32_t)i); };
+  const double2* src = reinterpret_cast<const double2*>(f.ap.src);
+  double2* dst = reinterpret_cast<double2*>(f.ap.dst);
+  const uint32_t ntile = 1u << f.nout;
+  const int obit = lane < f.nout ? f.obits[lane] : 0;
+  auto tile_base = [&](uint32_t tix) { return tile_base_warp(tix, f.nout, obit); };
+  auto load_tile = [&](uint32_t tb) {
+#pragma unroll
+    for (int i = 0; i < TS / 256; ++i) cp_async16(tile + cdst(i), src + (tb | coff(i)));
+    cp_async_commit();
+  };
+  uint32_t tix = blockIdx.x;
+  uint32_t tb = tix < ntile ? tile_base(tix) : 0u;
+  if (tix < ntile) load_tile(tb);
+  // B, overlapping the first copy: threads 0..127 the real embedding of K_m / sqrt(N) (7 slices,
+  // each row under its own exponent); thread = (row bn, reals 8 bkc .. 8 bkc + 7)
+  const int bn = (tid & 127) >> 2, bkc = tid & 3;
+  double bv[8];
+  int bE = 0;
+  if (tid < 128) {
+    const int br = bn >> 1;
+    const double scale = f.spec_unit ? 1.0 : 1.0 / sqrt(*f.ap.N);
+    const double2* Kg = reinterpret_cast<const double2*>(f.ap.kraus) + (m ? 256 : 0);
+    const bool w2 = f.ap.w == 2;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int l = 4 * bkc + j;
+      const double2 kv = !w2 ? Kg[br * 16 + l] : ((br >> 2) == (l >> 2) ? Kg[(br & 3) * 16 + (l & 3)] : make_double2(0.0, 0.0));
+      const double re = kv.x * scale, im = kv.y * scale;
+      bv[2 * j] = (bn & 1) ? im : re;
+      bv[2 * j + 1] = (bn & 1) ? re : -im;
+      bE = max(bE, max(oz::bexp(bv[2 * j]), oz::bexp(bv[2 * j + 1])));
+    }
+    bE = max(bE, __shfl_xor_sync(0xffffffffu, bE, 1));
+    bE = max(bE, __shfl_xor_sync(0xffffffffu, bE, 2));
+  }
+  if (tid == 0) {
+    s_err = 0;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(smem_u32(&tmem_base)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  __syncthreads();
+  if (tid < 128) {
+    uint64_t Xb[8];
+    if (bkc == 0) colE[bn] = bE;
+    put_slices8<oz::kSlices>(BA, 32 * 32, bn, 8 * bkc, bv, bE, Xb);
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  tc_sync();
+  const uint32_t tmem = tmem_base;
+  const uint32_t mb = smem_u32(&mbar);
+  const uint32_t tlane = (uint32_t)(32 * (warp & 3)) << 16;
+  int cmin = 4095, cmax = 0;
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    const int e = colE[16 * hf + j];
+    if (e) cmin = min(cmin, e);
+    cmax = max(cmax, e);
+  }
+  uint32_t phase = 0;
+  oz::SqSum24 sin_, sout;
+  while (tix < ntile) {
+    cp_async_wait<0>();
+    __syncthreads();
+    const uint32_t tnext = tix + gridDim.x;
+    // ---- digits of this thread's half row under the row's exponent; Nin^ from their top 24 bits
+    {
+      double x[16];
+      int E = 0;
+#pragma unroll
+      for (int l = 0; l < 8; ++l) {
+        const double2 v = tile[gen(rda0, sa, l)];
+        x[2 * l] = v.x;
+        x[2 * l + 1] = v.y;
+        E = max(E, max(oz::bexp(v.x), oz::bexp(v.y)));
+      }
+      E = max(E, __shfl_xor_sync(0xffffffffu, E, 16));
+      if (sh == 0) rowE[sr] = E;
+      uint64_t X0[8], X1[8];
+      put_slices8(A, kOzSlab, sr, 16 * sh, x, E, X0);
+      put_slices8(A, kOzSlab, sr, 16 * sh + 8, x + 8, E, X1);
+      uint64_t nacc = 0;   // |x| = 2^(E - 1078) X = 2^(E - 1046) (X / 2^32): top 24 bits X >> 32
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const uint64_t a0 = X0[j] >> 32, a1 = X1[j] >> 32;
+        nacc += a0 * a0 + a1 * a1;
+      }
+      sin_.add(nacc, E);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    tc_sync();
+    const uint32_t tbn = tnext < ntile ? tile_base(tnext) : 0u;
+    if (tnext < ntile) load_tile(tbn);
+    if (tid == 0) {   // the 14 MMAs of k_oz<OZ_APPLY>
+      const uint64_t da = umma_desc(smem_u32(A), 128, 512), db = umma_desc(smem_u32(BA), 128, 512);
+#pragma unroll
+      for (int p = 0; p < oz::kSlices; ++p)
+#pragma unroll
+        for (int ks = 0; ks < 2; ++ks)
+          umma_f16(tmem + 32u * p, da + ((2u * kOzSlab * p + 256u * ks) >> 4), db + ((256u * ks) >> 4),
+                   idesc_f16(32u * (oz::kSlices - p)), (p > 0 || ks > 0) ? 1u : 0u);
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mb) : "memory");
+    }
+    if (!mbar_wait(mb, phase & 1)) s_err = 1;
+    ++phase;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (s_err) break;
+    {
+      const int E = rowE[r];
+      const bool in_range = E == 0 || (E + cmin >= 1076 && E + cmax <= 2980);
+      uint32_t emax = 0;
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        uint32_t R[oz::kSlices][8];
+#pragma unroll
+        for (int t = 0; t < oz::kSlices; ++t) tmem_ld8_nowait(tmem + tlane + 32u * t + 16u * hf + 8u * c, R[t]);
+        tmem_wait_ld();
+#pragma unroll
+        for (int t = 0; t < oz::kSlices; ++t) reg_fence8(R[t]);
+#pragma unroll
+        for (int j = 0; j < 8; j += 2) {
+          float d0[oz::kSlices], d1[oz::kSlices];
+#pragma unroll
+          for (int t = 0; t < oz::kSlices; ++t) {
+            d0[t] = __uint_as_float(R[t][j]);
+            d1[t] = __uint_as_float(R[t][j + 1]);
+          }
+          const int n = 16 * hf + 8 * c + j, l = 4 * c + j / 2;
+          const double y0 = in_range ? oz::assemble7_cvt_inrange(d0, E, colE[n]) : oz::assemble7_cvt(d0, E, colE[n]);
+          const double y1 = in_range ? oz::assemble7_cvt_inrange(d1, E, colE[n + 1]) : oz::assemble7_cvt(d1, E, colE[n + 1]);
+          outb[gen(sd0, sa, l)] = make_double2(y0, y1);
+          emax = max(emax, max((uint32_t)(oz::d2u(y0) >> 32) & 0x7FF00000u, (uint32_t)(oz::d2u(y1) >> 32) & 0x7FF00000u));
+        }
+      }
+      emax = __reduce_max_sync(0xffffffffu, emax);
+      if (lane == 0) s_emax[warp] = emax;
+    }
+    __syncthreads();   // the updated tile and its exponent are in shared memory
+    // ---- the updated tile to the register (whole 128-byte runs per quarter warp, as in k_ozf); Y^
+    // from the stored values' top 24 bits under the tile's largest exponent
+    uint32_t em = s_emax[0];
+#pragma unroll
+    for (int w = 1; w < 8; ++w) em = max(em, s_emax[w]);
+    const int Et = max((int)(em >> 20), 24);   // >= 24: zero and subnormal reals give 0
+    uint64_t yacc = 0;
+#pragma unroll
+    for (int i = 0; i < TS / 256; ++i) {
+      const double2 v = outb[cdst(i)];
+      dst[tb | coff(i)] = v;
+      const uint64_t a0 = oz::top24(oz::d2u(v.x), Et), a1 = oz::top24(oz::d2u(v.y), Et);
+      yacc += a0 * a0 + a1 * a1;
+    }
+    sout.add(yacc, Et);
+    // no barrier here: the loop-top barrier keeps outb (A slices 3..6), rowE and s_emax until every
+    // thread is past this tile; the next tile's MMAs follow its slicing barrier
+    tb = tbn;
+    tix = tnext;
+  }
+  cp_async_wait<0>();   // a copy still in flight after an early exit
+  tc_sync();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem));
+  if (s_err && tid == 0) atomicOr(&f.ap.ctl->status, 1u);
+  double nI, rI, nO, rO;
+  sin_.finish(nI, rI);
+  sout.finish(nO, rO);
+  spec_finish<FIX>(f, g, nI, rI, nO, rO, sred, &s_last);
+}
+
 // ---- final Z readout (Sec. III.B): sequential per-qubit sampling -------------------------
 // Qubit j gets outcome [u_j < P(q_j = 1 | outcomes of qubits < j)].  The conditional
 // marginals of the low k1 qubits come from one histogram pass over the register; the
@@ -2024,6 +2336,42 @@ cudaError_t launch_prob_oz_check(const PassArgs& pr, int num_sms, cudaStream_t s
   return launch_oz(OZ_PROB, true, a, num_sms, s);
 }
 
+// The speculative pass's tile and grid: block ap's qubits (a weight-2 block with two spectators, as K
+// (x) I) plus low bits in a 2^11-amplitude tile, two CTAs per SM, 4 partial sums per CTA.
+static bool spec_args(const PassArgs& ap, double* n_next, bool unit_in, int num_sms, FusedArgs& f) {
+  f.ap = ap;
+  f.pr = ap;
+  f.skip_unless_uncertain = 0;
+  block_tile(ap, ap, 3, kOzTileBits, f);
+  if ((ap.w != 2 && ap.w != 4) || f.nt != kOzTileBits || ap.src == ap.dst) return false;
+  oz_block_bits(ap.w, f.qa, f.qa_s, f.nt);
+  f.n_next = n_next;
+  f.spec_unit = unit_in ? 1 : 0;
+  int64_t g = 2ll * num_sms;
+  if (g > (1ll << f.nout)) g = 1ll << f.nout;
+  if (g > MAX_PASS_GRID / 2) g = MAX_PASS_GRID / 2;
+  f.grid = (int)g;
+  return true;
+}
+
+cudaError_t launch_spec_oz(const PassArgs& ap, double* n_next, bool unit_in, int num_sms, cudaStream_t s) {
+  FusedArgs f;
+  if (!spec_args(ap, n_next, unit_in, num_sms, f)) return cudaErrorInvalidValue;
+  k_ozs<false><<<f.grid, 256, kOzsSmem, s>>>(f);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_spec_oz_fix(const PassArgs& ap, double* n_next, bool unit_in, int num_sms, cudaStream_t s) {
+  FusedArgs f;
+  if (!spec_args(ap, n_next, unit_in, num_sms, f)) return cudaErrorInvalidValue;
+  PassArgs a = ap;
+  a.store_n = 0;   // *N keeps the scale both applies of this block use
+  cudaError_t e = launch_oz(OZ_PROB, true, a, num_sms, s);
+  if (e != cudaSuccess) return e;
+  k_ozs<true><<<f.grid, 256, kOzsSmem, s>>>(f);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_wait_selftest(unsigned int* status, long limit, cudaStream_t s) {
   k_wait_selftest<<<1, 32, 0, s>>>(status, limit);
   return cudaGetLastError();
@@ -2054,6 +2402,10 @@ cudaError_t setup_kernels(int precision, int D) {
     oz_attrs((const void*)k_oz<OZ_PROB_BOUND>);
     if (e == cudaSuccess) e = cudaFuncSetAttribute((const void*)k_ozf, cudaFuncAttributeMaxDynamicSharedMemorySize, kOzfSmem);
     if (e == cudaSuccess) e = cudaFuncSetAttribute((const void*)k_ozf, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    for (const void* fn : {(const void*)k_ozs<false>, (const void*)k_ozs<true>}) {
+      if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kOzsSmem);
+      if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    }
     return e;
   }
   cudaError_t e = cudaFuncSetAttribute(k_sample<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);

@@ -24,6 +24,7 @@ struct Ctl {
   unsigned long long prob_fallbacks;    // exact probability passes run after an undecided one
   unsigned int tile_next;       // tile counter of the tensor-core complex128 apply pass (returned to 0)
   unsigned int tile_done;       // CTAs of such a pass that have finished (returned to 0)
+  unsigned long long spec_misses;       // corrective applies after a speculative pass guessed wrong
 };
 
 constexpr int KRAUS_STRIDE = 768;
@@ -66,6 +67,8 @@ struct PassArgs {
   int offset;             // syndrome = raw ^ offset
   int store_n = 1;        // 0: the pass leaves *N as it is (the exact pass after a fused tensor-core
                           // complex128 pass, whose norm estimate renormalises the state)
+  int spec_prev = -1;     // speculative pass: syndrome index of the same stabilizer one round
+                          // earlier, whose raw outcome is the guess; -1: the init round's (offset)
 };
 
 // Fused pass: apply block s (ap) and accumulate the probability of block s+1 (pr) on tiles
@@ -86,6 +89,8 @@ struct FusedArgs {
                           // spectators) sorted ascending, for the group base addresses
   int skip_unless_uncertain;   // exact tensor-core probability pass: run only if ctl->prob_uncertain
   int grid;
+  double* n_next = nullptr;    // speculative pass: receives |output|^2, the next block's *N (or null)
+  int spec_unit = 0;           // speculative pass: the input's scale is 1 (block 0, the init state)
 };
 
 struct ReadArgs {
@@ -124,6 +129,13 @@ bool fused_oz_applies(const PassArgs& ap, const PassArgs& pr);
 cudaError_t launch_fused_oz(const PassArgs& ap, const PassArgs& pr, int num_sms, cudaStream_t s);
 // The exact probability launch of block pr after a fused pass (returns at once unless needed).
 cudaError_t launch_prob_oz_check(const PassArgs& pr, int num_sms, cudaStream_t s);
+// Speculative tensor-core complex128 pass of block ap (apply_oz_applies; ap.src and ap.dst distinct
+// buffers): applies K_g / sqrt(*ap.N) (scale 1 with unit_in) for the guessed outcome g, decides the
+// outcome where its bound allows, and stores |output|^2 in *n_next (n_next may be null).
+cudaError_t launch_spec_oz(const PassArgs& ap, double* n_next, bool unit_in, int num_sms, cudaStream_t s);
+// Its completion: the exact probability launch (returns at once unless the bound left the outcome
+// open) and the corrective apply (returns at once unless the outcome is not the guess).
+cudaError_t launch_spec_oz_fix(const PassArgs& ap, double* n_next, bool unit_in, int num_sms, cudaStream_t s);
 int pass_grid(int D, int w, int num_sms);
 // One wave of resident CTAs for the probability (prob = true) or apply pass kernel.
 int pass_grid_for(int precision, bool prob, int D, int w, int num_sms);

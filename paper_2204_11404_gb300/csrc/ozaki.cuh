@@ -258,32 +258,48 @@ inline float u2f_ru(uint32_t v) { return f_up((double)v); }
 // same units are 16 s_N (sqrt(nacc) + 4) and 2^11 s_A (sqrt(aacc) + 512) with s_N = 2^(2 Et - 2028),
 // s_A = 2^(2 (Et + EP) - 4072).  Scales below the FP32 normal range (tiles whose squares are below
 // about 2^-138) count as 0 in the lower sums and as 2^-126 in the upper ones.
-struct FusedSums {
-  float nlo = 0.f, nhi = 0.f, alo = 0.f, ahi = 0.f, en = 0.f, ea = 0.f;
-  OZ_HD void add_tile(uint64_t nacc, uint64_t aacc, int Et, int EP) {
-    const int kN = 2 * Et - 2028, kA = 2 * (Et + EP) - 4072;
+// SqSum24 is one sum of the N kind (the speculative pass keeps two: its inputs under their group's
+// exponent and its outputs under the tile's); FusedSums adds the A kind beside it.
+struct SqSum24 {
+  float lo = 0.f, hi = 0.f, e = 0.f;
+  OZ_HD void add(uint64_t nacc, int Et) {
+    const int kN = 2 * Et - 2028;
     const float sN = kN >= -126 ? u2f(uint32_t(kN + 127) << 23) : 0.f;
     const float sNh = kN >= -126 ? sN : 0x1p-126f;
+    const uint32_t nh = (uint32_t)(nacc >> 32), nl = (uint32_t)nacc;   // nh < 2^20: exact in FP32
+    const float n_lo = f_fma_rd((float)nh, 4294967296.f, u2f_rd(nl)), n_hi = f_fma_ru((float)nh, 4294967296.f, u2f_ru(nl));
+    lo = f_add_rd(lo, f_mul_rd(n_lo, sN));
+    hi = f_add_ru(hi, f_mul_ru(n_hi, sNh));
+    e = f_add_ru(e, f_mul_ru(f_add_ru(f_sqrt_ru(n_hi), 4.f), f_mul_ru(16.f, sNh)));
+  }
+  // Midpoint and radius in real units: the sum lies in [n - rn, n + rn].
+  OZ_HD void finish(double& n, double& rn) const {
+    const double u = 0x1p-64;
+    n = 0.5 * ((double)lo + (double)hi) * u;
+    rn = (0.5 * ((double)hi - (double)lo) + (double)e) * u;
+  }
+};
+
+struct FusedSums {
+  SqSum24 n;
+  float alo = 0.f, ahi = 0.f, ea = 0.f;
+  OZ_HD void add_tile(uint64_t nacc, uint64_t aacc, int Et, int EP) {
+    const int kA = 2 * (Et + EP) - 4072;
     const float sA = EP && kA >= -126 ? u2f(uint32_t(kA + 127) << 23) : 0.f;
     const float sAh = EP ? (kA >= -126 ? sA : 0x1p-126f) : 0.f;
     const float two32 = 4294967296.f;
-    const uint32_t nh = (uint32_t)(nacc >> 32), nl = (uint32_t)nacc;   // nh < 2^20: exact in FP32
-    const float n_lo = f_fma_rd((float)nh, two32, u2f_rd(nl)), n_hi = f_fma_ru((float)nh, two32, u2f_ru(nl));
     const uint32_t ah = (uint32_t)(aacc >> 32), al = (uint32_t)aacc;
     const float a_lo = f_fma_rd(u2f_rd(ah), two32, u2f_rd(al)), a_hi = f_fma_ru(u2f_ru(ah), two32, u2f_ru(al));
-    nlo = f_add_rd(nlo, f_mul_rd(n_lo, sN));
-    nhi = f_add_ru(nhi, f_mul_ru(n_hi, sNh));
+    n.add(nacc, Et);
     alo = f_add_rd(alo, f_mul_rd(a_lo, sA));
     ahi = f_add_ru(ahi, f_mul_ru(a_hi, sAh));
-    en = f_add_ru(en, f_mul_ru(f_add_ru(f_sqrt_ru(n_hi), 4.f), f_mul_ru(16.f, sNh)));
     ea = f_add_ru(ea, f_mul_ru(f_add_ru(f_sqrt_ru(a_hi), 512.f), f_mul_ru(2048.f, sAh)));
   }
   // Midpoints and radii in real units: N in [n - rn, n + rn], A in [a - ra, a + ra].
-  OZ_HD void finish(double& n, double& rn, double& a, double& ra) const {
+  OZ_HD void finish(double& nn, double& rn, double& a, double& ra) const {
     const double u = 0x1p-64;
-    n = 0.5 * ((double)nlo + (double)nhi) * u;
+    n.finish(nn, rn);
     a = 0.5 * ((double)alo + (double)ahi) * u;
-    rn = (0.5 * ((double)nhi - (double)nlo) + (double)en) * u;
     ra = (0.5 * ((double)ahi - (double)alo) + (double)ea) * u;
   }
 };

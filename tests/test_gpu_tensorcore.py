@@ -102,9 +102,9 @@ def test_bounded_probability_pass_decides_like_the_exact_pass():
 
 
 def test_emulated_fp64_form_is_bit_reproducible():
-    """The apply pass draws its tiles from a device counter that its last CTA resets: a rerun of
-    the same trajectory, in the same simulator and in a new one, must give the same bits and the
-    same amplitudes bit for bit (a tile skipped or done twice would change the state)."""
+    """A rerun of the same trajectory, in the same simulator and in a new one, must give the same
+    bits and the same amplitudes bit for bit: the passes' sums are reduced in a fixed order, and a
+    tile skipped or done twice, or a mix-up of the two working states, would change the state."""
     pt = W.D5_CR["points"][7]
     with Simulator(5, 2, "cr", "c128tc", **pt) as a:
         r1 = a.run(91, 4, 1)
@@ -149,3 +149,55 @@ def test_fused_pass_on_repetition_code():
         for x, y in zip(ra, rb):
             assert (x == y).all()
         assert np.abs(a.state() - b.state()).max() < 1e-13
+
+
+def _detections(syn):
+    """Outcome changes of each stabilizer from one round to the next (the init round's row is 0)."""
+    return int(np.sum(np.diff(syn.astype(np.int8), axis=1) != 0))
+
+
+def test_speculative_pass_matches_oracle_with_corrections():
+    """The speculative pass guesses each outcome from the same stabilizer's previous outcome; a
+    wrong guess is re-applied from the untouched input.  On the stress noise (many detection events)
+    the trajectory must still match the FP64 oracle: outcomes identical, amplitudes within 1e-12;
+    and the corrective applies run exactly once per outcome change."""
+    from paper_2204_11404_gb300 import capi
+    pt = dict(W.STRESS)
+    o = run_trajectory(5, 2, "cr", "reduced", pt, seed=42, traj=3, want_state=True)
+    with Simulator(5, 2, "cr", "c128tc", **pt) as sim:
+        m0 = capi.qec_debug_speculation(sim.h, 1)
+        syn, bits, log = sim.run(42, 3, 1)
+        misses = capi.qec_debug_speculation(sim.h, -1) - m0
+        assert compare_trajectory(syn[0], bits[0], o, TAU["c128tc"]) == "exact"
+        assert np.abs(sim.state() - o["state"][: 1 << 25]).max() < AMP_TOL["c128tc"]
+    assert misses == _detections(syn) and misses > 0
+
+
+def test_speculative_pass_agrees_with_fused_pass():
+    """The same trajectories with the speculative passes and with the fused apply + bounded
+    next-probability passes: identical outcomes, states within a few FP64 roundings, and one
+    corrective apply per outcome change."""
+    from paper_2204_11404_gb300 import capi
+    pts = W.D5_CR["points"]
+    for i in (1, 8):
+        with Simulator(5, 3, "cr", "c128tc", **pts[i]) as a:
+            m0 = capi.qec_debug_speculation(a.h, 1)
+            ra = a.run(5000 + i, 0, 2)
+            sa = a.state()
+            m1 = capi.qec_debug_speculation(a.h, 0)
+            rb = a.run(5000 + i, 0, 2)
+            sb = a.state()
+            m2 = capi.qec_debug_speculation(a.h, 1)
+        for x, y in zip(ra, rb):
+            assert (x == y).all()
+        assert np.abs(sa - sb).max() < 1e-13
+        assert m1 - m0 == _detections(ra[0])
+        assert m2 == m1                       # the fused passes never correct
+
+
+def test_speculation_hook_rejects_forms_without_it():
+    from paper_2204_11404_gb300 import capi
+    with Simulator(3, 1, "cr", "c128tc", **W.STRESS) as a:   # 9-qubit register: below the tile
+        with pytest.raises(capi.QecError):
+            capi.qec_debug_speculation(a.h, 1)
+        assert capi.qec_debug_speculation(a.h, 0) == 0

@@ -270,7 +270,7 @@ def native_arm(args, rank, world, local):
     stream = bstream
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     fb0 = [capi.qec_debug_exact_probability(s.h, -1) for s in sims] if args.precision == "c128tc" else None
-    sm0 = [capi.qec_debug_speculation(s.h, -1) for s in sims] if args.precision == "c128tc" else None
+    sm0 = [capi.qec_debug_speculation(s.h, -1) for s in sims] if args.precision.startswith("c128") else None
     with ClockSampler(local) as clk:
         torch.cuda.synchronize()
         e0.record(stream)
@@ -312,14 +312,15 @@ def native_arm(args, rank, world, local):
 
     # roofline of the dominant kernel: the pass that applies a weight-4 block (psi <- K_m psi / sqrt(N));
     # in the complex64 forms it also computes the next block's probability (fused: one read + one
-    # write of the register per stabilizer); in the tensor-core complex128 form it applies the guessed
-    # outcome's operator and sums |in|^2 and |out|^2 for the decision (one read + one write)
+    # write of the register per stabilizer); in the complex128 forms it applies the guessed outcome's
+    # operator and sums |in|^2 and |out|^2 for the decision (one read + one write)
     ms_prob = float(np.mean([k[0] for k in kt]))
     ms_apply = float(np.mean([k[1] for k in kt]))
     amps = 1 << 25
-    flops_apply = amps * 16 * 8            # 16x16 complex mat-vec per 16 amplitudes: 16 cmacs/amp
+    # 16x16 complex mat-vec per 16 amplitudes: 16 cmacs/amp; the FP64 speculative pass adds |in|^2 and
+    # |out|^2 (2 FMA each per amplitude)
+    flops_apply = amps * (16 * 8 + (8 if args.precision == "c128" else 0))
     bytes_apply = amps * (32 if args.precision in ("c128", "c128tc") else 16)
-    flops_prob = amps * (16 * 8 * 136 // 256 + 4)
     if args.precision == "c128":
         roof = {"bound": "alu", "achieved": flops_apply / (ms_apply * 1e-3) / 1e12, "peak": FP64_PEAK_TFLOPS,
                 "unit": "TFLOP/s"}
@@ -343,7 +344,8 @@ def native_arm(args, rank, world, local):
             "block": blk, "ms": ms22, "achieved": bytes_apply / (ms22 * 1e-3) / 1e9,
             "frac": bytes_apply / (ms22 * 1e-3) / 1e9 / roof["peak"], "unit": "GB/s"}
     roof["traffic"] = traffic_record(args.precision)
-    roof["kernel"] = {"c128": "k_apply<double,4> (weight-4 block, 2^25 amplitudes)",
+    roof["kernel"] = {"c128": "k_apply_spec<4,false> (FP64: speculative apply of a weight-4 block, the outcome "
+                              "guessed from the previous round, + FP64 |in|^2 and |out|^2 sums, 2^25 amplitudes)",
                       "c64": "k_fused<float,4,4> (apply weight-4 block + next block's probability, 2^25 amplitudes)",
                       "c64tc": "k_fused_tc (tcgen05 3xTF32: apply weight-4 block + next probability, 2^25 amplitudes)",
                       "c128tc": "k_ozs<false> (tcgen05: speculative apply of a weight-4 block, the outcome guessed "
@@ -355,15 +357,13 @@ def native_arm(args, rank, world, local):
     roof["ms_apply"] = ms_apply
     roof["ms_prob"] = ms_prob
     roof["apply_hbm_gbs"] = bytes_apply / (ms_apply * 1e-3) / 1e9
-    if args.precision == "c128":
-        roof["prob_fp64_tflops"] = flops_prob / (ms_prob * 1e-3) / 1e12
     roof["timed_blocks"] = len(kt)
 
     # launches per trajectory: instantiate; the complex64 forms: the first block's probability pass,
-    # per later block one fused pass, the last block's apply; the FP64 CUDA-core form: a probability
-    # and an apply pass per block; the tensor-core complex128 form: per block the speculative pass,
-    # the exact-probability launch and the corrective launch (these two return at once unless the
-    # bound left the outcome open / the guess was wrong); the readout (3)
+    # per later block one fused pass, the last block's apply; the complex128 forms: per block the
+    # speculative pass and the corrective launch (returns at once unless the guess was wrong), with
+    # the exact-probability launch between them on the tensor cores (returns at once unless the
+    # bound left the outcome open); the readout (3)
     S = nst * R
     launches_per_traj = {"c128": 1 + 2 * S + 3, "c128tc": 1 + 3 * S + 3,
                          "c64": 1 + 1 + (S - 1) + 1 + 3, "c64tc": 1 + 1 + (S - 1) + 1 + 3}[args.precision]

@@ -41,7 +41,9 @@ typedef enum { QEC_CODE_SURFACE = 0, QEC_CODE_REPETITION = 1 } qec_code;
  * with data corrections after each part (Sec. III.A, Fig. 4). */
 typedef enum { QEC_GATES_CNOT = 0, QEC_GATES_CR = 1 } qec_gateset;
 
-/* Amplitude storage / arithmetic.  C128: complex128 state, FP64 arithmetic.
+/* Amplitude storage / arithmetic.  C128: complex128 state, FP64 arithmetic, one
+ * speculative pass per block as described under C128_TC, with FP64 sums that
+ * decide every outcome directly.
  * C64: complex64 state, FP32 gate arithmetic, FP64 probability reductions.
  * C64_TC: complex64 state; the fused apply + next-probability pass of every
  * pair of blocks with a weight-4 block on the tensor cores (3xTF32 split,
@@ -173,8 +175,8 @@ qec_status qec_get_events(qec_sim* sim, int32_t* host_events, uint32_t max_event
  * block of the middle noisy round, in the most recent trajectory (CUDA events
  * recorded inside the trajectory's graph).  With the fused passes ms[0] is
  * empty for a block whose probability the previous pass computed; with the
- * speculative passes (QEC_C128_TC) ms[0] is empty and ms[1] is the block's
- * speculative pass, without the exact and corrective launches after it.  *block gets that block's index
+ * speculative passes (the complex128 forms) ms[0] is empty and ms[1] is the
+ * block's speculative pass, without the launches that complete it.  *block gets that block's index
  * (round-major, d^2-1 per round).  QEC_EINVAL if no trajectory ran yet or the
  * sim has no noisy round.
  */
@@ -376,16 +378,16 @@ qec_status qec_debug_ozaki_gemm(const double* A, const double* B, int32_t m, int
 qec_status qec_debug_exact_probability(qec_sim* sim, int32_t force, uint64_t* fallbacks);
 
 /*
- * Test hook for QEC_C128_TC (the paper has no counterpart: an evaluation order of Sec. II.B's
- * measurement and collapse).  enable = 1: the speculative passes (the default wherever every
- * block's tile fits the register); 0: per block pair, the pass fused with the next block's
- * 3-slice bounded probability; -1: unchanged.  Both give the same outcomes (except within the
- * exact pass's own rounding of a threshold) and states within a few FP64 roundings.  *misses (may
- * be NULL) receives the number of corrective applies run on this handle so far (outcomes that
- * differed from the guess).  Waits for the handle's queued work; switching rebuilds the
- * trajectory graph and requires a new run before qec_get_state.  QEC_EINVAL on a null handle or
- * enable outside -1..1; QEC_EUNSUPPORTED for enable = 1 where the speculative pass does not
- * apply (another precision, or a register below 11 qubits).
+ * Test hook for the complex128 forms (the paper has no counterpart: an evaluation order of
+ * Sec. II.B's measurement and collapse).  enable = 1: the speculative passes (the default);
+ * 0: the passes that compute each probability before its apply (QEC_C128: a probability pass and
+ * an apply pass per block; QEC_C128_TC: per block pair, the apply fused with the next block's
+ * 3-slice bounded probability); -1: unchanged.  Both give the same outcomes (except within the
+ * rounding of a threshold) and states within a few FP64 roundings.  *misses (may be NULL)
+ * receives the number of corrective applies run on this handle so far (outcomes that differed
+ * from the guess).  Waits for the handle's queued work; switching rebuilds the trajectory graph
+ * and requires a new run before qec_get_state.  QEC_EINVAL on a null handle or enable outside
+ * -1..1; QEC_EUNSUPPORTED for enable = 1 on a complex64 form.
  */
 qec_status qec_debug_speculation(qec_sim* sim, int32_t enable, uint64_t* misses);
 

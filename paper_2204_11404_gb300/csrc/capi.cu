@@ -191,9 +191,9 @@ PassArgs traj_pass(const qec_sim* s, int b) {
   return pass_args(s, s->prog, b, src, s->psi, false, s->d_syn, rnd * s->nstab + k);
 }
 
-// Speculative passes (QEC_C128_TC where every block's tile fits the register): block b reads the
-// state block b-1 wrote (block 0 the init state) and writes the other working buffer, so that a
-// wrong guess is corrected from its untouched input.
+// Speculative passes (the complex128 forms): block b reads the state block b-1 wrote (block 0 the
+// init state) and writes the other working buffer, so that a wrong guess is corrected from its
+// untouched input.
 void* spec_out(const qec_sim* s, int b) { return (b & 1) ? s->psi2 : s->psi; }
 
 PassArgs spec_pass(const qec_sim* s, int b) {
@@ -204,17 +204,7 @@ PassArgs spec_pass(const qec_sim* s, int b) {
   return a;
 }
 
-bool spec_applies(const qec_sim* s) {
-  if (s->p.precision != QEC_C128_TC) return false;
-  for (int k = 0; k < s->nstab; ++k) {
-    PassArgs a;
-    a.D = s->D;
-    a.w = s->prog.blocks[k].w;
-    for (int j = 0; j < 4; ++j) a.q[j] = s->prog.blocks[k].q[j] < 0 ? 0 : s->prog.blocks[k].q[j];
-    if (!apply_oz_applies(a)) return false;
-  }
-  return true;
-}
+bool spec_applies(const qec_sim* s) { return is_f64(s->p.precision); }
 
 // The state the last block wrote (the init state when there are no noisy rounds).
 const void* final_state(const qec_sim* s) {
@@ -225,7 +215,8 @@ const void* final_state(const qec_sim* s) {
 // Block b's apply pass is fused with block b+1's probability pass (one HBM read + write per
 // stabilizer) in the complex64 forms (k_fused, k_fused_tc) and in the tensor-core complex128 form
 // (k_ozf) wherever both blocks fit one tile; the FP64 CUDA-core form keeps them separate (both of its
-// passes are bound by the FP64 pipe, so one pass saves no time there).
+// passes are bound by the FP64 pipe, so one pass saves no time there).  The complex128 forms take
+// this path only with their speculative passes switched off (qec_debug_speculation).
 bool fused_step(const qec_sim* s, int b) {
   if (b < 0 || b + 1 >= s->S) return false;
   if (!is_f64(s->p.precision)) return true;
@@ -287,9 +278,9 @@ qec_status enqueue_trajectory(qec_sim* s) {
       const PassArgs a = spec_pass(s, b);
       double* n_next = b + 1 < s->S ? s->d_N + b + 1 : nullptr;
       if (timed && ((st = record(s, 0)) || (st = record(s, 1)))) return st;
-      QEC_CUDA(launch_spec_oz(a, n_next, b == 0, s->num_sms, s->work));
+      QEC_CUDA(launch_spec(s->p.precision, a, n_next, b == 0, s->num_sms, s->work));
       if (timed && (st = record(s, 2))) return st;
-      QEC_CUDA(launch_spec_oz_fix(a, n_next, b == 0, s->num_sms, s->work));
+      QEC_CUDA(launch_spec_fix(s->p.precision, a, n_next, b == 0, s->num_sms, s->work));
     }
     return st == QEC_OK ? enqueue_readout(s) : st;
   }

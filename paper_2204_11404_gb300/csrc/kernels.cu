@@ -397,6 +397,140 @@ __global__ void __launch_bounds__(256) k_apply(PassArgs a) {
   }
 }
 
+// The guessed raw outcome of block a: the forced one, else the same stabilizer's raw outcome one round
+// earlier (the init round's, forced to offset, for the first noisy round).
+__device__ __forceinline__ int spec_guess(const PassArgs& a) {
+  if (a.forced >= 0) return a.forced;
+  if (a.spec_prev < 0 || !a.syn) return a.offset;
+  const unsigned long long t = a.ctl->traj - a.ctl->first;
+  return (int)(a.syn[t * (unsigned long long)a.syn_stride + a.spec_prev] & 1u) ^ a.offset;
+}
+
+// End of a speculative (FIX = false) or corrective (FIX = true) pass (Sec. II.B, evaluated as the
+// tensor-core k_ozs below describes): block sums of (Nin^ = |input|^2, its bound) and (Y^ = |output|^2,
+// its bound) into 4 partials per CTA; the last CTA sums them in a fixed order and stores Y^ as the
+// next block's N.  The speculative pass then decides where |u N' - P(1) N'| exceeds twice the summed
+// bounds plus 1e-10 (N' + Y^), N' = Nin^ / N, P(1) N' = Y^ for g = 1 and N' - Y^ for g = 0, and
+// otherwise flags the exact pass.  exact: the sums are FP64 sums of the FP64 values themselves (the
+// CUDA-core pass) and decide every outcome directly, as the FP64 probability pass does.
+template <bool FIX>
+__device__ void spec_finish(const FusedArgs& f, int g, double nI, double rI, double nO, double rO, double* sred,
+                            int* s_last, bool exact = false) {
+  const PassArgs& a = f.ap;
+  block_sum2(nI, rI, sred);
+  block_sum2(nO, rO, sred);
+  if (threadIdx.x == 0) {
+    double* p = a.partials + 4 * blockIdx.x;
+    p[0] = nI;
+    p[1] = rI;
+    p[2] = nO;
+    p[3] = rO;
+    __threadfence();
+    const unsigned int t = atomicAdd(&a.ctl->ticket, 1u);
+    *s_last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!*s_last) return;
+  __threadfence();
+  double sI = 0.0, sRI = 0.0, sO = 0.0, sRO = 0.0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
+    sI += __ldcg(&a.partials[4 * i]);
+    sRI += __ldcg(&a.partials[4 * i + 1]);
+    sO += __ldcg(&a.partials[4 * i + 2]);
+    sRO += __ldcg(&a.partials[4 * i + 3]);
+  }
+  block_sum2(sI, sRI, sred);
+  block_sum2(sO, sRO, sred);
+  if (threadIdx.x == 0) {
+    if (f.n_next) *f.n_next = sO;
+    if (FIX) {
+      atomicAdd(&a.ctl->spec_misses, 1ull);
+    } else {
+      const double inv = f.spec_unit ? 1.0 : 1.0 / *a.N;   // the inputs' scale squared
+      const double Np = sI * inv, rNp = sRI * inv;
+      const double A1 = g ? sO : Np - sO;                  // P(1) N'
+      bool decided = true;
+      int m = a.forced;
+      if (m < 0) {
+        const double u = *a.u;
+        decided = exact || (!a.ctl->prob_force_exact && fabs(u * Np - A1) > 2.0 * (rNp + sRO) + 1e-10 * (Np + sO));
+        m = u * Np < A1 ? 1 : 0;
+      }
+      a.ctl->prob_uncertain = decided ? 0u : 1u;
+      if (decided) {
+        *a.A = A1;
+        *a.m = m;
+        if (a.syn) {
+          const unsigned long long t = a.ctl->traj - a.ctl->first;
+          a.syn[t * (unsigned long long)a.syn_stride + a.syn_idx] = (uint8_t)(m ^ a.offset);
+        }
+      }
+    }
+    a.ctl->ticket = 0u;
+  }
+}
+
+// ---- speculative FP64 pass (QEC_C128, and QEC_C128_TC where the tensor-core tile does not fit) ----
+// The order of evaluation of the tensor-core k_ozs (Sec. II.B; guess = the same stabilizer's outcome
+// one round earlier): y = K_g psi / sqrt(N) out of place, with Nin = sum |psi|^2 and Y = sum |y|^2
+// summed in FP64 per thread; the last CTA decides u N' < P(1) N' (N' = Nin / N; P(1) N' = Y for
+// g = 1, N' - Y for g = 0) and stores Y as the next block's N.  FIX: the corrective apply of the
+// decided K_m from the untouched input, only where m != g.  Grid-stride over groups as k_apply, so
+// every sum and outcome is the same in every run for a fixed grid.
+template <int W, bool FIX>
+__global__ void __launch_bounds__(256) k_apply_spec(FusedArgs f) {
+  const PassArgs& a = f.ap;
+  const int gs = spec_guess(a);
+  const int m = FIX ? *a.m : gs;
+  if (FIX && m == gs) return;
+  constexpr int C = 1 << W;
+  __shared__ double2 sK[C * C];
+  __shared__ double sred[64];
+  __shared__ int s_last;
+  const double scale = f.spec_unit ? 1.0 : 1.0 / sqrt(*a.N);
+  const double2* Kg = reinterpret_cast<const double2*>(a.kraus) + (m ? 256 : 0);
+  for (int i = threadIdx.x; i < C * C; i += blockDim.x) {
+    double2 kv = Kg[(i / C) * 16 + (i % C)];
+    kv.x *= scale;
+    kv.y *= scale;
+    sK[i] = kv;
+  }
+  __syncthreads();
+  int q[4];
+  load_q<W>(a, q);
+  uint32_t off[C];
+#pragma unroll
+  for (int l = 0; l < C; ++l) off[l] = member_off<W>(l, q);
+  const double2* src = reinterpret_cast<const double2*>(a.src);
+  double2* dst = reinterpret_cast<double2*>(a.dst);
+  const uint32_t G = 1u << (a.D - W);
+  double accI = 0.0, accO = 0.0;
+  for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
+    const uint32_t base = group_base<W>(g, q);
+    double2 v[C];
+#pragma unroll
+    for (int l = 0; l < C; ++l) {
+      v[l] = src[base + off[l]];
+      accI = fma(v[l].x, v[l].x, fma(v[l].y, v[l].y, accI));
+    }
+#pragma unroll
+    for (int r = 0; r < C; ++r) {
+      double sr = 0, si = 0;
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        const double2 k = lds_v2(&sK[r * C + c]);
+        sr = fma(k.x, v[c].x, sr);
+        sr = fma(-k.y, v[c].y, sr);
+        si = fma(k.x, v[c].y, si);
+        si = fma(k.y, v[c].x, si);
+      }
+      dst[base + off[r]] = make_double2(sr, si);
+      accO = fma(sr, sr, fma(si, si, accO));
+    }
+  }
+  spec_finish<FIX>(f, gs, accI, 0.0, accO, 0.0, sred, &s_last, true);
+}
+
 // ---- fused pass: apply block s, then probability of block s+1, per shared-memory tile ----
 template <int W>
 __device__ __forceinline__ uint32_t local_base(uint32_t g, const int (&q)[4]) {
@@ -1623,75 +1757,6 @@ __global__ void __launch_bounds__(256, 2) k_ozf(FusedArgs f) {
 constexpr int kOzsSmem = 16 * (1 << kOzTileBits) + 2 * oz::kSlices * kOzSlab + 2 * oz::kSlices * 32 * 32 +
                          4 * 128 + 4 * 32;
 
-// The guessed raw outcome of block a: the forced one, else the same stabilizer's raw outcome one round
-// earlier (the init round's, forced to offset, for the first noisy round).
-__device__ __forceinline__ int spec_guess(const PassArgs& a) {
-  if (a.forced >= 0) return a.forced;
-  if (a.spec_prev < 0 || !a.syn) return a.offset;
-  const unsigned long long t = a.ctl->traj - a.ctl->first;
-  return (int)(a.syn[t * (unsigned long long)a.syn_stride + a.spec_prev] & 1u) ^ a.offset;
-}
-
-// End of a speculative (FIX = false) or corrective (FIX = true) pass: block sums of (Nin^, its bound)
-// and (Y^, its bound) into 4 partials per CTA; the last CTA sums them in a fixed order, stores Y^ for
-// the next block, and (speculative pass) decides the outcome as above.
-template <bool FIX>
-__device__ void spec_finish(const FusedArgs& f, int g, double nI, double rI, double nO, double rO, double* sred,
-                            int* s_last) {
-  const PassArgs& a = f.ap;
-  block_sum2(nI, rI, sred);
-  block_sum2(nO, rO, sred);
-  if (threadIdx.x == 0) {
-    double* p = a.partials + 4 * blockIdx.x;
-    p[0] = nI;
-    p[1] = rI;
-    p[2] = nO;
-    p[3] = rO;
-    __threadfence();
-    const unsigned int t = atomicAdd(&a.ctl->ticket, 1u);
-    *s_last = (t == gridDim.x - 1);
-  }
-  __syncthreads();
-  if (!*s_last) return;
-  __threadfence();
-  double sI = 0.0, sRI = 0.0, sO = 0.0, sRO = 0.0;
-  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
-    sI += __ldcg(&a.partials[4 * i]);
-    sRI += __ldcg(&a.partials[4 * i + 1]);
-    sO += __ldcg(&a.partials[4 * i + 2]);
-    sRO += __ldcg(&a.partials[4 * i + 3]);
-  }
-  block_sum2(sI, sRI, sred);
-  block_sum2(sO, sRO, sred);
-  if (threadIdx.x == 0) {
-    if (f.n_next) *f.n_next = sO;
-    if (FIX) {
-      atomicAdd(&a.ctl->spec_misses, 1ull);
-    } else {
-      const double inv = f.spec_unit ? 1.0 : 1.0 / *a.N;   // the inputs' scale squared
-      const double Np = sI * inv, rNp = sRI * inv;
-      const double A1 = g ? sO : Np - sO;                  // P(1) N'
-      bool decided = true;
-      int m = a.forced;
-      if (m < 0) {
-        const double u = *a.u;
-        decided = !a.ctl->prob_force_exact && fabs(u * Np - A1) > 2.0 * (rNp + sRO) + 1e-10 * (Np + sO);
-        m = u * Np < A1 ? 1 : 0;
-      }
-      a.ctl->prob_uncertain = decided ? 0u : 1u;
-      if (decided) {
-        *a.A = A1;
-        *a.m = m;
-        if (a.syn) {
-          const unsigned long long t = a.ctl->traj - a.ctl->first;
-          a.syn[t * (unsigned long long)a.syn_stride + a.syn_idx] = (uint8_t)(m ^ a.offset);
-        }
-      }
-    }
-    a.ctl->ticket = 0u;
-  }
-}
-
 template <bool FIX>
 __global__ void __launch_bounds__(256, 2) k_ozs(FusedArgs f) {
   const int g = spec_guess(f.ap);
@@ -2354,21 +2419,52 @@ static bool spec_args(const PassArgs& ap, double* n_next, bool unit_in, int num_
   return true;
 }
 
-cudaError_t launch_spec_oz(const PassArgs& ap, double* n_next, bool unit_in, int num_sms, cudaStream_t s) {
+// The FP64 CUDA-core speculative pass: grid-stride over groups, one wave of resident CTAs, 4 partial
+// sums per CTA.
+static bool spec_fp64_args(const PassArgs& ap, double* n_next, bool unit_in, int num_sms, FusedArgs& f) {
+  if ((ap.w != 2 && ap.w != 4) || ap.src == ap.dst) return false;
+  f.ap = ap;
+  f.pr = ap;
+  f.n_next = n_next;
+  f.spec_unit = unit_in ? 1 : 0;
+  const void* fn = ap.w == 4 ? (const void*)k_apply_spec<4, false> : (const void*)k_apply_spec<2, false>;
+  f.grid = wave_grid(fn, 0, num_sms, ((1ll << (ap.D - ap.w)) + 255) / 256);
+  if (f.grid > MAX_PASS_GRID / 2) f.grid = MAX_PASS_GRID / 2;
+  return true;
+}
+
+static bool spec_on_tensor_cores(int precision, const PassArgs& ap) {
+  return precision == QEC_C128_TC && apply_oz_applies(ap);
+}
+
+cudaError_t launch_spec(int precision, const PassArgs& ap, double* n_next, bool unit_in, int num_sms, cudaStream_t s) {
   FusedArgs f;
-  if (!spec_args(ap, n_next, unit_in, num_sms, f)) return cudaErrorInvalidValue;
-  k_ozs<false><<<f.grid, 256, kOzsSmem, s>>>(f);
+  if (spec_on_tensor_cores(precision, ap)) {
+    if (!spec_args(ap, n_next, unit_in, num_sms, f)) return cudaErrorInvalidValue;
+    k_ozs<false><<<f.grid, 256, kOzsSmem, s>>>(f);
+    return cudaGetLastError();
+  }
+  if (!is_f64(precision) || !spec_fp64_args(ap, n_next, unit_in, num_sms, f)) return cudaErrorInvalidValue;
+  if (ap.w == 4) k_apply_spec<4, false><<<f.grid, 256, 0, s>>>(f);
+  else k_apply_spec<2, false><<<f.grid, 256, 0, s>>>(f);
   return cudaGetLastError();
 }
 
-cudaError_t launch_spec_oz_fix(const PassArgs& ap, double* n_next, bool unit_in, int num_sms, cudaStream_t s) {
+cudaError_t launch_spec_fix(int precision, const PassArgs& ap, double* n_next, bool unit_in, int num_sms,
+                            cudaStream_t s) {
   FusedArgs f;
-  if (!spec_args(ap, n_next, unit_in, num_sms, f)) return cudaErrorInvalidValue;
-  PassArgs a = ap;
-  a.store_n = 0;   // *N keeps the scale both applies of this block use
-  cudaError_t e = launch_oz(OZ_PROB, true, a, num_sms, s);
-  if (e != cudaSuccess) return e;
-  k_ozs<true><<<f.grid, 256, kOzsSmem, s>>>(f);
+  if (spec_on_tensor_cores(precision, ap)) {
+    if (!spec_args(ap, n_next, unit_in, num_sms, f)) return cudaErrorInvalidValue;
+    PassArgs a = ap;
+    a.store_n = 0;   // *N keeps the scale both applies of this block use
+    cudaError_t e = launch_oz(OZ_PROB, true, a, num_sms, s);
+    if (e != cudaSuccess) return e;
+    k_ozs<true><<<f.grid, 256, kOzsSmem, s>>>(f);
+    return cudaGetLastError();
+  }
+  if (!is_f64(precision) || !spec_fp64_args(ap, n_next, unit_in, num_sms, f)) return cudaErrorInvalidValue;
+  if (ap.w == 4) k_apply_spec<4, true><<<f.grid, 256, 0, s>>>(f);
+  else k_apply_spec<2, true><<<f.grid, 256, 0, s>>>(f);
   return cudaGetLastError();
 }
 

@@ -129,13 +129,16 @@ bool fused_oz_applies(const PassArgs& ap, const PassArgs& pr);
 cudaError_t launch_fused_oz(const PassArgs& ap, const PassArgs& pr, int num_sms, cudaStream_t s);
 // The exact probability launch of block pr after a fused pass (returns at once unless needed).
 cudaError_t launch_prob_oz_check(const PassArgs& pr, int num_sms, cudaStream_t s);
-// Speculative tensor-core complex128 pass of block ap (apply_oz_applies; ap.src and ap.dst distinct
-// buffers): applies K_g / sqrt(*ap.N) (scale 1 with unit_in) for the guessed outcome g, decides the
-// outcome where its bound allows, and stores |output|^2 in *n_next (n_next may be null).
-cudaError_t launch_spec_oz(const PassArgs& ap, double* n_next, bool unit_in, int num_sms, cudaStream_t s);
-// Its completion: the exact probability launch (returns at once unless the bound left the outcome
-// open) and the corrective apply (returns at once unless the outcome is not the guess).
-cudaError_t launch_spec_oz_fix(const PassArgs& ap, double* n_next, bool unit_in, int num_sms, cudaStream_t s);
+// Speculative complex128 pass of block ap (ap.src and ap.dst distinct buffers): applies K_g / sqrt(*ap.N)
+// (scale 1 with unit_in) for the guessed outcome g, decides the outcome (on the tensor cores where
+// its bound allows), and stores |output|^2 in *n_next (n_next may be null).  QEC_C128_TC blocks whose
+// tile fits (apply_oz_applies) run on the tensor cores, every other complex128 block on the FP64
+// CUDA cores; cudaErrorInvalidValue for complex64.
+cudaError_t launch_spec(int precision, const PassArgs& ap, double* n_next, bool unit_in, int num_sms, cudaStream_t s);
+// Its completion: on the tensor cores the exact probability launch (returns at once unless the bound
+// left the outcome open); then the corrective apply (returns at once unless the outcome is not g).
+cudaError_t launch_spec_fix(int precision, const PassArgs& ap, double* n_next, bool unit_in, int num_sms,
+                            cudaStream_t s);
 int pass_grid(int D, int w, int num_sms);
 // One wave of resident CTAs for the probability (prob = true) or apply pass kernel.
 int pass_grid_for(int precision, bool prob, int D, int w, int num_sms);

@@ -99,6 +99,7 @@ qec_status run_noalloc(const qec_params* params, uint64_t seed, uint64_t first_t
   if (pg4 > pgrid) pgrid = pg4;
   Carve c;
   const size_t o_psi = c.take(((size_t)1 << D) * amp), o_psi0 = c.take(((size_t)1 << D) * amp);
+  const size_t o_psi2 = c.take(((size_t)1 << D) * amp);   // second working state (speculative passes)
   const size_t o_ops0 = c.take(sizeof(ProgOp) * (init_prog.ops.size() + 1));
   const size_t o_ops1 = c.take(sizeof(ProgOp) * (prog.ops.size() + 1));
   const size_t o_blk0 = c.take(sizeof(BlockInfo) * nstab), o_blk1 = c.take(sizeof(BlockInfo) * nstab);
@@ -114,6 +115,7 @@ qec_status run_noalloc(const qec_params* params, uint64_t seed, uint64_t first_t
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   void* psi = base + o_psi;
   void* psi0 = base + o_psi0;
+  void* psi2 = base + o_psi2;
   ProgOp* ops[2] = {reinterpret_cast<ProgOp*>(base + o_ops0), reinterpret_cast<ProgOp*>(base + o_ops1)};
   BlockInfo* blks[2] = {reinterpret_cast<BlockInfo*>(base + o_blk0), reinterpret_cast<BlockInfo*>(base + o_blk1)};
   double* mats[2] = {reinterpret_cast<double*>(base + o_mat0), reinterpret_cast<double*>(base + o_mat1)};
@@ -178,13 +180,14 @@ qec_status run_noalloc(const qec_params* params, uint64_t seed, uint64_t first_t
   };
 
   // The same launches, grids and kernel sequence as qec_create / qec_run_trajectories, so that the
-  // reductions add in the same order and the results are identical: probability then apply per
-  // block for complex128; for complex64 each block's apply pass fused with the next block's
-  // probability pass.  (At d <= 3 the tensor-core passes do not apply: their tiles are larger than
-  // the register.)
+  // reductions add in the same order and the results are identical: for complex128 per block the
+  // speculative pass and its corrective launch, alternating between two working states; for
+  // complex64 each block's apply pass fused with the next block's probability pass.  (At d <= 3 the
+  // tensor-core passes do not apply: their tiles are larger than the register.)
   auto prob = [&](const PassArgs& a) { return launch_prob(prec, a, pass_grid_for(prec, true, D, a.w, sms), st); };
   auto apply = [&](const PassArgs& a) { return launch_apply(prec, a, pass_grid_for(prec, false, D, a.w, sms), st); };
-  const bool fused = !is_f64(prec);
+  const bool fused = !is_f64(prec), spec = is_f64(prec);
+  auto spec_out = [&](int b) { return (b & 1) ? psi2 : psi; };
   // Noise-free init round with outcomes forced to the zero syndrome (Sec. III.B), in psi0.
   e = launch_set_basis0(prec, psi0, D, st);
   if (e == cudaSuccess) e = launch_instantiate(prec, inst(0, 0, nstab, false), st);
@@ -200,8 +203,17 @@ qec_status run_noalloc(const qec_params* params, uint64_t seed, uint64_t first_t
   };
   for (uint32_t t = 0; t < n && e == cudaSuccess; ++t) {
     if (S > 0) e = launch_instantiate(prec, inst(1, 1, S, true), st);
-    if (S > 0 && e == cudaSuccess) e = prob(traj_pass(0));
-    for (int b = 0; b < S && e == cudaSuccess; ++b) {
+    for (int b = 0; spec && b < S && e == cudaSuccess; ++b) {
+      PassArgs a = traj_pass(b);
+      a.src = b == 0 ? psi0 : spec_out(b - 1);
+      a.dst = spec_out(b);
+      a.spec_prev = b >= nstab ? a.syn_idx - nstab : -1;
+      double* n_next = b + 1 < S ? reinterpret_cast<double*>(base + o_N) + b + 1 : nullptr;
+      e = launch_spec(prec, a, n_next, b == 0, sms, st);
+      if (e == cudaSuccess) e = launch_spec_fix(prec, a, n_next, b == 0, sms, st);
+    }
+    if (S > 0 && !spec && e == cudaSuccess) e = prob(traj_pass(0));
+    for (int b = 0; !spec && b < S && e == cudaSuccess; ++b) {
       const PassArgs a = traj_pass(b);
       if (fused && b + 1 < S) {
         PassArgs nx = traj_pass(b + 1);
@@ -214,7 +226,7 @@ qec_status run_noalloc(const qec_params* params, uint64_t seed, uint64_t first_t
     }
     if (e != cudaSuccess) break;
     ReadArgs r;
-    r.src = S > 0 ? psi : psi0;
+    r.src = S > 0 ? (spec ? spec_out(S - 1) : psi) : psi0;
     r.D = D;
     r.k1 = k1;
     r.d = params->d;

@@ -57,10 +57,10 @@ class Job:
 
 
 def state_bytes(d, precision):
-    """Device bytes of one slot: working state + resident init state, and a second working state
-    where the tensor-core complex128 form runs its speculative passes (registers of >= 11 qubits)."""
-    copies = 3 if precision == "c128tc" and d * d >= 11 else 2
-    return copies * (1 << (d * d)) * (16 if precision.startswith("c128") else 8)
+    """Device bytes of one slot: working state + resident init state, and the second working state
+    of the complex128 forms' speculative passes."""
+    c128 = precision.startswith("c128")
+    return (3 if c128 else 2) * (1 << (d * d)) * (16 if c128 else 8)
 
 
 @dataclass

@@ -359,7 +359,11 @@ qec_status qec_debug_blocks(const qec_params* params, uint64_t seed, uint64_t tr
  * <= out[r][1]); 4: the fused tensor-core pass's probability, A taken as one tile (one exponent for
  * all of A and one for all of B), 24-bit truncations, 3 slices each, diagonals 0..2:
  * out[r][0] = estimate of sum_n (A[r] . B[n])^2, out[r][1] its error bound, out[r][2] = estimate
- * of sum_k A[r][k]^2, out[r][3] its error bound.  Returns QEC_EINVAL for any other variant.  The paper has no counterpart
+ * of sum_k A[r][k]^2, out[r][3] its error bound; 5: the speculative pass's sums of squares of A's
+ * reals (B unused): out[r][0] = estimate of sum_k A[r][k]^2 from each real's top 24 bits under
+ * the row's largest exponent, out[r][1] its error bound, out[r][2] = the same sum from the top 24
+ * bits under the largest exponent of all of A, out[r][3] its error bound.  Returns QEC_EINVAL for
+ * any other variant.  The paper has no counterpart
  * (an arithmetic form of the gate application of Sec. III).  Returns QEC_EINVAL on null
  * pointers or m <= 0.
  */

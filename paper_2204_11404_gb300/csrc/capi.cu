@@ -707,10 +707,43 @@ static void ozaki_fused_prob(const double* A, const double* B, int m, double* ou
   }
 }
 
+// Variant 5: the speculative pass's two sums of squares on the CPU, over the reals of A (m rows of
+// 32, each row two threads' 16): out[r][0], out[r][1] = the input-side sum of row r (each real's top
+// 24 bits under the row's largest exponent, as the slicing holds them) and its bound; out[r][2],
+// out[r][3] = the output-side sum of the same reals (top 24 bits under the largest exponent of all of
+// A, as one tile) and its bound.
+static void ozaki_spec_sums(const double* A, int m, double* out) {
+  int Et = 0;
+  for (int i = 0; i < m * 32; ++i) Et = std::max(Et, oz::bexp(A[i]));
+  Et = std::max(Et, 24);
+  for (int r = 0; r < m; ++r) {
+    int E = 0;
+    for (int k = 0; k < 32; ++k) E = std::max(E, oz::bexp(A[r * 32 + k]));
+    oz::SqSum24 in, o;
+    for (int h = 0; h < 2; ++h) {
+      uint64_t nin = 0, nout = 0;
+      for (int k = 16 * h; k < 16 * h + 16; ++k) {
+        const uint64_t a = (E ? oz::mag56(A[r * 32 + k], E) : 0ull) >> 32;
+        const uint64_t b = oz::top24(oz::d2u(A[r * 32 + k]), Et);
+        nin += a * a;
+        nout += b * b;
+      }
+      in.add(nin, E);
+      o.add(nout, Et);
+    }
+    in.finish(out[r * 32], out[r * 32 + 1]);
+    o.finish(out[r * 32 + 2], out[r * 32 + 3]);
+  }
+}
+
 qec_status qec_debug_ozaki_gemm(const double* A, const double* B, int32_t m, int32_t variant, double* out) {
-  if (!A || !B || !out || m <= 0 || variant < 0 || variant > 4) return fail(QEC_EINVAL, "bad argument");
+  if (!A || !B || !out || m <= 0 || variant < 0 || variant > 5) return fail(QEC_EINVAL, "bad argument");
   if (variant == 4) {
     ozaki_fused_prob(A, B, m, out);
+    return QEC_OK;
+  }
+  if (variant == 5) {
+    ozaki_spec_sums(A, m, out);
     return QEC_OK;
   }
   std::vector<int> ea(m), eb(32);

@@ -101,7 +101,7 @@ def test_largest_digits_recombine_exactly(variant):
 def test_bad_variant_rejected():
     a = np.zeros((1, 32))
     with pytest.raises(capi.QecError):
-        capi.qec_debug_ozaki_gemm(a.ctypes.data, np.zeros((32, 32)).ctypes.data, 1, 5, a.ctypes.data)
+        capi.qec_debug_ozaki_gemm(a.ctypes.data, np.zeros((32, 32)).ctypes.data, 1, 6, a.ctypes.data)
 
 
 @pytest.mark.parametrize("seed", [0, 3])
@@ -205,3 +205,40 @@ def test_fused_probability_bound_is_tight_on_an_ordinary_tile(seed):
     assert abs(a_sum - float(((A @ B.T) ** 2).sum())) <= out[:, 1].sum()
     assert abs(n_sum - float((A ** 2).sum())) <= out[:, 3].sum()
     assert out[:, 1].sum() + out[:, 3].sum() < 2e-4 * (a_sum + n_sum)
+
+
+@pytest.mark.parametrize("seed", [0, 5, 9])
+def test_speculative_sums_contain_the_exact_values(seed):
+    """Variant 5, the speculative pass's two sums of squares: each real cut to its top 24 bits under
+    its row's largest exponent (the inputs) or under the whole tile's (the outputs), squared and
+    summed in integers, then as FP32 intervals with directed rounding.  Per row the exact sum of
+    squares must lie within each estimate's bound, whatever the row's scale (zero rows, rows far
+    below the tile's largest value, subnormals, ties)."""
+    rng = np.random.default_rng(seed)
+    m = 16
+    A = _rows(rng, m)
+    out = np.zeros((m, 32))
+    capi.qec_debug_ozaki_gemm(A.ctypes.data, np.zeros((32, 32)).ctypes.data, m, 5, out.ctypes.data)
+    tiny = Fraction(2.0 ** -1074)
+    for r in range(m):
+        n_ex = sum((Fraction(float(v)) ** 2 for v in A[r]), Fraction(0))
+        assert abs(Fraction(out[r, 0]) - n_ex) <= Fraction(out[r, 1]) + tiny, (r, out[r, 0], float(n_ex), out[r, 1])
+        assert abs(Fraction(out[r, 2]) - n_ex) <= Fraction(out[r, 3]) + tiny, (r, out[r, 2], float(n_ex), out[r, 3])
+    assert out[0, 0] == 0.0 and out[0, 2] == 0.0          # the all-zero row
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_speculative_sums_are_tight_on_an_ordinary_tile(seed):
+    """On a tile of amplitude-like values (half of them 1e-3 smaller), both bounds stay below 5e-6
+    of the sum (measured: 1.1e-6 with the rows' exponents, 1.4e-6 with the tile's), so the outcome
+    is left to the exact pass only for draws within about 1e-5 of their probability."""
+    rng = np.random.default_rng(seed)
+    m = 128
+    A = rng.standard_normal((m, 32)) / 64
+    A[rng.random((m, 32)) < 0.5] *= 1e-3
+    out = np.zeros((m, 32))
+    capi.qec_debug_ozaki_gemm(A.ctypes.data, np.zeros((32, 32)).ctypes.data, m, 5, out.ctypes.data)
+    ex = float((A ** 2).sum())
+    for c in (0, 2):
+        assert abs(out[:, c].sum() - ex) <= out[:, c + 1].sum()
+        assert out[:, c + 1].sum() < 5e-6 * ex, (c, out[:, c + 1].sum() / ex)

@@ -44,7 +44,9 @@ typedef enum { QEC_GATES_CNOT = 0, QEC_GATES_CR = 1 } qec_gateset;
 /* Amplitude storage / arithmetic.  C128: complex128 state, FP64 arithmetic, one
  * speculative pass per block as described under C128_TC, with FP64 sums that
  * decide every outcome directly.
- * C64: complex64 state, FP32 gate arithmetic, FP64 probability reductions.
+ * C64: complex64 state, FP32 gate arithmetic, FP64 probability reductions;
+ * one speculative pass per block as described under C128_TC (FP32 sums per
+ * tile, FP64 across tiles, deciding every outcome directly).
  * C64_TC: complex64 state; the fused apply + next-probability pass of every
  * pair of blocks with a weight-4 block on the tensor cores (3xTF32 split,
  * FP32 accumulation; a weight-2 block of the pair as K (x) I over two
@@ -382,16 +384,17 @@ qec_status qec_debug_ozaki_gemm(const double* A, const double* B, int32_t m, int
 qec_status qec_debug_exact_probability(qec_sim* sim, int32_t force, uint64_t* fallbacks);
 
 /*
- * Test hook for the complex128 forms (the paper has no counterpart: an evaluation order of
- * Sec. II.B's measurement and collapse).  enable = 1: the speculative passes (the default);
- * 0: the passes that compute each probability before its apply (QEC_C128: a probability pass and
- * an apply pass per block; QEC_C128_TC: per block pair, the apply fused with the next block's
- * 3-slice bounded probability); -1: unchanged.  Both give the same outcomes (except within the
+ * Test hook for QEC_C128, QEC_C128_TC and QEC_C64 (the paper has no counterpart: an evaluation
+ * order of Sec. II.B's measurement and collapse).  enable = 1: the speculative passes (the
+ * default); 0: the passes that compute each probability before its apply (QEC_C128: a probability
+ * pass and an apply pass per block; QEC_C128_TC: per block pair, the apply fused with the next
+ * block's 3-slice bounded probability; QEC_C64: the apply fused with the next block's
+ * probability); -1: unchanged.  Both give the same outcomes (except within the
  * rounding of a threshold) and states within a few FP64 roundings.  *misses (may be NULL)
  * receives the number of corrective applies run on this handle so far (outcomes that differed
  * from the guess).  Waits for the handle's queued work; switching rebuilds the trajectory graph
  * and requires a new run before qec_get_state.  QEC_EINVAL on a null handle or enable outside
- * -1..1; QEC_EUNSUPPORTED for enable = 1 on a complex64 form.
+ * -1..1; QEC_EUNSUPPORTED for enable = 1 on QEC_C64_TC.
  */
 qec_status qec_debug_speculation(qec_sim* sim, int32_t enable, uint64_t* misses);
 

@@ -706,6 +706,116 @@ __global__ void __launch_bounds__(256) k_fused(FusedArgs f) {
   prob_finish(f.pr, accA, accN, sred, &s_last);
 }
 
+// ---- speculative complex64 pass (QEC_C64), per shared-memory tile -------------------------------
+// The order of evaluation of k_apply_spec (Sec. II.B; guess = the same stabilizer's outcome one round
+// earlier) on k_fused's double-buffered tiles of block a's qubits and the low register bits: the
+// tile's groups are multiplied by K_g / sqrt(N) in FP32, in shared memory, with |in|^2 and |out|^2
+// summed per thread in FP32 over the tile and in FP64 across tiles (as k_fused sums its
+// probabilities); the tile is stored to the other working state.  The last CTA decides
+// u N' < P(1) N' directly, as the complex64 probability pass does.  FIX: the corrective apply where
+// the drawn outcome differs from g.
+template <int W, bool FIX>
+__global__ void __launch_bounds__(256) k_fused_spec(FusedArgs f) {
+  const int gs = spec_guess(f.ap);
+  const int m = FIX ? *f.ap.m : gs;
+  if (FIX && m == gs) return;
+  constexpr int C = 1 << W;
+  constexpr int CH = 2;   // complex64 amplitudes per 16-byte copy
+  extern __shared__ __align__(16) unsigned char fsm[];
+  const uint32_t tsz = 1u << f.nt, lmask = (1u << f.lb) - 1u;
+  float2* buf0 = reinterpret_cast<float2*>(fsm);
+  float2* buf1 = buf0 + tsz;
+  uint32_t* hoff = reinterpret_cast<uint32_t*>(buf1 + tsz);
+  __shared__ __align__(16) float2 sK[C * C];
+  __shared__ double sred[64];
+  __shared__ int s_last;
+  {
+    const double scale = f.spec_unit ? 1.0 : 1.0 / sqrt(*f.ap.N);
+    const float2* Kg = reinterpret_cast<const float2*>(f.ap.kraus) + (m ? 256 : 0);
+    for (int i = threadIdx.x; i < C * C; i += blockDim.x) {
+      float2 kv = Kg[(i / C) * 16 + (i % C)];
+      kv.x = (float)((double)kv.x * scale);
+      kv.y = (float)((double)kv.y * scale);
+      sK[i] = kv;
+    }
+    const int nh = f.nt - f.lb;
+    for (int h = threadIdx.x; h < (1 << nh); h += blockDim.x) {
+      uint32_t o = 0;
+      for (int j = 0; j < nh; ++j) o |= (uint32_t)((h >> j) & 1) << f.hbits[j];
+      hoff[h] = o;
+    }
+  }
+  __syncthreads();
+  int qa[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) qa[j] = j < W ? f.qa[j] : 0;
+  uint32_t offa[C];
+#pragma unroll
+  for (int l = 0; l < C; ++l) offa[l] = member_off<W>(l, qa);
+  const float2* src = reinterpret_cast<const float2*>(f.ap.src);
+  float2* dst = reinterpret_cast<float2*>(f.ap.dst);
+  const uint32_t ntile = 1u << f.nout;
+  const int obit = (threadIdx.x & 31) < (unsigned)f.nout ? f.obits[threadIdx.x & 31] : 0;
+  auto tile_base = [&](uint32_t tix) { return tile_base_warp(tix, f.nout, obit); };
+  auto issue = [&](uint32_t tix, float2* buf) {
+    const uint32_t tb = tile_base(tix);
+    for (uint32_t e = threadIdx.x * CH; e < tsz; e += blockDim.x * CH)
+      cp_async16(buf + e, src + (tb | hoff[e >> f.lb] | (e & lmask)));
+    cp_async_commit();
+  };
+  double accI = 0.0, accO = 0.0;
+  uint32_t tix = blockIdx.x;
+  if (tix < ntile) issue(tix, buf0);
+  int cur = 0;
+  for (; tix < ntile; tix += gridDim.x) {
+    float2* tile = cur ? buf1 : buf0;
+    const uint32_t nxt = tix + gridDim.x;
+    if (nxt < ntile) issue(nxt, cur ? buf0 : buf1);
+    else cp_async_commit();
+    cp_async_wait<1>();
+    __syncthreads();
+    float tI = 0.f, tO = 0.f;   // this thread's sums over its groups of the tile
+    for (uint32_t g = threadIdx.x; g < (tsz >> W); g += blockDim.x) {
+      const uint32_t b = local_base<W>(g, qa);
+      float2 v[C];
+#pragma unroll
+      for (int l = 0; l < C; ++l) {
+        v[l] = tile[b + offa[l]];
+        tI = fmaf(v[l].x, v[l].x, fmaf(v[l].y, v[l].y, tI));
+      }
+#pragma unroll
+      for (int r = 0; r < C; ++r) {
+        float sr = 0.f, si = 0.f;
+#pragma unroll
+        for (int c = 0; c < C; c += 2) {
+          float2 k0, k1;
+          lds_pair(&sK[r * C + c], k0, k1);
+          sr = fmaf(k0.x, v[c].x, sr);
+          sr = fmaf(-k0.y, v[c].y, sr);
+          si = fmaf(k0.x, v[c].y, si);
+          si = fmaf(k0.y, v[c].x, si);
+          sr = fmaf(k1.x, v[c + 1].x, sr);
+          sr = fmaf(-k1.y, v[c + 1].y, sr);
+          si = fmaf(k1.x, v[c + 1].y, si);
+          si = fmaf(k1.y, v[c + 1].x, si);
+        }
+        tile[b + offa[r]] = make_float2(sr, si);
+        tO = fmaf(sr, sr, fmaf(si, si, tO));
+      }
+    }
+    accI += (double)tI;
+    accO += (double)tO;
+    __syncthreads();
+    const uint32_t tb = tile_base(tix);
+    for (uint32_t e = threadIdx.x * CH; e < tsz; e += blockDim.x * CH)
+      *reinterpret_cast<float4*>(dst + (tb | hoff[e >> f.lb] | (e & lmask))) = *reinterpret_cast<const float4*>(tile + e);
+    __syncthreads();
+    cur ^= 1;
+  }
+  cp_async_wait<0>();
+  spec_finish<FIX>(f, gs, accI, 0.0, accO, 0.0, sred, &s_last, true);
+}
+
 // ---- tensor-core complex64 fused pass (tcgen05, 3xTF32, FP32 accumulation in TMEM) --------
 // A weight-4 block's 16x16 complex matrix acts on every 16-amplitude group of a tile as a real
 // GEMM: rows = groups (M = 256 per tile, two M = 128 MMAs), K = 32 input reals (re, im
@@ -2433,11 +2543,40 @@ static bool spec_fp64_args(const PassArgs& ap, double* n_next, bool unit_in, int
   return true;
 }
 
+// The complex64 speculative pass: k_fused's tile rule for block ap alone (low bits for 128-byte runs,
+// raised to at least 2^12 amplitudes), one wave of resident CTAs, 4 partial sums per CTA.
+static bool spec_c64_args(const PassArgs& ap, double* n_next, bool unit_in, int num_sms, FusedArgs& f,
+                          size_t& smem) {
+  if ((ap.w != 2 && ap.w != 4) || ap.src == ap.dst) return false;
+  f.ap = ap;
+  f.pr = ap;
+  f.n_next = n_next;
+  f.spec_unit = unit_in ? 1 : 0;
+  block_tile(ap, ap, 4, 12, f);
+  smem = 2 * 8 * ((size_t)1 << f.nt) + sizeof(uint32_t) * ((size_t)1 << (f.nt - f.lb));
+  if (smem > (size_t)kFusedSmemMax) return false;
+  const void* fn = ap.w == 4 ? (const void*)k_fused_spec<4, false> : (const void*)k_fused_spec<2, false>;
+  f.grid = wave_grid(fn, smem, num_sms, 1ll << f.nout);
+  if (f.grid > MAX_PASS_GRID / 2) f.grid = MAX_PASS_GRID / 2;
+  return true;
+}
+
+template <bool FIX>
+static cudaError_t launch_spec_c64(const PassArgs& ap, double* n_next, bool unit_in, int num_sms, cudaStream_t s) {
+  FusedArgs f;
+  size_t smem = 0;
+  if (!spec_c64_args(ap, n_next, unit_in, num_sms, f, smem)) return cudaErrorInvalidValue;
+  if (ap.w == 4) k_fused_spec<4, FIX><<<f.grid, 256, smem, s>>>(f);
+  else k_fused_spec<2, FIX><<<f.grid, 256, smem, s>>>(f);
+  return cudaGetLastError();
+}
+
 static bool spec_on_tensor_cores(int precision, const PassArgs& ap) {
   return precision == QEC_C128_TC && apply_oz_applies(ap);
 }
 
 cudaError_t launch_spec(int precision, const PassArgs& ap, double* n_next, bool unit_in, int num_sms, cudaStream_t s) {
+  if (precision == QEC_C64) return launch_spec_c64<false>(ap, n_next, unit_in, num_sms, s);
   FusedArgs f;
   if (spec_on_tensor_cores(precision, ap)) {
     if (!spec_args(ap, n_next, unit_in, num_sms, f)) return cudaErrorInvalidValue;
@@ -2452,6 +2591,7 @@ cudaError_t launch_spec(int precision, const PassArgs& ap, double* n_next, bool 
 
 cudaError_t launch_spec_fix(int precision, const PassArgs& ap, double* n_next, bool unit_in, int num_sms,
                             cudaStream_t s) {
+  if (precision == QEC_C64) return launch_spec_c64<true>(ap, n_next, unit_in, num_sms, s);
   FusedArgs f;
   if (spec_on_tensor_cores(precision, ap)) {
     if (!spec_args(ap, n_next, unit_in, num_sms, f)) return cudaErrorInvalidValue;
@@ -2506,6 +2646,11 @@ cudaError_t setup_kernels(int precision, int D) {
   }
   cudaError_t e = cudaFuncSetAttribute(k_sample<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e == cudaSuccess) e = fused_attrs<float>();
+  for (const void* fn : {(const void*)k_fused_spec<2, false>, (const void*)k_fused_spec<2, true>,
+                         (const void*)k_fused_spec<4, false>, (const void*)k_fused_spec<4, true>}) {
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kFusedSmemMax);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  }
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fused_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kFusedSmemMax);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fused_tc, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   return e;

@@ -180,13 +180,13 @@ qec_status run_noalloc(const qec_params* params, uint64_t seed, uint64_t first_t
   };
 
   // The same launches, grids and kernel sequence as qec_create / qec_run_trajectories, so that the
-  // reductions add in the same order and the results are identical: for complex128 per block the
-  // speculative pass and its corrective launch, alternating between two working states; for
-  // complex64 each block's apply pass fused with the next block's probability pass.  (At d <= 3 the
-  // tensor-core passes do not apply: their tiles are larger than the register.)
+  // reductions add in the same order and the results are identical: for complex128 and QEC_C64 per
+  // block the speculative pass and its corrective launch, alternating between two working states;
+  // for QEC_C64_TC each block's apply pass fused with the next block's probability pass.  (At d <= 3
+  // the tensor-core passes do not apply: their tiles are larger than the register.)
   auto prob = [&](const PassArgs& a) { return launch_prob(prec, a, pass_grid_for(prec, true, D, a.w, sms), st); };
   auto apply = [&](const PassArgs& a) { return launch_apply(prec, a, pass_grid_for(prec, false, D, a.w, sms), st); };
-  const bool fused = !is_f64(prec), spec = is_f64(prec);
+  const bool spec = is_f64(prec) || prec == QEC_C64, fused = !spec;
   auto spec_out = [&](int b) { return (b & 1) ? psi2 : psi; };
   // Noise-free init round with outcomes forced to the zero syndrome (Sec. III.B), in psi0.
   e = launch_set_basis0(prec, psi0, D, st);

@@ -58,9 +58,8 @@ class Job:
 
 def state_bytes(d, precision):
     """Device bytes of one slot: working state + resident init state, and the second working state
-    of the complex128 forms' speculative passes."""
-    c128 = precision.startswith("c128")
-    return (3 if c128 else 2) * (1 << (d * d)) * (16 if c128 else 8)
+    of the speculative passes (every form but c64tc)."""
+    return (2 if precision == "c64tc" else 3) * (1 << (d * d)) * (16 if precision.startswith("c128") else 8)
 
 
 @dataclass

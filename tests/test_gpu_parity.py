@@ -191,16 +191,18 @@ def test_d3_sign_follows_variant_matches_oracle(prec):
         assert kinds.count("ambiguous") <= (0 if prec == "c128" else 2)
 
 
-@pytest.mark.parametrize("d,rounds,n", [(3, 4, 16), (5, 2, 1)])
-def test_fp64_speculative_pass_matches_probability_passes_and_oracle(d, rounds, n):
-    """The FP64 form applies each block's guessed outcome (the same stabilizer's previous outcome)
-    and re-applies from the untouched input where the drawn outcome differs.  On the stress noise:
-    against the FP64 oracle (outcomes identical, amplitudes within 1e-12), against the same form
-    with a probability pass before each apply (identical outcomes, states within 1e-13), and one
-    corrective apply per outcome change."""
+@pytest.mark.parametrize("prec,d,rounds,n,bar", [("c128", 3, 4, 16, 1e-13), ("c128", 5, 2, 1, 1e-13),
+                                                 ("c64", 3, 4, 16, 4e-5)])
+def test_speculative_pass_matches_probability_passes_and_oracle(prec, d, rounds, n, bar):
+    """The FP64 and complex64 CUDA-core forms apply each block's guessed outcome (the same
+    stabilizer's previous outcome) and re-apply from the untouched input where the drawn outcome
+    differs.  On the stress noise (every trajectory's draws at least 2e-4 from their probabilities):
+    against the FP64 oracle (outcomes identical, amplitudes within the form's bar), against the
+    same form with each probability computed before its apply (identical outcomes, states within a
+    few roundings), and one corrective apply per outcome change."""
     from paper_2204_11404_gb300 import capi
     pt = dict(W.STRESS)
-    with Simulator(d, rounds, "cr", "c128", **pt) as a:
+    with Simulator(d, rounds, "cr", prec, **pt) as a:
         m0 = capi.qec_debug_speculation(a.h, 1)
         ra = a.run(77, 0, n)
         sa = a.state()
@@ -209,9 +211,9 @@ def test_fp64_speculative_pass_matches_probability_passes_and_oracle(d, rounds, 
         sb = a.state()
     for x, y in zip(ra, rb):
         assert (x == y).all()
-    assert np.abs(sa - sb).max() < 1e-13
+    assert np.abs(sa - sb).max() < bar
     changes = int(np.sum(np.diff(ra[0].astype(np.int8), axis=1) != 0))
     assert m1 - m0 == changes and changes > 0
     o = oracle_traj(d, rounds, "cr", pt, 77, n - 1, want_state=True)
-    assert compare_trajectory(ra[0][n - 1], ra[1][n - 1], o, TAU["c128"]) == "exact"
-    assert np.abs(sa - o["state"][: 1 << (d * d)]).max() < AMP_TOL["c128"]
+    assert compare_trajectory(ra[0][n - 1], ra[1][n - 1], o, TAU[prec]) == "exact"
+    assert np.abs(sa - o["state"][: 1 << (d * d)]).max() < AMP_TOL[prec]

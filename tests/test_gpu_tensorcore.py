@@ -197,7 +197,7 @@ def test_speculative_pass_agrees_with_fused_pass():
 
 def test_speculation_hook_rejects_forms_without_it():
     from paper_2204_11404_gb300 import capi
-    with Simulator(3, 1, "cr", "c64", **W.STRESS) as a:   # complex64: no speculative pass
+    with Simulator(3, 1, "cr", "c64tc", **W.STRESS) as a:   # complex64 on tensor cores: none
         with pytest.raises(capi.QecError):
             capi.qec_debug_speculation(a.h, 1)
         assert capi.qec_debug_speculation(a.h, 0) == 0

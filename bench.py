@@ -270,7 +270,7 @@ def native_arm(args, rank, world, local):
     stream = bstream
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     fb0 = [capi.qec_debug_exact_probability(s.h, -1) for s in sims] if args.precision == "c128tc" else None
-    sm0 = [capi.qec_debug_speculation(s.h, -1) for s in sims] if args.precision != "c64tc" else None
+    sm0 = [capi.qec_debug_speculation(s.h, -1) for s in sims]
     with ClockSampler(local) as clk:
         torch.cuda.synchronize()
         e0.record(stream)
@@ -283,7 +283,7 @@ def native_arm(args, rank, world, local):
     used = sorted({(args.warmup + i) % len(pts) for i in range(args.steps)})
     kt = [capi.qec_kernel_times(sims[j].h) for j in used]
     fallbacks = (sum(capi.qec_debug_exact_probability(s.h, -1) for s in sims) - sum(fb0)) if fb0 else None
-    misses = (sum(capi.qec_debug_speculation(s.h, -1) for s in sims) - sum(sm0)) if sm0 else None
+    misses = sum(capi.qec_debug_speculation(s.h, -1) for s in sims) - sum(sm0)
     if world > 1:
         dist.barrier()
     secs = e0.elapsed_time(e1) / 1e3
@@ -339,7 +339,7 @@ def native_arm(args, rank, world, local):
             ms22.append(capi.qec_kernel_times(sims[0].h)[1])
         ms22 = float(np.median(ms22))
         roof["weight2_pair"] = {
-            "kernel": {"c64": "k_fused_spec<2,false> (weight-2 block)", "c64tc": "k_fused<float,2,2> (CUDA cores)",
+            "kernel": {"c64": "k_fused_spec<2,false> (weight-2 block)", "c64tc": "k_fused_spec<2,false> (CUDA cores)",
                        "c128tc": "k_ozs<false> (weight-2 block as K (x) I)"}[args.precision],
             "block": blk, "ms": ms22, "achieved": bytes_apply / (ms22 * 1e-3) / 1e9,
             "frac": bytes_apply / (ms22 * 1e-3) / 1e9 / roof["peak"], "unit": "GB/s"}
@@ -348,7 +348,8 @@ def native_arm(args, rank, world, local):
                               "guessed from the previous round, + FP64 |in|^2 and |out|^2 sums, 2^25 amplitudes)",
                       "c64": "k_fused_spec<4,false> (FP32: speculative apply of a weight-4 block, the outcome guessed "
                              "from the previous round, + |in|^2 and |out|^2 sums, 2^25 amplitudes)",
-                      "c64tc": "k_fused_tc (tcgen05 3xTF32: apply weight-4 block + next probability, 2^25 amplitudes)",
+                      "c64tc": "k_fused_tc_spec<false> (tcgen05 3xTF32: speculative apply of a weight-4 block, the "
+                               "outcome guessed from the previous round, + |in|^2 and |out|^2 sums, 2^25 amplitudes)",
                       "c128tc": "k_ozs<false> (tcgen05: speculative apply of a weight-4 block, the outcome guessed "
                                 "from the previous round, as FP64-exact 8-bit-slice products + bounded |in|^2 and "
                                 "|out|^2 sums on the same tiles, 2^25 amplitudes)",
@@ -367,7 +368,7 @@ def native_arm(args, rank, world, local):
     # bound left the outcome open); the readout (3)
     S = nst * R
     launches_per_traj = {"c128": 1 + 2 * S + 3, "c128tc": 1 + 3 * S + 3,
-                         "c64": 1 + 2 * S + 3, "c64tc": 1 + 1 + (S - 1) + 1 + 3}[args.precision]
+                         "c64": 1 + 2 * S + 3, "c64tc": 1 + 2 * S + 3}[args.precision]
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,
@@ -378,8 +379,8 @@ def native_arm(args, rank, world, local):
     }
     if fallbacks is not None:   # measurements the bound left open (exact pass run), of S per trajectory
         out["exact_probability_passes"] = {"count": fallbacks, "measurements": S * args.steps}
-    if misses is not None:      # outcomes that differed from the guess (corrective apply run)
-        out["speculation"] = {"corrective_applies": misses, "measurements": S * args.steps}
+    # outcomes that differed from the guess (corrective apply run)
+    out["speculation"] = {"corrective_applies": misses, "measurements": S * args.steps}
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.code == "surface":
         from oracle.runner import set_threads
 

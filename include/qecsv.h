@@ -47,11 +47,13 @@ typedef enum { QEC_GATES_CNOT = 0, QEC_GATES_CR = 1 } qec_gateset;
  * C64: complex64 state, FP32 gate arithmetic, FP64 probability reductions;
  * one speculative pass per block as described under C128_TC (FP32 sums per
  * tile, FP64 across tiles, deciding every outcome directly).
- * C64_TC: complex64 state; the fused apply + next-probability pass of every
- * pair of blocks with a weight-4 block on the tensor cores (3xTF32 split,
- * FP32 accumulation; a weight-2 block of the pair as K (x) I over two
- * spectator qubits; tiles of 2^12 amplitudes, so d >= 5), pairs of weight-2
- * blocks on the CUDA cores; FP64 probability reductions.
+ * C64_TC: complex64 state; the speculative pass of every weight-4 block on the
+ * tensor cores (3xTF32 split, FP32 accumulation; tiles of 2^12 amplitudes, so
+ * d >= 5), of the weight-2 blocks as C64; FP64 reductions across tiles.  With
+ * the speculative passes off, the fused apply + next-probability pass of every
+ * pair of blocks with a weight-4 block on the tensor cores (a weight-2 block of
+ * the pair as K (x) I over two spectator qubits), pairs of weight-2 blocks on
+ * the CUDA cores.
  * C128_TC: complex128 state; the apply of every stabilizer block (tiles of
  * 2^11 amplitudes, so registers of at least 11 qubits: d >= 4) as emulated
  * FP64 products on the FP16 tensor cores: each operand row split into 7
@@ -384,17 +386,16 @@ qec_status qec_debug_ozaki_gemm(const double* A, const double* B, int32_t m, int
 qec_status qec_debug_exact_probability(qec_sim* sim, int32_t force, uint64_t* fallbacks);
 
 /*
- * Test hook for QEC_C128, QEC_C128_TC and QEC_C64 (the paper has no counterpart: an evaluation
- * order of Sec. II.B's measurement and collapse).  enable = 1: the speculative passes (the
- * default); 0: the passes that compute each probability before its apply (QEC_C128: a probability
- * pass and an apply pass per block; QEC_C128_TC: per block pair, the apply fused with the next
- * block's 3-slice bounded probability; QEC_C64: the apply fused with the next block's
- * probability); -1: unchanged.  Both give the same outcomes (except within the
+ * Test hook (the paper has no counterpart: an evaluation order of Sec. II.B's measurement and
+ * collapse).  enable = 1: the speculative passes (the default); 0: the passes that compute each
+ * probability before its apply (QEC_C128: a probability pass and an apply pass per block;
+ * QEC_C128_TC: per block pair, the apply fused with the next block's 3-slice bounded probability;
+ * the complex64 forms: the apply fused with the next block's probability); -1: unchanged.  Both give the same outcomes (except within the
  * rounding of a threshold) and states within a few FP64 roundings.  *misses (may be NULL)
  * receives the number of corrective applies run on this handle so far (outcomes that differed
  * from the guess).  Waits for the handle's queued work; switching rebuilds the trajectory graph
  * and requires a new run before qec_get_state.  QEC_EINVAL on a null handle or enable outside
- * -1..1; QEC_EUNSUPPORTED for enable = 1 on QEC_C64_TC.
+ * -1..1.
  */
 qec_status qec_debug_speculation(qec_sim* sim, int32_t enable, uint64_t* misses);
 

@@ -191,9 +191,8 @@ PassArgs traj_pass(const qec_sim* s, int b) {
   return pass_args(s, s->prog, b, src, s->psi, false, s->d_syn, rnd * s->nstab + k);
 }
 
-// Speculative passes (the complex128 forms and QEC_C64): block b reads the state block b-1 wrote
-// (block 0 the init state) and writes the other working buffer, so that a wrong guess is corrected
-// from its untouched input.
+// Speculative passes (every form): block b reads the state block b-1 wrote (block 0 the init state)
+// and writes the other working buffer, so that a wrong guess is corrected from its untouched input.
 void* spec_out(const qec_sim* s, int b) { return (b & 1) ? s->psi2 : s->psi; }
 
 PassArgs spec_pass(const qec_sim* s, int b) {
@@ -204,7 +203,7 @@ PassArgs spec_pass(const qec_sim* s, int b) {
   return a;
 }
 
-bool spec_applies(const qec_sim* s) { return is_f64(s->p.precision) || s->p.precision == QEC_C64; }
+bool spec_applies(const qec_sim*) { return true; }
 
 // The state the last block wrote (the init state when there are no noisy rounds).
 const void* final_state(const qec_sim* s) {

@@ -1160,6 +1160,134 @@ __global__ void __launch_bounds__(256, 2) k_fused_tc(FusedArgs f) {
   prob_finish(f.pr, accA, accN, sred, &s_last);
 }
 
+// Speculative complex64 pass on the tensor cores (QEC_C64_TC, weight-4 blocks): the order of
+// evaluation of k_apply_spec (Sec. II.B; guess = the same stabilizer's outcome one round earlier)
+// with k_fused_tc's apply: per 4096-amplitude tile, gather each group into the 3xTF32 A operands
+// (summing |in|^2), the apply GEMM into tensor memory, its outputs (summing |out|^2) into the
+// updated tile, which is stored to the other working state.  Without the probability GEMM, its
+// regrouping and its tensor-memory operands.  Sums in FP32 per tile, FP64 across tiles; the last
+// CTA decides directly, as the complex64 probability pass does.  FIX: the corrective apply where
+// the drawn outcome differs from g.
+template <bool FIX>
+__global__ void __launch_bounds__(256, 2) k_fused_tc_spec(FusedArgs f) {
+  const int gs = spec_guess(f.ap);
+  const int m = FIX ? *f.ap.m : gs;
+  if (FIX && m == gs) return;
+  constexpr int C = 16;
+  extern __shared__ __align__(128) unsigned char tsm[];
+  const uint32_t tsz = 1u << f.nt, lmask = (1u << f.lb) - 1u;     // tsz = 4096 (checked by the launcher)
+  float2* tile = reinterpret_cast<float2*>(tsm);
+  float* Ahi = reinterpret_cast<float*>(tile + tsz);
+  float* Alo = Ahi + 256 * 32;
+  float2* outt = reinterpret_cast<float2*>(Ahi);                  // the updated tile (tile slots)
+  float* Bahi = Alo + 256 * 32;
+  float* Balo = Bahi + 32 * 32;
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_base;
+  __shared__ int s_err;
+  __shared__ double sred[64];
+  __shared__ int s_last;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  {
+    const double scale = f.spec_unit ? 1.0 : 1.0 / sqrt(*f.ap.N);
+    build_b(reinterpret_cast<const float2*>(f.ap.kraus) + (m ? 256 : 0), scale, Bahi, Balo, f.ap.w == 2);
+    if (tid == 0) {
+      s_err = 0;
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(smem_u32(&tmem_base)));
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  tc_sync();
+  const uint32_t tmem = tmem_base;
+  const uint32_t mb = smem_u32(&mbar);
+  int qa[4], qas[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    qa[j] = f.qa[j];
+    qas[j] = f.qa_s[j];
+  }
+  // tile slots and chunk offsets as in k_fused_tc
+  auto slot = [](uint32_t e) { return e ^ ((((e >> 4) ^ (e >> 7) ^ (e >> 10)) & 7u) << 1); };
+  uint32_t offa[C];
+#pragma unroll
+  for (int l = 0; l < C; ++l) offa[l] = slot(member_off<4>(l, qa));
+  uint32_t coff[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const uint32_t e = (uint32_t)tid * 2 + 512u * i, h = e >> f.lb;
+    uint32_t o = 0;
+    for (int j = 0; j < f.nt - f.lb; ++j) o |= ((h >> j) & 1u) << f.hbits[j];
+    coff[i] = o | (e & lmask);
+  }
+  const uint32_t sba = slot(local_base<4>((uint32_t)tid, qas));
+  uint32_t cd[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) cd[i] = slot((uint32_t)tid * 2 + 512u * i);
+  const uint32_t taddr = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + 32u * (warp >> 2);
+  const float2* src = reinterpret_cast<const float2*>(f.ap.src);
+  float2* dst = reinterpret_cast<float2*>(f.ap.dst);
+  const uint32_t ntile = 1u << f.nout;
+  double accI = 0.0, accO = 0.0;
+  uint32_t ph = 0;
+  const int obit = (threadIdx.x & 31) < (unsigned)f.nout ? f.obits[threadIdx.x & 31] : 0;
+  auto tile_base = [&](uint32_t tix) { return tile_base_warp(tix, f.nout, obit); };
+  auto load_tile = [&](uint32_t tix) {
+    const uint32_t tb = tile_base(tix);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) cp_async16(tile + cd[i], src + (tb | coff[i]));
+    cp_async_commit();
+  };
+  if (blockIdx.x < ntile) load_tile(blockIdx.x);
+  for (uint32_t tix = blockIdx.x; tix < ntile; tix += gridDim.x) {
+    const uint32_t tb = tile_base(tix);
+    cp_async_wait<0>();
+    __syncthreads();   // the input tile is in; the previous tile's readers of the updated tile are done
+    float sI = 0.f;
+#pragma unroll
+    for (int l = 0; l < C; l += 2) {
+      const float2 a = tile[sba ^ offa[l]], b = tile[sba ^ offa[l + 1]];
+      sI = fmaf(a.x, a.x, fmaf(a.y, a.y, fmaf(b.x, b.x, fmaf(b.y, b.y, sI))));
+      put_a4(Ahi, Alo, tid, 2 * l, a, b);
+    }
+    accI += (double)sI;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    tc_sync();
+    if (tix + gridDim.x < ntile) load_tile(tix + gridDim.x);   // the input tile is free
+    if (tid == 0) issue_gemm(tmem, Ahi, Alo, Bahi, Balo, mb);
+    if (!mbar_wait(mb, ph & 1)) s_err = 1;
+    ++ph;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (s_err) break;
+    {
+      float d[32];
+      tmem_ld32(taddr, d);
+      float sO = 0.f;
+#pragma unroll
+      for (int r = 0; r < C; ++r) {
+        outt[sba ^ offa[r]] = make_float2(d[2 * r], d[2 * r + 1]);
+        sO = fmaf(d[2 * r], d[2 * r], fmaf(d[2 * r + 1], d[2 * r + 1], sO));
+      }
+      accO += (double)sO;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+      *reinterpret_cast<float4*>(dst + (tb | coff[i])) = *reinterpret_cast<const float4*>(outt + cd[i]);
+  }
+  cp_async_wait<0>();
+  tc_sync();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tmem));
+  if (s_err && tid == 0) atomicOr(&f.ap.ctl->status, 1u);
+  spec_finish<FIX>(f, gs, accI, 0.0, accO, 0.0, sred, &s_last, true);
+}
+
 // ---- complex128 passes, FP64-exact on the FP16 tensor cores (Ozaki slices) ---------------------
 enum OzMode { OZ_APPLY = 0, OZ_PROB = 1, OZ_PROB_BOUND = 2 };
 // A weight-4 block's 16x16 complex matrix (times 1/sqrt(N)) on the 128 groups of a 2048-amplitude
@@ -2561,11 +2689,23 @@ static bool spec_c64_args(const PassArgs& ap, double* n_next, bool unit_in, int 
   return true;
 }
 
+// QEC_C64_TC: weight-4 blocks whose tile has 2^12 amplitudes on the tensor cores (k_fused_tc_spec, two
+// CTAs per SM), the rest as QEC_C64.
 template <bool FIX>
-static cudaError_t launch_spec_c64(const PassArgs& ap, double* n_next, bool unit_in, int num_sms, cudaStream_t s) {
+static cudaError_t launch_spec_c64(int precision, const PassArgs& ap, double* n_next, bool unit_in, int num_sms,
+                                   cudaStream_t s) {
   FusedArgs f;
   size_t smem = 0;
   if (!spec_c64_args(ap, n_next, unit_in, num_sms, f, smem)) return cudaErrorInvalidValue;
+  if (precision == QEC_C64_TC && ap.w == 4 && f.nt == 12) {
+    oz_block_bits(ap.w, f.qa, f.qa_s, f.nt);
+    int64_t g = 2ll * num_sms;
+    if (g > (1ll << f.nout)) g = 1ll << f.nout;
+    if (g > MAX_PASS_GRID / 2) g = MAX_PASS_GRID / 2;
+    f.grid = (int)g;
+    k_fused_tc_spec<FIX><<<f.grid, 256, kTcSmem, s>>>(f);
+    return cudaGetLastError();
+  }
   if (ap.w == 4) k_fused_spec<4, FIX><<<f.grid, 256, smem, s>>>(f);
   else k_fused_spec<2, FIX><<<f.grid, 256, smem, s>>>(f);
   return cudaGetLastError();
@@ -2576,7 +2716,7 @@ static bool spec_on_tensor_cores(int precision, const PassArgs& ap) {
 }
 
 cudaError_t launch_spec(int precision, const PassArgs& ap, double* n_next, bool unit_in, int num_sms, cudaStream_t s) {
-  if (precision == QEC_C64) return launch_spec_c64<false>(ap, n_next, unit_in, num_sms, s);
+  if (!is_f64(precision)) return launch_spec_c64<false>(precision, ap, n_next, unit_in, num_sms, s);
   FusedArgs f;
   if (spec_on_tensor_cores(precision, ap)) {
     if (!spec_args(ap, n_next, unit_in, num_sms, f)) return cudaErrorInvalidValue;
@@ -2591,7 +2731,7 @@ cudaError_t launch_spec(int precision, const PassArgs& ap, double* n_next, bool 
 
 cudaError_t launch_spec_fix(int precision, const PassArgs& ap, double* n_next, bool unit_in, int num_sms,
                             cudaStream_t s) {
-  if (precision == QEC_C64) return launch_spec_c64<true>(ap, n_next, unit_in, num_sms, s);
+  if (!is_f64(precision)) return launch_spec_c64<true>(precision, ap, n_next, unit_in, num_sms, s);
   FusedArgs f;
   if (spec_on_tensor_cores(precision, ap)) {
     if (!spec_args(ap, n_next, unit_in, num_sms, f)) return cudaErrorInvalidValue;
@@ -2651,8 +2791,10 @@ cudaError_t setup_kernels(int precision, int D) {
     if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kFusedSmemMax);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   }
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fused_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kFusedSmemMax);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fused_tc, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  for (const void* fn : {(const void*)k_fused_tc, (const void*)k_fused_tc_spec<false>, (const void*)k_fused_tc_spec<true>}) {
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kFusedSmemMax);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  }
   return e;
 }
 

@@ -133,8 +133,8 @@ cudaError_t launch_prob_oz_check(const PassArgs& pr, int num_sms, cudaStream_t s
 // (scale 1 with unit_in) for the guessed outcome g, decides the outcome (on the tensor cores where
 // its bound allows), and stores |output|^2 in *n_next (n_next may be null).  QEC_C128_TC blocks whose
 // tile fits (apply_oz_applies) run on the tensor cores, every other complex128 block on the FP64
-// CUDA cores; QEC_C64 blocks on the FP32 CUDA cores (shared-memory tiles); cudaErrorInvalidValue for
-// QEC_C64_TC.
+// CUDA cores; QEC_C64_TC weight-4 blocks whose tile has 2^12 amplitudes on the tensor cores (3xTF32),
+// every other complex64 block on the FP32 CUDA cores (shared-memory tiles).
 cudaError_t launch_spec(int precision, const PassArgs& ap, double* n_next, bool unit_in, int num_sms, cudaStream_t s);
 // Its completion: on the tensor cores the exact probability launch (returns at once unless the bound
 // left the outcome open); then the corrective apply (returns at once unless the outcome is not g).

@@ -180,13 +180,11 @@ qec_status run_noalloc(const qec_params* params, uint64_t seed, uint64_t first_t
   };
 
   // The same launches, grids and kernel sequence as qec_create / qec_run_trajectories, so that the
-  // reductions add in the same order and the results are identical: for complex128 and QEC_C64 per
-  // block the speculative pass and its corrective launch, alternating between two working states;
-  // for QEC_C64_TC each block's apply pass fused with the next block's probability pass.  (At d <= 3
-  // the tensor-core passes do not apply: their tiles are larger than the register.)
+  // reductions add in the same order and the results are identical: per block the speculative pass
+  // and its corrective launch, alternating between two working states.  (At d <= 3 the tensor-core
+  // passes do not apply: their tiles are larger than the register.)
   auto prob = [&](const PassArgs& a) { return launch_prob(prec, a, pass_grid_for(prec, true, D, a.w, sms), st); };
   auto apply = [&](const PassArgs& a) { return launch_apply(prec, a, pass_grid_for(prec, false, D, a.w, sms), st); };
-  const bool spec = is_f64(prec) || prec == QEC_C64, fused = !spec;
   auto spec_out = [&](int b) { return (b & 1) ? psi2 : psi; };
   // Noise-free init round with outcomes forced to the zero syndrome (Sec. III.B), in psi0.
   e = launch_set_basis0(prec, psi0, D, st);
@@ -199,11 +197,11 @@ qec_status run_noalloc(const qec_params* params, uint64_t seed, uint64_t first_t
   }
   auto traj_pass = [&](int b) {
     const int rnd = 1 + b / nstab, k = b % nstab;
-    return pass(prog, b, b == 0 ? psi0 : psi, false, d_syndromes, rnd * nstab + k);
+    return pass(prog, b, b == 0 ? psi0 : spec_out(b - 1), false, d_syndromes, rnd * nstab + k);
   };
   for (uint32_t t = 0; t < n && e == cudaSuccess; ++t) {
     if (S > 0) e = launch_instantiate(prec, inst(1, 1, S, true), st);
-    for (int b = 0; spec && b < S && e == cudaSuccess; ++b) {
+    for (int b = 0; b < S && e == cudaSuccess; ++b) {
       PassArgs a = traj_pass(b);
       a.src = b == 0 ? psi0 : spec_out(b - 1);
       a.dst = spec_out(b);
@@ -212,21 +210,9 @@ qec_status run_noalloc(const qec_params* params, uint64_t seed, uint64_t first_t
       e = launch_spec(prec, a, n_next, b == 0, sms, st);
       if (e == cudaSuccess) e = launch_spec_fix(prec, a, n_next, b == 0, sms, st);
     }
-    if (S > 0 && !spec && e == cudaSuccess) e = prob(traj_pass(0));
-    for (int b = 0; !spec && b < S && e == cudaSuccess; ++b) {
-      const PassArgs a = traj_pass(b);
-      if (fused && b + 1 < S) {
-        PassArgs nx = traj_pass(b + 1);
-        nx.src = psi;
-        e = launch_fused(prec, a, nx, sms, st);
-        continue;
-      }
-      e = apply(a);
-      if (e == cudaSuccess && !fused && b + 1 < S) e = prob(traj_pass(b + 1));
-    }
     if (e != cudaSuccess) break;
     ReadArgs r;
-    r.src = S > 0 ? (spec ? spec_out(S - 1) : psi) : psi0;
+    r.src = S > 0 ? spec_out(S - 1) : psi0;
     r.D = D;
     r.k1 = k1;
     r.d = params->d;

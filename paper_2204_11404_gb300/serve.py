@@ -57,9 +57,9 @@ class Job:
 
 
 def state_bytes(d, precision):
-    """Device bytes of one slot: working state + resident init state, and the second working state
-    of the speculative passes (every form but c64tc)."""
-    return (2 if precision == "c64tc" else 3) * (1 << (d * d)) * (16 if precision.startswith("c128") else 8)
+    """Device bytes of one slot: two working states (the speculative passes) + the resident init
+    state."""
+    return 3 * (1 << (d * d)) * (16 if precision.startswith("c128") else 8)
 
 
 @dataclass

@@ -1162,12 +1162,18 @@ __global__ void __launch_bounds__(256, 2) k_fused_tc(FusedArgs f) {
 
 // Speculative complex64 pass on the tensor cores (QEC_C64_TC, weight-4 blocks): the order of
 // evaluation of k_apply_spec (Sec. II.B; guess = the same stabilizer's outcome one round earlier)
-// with k_fused_tc's apply: per 4096-amplitude tile, gather each group into the 3xTF32 A operands
-// (summing |in|^2), the apply GEMM into tensor memory, its outputs (summing |out|^2) into the
-// updated tile, which is stored to the other working state.  Without the probability GEMM, its
-// regrouping and its tensor-memory operands.  Sums in FP32 per tile, FP64 across tiles; the last
-// CTA decides directly, as the complex64 probability pass does.  FIX: the corrective apply where
-// the drawn outcome differs from g.
+// with k_fused_tc's 3xTF32 apply.  Per 4096-amplitude tile (256 groups of 16, one per thread):
+//  1. gather the thread's group from the input tile, split hi + lo in TF32 straight into tensor memory
+//     as the GEMM's A operand (the layout of k_fused_tc's probability GEMM), summing |in|^2;
+//  2. the input buffer takes the copy of the tile two ahead (two input buffers, so that two tile
+//     copies are in flight while one tile is computed);
+//  3. the apply GEMM, A from tensor memory, B (K_g / sqrt(N)) from shared memory, D in columns 0..63;
+//  4. its outputs into the updated tile in shared memory, summing |out|^2, then stored to the other
+//     working state in whole 16-byte chunks.
+// Sums in FP32 per tile, FP64 across tiles; the last CTA decides directly, as the complex64
+// probability pass does.  FIX: the corrective apply where the drawn outcome differs from g.
+// Shared memory: two input tiles and the updated tile (3 x 32 KiB) and B (8 KiB): 104 KiB, two CTAs
+// per SM; tensor memory: 256 columns per CTA.
 template <bool FIX>
 __global__ void __launch_bounds__(256, 2) k_fused_tc_spec(FusedArgs f) {
   const int gs = spec_guess(f.ap);
@@ -1176,11 +1182,9 @@ __global__ void __launch_bounds__(256, 2) k_fused_tc_spec(FusedArgs f) {
   constexpr int C = 16;
   extern __shared__ __align__(128) unsigned char tsm[];
   const uint32_t tsz = 1u << f.nt, lmask = (1u << f.lb) - 1u;     // tsz = 4096 (checked by the launcher)
-  float2* tile = reinterpret_cast<float2*>(tsm);
-  float* Ahi = reinterpret_cast<float*>(tile + tsz);
-  float* Alo = Ahi + 256 * 32;
-  float2* outt = reinterpret_cast<float2*>(Ahi);                  // the updated tile (tile slots)
-  float* Bahi = Alo + 256 * 32;
+  float2* tiles = reinterpret_cast<float2*>(tsm);                 // input tiles i even / odd
+  float2* outt = tiles + 2 * tsz;                                 // the updated tile (tile slots)
+  float* Bahi = reinterpret_cast<float*>(outt + tsz);
   float* Balo = Bahi + 32 * 32;
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t tmem_base;
@@ -1197,7 +1201,7 @@ __global__ void __launch_bounds__(256, 2) k_fused_tc_spec(FusedArgs f) {
       asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
-      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(smem_u32(&tmem_base)));
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(smem_u32(&tmem_base)));
       asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
   }
@@ -1228,7 +1232,10 @@ __global__ void __launch_bounds__(256, 2) k_fused_tc_spec(FusedArgs f) {
   uint32_t cd[8];
 #pragma unroll
   for (int i = 0; i < 8; ++i) cd[i] = slot((uint32_t)tid * 2 + 512u * i);
-  const uint32_t taddr = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + 32u * (warp >> 2);
+  // Thread tid owns row tid: M-half tid / 128, TMEM lane tid % 128 (its warp's lane quarter).
+  const uint32_t tq = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
+  const uint32_t taddr = tq + 32u * (warp >> 2);                 // D, this row
+  const uint32_t tA = tq + kTcColA2 + 64u * (warp >> 2);         // A of this row (hi; lo at +32)
   const float2* src = reinterpret_cast<const float2*>(f.ap.src);
   float2* dst = reinterpret_cast<float2*>(f.ap.dst);
   const uint32_t ntile = 1u << f.nout;
@@ -1236,29 +1243,45 @@ __global__ void __launch_bounds__(256, 2) k_fused_tc_spec(FusedArgs f) {
   uint32_t ph = 0;
   const int obit = (threadIdx.x & 31) < (unsigned)f.nout ? f.obits[threadIdx.x & 31] : 0;
   auto tile_base = [&](uint32_t tix) { return tile_base_warp(tix, f.nout, obit); };
-  auto load_tile = [&](uint32_t tix) {
-    const uint32_t tb = tile_base(tix);
+  // one commit group per call, empty past the last tile, so that wait_group<1> always means "all but
+  // the newest copy are in"
+  auto load_tile = [&](uint32_t tix, float2* buf) {
+    if (tix < ntile) {
+      const uint32_t tb = tile_base(tix);
 #pragma unroll
-    for (int i = 0; i < 8; ++i) cp_async16(tile + cd[i], src + (tb | coff[i]));
+      for (int i = 0; i < 8; ++i) cp_async16(buf + cd[i], src + (tb | coff[i]));
+    }
     cp_async_commit();
   };
-  if (blockIdx.x < ntile) load_tile(blockIdx.x);
+  load_tile(blockIdx.x, tiles);
+  load_tile(blockIdx.x + gridDim.x, tiles + tsz);
+  int cur = 0;
   for (uint32_t tix = blockIdx.x; tix < ntile; tix += gridDim.x) {
     const uint32_t tb = tile_base(tix);
-    cp_async_wait<0>();
-    __syncthreads();   // the input tile is in; the previous tile's readers of the updated tile are done
+    float2* tile = tiles + (cur ? tsz : 0u);
+    cp_async_wait<1>();
+    __syncthreads();   // this tile is in; the previous tile's readers of the updated tile are done
     float sI = 0.f;
 #pragma unroll
-    for (int l = 0; l < C; l += 2) {
-      const float2 a = tile[sba ^ offa[l]], b = tile[sba ^ offa[l + 1]];
-      sI = fmaf(a.x, a.x, fmaf(a.y, a.y, fmaf(b.x, b.x, fmaf(b.y, b.y, sI))));
-      put_a4(Ahi, Alo, tid, 2 * l, a, b);
+    for (int l = 0; l < C; l += 4) {
+      float hv[8], lv[8];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float2 v = tile[sba ^ offa[l + q]];
+        sI = fmaf(v.x, v.x, fmaf(v.y, v.y, sI));
+        hv[2 * q] = tf32_rna(v.x);
+        lv[2 * q] = tf32_rna(v.x - hv[2 * q]);
+        hv[2 * q + 1] = tf32_rna(v.y);
+        lv[2 * q + 1] = tf32_rna(v.y - hv[2 * q + 1]);
+      }
+      tmem_st8(tA + 2u * l, hv);
+      tmem_st8(tA + 32u + 2u * l, lv);
     }
     accI += (double)sI;
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
     tc_sync();
-    if (tix + gridDim.x < ntile) load_tile(tix + gridDim.x);   // the input tile is free
-    if (tid == 0) issue_gemm(tmem, Ahi, Alo, Bahi, Balo, mb);
+    load_tile(tix + 2 * gridDim.x, tile);   // every thread has read this tile: the copy two ahead
+    if (tid == 0) issue_gemm_ts(tmem, 0u, kTcColA2, Bahi, Balo, mb);
     if (!mbar_wait(mb, ph & 1)) s_err = 1;
     ++ph;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -1280,10 +1303,11 @@ __global__ void __launch_bounds__(256, 2) k_fused_tc_spec(FusedArgs f) {
 #pragma unroll
     for (int i = 0; i < 8; ++i)
       *reinterpret_cast<float4*>(dst + (tb | coff[i])) = *reinterpret_cast<const float4*>(outt + cd[i]);
+    cur ^= 1;
   }
   cp_async_wait<0>();
   tc_sync();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tmem));
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem));
   if (s_err && tid == 0) atomicOr(&f.ap.ctl->status, 1u);
   spec_finish<FIX>(f, gs, accI, 0.0, accO, 0.0, sred, &s_last, true);
 }

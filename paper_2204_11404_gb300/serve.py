@@ -85,9 +85,9 @@ class Server:
     that long jobs are not held back indefinitely by a stream of short ones) or "fifo" (arrival
     order)."""
 
-    # relative device time of one trajectory-round per engine at d = 5 (measured rounds/s: c128tc 95,
-    # c64tc 300, c64 240, c128 10); d = 3 jobs are far cheaper and run beside the heavy ones
-    COST_D5 = {"c128tc": 1.0 / 95, "c64tc": 1.0 / 300, "c64": 1.0 / 240, "c128": 1.0 / 10}
+    # relative device time of one trajectory-round per engine at d = 5 (measured rounds/s: c128tc 102,
+    # c64tc 346, c64 261, c128 13.8); d = 3 jobs are far cheaper and run beside the heavy ones
+    COST_D5 = {"c128tc": 1.0 / 102, "c64tc": 1.0 / 346, "c64": 1.0 / 261, "c128": 1.0 / 13.8}
 
     def __init__(self, mem_budget_bytes, device=0, max_heavy=2, heavy_d=5, fp64_on_tensor_cores=True,
                  fp32_on_tensor_cores=True, policy="sjf", sjf_aging_s=30.0):

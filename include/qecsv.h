@@ -55,7 +55,8 @@ typedef enum { QEC_GATES_CNOT = 0, QEC_GATES_CR = 1 } qec_gateset;
  * the pair as K (x) I over two spectator qubits), pairs of weight-2 blocks on
  * the CUDA cores.
  * C128_TC: complex128 state; the apply of every stabilizer block (tiles of
- * 2^11 amplitudes, so registers of at least 11 qubits: d >= 4) as emulated
+ * 2^11 amplitudes, so registers of at least 11 qubits: the d = 5 surface code
+ * and the repetition code from d = 11; smaller registers as C128) as emulated
  * FP64 products on the FP16 tensor cores: each operand row split into 7
  * signed 8-bit slices under one exponent, slice products accumulated exactly,
  * recombined in integers and rounded once (Ozaki scheme).  One speculative

@@ -218,8 +218,8 @@ qec_status qec_selftest_wait(qec_sim* sim, uint32_t polls);
  * of qec_run_trajectories (all three required when n > 0); results are
  * identical to qec_run_trajectories for the same parameters, seed and
  * trajectory indices: it launches the same kernels with the same grids in the
- * same order (for complex64, each block's apply pass fused with the next
- * block's probability pass), so every reduction adds in the same order.  Work
+ * same order (per block the speculative pass and its corrective launch, over
+ * two working states), so every reduction adds in the same order.  Work
  * is enqueued asynchronously on cuda_stream (NULL = the legacy default
  * stream); no sim handle is involved.  At the sizes it accepts none of its
  * kernels waits on a barrier or flag, so it has no bounded-wait timeout to

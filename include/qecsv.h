@@ -190,9 +190,9 @@ qec_status qec_kernel_times(qec_sim* sim, float* ms, int32_t* block);
 /*
  * Measurement hook: instrument, from the next trajectory on, the first block
  * of the middle noisy round whose weight is w_apply and whose successor's
- * weight is w_next (2 or 4; with the fused passes, ms[1] of qec_kernel_times
- * is then the pass that applies that block and computes its successor's
- * probability).  *block gets its index.  QEC_EINVAL if the sim has no noisy
+ * weight is w_next (2 or 4; ms[1] of qec_kernel_times is then that block's
+ * speculative pass, or with the fused passes the pass that applies that block
+ * and computes its successor's probability).  *block gets its index.  QEC_EINVAL if the sim has no noisy
  * round or no such pair of blocks.  The trajectory graph is rebuilt at the
  * next run; results do not change.
  */
@@ -390,12 +390,13 @@ qec_status qec_debug_exact_probability(qec_sim* sim, int32_t force, uint64_t* fa
  * Test hook (the paper has no counterpart: an evaluation order of Sec. II.B's measurement and
  * collapse).  enable = 1: the speculative passes (the default); 0: the passes that compute each
  * probability before its apply (QEC_C128: a probability pass and an apply pass per block;
- * QEC_C128_TC: per block pair, the apply fused with the next block's 3-slice bounded probability;
- * the complex64 forms: the apply fused with the next block's probability); -1: unchanged.  Both give the same outcomes (except within the
- * rounding of a threshold) and states within a few FP64 roundings.  *misses (may be NULL)
- * receives the number of corrective applies run on this handle so far (outcomes that differed
- * from the guess).  Waits for the handle's queued work; switching rebuilds the trajectory graph
- * and requires a new run before qec_get_state.  QEC_EINVAL on a null handle or enable outside
+ * QEC_C128_TC: per block pair, the apply fused with the next block's 3-slice bounded
+ * probability; the complex64 forms: the apply fused with the next block's probability);
+ * -1: unchanged.  Both give the same outcomes (except within the rounding of a threshold) and
+ * states within a few roundings of the form's arithmetic.  *misses (may be NULL) receives the
+ * number of corrective applies run on this handle so far (outcomes that differed from the
+ * guess).  Waits for the handle's queued work; switching rebuilds the trajectory graph and
+ * requires a new run before qec_get_state.  QEC_EINVAL on a null handle or enable outside
  * -1..1.
  */
 qec_status qec_debug_speculation(qec_sim* sim, int32_t enable, uint64_t* misses);

@@ -109,3 +109,24 @@ def test_repetition_code_params_validated():
     p.code = 2
     with pytest.raises(capi.QecError):
         capi.qec_debug_program(p, n.ctypes.data, 0, n.ctypes.data, 0)
+
+
+@pytest.mark.parametrize("d,gates", [(3, "cr"), (3, "cnot"), (5, "cr")])
+def test_kraus_pairs_are_complete(d, gates):
+    """The speculative passes take P(1) = 1 - |K_0 psi|^2 / |psi|^2 when they apply K_0 (Sec. II.B with
+    K_0^dagger K_0 + K_1^dagger K_1 = I: the ancilla's two outcomes exhaust its measurement).  The
+    pairs the device builds (the host copy runs the same arithmetic) must be complete far inside the
+    1e-10 margin of the decision, on every block of noisy rounds with every noise term on."""
+    from kraus_ref import blocks, block_meta
+    params = capi.make_params(d, 2, gates, **NOISY)
+    info = block_meta(params)
+    worst = 0.0
+    for traj in range(3):
+        for rnd in (1, 2):
+            kr, _ = blocks(params, 29, traj, rnd)
+            for k in range(kr.shape[0]):
+                c = 1 << int(info[k, 0])
+                k0, k1 = kr[k, 0, :c, :c], kr[k, 1, :c, :c]
+                gram = k0.conj().T @ k0 + k1.conj().T @ k1
+                worst = max(worst, float(np.abs(gram - np.eye(c)).max()))
+    assert worst < 1e-13, worst

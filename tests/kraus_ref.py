@@ -44,7 +44,12 @@ def apply_block(psi, D, qs, K):
     return np.ascontiguousarray(t).reshape(-1)
 
 
-def run(params, seed, traj):
+def run(params, seed, traj, speculative=False):
+    """One trajectory with numpy.  Each noisy measurement draws m with P(1) = |K_1 psi|^2 / |psi|^2
+    and continues with K_m psi / |psi|.  speculative: the order of the speculative passes instead,
+    K_g applied first for the guess g (the same stabilizer's previous raw outcome), P(1) taken from
+    |K_g psi|^2 (as 1 - P(0) for g = 0), K_m re-applied from the input where m != g; returns the
+    number of such corrections as a third value."""
     R = params.rounds
     D = ndata(params)
     nst = D - 1
@@ -52,17 +57,33 @@ def run(params, seed, traj):
     psi = np.zeros(1 << D, dtype=np.complex128)
     psi[0] = 1.0
     syn = np.zeros((R + 1, nst), dtype=np.uint8)
+    raw = np.zeros(nst, dtype=np.int64)
+    fixes = 0
     for rnd in range(R + 1):
         kr, u = blocks(params, seed, traj, rnd)
         for k in range(nst):
             w, offset = info[k, 0], info[k, 5]
             qs = [int(x) for x in info[k, 1:1 + w]]
             C = 1 << w
-            K0, K1 = kr[k, 0, :C, :C], kr[k, 1, :C, :C]
+            K = (kr[k, 0, :C, :C], kr[k, 1, :C, :C])
             N = np.vdot(psi, psi).real
-            A = np.vdot(apply_block(psi, D, qs, K1), apply_block(psi, D, qs, K1)).real
-            m = offset if rnd == 0 else int(u[k] < A / N)
-            psi = apply_block(psi, D, qs, K1 if m else K0) / np.sqrt(N)
+            if rnd == 0:
+                m = offset
+                out = apply_block(psi, D, qs, K[m])
+            elif speculative:
+                g = int(raw[k])
+                out = apply_block(psi, D, qs, K[g])
+                pg = np.vdot(out, out).real / N
+                m = int(u[k] < (pg if g else 1.0 - pg))
+                if m != g:
+                    fixes += 1
+                    out = apply_block(psi, D, qs, K[m])
+            else:
+                y1 = apply_block(psi, D, qs, K[1])
+                m = int(u[k] < np.vdot(y1, y1).real / N)
+                out = y1 if m else apply_block(psi, D, qs, K[0])
+            psi = out / np.sqrt(N)
+            raw[k] = m
             syn[rnd, k] = m ^ offset
     psi = psi / np.linalg.norm(psi)
-    return syn, psi
+    return (syn, psi, fixes) if speculative else (syn, psi)

@@ -130,3 +130,21 @@ def test_kraus_pairs_are_complete(d, gates):
                 gram = k0.conj().T @ k0 + k1.conj().T @ k1
                 worst = max(worst, float(np.abs(gram - np.eye(c)).max()))
     assert worst < 1e-13, worst
+
+
+@pytest.mark.parametrize("gates", ["cnot", "cr"])
+def test_speculative_order_matches_oracle_d3(gates):
+    """Reading R19 on the CPU: the speculative order of evaluation (apply the previous outcome's
+    Kraus operator, take P(1) from its output, re-apply from the input on a change) reproduces the
+    FP64 oracle's syndromes and states on the stress noise, and corrects exactly the outcome
+    changes between rounds."""
+    params = capi.make_params(3, 3, gates, **NOISY)
+    total = 0
+    for traj in range(6):
+        syn, psi, fixes = kraus_run(params, 23, traj, speculative=True)
+        o = run_trajectory(3, 3, gates, "reduced", NOISY, seed=23, traj=traj, want_state=True)
+        assert (syn == o["syndromes"]).all()
+        assert np.abs(psi - o["state"][: 1 << 9]).max() < 1e-13
+        assert fixes == int(np.sum(np.diff(syn.astype(np.int8), axis=0) != 0))
+        total += fixes
+    assert total > 0
